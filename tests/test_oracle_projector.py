@@ -1,0 +1,172 @@
+"""Pins of the oracle's projector pair and bases against facts fixed outside it.
+
+Each test checks the FP64 oracle against mathematics the paper fixes: the
+adjoint identity of Eq. (radadjapr), the half-turn symmetry of Sec. 4, exact
+line sums at special angles, a hand-worked 2x2 example, brute-force matrix
+transposes, closed-form line integrals of disks, and textbook basis values.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1809_09725_gb300 import synth
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _dense_fwd(nx, ny, ns, theta):
+    """Matrix of the oracle's single-angle Joseph projector, column by column."""
+    A = np.zeros((ns, ny * nx))
+    for q in range(ny * nx):
+        e = np.zeros(ny * nx)
+        e[q] = 1.0
+        A[:, q] = oracle.joseph_fwd_slice(e.reshape(ny, nx), theta, ns)
+    return A
+
+
+def _dense_adj(nx, ny, ns, theta):
+    B = np.zeros((ny * nx, ns))
+    for b in range(ns):
+        e = np.zeros(ns)
+        e[b] = 1.0
+        B[:, b] = oracle.joseph_adj_slice(e, theta, nx, ny).ravel()
+    return B
+
+
+ANGLES = [0.0, math.pi / 2, math.pi / 4, 3 * math.pi / 4, 0.3, 1.1, 2.0, 2.9, 3.5, 5.0, -0.7,
+          math.atan2(0.6, 0.8)]
+
+
+@pytest.mark.parametrize("nx,ny,ns", [(8, 8, 8), (8, 6, 11), (5, 7, 6)])
+@pytest.mark.parametrize("theta", ANGLES)
+def test_gather_adjoint_is_exact_transpose(nx, ny, ns, theta):
+    A = _dense_fwd(nx, ny, ns, theta)
+    B = _dense_adj(nx, ny, ns, theta)
+    assert np.max(np.abs(A.T - B)) <= 1e-14 * max(1.0, np.max(np.abs(A)))
+
+
+def test_hand_worked_2x2_example():
+    gold = json.load(open(os.path.join(GOLD, "joseph_2x2.json")))
+    img = np.array(gold["image_rows_y_then_x"])
+    theta = math.atan2(gold["sin"], gold["cos"])
+    out = oracle.joseph_fwd_slice(img, theta, gold["ns"])
+    np.testing.assert_allclose(out, gold["expected"], rtol=0, atol=1e-13)
+
+
+def test_special_angles_are_exact_line_sums():
+    rng = synth.rng_for(1)
+    N = 9
+    F = rng.standard_normal((N, N))
+    # theta = 0: line x = s -> column sums; theta = pi/2: line y = s -> row sums
+    np.testing.assert_allclose(oracle.joseph_fwd_slice(F, 0.0, N), F.sum(axis=0), atol=1e-12)
+    np.testing.assert_allclose(oracle.joseph_fwd_slice(F, math.pi / 2, N), F.sum(axis=1), atol=1e-12)
+    # theta = pi: x = -s -> reversed column sums
+    np.testing.assert_allclose(oracle.joseph_fwd_slice(F, math.pi, N), F.sum(axis=0)[::-1],
+                               atol=1e-12)
+    # theta = pi/4, centre bin: samples on the anti-diagonal, weight sqrt(2)
+    g = oracle.joseph_fwd_slice(F, math.pi / 4, N)
+    anti = sum(F[j, N - 1 - j] for j in range(N))
+    assert abs(g[N // 2] - math.sqrt(2.0) * anti) < 1e-12
+    # theta = 3pi/4 (cos < 0), centre bin: main diagonal
+    g = oracle.joseph_fwd_slice(F, 3 * math.pi / 4, N)
+    assert abs(g[N // 2] - math.sqrt(2.0) * np.trace(F)) < 1e-12
+
+
+@pytest.mark.parametrize("theta", [0.2, 0.9, 1.7, 2.6, math.pi / 4])
+def test_half_turn_symmetry(theta):
+    """Sec. 4: R f(theta + pi, s) = R f(theta, -s), exact on the symmetric bin grid."""
+    rng = synth.rng_for(2)
+    F = rng.standard_normal((10, 12))
+    a = oracle.joseph_fwd_slice(F, theta, 15)
+    b = oracle.joseph_fwd_slice(F, theta + math.pi, 15)
+    np.testing.assert_allclose(b, a[::-1], atol=1e-12)
+
+
+@pytest.mark.parametrize("basis", [oracle.FOURIER, oracle.LEGENDRE])
+def test_dynamic_adjoint_dot_product(basis):
+    """<R u, g> = <u, R* g> (Sec. 4, the adjoint equality behind Eq. radadjapr)."""
+    rng = synth.rng_for(3)
+    nz, ny, nx, m, K, ns = 2, 12, 10, 5, 37, 15
+    theta, t = synth.scan(K, 3.3)
+    Phi = oracle.basis_table(basis, m, t)
+    u = rng.standard_normal((nz, ny, nx, m))
+    g = rng.standard_normal((nz, K, ns))
+    lhs = np.vdot(oracle.dyn_fwd(u, theta, Phi, ns), g)
+    rhs = np.vdot(u, oracle.dyn_adj(g, theta, Phi, nx, ny))
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+def test_static_reduction_m1():
+    """m = 1 with phi_0 = 1: the dynamic operator is the static Radon transform."""
+    rng = synth.rng_for(4)
+    nz, ny, nx, K, ns = 2, 9, 9, 11, 9
+    theta, t = synth.scan(K, 2.0)
+    Phi = oracle.basis_table(oracle.FOURIER, 1, t)
+    assert np.all(Phi == 1.0)
+    u = rng.standard_normal((nz, ny, nx, 1))
+    g = oracle.dyn_fwd(u, theta, Phi, ns)
+    for z in range(nz):
+        for k in range(K):
+            np.testing.assert_allclose(g[z, k], oracle.joseph_fwd_slice(u[z, :, :, 0], theta[k], ns),
+                                       atol=1e-12)
+
+
+def test_time_dependence_special_times():
+    """f(t) = U + cos(2 pi t) V: at t = 0, 1/2, 1/4 the projection is of U+V, U-V, U."""
+    rng = synth.rng_for(5)
+    n, ns = 8, 8
+    U, V = rng.standard_normal((n, n)), rng.standard_normal((n, n))
+    u = np.stack([U, V], axis=-1)[None]
+    t = np.array([0.0, 0.5, 0.25])
+    theta = np.array([0.4, 1.3, 2.2])
+    Phi = oracle.basis_table(oracle.FOURIER, 2, t)
+    g = oracle.dyn_fwd(u, theta, Phi, ns)[0]
+    np.testing.assert_allclose(g[0], oracle.joseph_fwd_slice(U + V, theta[0], ns), atol=1e-12)
+    np.testing.assert_allclose(g[1], oracle.joseph_fwd_slice(U - V, theta[1], ns), atol=1e-12)
+    np.testing.assert_allclose(g[2], oracle.joseph_fwd_slice(U, theta[2], ns), atol=1e-12)
+
+
+def test_fourier_basis_values_and_orthogonality():
+    P = oracle.basis_table(oracle.FOURIER, 5, [0.25, 0.125])
+    # phi = {1, cos 2pi t, sin 2pi t, cos 4pi t, sin 4pi t}
+    np.testing.assert_allclose(P[0], [1, 0, 1, -1, 0], atol=1e-15)
+    np.testing.assert_allclose(P[1], [1, math.sqrt(0.5), math.sqrt(0.5), 0, 1], atol=1e-15)
+    K = 64
+    Pk = oracle.basis_table(oracle.FOURIER, 7, np.arange(K) / K)
+    G = Pk.T @ Pk
+    np.testing.assert_allclose(G, np.diag([K] + [K / 2] * 6), atol=1e-11)
+
+
+def test_legendre_textbook_values():
+    # shifted Legendre phi_j(t) = P_j(2t - 1)
+    P = oracle.basis_table(oracle.LEGENDRE, 5, [1.0, 0.0, 0.5, 0.75])
+    np.testing.assert_allclose(P[0], [1, 1, 1, 1, 1], atol=1e-15)
+    np.testing.assert_allclose(P[1], [1, -1, 1, -1, 1], atol=1e-15)
+    np.testing.assert_allclose(P[2], [1, 0, -0.5, 0, 0.375], atol=1e-15)
+    np.testing.assert_allclose(P[3][:4], [1, 0.5, -0.125, -0.4375], atol=1e-15)
+    # orthogonality on [0,1]: int phi_i phi_j dt = delta_ij / (2j+1), Gauss-Legendre quadrature
+    x, wq = np.polynomial.legendre.leggauss(20)
+    Pq = oracle.basis_table(oracle.LEGENDRE, 6, (x + 1) / 2)
+    G = (Pq * (wq / 2)[:, None]).T @ Pq
+    np.testing.assert_allclose(G, np.diag(1.0 / (2 * np.arange(6) + 1)), atol=1e-13)
+
+
+def test_disk_line_integrals_converge():
+    """Joseph sums of an area-sampled disk approach the closed-form line integral
+    2 sqrt(r^2 - s^2) as the grid is refined (error falls roughly like 1/N)."""
+    errs = []
+    for N in (32, 64, 128):
+        h = 2.0 / N  # field of view [-1, 1]
+        blob = synth.Blob(0.21 / h, -0.13 / h, 0, 0, 0, 0, 0.37 / h, 0.37 / h, 1e9, 0, 1.0, 0, 0)
+        img = synth.rasterize([blob], N, 1, 0.0, supersample=8)[0]
+        thetas = np.array([0.1, 0.7, 1.3, 2.2])
+        exact = synth.sinogram([blob], thetas, np.zeros(4), N, 1)[0]
+        approx = np.stack([oracle.joseph_fwd_slice(img, th, N) for th in thetas])
+        errs.append(np.linalg.norm(approx - exact) / np.linalg.norm(exact))
+    assert errs[0] < 0.05
+    assert errs[1] < 0.75 * errs[0]
+    assert errs[2] < 0.75 * errs[1]
