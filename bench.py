@@ -1,0 +1,336 @@
+"""Benchmark of the dynamic-tomography hot path on GB300.
+
+Workload (default): 16 slices of 256^2 voxels, 256 detector bins, K = 1800
+projections over 10 continuous half-turns, m = 8 real Fourier coefficient
+volumes, nt = 10 frames, moving-ellipsoid phantom with Poisson noise (1e4
+photons), FP32 -- reconstructed with ADMM-CG (4 CG steps per u-step).
+
+One step = one ADMM-CG iteration: 5 dynamic forward projections, 5 dynamic
+back-projections (1 residual + 4 CG), the 4D TV stencils, the prox and the
+FP64 inner products, replayed as a CUDA graph by admm_solve.  The metric is
+voxel-projection updates per second: each projector application counts K * V
+voxel-projection pairs, 10 applications per iteration.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs one independent replica per GPU (the path has no exchange step
+at this size: weak scaling, no collective on the data path).  The reference
+arm times the FP64 CPU oracle on the host cores on a bounded sample.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP32 FMA pipe: 152 SMs x 128 lanes x 2 flop x 2.07 GHz (maximum SM clock).
+SMS, FP32_LANES, SM_MAX_GHZ = 152, 128, 2.07
+
+
+def fp32_peak_tflops(sm_mhz=None):
+    ghz = (sm_mhz / 1000.0) if sm_mhz else SM_MAX_GHZ
+    return SMS * FP32_LANES * 2 * ghz * 1e9 / 1e12
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="ellipsoids256")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-small", action="store_true",
+                    help="run only a few operator launches of a 2-slice cut (for ncu captures)")
+    return ap.parse_args()
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._th = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                     timeout=5).stdout.strip()
+                if out:
+                    self.samples.append([x.strip() for x in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._th = threading.Thread(target=self._run, daemon=True)
+        self._th.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        if self._th:
+            self._th.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if len(s) > 4 + i and
+                          s[4 + i].lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def dist_init(n):
+    if n <= 1 and "RANK" not in os.environ:
+        return 0, 1, None
+    import torch.distributed as tdist
+    backend = "nccl"
+    tdist.init_process_group(backend=backend)
+    return tdist.get_rank(), tdist.get_world_size(), tdist
+
+
+def barrier_max(tdist, value: float, device):
+    if tdist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def roofline_entry(kind, P, w, t_ms):
+    """ALU roofline of a projector launch: algorithmic FP32 flops = 2 (m + 2)
+    per voxel-projection pair (m FMAs of the basis combine + 2 of the
+    interpolation / footprint), K V pairs per launch."""
+    flops = 2.0 * (w.m + 2) * w.K * w.voxels()
+    achieved = flops / (t_ms * 1e-3) / 1e12
+    return flops, achieved
+
+
+def run_ours(a):
+    import torch
+
+    from paper_1809_09725_gb300 import dynrecon as dr
+    from paper_1809_09725_gb300 import synth
+
+    rank, world, tdist = dist_init(a.gpus)
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = synth.WORKLOADS[a.workload]
+    theta, t, g_np = synth.make_data(w)
+    plan = dr.Plan(w.N, w.N, w.nz, w.ns, theta, t, w.basis, w.m, w.nt, dr.F32)
+    g = torch.from_numpy(g_np.astype(np.float32)).to(dev)
+    u = torch.zeros(plan.u_shape(), dtype=torch.float32, device=dev)
+    units_per_iter = 2 * (w.n_cg + 1) * w.K * w.voxels()  # projector applications x K V
+
+    if a.profile_small:
+        # a few plain operator launches (fwd, adj) for profiler captures
+        for _ in range(2):
+            dr.dyn_radon_fwd(plan, u, g)
+            dr.dyn_radon_adj(plan, g, u)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_small": True}))
+        return
+
+    prm = dr.solve_params(dr.ADMM_CG, iters=a.warmup, n_cg=w.n_cg, lambda1=w.lambda1, lambda2=w.lambda2,
+                          rho=w.rho)
+    dr.admm_solve(plan, g, u, prm, want_objective=False)  # warm-up iterations (untimed)
+    u.zero_()
+    torch.cuda.synchronize()
+    prm = dr.solve_params(dr.ADMM_CG, iters=a.steps, n_cg=w.n_cg, lambda1=w.lambda1, lambda2=w.lambda2,
+                          rho=w.rho)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        if tdist is not None:
+            tdist.barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        res = dr.admm_solve(plan, g, u, prm, want_objective=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if tdist is not None:
+            tdist.barrier()
+    ms = e0.elapsed_time(e1)
+    ms = barrier_max(tdist, ms, dev)
+    total_units = units_per_iter * a.steps * world
+    value = total_units / (ms * 1e-3)
+    obj = res["objective"]
+
+    # dominant kernels: time the projector pair alone on the same stream
+    p_in = torch.randn(plan.u_shape(), dtype=torch.float32, device=dev)
+    gbuf = torch.empty(plan.g_shape(), dtype=torch.float32, device=dev)
+    ubuf = torch.empty(plan.u_shape(), dtype=torch.float32, device=dev)
+    for _ in range(3):
+        dr.dyn_radon_fwd(plan, p_in, gbuf)
+        dr.dyn_radon_adj(plan, gbuf, ubuf)
+    reps = 10
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for _ in range(reps):
+        dr.dyn_radon_fwd(plan, p_in, gbuf)
+    ev[1].record(stream)
+    for _ in range(reps):
+        dr.dyn_radon_adj(plan, gbuf, ubuf)
+    ev[2].record(stream)
+    torch.cuda.synchronize()
+    fwd_ms = ev[0].elapsed_time(ev[1]) / reps
+    adj_ms = ev[1].elapsed_time(ev[2]) / reps
+    kern = ("fwd_kernel", fwd_ms) if fwd_ms >= adj_ms else ("adj_kernel", adj_ms)
+    flops, achieved = roofline_entry(kern[0], plan, w, kern[1])
+    clocks = clk.summary()
+    peak = fp32_peak_tflops()
+    traffic = load_traffic(kern[0])
+
+    # end to end through the public call with host buffers (one full job per call)
+    e2e = None
+    if not a.no_e2e:
+        gh = torch.from_numpy(g_np.astype(np.float32)).pin_memory()
+        uh = torch.zeros(plan.u_shape(), dtype=torch.float32).pin_memory()
+        ghn, uhn = gh.numpy(), uh.numpy()
+        jobs = 2
+        prm_e = dr.solve_params(dr.ADMM_CG, iters=w.iters, n_cg=w.n_cg, lambda1=w.lambda1, lambda2=w.lambda2,
+                                rho=w.rho)
+        dr.admm_solve(plan, ghn, uhn, dr.solve_params(dr.ADMM_CG, iters=2, n_cg=w.n_cg, lambda1=w.lambda1,
+                                                      lambda2=w.lambda2, rho=w.rho), want_objective=False)
+        torch.cuda.synchronize()
+        if tdist is not None:
+            tdist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(jobs):
+            uhn[...] = 0.0
+            dr.admm_solve(plan, ghn, uhn, prm_e, want_objective=False)
+        torch.cuda.synchronize()
+        el = barrier_max(tdist, time.perf_counter() - t0, dev)
+        e2e = {"value": units_per_iter * w.iters * jobs * world / el, "unit": "voxel*projection/s",
+               "h2d_bytes_per_step": int(g_np.size * 4 + uhn.nbytes), "d2h_bytes_per_step": int(uhn.nbytes),
+               "step": "one %d-iteration reconstruction job via admm_solve on pinned host buffers" % w.iters,
+               "jobs": jobs, "s_per_job": el / jobs}
+
+    cpu = None
+    if rank == 0 and not a.no_cpu_baseline:
+        cpu = cpu_baseline(w, theta, t, g_np)
+
+    if rank == 0:
+        launches_per_iter = 6 + 5 * w.n_cg
+        line = {
+            "metric": "voxel*projection updates/s (dynamic projector + back-projector applications "
+                      "inside ADMM-CG iterations)",
+            "value": value, "unit": "voxel*projection/s", "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded moving ellipsoids, Poisson 1e4)",
+            "config": {"workload": "ellipsoids256: nz=16 x 256^2 voxels, 256 bins, K=1800 over 10 half-turns, "
+                                   "m=8 Fourier, nt=10, ADMM-CG n_cg=4, FP32",
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "l2": "per-iteration working set 0.54 GB > 129 MB L2 (duals stream through every iteration)"},
+            "admm_iters_per_s": a.steps * world / (ms * 1e-3),
+            "objective_first_last": [float(obj[0]), float(obj[-1])],
+            "clocks": clocks,
+            "e2e": e2e,
+            "gpu_launches": launches_per_iter * a.steps + 2,
+            "roofline": {"bound": "alu", "kernel": kern[0], "achieved": achieved, "peak": peak,
+                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+                         "launch_ms": kern[1], "fwd_ms": fwd_ms, "adj_ms": adj_ms,
+                         "algorithmic_flops_per_launch": flops,
+                         "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz max SM clock"},
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+
+
+def load_traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if present."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(path))
+        return d.get(kernel)
+    except Exception:
+        return None
+
+
+def cpu_baseline(w, theta, t, g_np, sample_slices=None):
+    """The FP64 oracle as it stands, on the host cores: one forward and one
+    back-projection of the same workload (bounded sample)."""
+    import oracle
+    nz = w.nz if sample_slices is None else sample_slices
+    P = oracle.Problem(w.N, w.N, nz, w.ns, theta, t, w.basis, w.m, w.nt)
+    rng = np.random.default_rng(1)
+    u = rng.standard_normal((nz, w.N, w.N, w.m))
+    t0 = time.perf_counter()
+    P.fwd(u)
+    P.adj(g_np[:nz])
+    el = time.perf_counter() - t0
+    units = 2 * w.K * w.N * w.N * nz
+    return {"value": units / el, "unit": "voxel*projection/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "one forward + one back-projection, FP64 oracle, %d slices of the workload (%.1f s)"
+                      % (nz, el)}
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_1809_09725_gb300 import synth
+    w = synth.WORKLOADS[a.workload]
+    theta, t, g_np = synth.make_data(w)
+    nz = 4
+    for _ in range(a.warmup):
+        cpu_baseline(w, theta, t, g_np, sample_slices=1)
+    t0 = time.perf_counter()
+    vals = []
+    for _ in range(a.steps):
+        vals.append(cpu_baseline(w, theta, t, g_np, sample_slices=nz))
+    el = time.perf_counter() - t0
+    units = 2 * w.K * w.N * w.N * nz * a.steps
+    value = units / el
+    line = {"impl": "reference", "metric": "voxel*projection updates/s (dynamic projector + back-projector "
+                                           "applications inside ADMM-CG iterations)",
+            "value": value, "unit": "voxel*projection/s", "n_gpus": 0, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": el * 1e3 / a.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded moving ellipsoids, Poisson 1e4)",
+            "config": {"workload": "ellipsoids256 (4-slice sample per step)"},
+            "cpu_baseline": {"value": value, "unit": "voxel*projection/s", "cores": os.cpu_count(),
+                             "kind": "oracle", "sample": "per step: one forward + one back-projection on 4 of "
+                                                         "the 16 slices, FP64 oracle"},
+            "e2e": {"value": value, "unit": "voxel*projection/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,199 @@
+/*
+ * dynrecon.h -- C ABI of the GB300 (sm_103a) library for four-dimensional
+ * tomographic reconstruction by time-domain decomposition (Nikitin,
+ * Carlsson, Andersson, Mokso, arXiv 1809.09725).
+ *
+ * The object f(x, y, z, t) is represented by m temporal-basis coefficient
+ * volumes u_j (Sec. 4, Eq. repr):  f(x, t) = sum_j phi_j(t) u_j(x).
+ * Projection k is acquired at angle theta_k and time t_k under continuous
+ * rotation (Sec. 2, Eq. Rfwd).  The regularised model is Eq. (lr12):
+ *     min_u  1/2 || R u - g ||^2 + lambda1 sum_{x,l} | nabla_{lambda2} f(x, t_l) |
+ * with the isotropic 4D gradient of Eq. (TV1) on nt reconstruction frames
+ * t_l = l / nt (Sec. 4, Eq. discrt).
+ *
+ * Discretisation (the paper leaves it open; this is the library's):
+ *   pixel centres  x_i = i - (nx-1)/2, y_j = j - (ny-1)/2 (unit pixels),
+ *   detector bins  s_b = b - (ns-1)/2 (unit spacing), slices independent;
+ *   R is the Joseph ray-driven projector (linear interpolation along the
+ *   axis closer to the ray, weighted 1/max(|cos|,|sin|)); R* is its exact
+ *   transpose; nabla uses forward differences with zero difference across
+ *   the last index of each dimension, lambda2 scaling the time component.
+ *
+ * Layouts (row-major, last index fastest; all arrays dense):
+ *   u    [nz][ny][nx][m]      coefficient volumes
+ *   g    [nz][K][ns]          projection data
+ *   p,mu,w [nz][ny][nx][nt][4] 4-vector fields on frames
+ *        (components d/dx, d/dy, d/dz, lambda2 d/dt)
+ * Element type is set by the plan's precision:
+ *   DR_F32          u, g, fields: float
+ *   DR_BF16_F32ACC  u, g: bfloat16 (raw 16-bit); fields: float; all
+ *                   arithmetic in float, inner products in double
+ *   DR_F64          everything double
+ *
+ * Memory and execution: unless a call says otherwise, data pointers are
+ * DEVICE pointers owned by the caller, and calls are asynchronous on the
+ * plan's stream.  The plan owns its tables and solver workspace.  No call
+ * throws; every call returns a dr_status and, on failure, records a message
+ * readable with dr_last_error() on the calling thread.
+ */
+#ifndef DYNRECON_H
+#define DYNRECON_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DR_OK = 0,
+    DR_EINVAL = -1,     /* bad shape, pointer, parameter or unsupported size */
+    DR_ENOMEM = -2,     /* device allocation failed or memory budget exceeded */
+    DR_ECUDA = -3,      /* a CUDA runtime call failed */
+    DR_ETIMEOUT = -4,   /* a bounded device-side wait gave up (status flag set) */
+    DR_ENOTCONV = -5,   /* reserved: solver reported non-convergence */
+    DR_ECANCELED = -6   /* a job was cancelled */
+} dr_status;
+
+typedef enum {
+    DR_FOURIER_REAL = 0, /* phi_0 = 1, phi_{2i-1} = cos(2 pi i t), phi_{2i} = sin(2 pi i t) */
+    DR_LEGENDRE = 1      /* phi_j(t) = P_j(2t - 1), Legendre polynomials, unnormalised */
+} dr_basis;
+
+typedef enum { DR_F32 = 0, DR_BF16_F32ACC = 1, DR_F64 = 2 } dr_precision;
+
+typedef enum {
+    DR_ADMM_CG = 0,        /* ADMM split psi = D u, u-step by n_cg conjugate-gradient steps */
+    DR_CHAMBOLLE_POCK = 1  /* primal-dual iteration of Sec. 3, Fig. 2 */
+} dr_algo;
+
+typedef struct dr_plan dr_plan;
+
+/*
+ * Create a plan for one reconstruction geometry (Sec. 4, Eq. discrt).
+ *   nx, ny, nz  volume size (pixels per row, rows, slices), each >= 1
+ *   ns          detector bins per projection row, 1 <= ns <= 2048
+ *   K           number of projections, >= 1
+ *   theta       host [K] projection angles in radians (any real value)
+ *   t           host [K] acquisition times in [0, 1) (scan-normalised)
+ *   basis, m    temporal basis kind and size, 1 <= m <= 32 (Sec. 4, Eq. repr)
+ *   nt_frames   number of reconstruction frames for the time derivative (<= 256),
+ *               frame l at t = l / nt_frames, >= 1
+ *   prec        storage/arithmetic precision (see above)
+ *   cuda_stream cudaStream_t on which calls are issued (NULL = default stream)
+ * Copies theta and t; allocates device tables.  Returns DR_EINVAL for bad
+ * arguments, DR_ENOMEM / DR_ECUDA on allocation or runtime failure; *out is
+ * left NULL on failure.  The current CUDA device at creation is the plan's.
+ */
+dr_status dr_plan_create(dr_plan **out, int nx, int ny, int nz, int ns, int K,
+                         const double *theta, const double *t, dr_basis basis, int m,
+                         int nt_frames, dr_precision prec, void *cuda_stream);
+
+/* Release the plan and everything it owns (synchronises its stream).  NULL is a no-op. */
+dr_status dr_plan_destroy(dr_plan *plan);
+
+/* Change the stream later calls are issued on. */
+dr_status dr_plan_set_stream(dr_plan *plan, void *cuda_stream);
+
+/* Bytes of device memory the plan holds now (tables plus solver workspace). */
+size_t dr_plan_device_bytes(const dr_plan *plan);
+
+/* Bytes of solver workspace admm_solve would allocate for this plan and algo. */
+size_t dr_plan_workspace_bytes(const dr_plan *plan, dr_algo algo);
+
+/*
+ * Wait for the plan's stream, then report any failure recorded by its
+ * kernels (DR_ETIMEOUT if a bounded wait gave up) or by the CUDA runtime.
+ * Clears the plan's device status word.
+ */
+dr_status dr_plan_sync(dr_plan *plan);
+
+/*
+ * Dynamic forward projection, Eq. (radapr) (Eq. Rfwd with Eq. repr):
+ *     g[z][k][b] = sum_j phi_j(t_k) (R_{theta_k} u_j[z])(s_b)
+ * u: device [nz][ny][nx][m], g: device [nz][K][ns] (overwritten).  u and g
+ * must not overlap.  Asynchronous.
+ */
+dr_status dyn_radon_fwd(dr_plan *plan, const void *u, void *g);
+
+/*
+ * Adjoint (back-projection), Eq. (radadjapr) for a real basis:
+ *     u_j[z] = beta * u_j[z] + sum_k phi_j(t_k) (R*_{theta_k} g[z][k])
+ * R* is the exact transpose of dyn_radon_fwd's R.  g: device [nz][K][ns],
+ * u: device [nz][ny][nx][m] (read when beta != 0, then overwritten).
+ * Asynchronous.
+ */
+dr_status dyn_radon_adj(dr_plan *plan, const void *g, void *u, double beta);
+
+/*
+ * 4D gradient of the synthesised frames, D = nabla_{lambda2} o PhiF
+ * (Eq. TV1; frames f(t_l) = sum_j phi_j(t_l) u_j):  p = D u.
+ * u: device [nz][ny][nx][m]; p: device [nz][ny][nx][nt][4] (overwritten).
+ */
+dr_status tv4d_grad(dr_plan *plan, const void *u, void *p, double lambda2);
+
+/*
+ * Adjoint of tv4d_grad (Sec. 3: K_2^* = -div_{lambda2}, then PhiF^T):
+ *     u = beta * u + D^T p
+ */
+dr_status tv4d_grad_adj(dr_plan *plan, const void *p, void *u, double lambda2, double beta);
+
+/*
+ * ADMM proximal and dual step on psi = D u (the shrink is the Moreau dual of
+ * the projection that Sec. 3 uses as prox of sigma F_2^*):
+ *     v = D u + mu/rho;  psi = v * max(0, 1 - (lambda1/rho)/|v|)  per (voxel, frame);
+ *     mu <- mu + rho (D u - psi);  w <- psi - mu/rho.
+ * u: device [nz][ny][nx][m]; mu (in/out), w (out): device [nz][ny][nx][nt][4].
+ * primal_res: HOST double, nullable; when given the call synchronises and
+ * stores ||D u - psi||_2 (accumulated in double).  rho > 0, lambda1 >= 0.
+ */
+dr_status tv4d_prox(dr_plan *plan, const void *u, void *mu, void *w, double rho, double lambda1,
+                    double lambda2, double *primal_res);
+
+typedef struct {
+    dr_algo algo;
+    int iters;              /* outer iterations, >= 0 */
+    int n_cg;               /* ADMM: CG steps per u-step (warm started), >= 1 */
+    double lambda1;         /* TV weight, >= 0 */
+    double lambda2;         /* time-derivative weight inside the norm, >= 0 */
+    double rho;             /* ADMM penalty; <= 0 selects 10 * lambda1 (or 1 if lambda1 = 0) */
+    double cp_theta;        /* Chambolle-Pock extrapolation theta in [0, 1] */
+    int power_iters;        /* Chambolle-Pock: power iterations for ||[R; D]||; <= 0 selects 100 */
+    double *objective_out;  /* HOST [iters], nullable: Eq. (lr12) at u after each iteration */
+    double *primal_res_out; /* HOST [iters], nullable: ADMM ||D u - psi|| after each iteration */
+    double *op_norm_out;    /* HOST, nullable: Chambolle-Pock operator norm estimate used */
+} dr_solve_params;
+
+/* Fill params with defaults: ADMM-CG, 20 iterations, 4 CG steps, lambda1 = lambda2 = 1e-3... */
+void dr_solve_params_default(dr_solve_params *params);
+
+/*
+ * Solve Eq. (lr12) for the coefficients u.
+ *   DR_ADMM_CG: split psi = D u; per iteration n_cg CG steps on
+ *       (R*R + rho D^T D) u = R* g + rho D^T (psi - mu/rho)   (warm start,
+ *       explicit residual, early stop when <r,r> = 0 or <p,Ap> <= 0), then
+ *       the tv4d_prox step.  mu = psi = 0 at the start.
+ *   DR_CHAMBOLLE_POCK: Sec. 3, Fig. 2 with h1 = h2 = 0 at the start and
+ *       tau = sigma = 0.99 / L, L = ||[R; D]|| from power_iters power
+ *       iterations started from a SplitMix64 vector (seed 1809).
+ * g: [nz][K][ns]; u: [nz][ny][nx][m], initial guess in, result out.  Either
+ * may be a host or a device pointer (host buffers are copied inside the
+ * call).  The call synchronises the plan's stream before returning; inner
+ * products, step sizes and residuals are kept on the device in double, and
+ * each iteration is replayed as one CUDA graph.  Allocates the workspace on
+ * first use (kept by the plan).  Returns DR_ETIMEOUT if a device wait gave up.
+ */
+dr_status admm_solve(dr_plan *plan, const void *g, void *u, const dr_solve_params *params);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *dr_last_error(void);
+
+/* Library version string. */
+const char *dr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DYNRECON_H */

@@ -175,16 +175,34 @@ void or_dyn_adj(const double *g, int nx, int ny, int nz, int m, int K,
 {
     i64 npix = (i64)nx * ny;
     memset(u, 0, sizeof(double) * (size_t)(nz * npix * m));
-#pragma omp parallel for schedule(dynamic)
+    /* pixel-driven: every pixel sums its projections in ascending k */
+#pragma omp parallel for collapse(2) schedule(dynamic)
     for (int z = 0; z < nz; ++z) {
-        double *bp = (double *)malloc(sizeof(double) * npix);
-        for (int k = 0; k < K; ++k) {
-            or_joseph_adj_slice(g + ((i64)z * K + k) * ns, ns, theta[k], nx, ny, bp);
-            for (i64 q = 0; q < npix; ++q)
-                for (int j = 0; j < m; ++j)
-                    u[((i64)z * npix + q) * m + j] += Phi[(i64)k * m + j] * bp[q];
+        for (int j = 0; j < ny; ++j) {
+            double yj = (double)j - 0.5 * (ny - 1);
+            for (int k = 0; k < K; ++k) {
+                const double *gk = g + ((i64)z * K + k) * ns;
+                double c = cos(theta[k]), s = sin(theta[k]);
+                double cm = fabs(c) >= fabs(s) ? fabs(c) : fabs(s);
+                for (int i = 0; i < nx; ++i) {
+                    double xi = (double)i - 0.5 * (nx - 1);
+                    double p = xi * c + yj * s;
+                    double pos = p + 0.5 * (ns - 1);
+                    i64 blo = (i64)ceil(pos - cm) - 1;
+                    i64 bhi = (i64)floor(pos + cm) + 1;
+                    if (blo < 0) blo = 0;
+                    if (bhi > ns - 1) bhi = ns - 1;
+                    double acc = 0.0;
+                    for (i64 b = blo; b <= bhi; ++b) {
+                        double sb = (double)b - 0.5 * (ns - 1);
+                        double wt = 1.0 - fabs(sb - p) / cm;
+                        if (wt > 0.0) acc += gk[b] * wt / cm;
+                    }
+                    double *uq = u + ((i64)z * npix + (i64)j * nx + i) * m;
+                    for (int jj = 0; jj < m; ++jj) uq[jj] += Phi[(i64)k * m + jj] * acc;
+                }
+            }
         }
-        free(bp);
     }
 }
 

@@ -1,0 +1,213 @@
+// dr_internal.cuh -- internal declarations shared by the CUDA sources of the
+// dynrecon library (plan layout, per-projection tables, launch helpers).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/dynrecon.h"
+
+namespace dr {
+
+typedef __nv_bfloat16 bf16;
+
+// ---------------------------------------------------------------------------
+// Error reporting (thread-local message, status codes).
+// ---------------------------------------------------------------------------
+dr_status fail(dr_status st, const std::string &msg);
+dr_status cuda_fail(cudaError_t e, const char *what);
+void clear_error();
+
+#define DR_CUDA_TRY(expr)                                  \
+    do {                                                   \
+        cudaError_t _e = (expr);                           \
+        if (_e != cudaSuccess) return dr::cuda_fail(_e, #expr); \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// Device status word: kernels OR these bits in when a bounded wait gives up.
+// ---------------------------------------------------------------------------
+enum : int { kStatusTimeout = 1 };
+
+// Template sizes for the number of basis functions: m is rounded up to the
+// next supported M; tables are zero padded so the extra lanes add zeros.
+int template_m(int m);
+
+// ---------------------------------------------------------------------------
+// Per-projection forward (Joseph) parameters.  For branch 0 the "lines" are
+// image rows y_r and samples run along x; for branch 1 lines are columns x_r
+// and samples run along y.  The sample position in pixel-index units along
+// the line for bin b and line r is  xi = C + b*A + r*B.
+// ---------------------------------------------------------------------------
+struct FwdProj {
+    long long A_fx, B_fx, C_fx;  // xi in 32.32 fixed point
+    double A, B, C;              // xi in double (FP64 path)
+    float Af, Bf, Cf;            // float copies for the loop-range estimate
+    float scale;                 // 1/|cos| (branch 0) or 1/|sin| (branch 1)
+    double scale_d;
+    int branch;
+    int pad_;
+};
+
+// Per-projection adjoint parameters: pos(i, j) = i*c + j*s + C0 is the ray
+// coordinate of pixel (i, j) in bin-index units; cm = max(|c|, |s|).
+struct AdjProj {
+    double c, s, C0, inv_c;
+};
+
+// Adjoint tile shape: 8*VPT x 16 voxels, 128 threads, VPT voxels per thread.
+constexpr int kAdjThreads = 128;
+constexpr int kAdjTY = 16;
+constexpr int kAdjP = 32;      // projections per pipeline stage
+constexpr int kAdjStages = 3;  // TMA pipeline depth
+
+constexpr int kFwdThreads = 256;
+constexpr int kFwdRPT = 8;   // rays per thread
+constexpr int kFwdGuard = 4; // zero cells on each side of a staged line
+
+constexpr int kRedThreads = 256;
+constexpr int kRedBlocksMax = 1024;
+constexpr int kRedSlots = 16;
+constexpr int kRedSlotStride = 2 * kRedBlocksMax;  // doubles per slot (up to 2 values per block)
+
+// Device-resident solver scalars (double).
+struct DevScalars {
+    double rr;      // <r, r>
+    double pq;      // <p, A p>
+    double alpha;   // CG step
+    double beta;    // CG direction update
+    double lam;     // power iteration: ||y||
+    double acc0, acc1, acc2;
+    int active;     // CG still running this u-step
+    int iter;       // outer iteration counter (graph replay index)
+    int pad_[2];
+};
+
+// Reduction slots (one per reducing kernel of an iteration).
+enum RedSlot {
+    kSlotRhs = 0,
+    kSlotLap = 1,
+    kSlotUpd = 2,
+    kSlotFid = 3,
+    kSlotProx = 4,
+    kSlotPow = 5,
+    kSlotTv = 6,
+    kSlotDot = 7,
+};
+
+struct Workspace {
+    size_t bytes = 0;
+    dr_algo algo = DR_ADMM_CG;
+    void *r = nullptr, *p = nullptr, *q = nullptr;  // [V][m] T
+    void *ut = nullptr, *uold = nullptr;            // CP
+    void *gd = nullptr;                             // data-sized scratch (S)
+    void *h1 = nullptr;                             // CP dual, data sized (S)
+    void *mu = nullptr, *w = nullptr;               // [V][nt][4] field type
+    void *u_dev = nullptr, *g_dev = nullptr;        // staging copies of host buffers
+    double *obj = nullptr;                          // [iters][3] fid, tv, primal^2
+    int obj_cap = 0;
+};
+
+}  // namespace dr
+
+// The opaque plan.
+struct dr_plan {
+    int nx, ny, nz, ns, K, m, nt;
+    int M;   // template size >= m
+    int MP;  // padded row length of the projection basis table (multiple of 4)
+    int MT;  // TV template size >= m (4, 8, 16 or 32): row stride of the frame tables
+    dr_basis basis;
+    dr_precision prec;
+    cudaStream_t stream;
+    cudaStream_t graph_stream;
+    cudaEvent_t ev_a, ev_b;
+    int device;
+    int num_sms;
+
+    std::vector<double> theta, t, Phi, PhiF;  // host, double
+
+    // device tables
+    dr::FwdProj *d_fwd = nullptr;
+    dr::AdjProj *d_adj = nullptr;
+    void *d_PhiP = nullptr;      // [K][MP] T (zero padded)
+    int *d_fwd_blocks = nullptr; // [n_fwd_blocks][fwd_P]
+    int n_fwd_blocks = 0;
+    int fwd_P = 0;
+    int fwd_R = 0;
+    void *d_PhiF = nullptr;   // [nt][MT] T
+    void *d_dPhiF = nullptr;  // [nt][MT] T, row l = PhiF[l+1] - PhiF[l] (0 for the last)
+    void *d_G = nullptr;      // [MT][MT] T, PhiF^T PhiF
+    void *d_Lt = nullptr;     // [MT][MT] T, PhiF^T Lt PhiF (Lt = 1D Neumann Laplacian in l)
+    double *d_partials = nullptr;
+    unsigned *d_counters = nullptr;
+    dr::DevScalars *d_scal = nullptr;
+    int *d_status = nullptr;
+    size_t table_bytes = 0;
+
+    dr::Workspace ws;
+};
+
+namespace dr {
+
+inline size_t elem_size(dr_precision p) { return p == DR_F64 ? 8 : (p == DR_BF16_F32ACC ? 2 : 4); }
+inline size_t calc_size(dr_precision p) { return p == DR_F64 ? 8 : 4; }
+inline size_t nvox(const dr_plan *P) { return (size_t)P->nx * P->ny * P->nz; }
+inline size_t nu_elems(const dr_plan *P) { return nvox(P) * P->m; }
+inline size_t ng_elems(const dr_plan *P) { return (size_t)P->nz * P->K * P->ns; }
+inline size_t nf_elems(const dr_plan *P) { return nvox(P) * P->nt * 4; }
+
+inline int red_grid(size_t n) {
+    size_t b = (n + kRedThreads - 1) / kRedThreads;
+    if (b < 1) b = 1;
+    if (b > (size_t)kRedBlocksMax) b = kRedBlocksMax;
+    return (int)b;
+}
+
+// Launchers (cudaStream_t = the stream to enqueue on).  Storage-typed
+// pointers are void*; the plan's precision selects the instantiation.
+//
+// Forward projection epilogues: out = R u (mode 0), out = R u - gm (mode 1),
+// out = (out + sigma R u - sigma gm) / (1 + sigma) (mode 2, CP dual h1).
+dr_status launch_fwd(dr_plan *P, const void *u, void *out, const void *gm, int mode, double sigma,
+                     cudaStream_t st);
+// u = alpha R* g + beta u.  g and u are storage typed unless u_calc is set,
+// in which case u is a compute-typed (float/double) vector.
+dr_status launch_adj(dr_plan *P, const void *g, void *u, double alpha, double beta, bool u_calc,
+                     cudaStream_t st);
+
+// TV family (tv.cu).  "calc" pointers are compute typed, storage pointers S.
+dr_status launch_grad(dr_plan *P, const void *u, bool u_calc, void *p, double lambda2, cudaStream_t st);
+dr_status launch_grad_adj(dr_plan *P, const void *p, void *u, bool u_calc, double lambda2,
+                          double alpha, double beta, cudaStream_t st);
+dr_status launch_prox(dr_plan *P, const void *u, bool u_calc, void *mu, void *w, double rho,
+                      double lambda1, double lambda2, double *obj_row, cudaStream_t st);
+// out = beta*out + alpha * D^T D x, with <x, out> reduced into scal->pq and
+// the CG step decided when cg_step is set.
+dr_status launch_lap(dr_plan *P, const void *x, void *out, double alpha, double beta, double lambda2,
+                     int cg_step, cudaStream_t st);
+// r = r + rho (D^T w - D^T D u); p = r; scal->rr = <r, r>; scal->active = 1.
+dr_status launch_rhs(dr_plan *P, const void *u, const void *w, void *r, void *p, double rho,
+                     double lambda2, cudaStream_t st);
+// h2 = project(h2 + sigma D ut, lambda1) (CP step 4).
+dr_status launch_cp_dual(dr_plan *P, const void *ut, void *h2, double sigma, double lambda1,
+                         double lambda2, cudaStream_t st);
+// u_new = u - tau (a + D^T h2); ut = u_new + theta (u_new - u) (CP steps 5, 6).
+dr_status launch_cp_primal(dr_plan *P, void *u, void *ut, const void *a, const void *h2, double tau,
+                           double theta, double lambda2, cudaStream_t st);
+// tv = sum |D u| into obj_row[1] (objective for CP).
+dr_status launch_tv_sum(dr_plan *P, const void *u, double lambda2, double *obj_row, cudaStream_t st);
+
+// Vector kernels (solver.cu).
+dr_status launch_dot_to(dr_plan *P, const void *a, const void *b, size_t n, bool storage, double *dst,
+                        cudaStream_t st);
+
+// Host-side tensor-map encoder (driver entry point, resolved once).
+bool encode_tensor_map_2d(CUtensorMap *map, CUtensorMapDataType dt, void *base, uint64_t dim0,
+                          uint64_t dim1, uint64_t stride1_bytes, uint32_t box0, uint32_t box1);
+
+}  // namespace dr

@@ -1,0 +1,346 @@
+// plan.cu -- plan construction (geometry and basis tables), error reporting,
+// status handling and the tensor-map encoder of the dynrecon library.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include "dr_internal.cuh"
+
+namespace dr {
+
+static thread_local std::string g_last_error;
+
+dr_status fail(dr_status st, const std::string &msg) {
+    g_last_error = msg;
+    return st;
+}
+
+dr_status cuda_fail(cudaError_t e, const char *what) {
+    g_last_error = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return e == cudaErrorMemoryAllocation ? DR_ENOMEM : DR_ECUDA;
+}
+
+void clear_error() { g_last_error.clear(); }
+
+int template_m(int m) {
+    static const int sizes[] = {1, 2, 4, 8, 12, 16, 24, 32};
+    for (int s : sizes)
+        if (m <= s) return s;
+    return -1;
+}
+
+// ---------------------------------------------------------------------------
+// Temporal basis evaluation (Sec. 4, Eq. repr).  Real Fourier:
+// phi_0 = 1, phi_{2i-1} = cos(2 pi i t), phi_{2i} = sin(2 pi i t).
+// Shifted Legendre: phi_j(t) = P_j(2t - 1) by Bonnet's recurrence.
+// ---------------------------------------------------------------------------
+static void eval_basis(dr_basis kind, int m, double t, double *row) {
+    if (kind == DR_FOURIER_REAL) {
+        row[0] = 1.0;
+        for (int j = 1; j < m; ++j) {
+            const int freq = (j + 1) / 2;
+            const double a = 2.0 * M_PI * freq * t;
+            row[j] = (j & 1) ? std::cos(a) : std::sin(a);
+        }
+    } else {
+        const double x = 2.0 * t - 1.0;
+        double pm1 = 1.0, p = x;
+        row[0] = 1.0;
+        if (m > 1) row[1] = x;
+        for (int n = 1; n + 1 < m; ++n) {
+            const double pn1 = ((2 * n + 1) * x * p - n * pm1) / (n + 1);
+            row[n + 1] = pn1;
+            pm1 = p;
+            p = pn1;
+        }
+    }
+}
+
+static std::once_flag g_tmap_once;
+static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+bool encode_tensor_map_2d(CUtensorMap *map, CUtensorMapDataType dt, void *base, uint64_t dim0,
+                          uint64_t dim1, uint64_t stride1_bytes, uint32_t box0, uint32_t box1) {
+    std::call_once(g_tmap_once, [] {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    });
+    if (!g_encode) return false;
+    cuuint64_t gdim[2] = {dim0, dim1};
+    cuuint64_t gstride[1] = {stride1_bytes};
+    cuuint32_t box[2] = {box0, box1};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = g_encode(map, dt, 2, base, gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+template <typename T>
+static dr_status upload(void **dst, const std::vector<double> &src, size_t &bytes) {
+    std::vector<T> tmp(src.size());
+    for (size_t i = 0; i < src.size(); ++i) tmp[i] = (T)src[i];
+    const size_t nb = std::max<size_t>(tmp.size(), 1) * sizeof(T);
+    DR_CUDA_TRY(cudaMalloc(dst, nb));
+    bytes += nb;
+    if (!tmp.empty()) DR_CUDA_TRY(cudaMemcpy(*dst, tmp.data(), tmp.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return DR_OK;
+}
+
+static dr_status build_tables(dr_plan *P) {
+    const int K = P->K, m = P->m, MP = P->MP, MT = P->MT, nt = P->nt;
+    const bool dbl = P->prec == DR_F64;
+    size_t &bytes = P->table_bytes;
+
+    // basis at acquisition times and on the frame grid
+    P->Phi.assign((size_t)K * m, 0.0);
+    for (int k = 0; k < K; ++k) eval_basis(P->basis, m, P->t[k], &P->Phi[(size_t)k * m]);
+    P->PhiF.assign((size_t)nt * m, 0.0);
+    for (int l = 0; l < nt; ++l) eval_basis(P->basis, m, (double)l / nt, &P->PhiF[(size_t)l * m]);
+
+    std::vector<double> phip((size_t)K * MP, 0.0);
+    for (int k = 0; k < K; ++k)
+        for (int j = 0; j < m; ++j) phip[(size_t)k * MP + j] = P->Phi[(size_t)k * m + j];
+    std::vector<double> phif((size_t)nt * MT, 0.0), dphif((size_t)nt * MT, 0.0);
+    for (int l = 0; l < nt; ++l)
+        for (int j = 0; j < m; ++j) {
+            phif[(size_t)l * MT + j] = P->PhiF[(size_t)l * m + j];
+            if (l + 1 < nt)
+                dphif[(size_t)l * MT + j] = P->PhiF[(size_t)(l + 1) * m + j] - P->PhiF[(size_t)l * m + j];
+        }
+    // G = PhiF^T PhiF ; Lt = PhiF^T Lt PhiF with (Lt F)_l = sum_{valid l' = l+-1} (F_l - F_l')
+    std::vector<double> G((size_t)MT * MT, 0.0), Lt((size_t)MT * MT, 0.0);
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) {
+            double g = 0.0, lt = 0.0;
+            for (int l = 0; l < nt; ++l) {
+                const double a = P->PhiF[(size_t)l * m + i];
+                g += a * P->PhiF[(size_t)l * m + j];
+                double lf = 0.0;
+                if (l > 0) lf += P->PhiF[(size_t)l * m + j] - P->PhiF[(size_t)(l - 1) * m + j];
+                if (l + 1 < nt) lf += P->PhiF[(size_t)l * m + j] - P->PhiF[(size_t)(l + 1) * m + j];
+                lt += a * lf;
+            }
+            G[(size_t)i * MT + j] = g;
+            Lt[(size_t)i * MT + j] = lt;
+        }
+    dr_status st;
+    if (dbl) {
+        if ((st = upload<double>(&P->d_PhiP, phip, bytes)) != DR_OK) return st;
+        if ((st = upload<double>(&P->d_PhiF, phif, bytes)) != DR_OK) return st;
+        if ((st = upload<double>(&P->d_dPhiF, dphif, bytes)) != DR_OK) return st;
+        if ((st = upload<double>(&P->d_G, G, bytes)) != DR_OK) return st;
+        if ((st = upload<double>(&P->d_Lt, Lt, bytes)) != DR_OK) return st;
+    } else {
+        if ((st = upload<float>(&P->d_PhiP, phip, bytes)) != DR_OK) return st;
+        if ((st = upload<float>(&P->d_PhiF, phif, bytes)) != DR_OK) return st;
+        if ((st = upload<float>(&P->d_dPhiF, dphif, bytes)) != DR_OK) return st;
+        if ((st = upload<float>(&P->d_G, G, bytes)) != DR_OK) return st;
+        if ((st = upload<float>(&P->d_Lt, Lt, bytes)) != DR_OK) return st;
+    }
+
+    // projection geometry
+    const double hx = 0.5 * (P->nx - 1), hy = 0.5 * (P->ny - 1), hs = 0.5 * (P->ns - 1);
+    std::vector<FwdProj> fw(K);
+    std::vector<AdjProj> ad(K);
+    std::vector<int> rows_b0, rows_b1;
+    const double two32 = 4294967296.0;
+    for (int k = 0; k < K; ++k) {
+        const double c = std::cos(P->theta[k]), s = std::sin(P->theta[k]);
+        FwdProj f{};
+        if (std::fabs(c) >= std::fabs(s)) {
+            f.branch = 0;
+            f.A = 1.0 / c;
+            f.B = -s / c;
+            f.C = (-hs + hy * s) / c + hx;
+            f.scale_d = 1.0 / std::fabs(c);
+            rows_b0.push_back(k);
+        } else {
+            f.branch = 1;
+            f.A = 1.0 / s;
+            f.B = -c / s;
+            f.C = (-hs + hx * c) / s + hy;
+            f.scale_d = 1.0 / std::fabs(s);
+            rows_b1.push_back(k);
+        }
+        f.A_fx = std::llround(f.A * two32);
+        f.B_fx = std::llround(f.B * two32);
+        f.C_fx = std::llround(f.C * two32);
+        f.Af = (float)f.A;
+        f.Bf = (float)f.B;
+        f.Cf = (float)f.C;
+        f.scale = (float)f.scale_d;
+        fw[k] = f;
+        AdjProj a{};
+        a.c = c;
+        a.s = s;
+        a.C0 = -hx * c - hy * s + hs;
+        a.inv_c = 1.0 / std::max(std::fabs(c), std::fabs(s));
+        ad[k] = a;
+    }
+    DR_CUDA_TRY(cudaMalloc(&P->d_fwd, sizeof(FwdProj) * K));
+    DR_CUDA_TRY(cudaMalloc(&P->d_adj, sizeof(AdjProj) * K));
+    bytes += (sizeof(FwdProj) + sizeof(AdjProj)) * K;
+    DR_CUDA_TRY(cudaMemcpy(P->d_fwd, fw.data(), sizeof(FwdProj) * K, cudaMemcpyHostToDevice));
+    DR_CUDA_TRY(cudaMemcpy(P->d_adj, ad.data(), sizeof(AdjProj) * K, cudaMemcpyHostToDevice));
+
+    // forward CTA work lists: blocks of fwd_P projections of one branch
+    const int Pf = std::max(1, std::min(64, (kFwdThreads * kFwdRPT) / P->ns));
+    P->fwd_P = Pf;
+    const int Wmax = std::max(P->nx, P->ny);
+    const int wpad = Wmax + 2 * kFwdGuard + 1;
+    const size_t budget = 72 * 1024;
+    int R = (int)(budget / ((size_t)Pf * wpad * calc_size(P->prec)));
+    R = std::max(1, std::min(16, R));
+    P->fwd_R = R;
+    std::vector<int> blocks;
+    for (const std::vector<int> *grp : {&rows_b0, &rows_b1}) {
+        for (size_t i = 0; i < grp->size(); i += Pf) {
+            for (int q = 0; q < Pf; ++q) {
+                const size_t idx = i + q;
+                blocks.push_back(idx < grp->size() ? (*grp)[idx] : -1);
+            }
+        }
+    }
+    P->n_fwd_blocks = (int)(blocks.size() / Pf);
+    DR_CUDA_TRY(cudaMalloc(&P->d_fwd_blocks, sizeof(int) * std::max<size_t>(blocks.size(), 1)));
+    bytes += sizeof(int) * blocks.size();
+    if (!blocks.empty())
+        DR_CUDA_TRY(cudaMemcpy(P->d_fwd_blocks, blocks.data(), sizeof(int) * blocks.size(), cudaMemcpyHostToDevice));
+
+    // reductions, scalars, status
+    DR_CUDA_TRY(cudaMalloc(&P->d_partials, sizeof(double) * kRedSlots * kRedSlotStride));
+    DR_CUDA_TRY(cudaMalloc(&P->d_counters, sizeof(unsigned) * kRedSlots));
+    DR_CUDA_TRY(cudaMalloc(&P->d_scal, sizeof(DevScalars)));
+    DR_CUDA_TRY(cudaMalloc(&P->d_status, sizeof(int)));
+    bytes += sizeof(double) * kRedSlots * kRedSlotStride + sizeof(unsigned) * kRedSlots + sizeof(DevScalars) +
+             sizeof(int);
+    DR_CUDA_TRY(cudaMemset(P->d_counters, 0, sizeof(unsigned) * kRedSlots));
+    DR_CUDA_TRY(cudaMemset(P->d_scal, 0, sizeof(DevScalars)));
+    DR_CUDA_TRY(cudaMemset(P->d_status, 0, sizeof(int)));
+    return DR_OK;
+}
+
+void free_workspace(dr_plan *P);
+
+}  // namespace dr
+
+using namespace dr;
+
+extern "C" {
+
+const char *dr_last_error(void) { return g_last_error.c_str(); }
+
+const char *dr_version(void) { return "dynrecon 0.1 (sm_103a)"; }
+
+void dr_solve_params_default(dr_solve_params *p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->algo = DR_ADMM_CG;
+    p->iters = 20;
+    p->n_cg = 4;
+    p->lambda1 = 1e-3;
+    p->lambda2 = 1.0;
+    p->rho = 0.0;
+    p->cp_theta = 1.0;
+    p->power_iters = 100;
+}
+
+dr_status dr_plan_create(dr_plan **out, int nx, int ny, int nz, int ns, int K, const double *theta,
+                         const double *t, dr_basis basis, int m, int nt_frames, dr_precision prec,
+                         void *cuda_stream) {
+    clear_error();
+    if (!out) return fail(DR_EINVAL, "dr_plan_create: out is NULL");
+    *out = nullptr;
+    if (nx < 1 || ny < 1 || nz < 1 || ns < 1 || K < 1 || nt_frames < 1)
+        return fail(DR_EINVAL, "dr_plan_create: sizes must be >= 1");
+    if (ns > 2048) return fail(DR_EINVAL, "dr_plan_create: ns > 2048 is not supported");
+    if (nt_frames > 256) return fail(DR_EINVAL, "dr_plan_create: nt_frames > 256 is not supported");
+    if (nx > 65536 || ny > 65536 || nz > 65535 || K > (1 << 24))
+        return fail(DR_EINVAL, "dr_plan_create: size out of range");
+    if (m < 1 || m > 32) return fail(DR_EINVAL, "dr_plan_create: m must be in [1, 32]");
+    if (basis != DR_FOURIER_REAL && basis != DR_LEGENDRE) return fail(DR_EINVAL, "dr_plan_create: bad basis");
+    if (prec != DR_F32 && prec != DR_BF16_F32ACC && prec != DR_F64)
+        return fail(DR_EINVAL, "dr_plan_create: bad precision");
+    if (!theta || !t) return fail(DR_EINVAL, "dr_plan_create: theta/t are NULL");
+    for (int k = 0; k < K; ++k)
+        if (!std::isfinite(theta[k]) || !std::isfinite(t[k]))
+            return fail(DR_EINVAL, "dr_plan_create: theta/t must be finite");
+
+    dr_plan *P = new (std::nothrow) dr_plan();
+    if (!P) return fail(DR_ENOMEM, "dr_plan_create: host allocation failed");
+    P->nx = nx; P->ny = ny; P->nz = nz; P->ns = ns; P->K = K; P->m = m; P->nt = nt_frames;
+    P->M = template_m(m);
+    P->MP = (P->M + 3) / 4 * 4;
+    P->MT = m <= 4 ? 4 : (m <= 8 ? 8 : (m <= 16 ? 16 : 32));
+    P->basis = basis;
+    P->prec = prec;
+    P->stream = (cudaStream_t)cuda_stream;
+    P->theta.assign(theta, theta + K);
+    P->t.assign(t, t + K);
+    cudaError_t e = cudaGetDevice(&P->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P->graph_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->ev_a, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->ev_b, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        dr_status st = cuda_fail(e, "dr_plan_create");
+        dr_plan_destroy(P);
+        return st;
+    }
+    dr_status st = build_tables(P);
+    if (st != DR_OK) {
+        std::string msg = g_last_error;
+        dr_plan_destroy(P);
+        return fail(st, msg);
+    }
+    *out = P;
+    return DR_OK;
+}
+
+dr_status dr_plan_destroy(dr_plan *P) {
+    if (!P) return DR_OK;
+    if (P->stream || P->graph_stream) cudaDeviceSynchronize();
+    free_workspace(P);
+    void *ptrs[] = {P->d_fwd, P->d_adj, P->d_PhiP, P->d_fwd_blocks, P->d_PhiF, P->d_dPhiF, P->d_G, P->d_Lt,
+                    P->d_partials, P->d_counters, P->d_scal, P->d_status};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (P->graph_stream) cudaStreamDestroy(P->graph_stream);
+    if (P->ev_a) cudaEventDestroy(P->ev_a);
+    if (P->ev_b) cudaEventDestroy(P->ev_b);
+    delete P;
+    return DR_OK;
+}
+
+dr_status dr_plan_set_stream(dr_plan *P, void *s) {
+    if (!P) return fail(DR_EINVAL, "dr_plan_set_stream: NULL plan");
+    P->stream = (cudaStream_t)s;
+    return DR_OK;
+}
+
+size_t dr_plan_device_bytes(const dr_plan *P) { return P ? P->table_bytes + P->ws.bytes : 0; }
+
+dr_status dr_plan_sync(dr_plan *P) {
+    if (!P) return fail(DR_EINVAL, "dr_plan_sync: NULL plan");
+    DR_CUDA_TRY(cudaStreamSynchronize(P->stream));
+    DR_CUDA_TRY(cudaStreamSynchronize(P->graph_stream));
+    DR_CUDA_TRY(cudaGetLastError());
+    int flag = 0;
+    DR_CUDA_TRY(cudaMemcpy(&flag, P->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+        DR_CUDA_TRY(cudaMemset(P->d_status, 0, sizeof(int)));
+        return fail(DR_ETIMEOUT, "a bounded device-side wait gave up (status word set)");
+    }
+    return DR_OK;
+}
+
+}  // extern "C"

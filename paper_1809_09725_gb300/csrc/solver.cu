@@ -1,0 +1,451 @@
+// solver.cu -- iterative solvers for the model of Eq. (lr12) on the device:
+// ADMM with a conjugate-gradient u-step, and Chambolle-Pock (Sec. 3, Fig. 2).
+//
+// All inner products, CG step sizes and residuals are accumulated in double
+// on the device (deterministic last-block reductions) and never leave it
+// inside an iteration, so one iteration is a fixed launch sequence that is
+// captured once as a CUDA graph and replayed.  A device-side iteration
+// counter tells the reducing kernels which objective row to write.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "dr_device.cuh"
+
+namespace dr {
+
+// Counter-based SplitMix64 (Steele, Lea, Flood, OOPSLA 2014): output i of the
+// stream with seed s is the finaliser applied to s + (i+1) * golden gamma.
+__device__ __forceinline__ double splitmix_uniform(unsigned long long seed, unsigned long long i) {
+    unsigned long long z = seed + (i + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads)
+    dot_kernel(const T *__restrict__ a, const T *__restrict__ b, size_t n, double *partials, unsigned *counter,
+               DevScalars *scal, double *obj, int row_off, int col, int to_lam) {
+    double acc = 0.0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        acc += (double)a[i] * (double)b[i];
+    double v[1] = {acc}, tot[1];
+    if (block_reduce_last<1>(v, partials, counter, tot)) {
+        if (obj) obj[3 * (size_t)(scal->iter + row_off) + col] = tot[0];
+        if (to_lam) scal->lam = tot[0];
+        if (!obj && !to_lam) scal->acc0 = tot[0];
+    }
+}
+
+// u += alpha p; r -= alpha q; rr_new = <r, r>; beta = rr_new / rr.
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads)
+    cg_update_kernel(T *__restrict__ u, T *__restrict__ r, const T *__restrict__ p, const T *__restrict__ q,
+                     size_t n, double *partials, unsigned *counter, DevScalars *scal) {
+    const T a = (T)scal->alpha;
+    double acc = 0.0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        u[i] += a * p[i];
+        const T rn = r[i] - a * q[i];
+        r[i] = rn;
+        acc += (double)rn * (double)rn;
+    }
+    double v[1] = {acc}, tot[1];
+    if (block_reduce_last<1>(v, partials, counter, tot)) {
+        if (scal->active) {
+            scal->beta = tot[0] / scal->rr;
+            scal->rr = tot[0];
+        } else {
+            scal->beta = 0.0;
+        }
+    }
+}
+
+template <typename T>
+__global__ void cg_dir_kernel(T *__restrict__ p, const T *__restrict__ r, size_t n, const DevScalars *scal) {
+    const T b = (T)scal->beta;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        p[i] = r[i] + b * p[i];
+}
+
+template <typename T>
+__global__ void pow_init_kernel(T *__restrict__ x, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        x[i] = (T)(0.5 + splitmix_uniform(1809ull, (unsigned long long)i));
+}
+
+// x = y / sqrt(scal->lam) (normalise by the norm just reduced).
+template <typename T>
+__global__ void pow_scale_kernel(T *__restrict__ x, const T *__restrict__ y, size_t n, const DevScalars *scal) {
+    const double nrm = sqrt(scal->lam);
+    const T f = nrm > 0.0 ? (T)(1.0 / nrm) : T(0);
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        x[i] = y[i] * f;
+}
+
+__global__ void iter_kernel(DevScalars *scal, int set, int value) {
+    if (set) scal->iter = value;
+    else scal->iter += 1;
+}
+
+template <typename S, typename T>
+__global__ void convert_kernel(const S *__restrict__ in, T *__restrict__ out, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        stc<T>(out + i, ldc<T>(in + i));
+}
+template <>
+__global__ void convert_kernel<float, bf16>(const float *__restrict__ in, bf16 *__restrict__ out, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        out[i] = __float2bfloat16_rn(in[i]);
+}
+
+static dr_status launched(const char *what) {
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? DR_OK : cuda_fail(e, what);
+}
+
+static int vec_grid(size_t n) { return red_grid(n); }
+
+// ---------------------------------------------------------------------------
+// typed launch helpers (T = float or double)
+// ---------------------------------------------------------------------------
+template <typename T>
+static dr_status dot_t(dr_plan *P, const void *a, const void *b, size_t n, int slot, double *obj, int row_off,
+                       int col, int to_lam, cudaStream_t st) {
+    dot_kernel<T><<<vec_grid(n), kRedThreads, 0, st>>>((const T *)a, (const T *)b, n,
+                                                        P->d_partials + slot * kRedSlotStride, P->d_counters + slot,
+                                                        P->d_scal, obj, row_off, col, to_lam);
+    return launched("dot_kernel");
+}
+
+dr_status launch_dot_to(dr_plan *P, const void *a, const void *b, size_t n, bool storage, double *dst,
+                        cudaStream_t st) {
+    (void)storage;
+    (void)dst;
+    if (P->prec == DR_F64) return dot_t<double>(P, a, b, n, kSlotDot, nullptr, 0, 0, 0, st);
+    return dot_t<float>(P, a, b, n, kSlotDot, nullptr, 0, 0, 0, st);
+}
+
+void free_workspace(dr_plan *P) {
+    Workspace &w = P->ws;
+    void *ptrs[] = {w.r, w.p, w.q, w.ut, w.uold, w.gd, w.h1, w.mu, w.w, w.u_dev, w.g_dev, w.obj};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    w = Workspace();
+}
+
+static size_t ws_bytes(const dr_plan *P, dr_algo algo, int iters) {
+    const size_t T = calc_size(P->prec);
+    const size_t nu = nu_elems(P), ng = ng_elems(P), nf = nf_elems(P);
+    size_t b = 0;
+    if (algo == DR_ADMM_CG) b += 3 * nu * T + ng * T + 2 * nf * T;
+    else b += 2 * nu * T + 2 * ng * T + nf * T;
+    b += nu * T + ng * T;  // internal copies of u and g (host or bf16 inputs)
+    b += sizeof(double) * 3 * (size_t)(iters + 1);
+    return b;
+}
+
+static dr_status ensure_ws(dr_plan *P, dr_algo algo, int iters) {
+    Workspace &w = P->ws;
+    if (w.bytes && w.algo == algo && w.obj_cap >= iters + 1) return DR_OK;
+    free_workspace(P);
+    const size_t T = calc_size(P->prec);
+    const size_t nu = nu_elems(P), ng = ng_elems(P), nf = nf_elems(P);
+    auto alloc = [&](void **p, size_t bytes) -> bool {
+        if (cudaMalloc(p, std::max<size_t>(bytes, 16)) != cudaSuccess) return false;
+        w.bytes += bytes;
+        return true;
+    };
+    bool ok = true;
+    if (algo == DR_ADMM_CG) {
+        ok = ok && alloc(&w.r, nu * T) && alloc(&w.p, nu * T) && alloc(&w.q, nu * T);
+        ok = ok && alloc(&w.gd, ng * T) && alloc(&w.mu, nf * T) && alloc(&w.w, nf * T);
+    } else {
+        ok = ok && alloc(&w.ut, nu * T) && alloc(&w.q, nu * T);
+        ok = ok && alloc(&w.gd, ng * T) && alloc(&w.h1, ng * T) && alloc(&w.mu, nf * T);
+    }
+    ok = ok && alloc(&w.u_dev, nu * T) && alloc(&w.g_dev, ng * T);
+    ok = ok && alloc((void **)&w.obj, sizeof(double) * 3 * (size_t)(iters + 1));
+    if (!ok) {
+        cudaGetLastError();
+        free_workspace(P);
+        return fail(DR_ENOMEM, "admm_solve: device workspace allocation failed");
+    }
+    w.algo = algo;
+    w.obj_cap = iters + 1;
+    return DR_OK;
+}
+
+static bool is_device_ptr(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <typename T>
+static dr_status vec_launches(dr_plan *P, int which, void *a, void *b, void *c, void *d, size_t n, cudaStream_t st) {
+    switch (which) {
+        case 0:
+            cg_update_kernel<T><<<vec_grid(n), kRedThreads, 0, st>>>(
+                (T *)a, (T *)b, (const T *)c, (const T *)d, n, P->d_partials + kSlotUpd * kRedSlotStride,
+                P->d_counters + kSlotUpd, P->d_scal);
+            return launched("cg_update_kernel");
+        case 1:
+            cg_dir_kernel<T><<<vec_grid(n), kRedThreads, 0, st>>>((T *)a, (const T *)b, n, P->d_scal);
+            return launched("cg_dir_kernel");
+        case 2:
+            pow_init_kernel<T><<<vec_grid(n), kRedThreads, 0, st>>>((T *)a, n);
+            return launched("pow_init_kernel");
+        case 3:
+            pow_scale_kernel<T><<<vec_grid(n), kRedThreads, 0, st>>>((T *)a, (const T *)b, n, P->d_scal);
+            return launched("pow_scale_kernel");
+    }
+    return fail(DR_EINVAL, "vec_launches");
+}
+
+static dr_status vec(dr_plan *P, int which, void *a, void *b, void *c, void *d, size_t n, cudaStream_t st) {
+    return P->prec == DR_F64 ? vec_launches<double>(P, which, a, b, c, d, n, st)
+                             : vec_launches<float>(P, which, a, b, c, d, n, st);
+}
+
+static dr_status dot(dr_plan *P, const void *a, const void *b, size_t n, int slot, double *obj, int row_off, int col,
+                     int to_lam, cudaStream_t st) {
+    return P->prec == DR_F64 ? dot_t<double>(P, a, b, n, slot, obj, row_off, col, to_lam, st)
+                             : dot_t<float>(P, a, b, n, slot, obj, row_off, col, to_lam, st);
+}
+
+#define TRY(...)                       \
+    do {                               \
+        dr_status _s = (__VA_ARGS__);  \
+        if (_s != DR_OK) return _s;    \
+    } while (0)
+
+// The projector/TV launchers take "calc" (compute-typed) buffers here.
+dr_status launch_fwd_calc(dr_plan *P, const void *u, void *out, const void *gm, int mode, double sigma,
+                          cudaStream_t st);
+dr_status launch_adj_calc(dr_plan *P, const void *g, void *u, double alpha, double beta, cudaStream_t st);
+
+// One ADMM-CG iteration (the captured sequence).
+static dr_status admm_iteration(dr_plan *P, void *u, const void *g, const dr_solve_params &prm, double rho,
+                                cudaStream_t st) {
+    Workspace &w = P->ws;
+    const size_t nu = nu_elems(P), ng = ng_elems(P);
+    // d = R u - g ; fidelity of the current u ; r = R*(g - R u)
+    TRY(launch_fwd_calc(P, u, w.gd, g, 1, 0.0, st));
+    TRY(dot(P, w.gd, w.gd, ng, kSlotFid, w.obj, 0, 0, 0, st));
+    TRY(launch_adj_calc(P, w.gd, w.r, -1.0, 0.0, st));
+    // r += rho (D^T w - D^T D u); p = r; rr = <r,r>
+    TRY(launch_rhs(P, u, w.w, w.r, w.p, rho, prm.lambda2, st));
+    for (int c = 0; c < prm.n_cg; ++c) {
+        TRY(launch_fwd_calc(P, w.p, w.gd, nullptr, 0, 0.0, st));
+        TRY(launch_adj_calc(P, w.gd, w.q, 1.0, 0.0, st));
+        TRY(launch_lap(P, w.p, w.q, rho, 1.0, prm.lambda2, 1, st));
+        TRY(vec(P, 0, u, w.r, w.p, w.q, nu, st));
+        if (c + 1 < prm.n_cg) TRY(vec(P, 1, w.p, w.r, nullptr, nullptr, nu, st));
+    }
+    TRY(launch_prox(P, u, true, w.mu, w.w, rho, prm.lambda1, prm.lambda2, w.obj + 3, st));
+    iter_kernel<<<1, 1, 0, st>>>(P->d_scal, 0, 0);
+    return launched("iter_kernel");
+}
+
+static dr_status cp_iteration(dr_plan *P, void *u, const void *g, const dr_solve_params &prm, double sigma,
+                              double tau, bool want_obj, cudaStream_t st) {
+    Workspace &w = P->ws;
+    const size_t ng = ng_elems(P);
+    TRY(launch_fwd_calc(P, w.ut, w.h1, g, 2, sigma, st));
+    TRY(launch_cp_dual(P, w.ut, w.mu, sigma, prm.lambda1, prm.lambda2, st));
+    TRY(launch_adj_calc(P, w.h1, w.q, 1.0, 0.0, st));
+    TRY(launch_cp_primal(P, u, w.ut, w.q, w.mu, tau, prm.cp_theta, prm.lambda2, st));
+    if (want_obj) {
+        TRY(launch_fwd_calc(P, u, w.gd, g, 1, 0.0, st));
+        TRY(dot(P, w.gd, w.gd, ng, kSlotFid, w.obj, 1, 0, 0, st));
+        TRY(launch_tv_sum(P, u, prm.lambda2, w.obj + 3, st));
+    }
+    iter_kernel<<<1, 1, 0, st>>>(P->d_scal, 0, 0);
+    return launched("iter_kernel");
+}
+
+static dr_status power_norm(dr_plan *P, double lambda2, int iters, double *L, cudaStream_t st) {
+    Workspace &w = P->ws;
+    const size_t nu = nu_elems(P);
+    void *x = w.ut, *y = w.q;
+    TRY(vec(P, 2, x, nullptr, nullptr, nullptr, nu, st));
+    TRY(dot(P, x, x, nu, kSlotPow, nullptr, 0, 0, 1, st));
+    TRY(vec(P, 3, x, x, nullptr, nullptr, nu, st));
+    for (int it = 0; it < iters; ++it) {
+        TRY(launch_fwd_calc(P, x, w.gd, nullptr, 0, 0.0, st));
+        TRY(launch_adj_calc(P, w.gd, y, 1.0, 0.0, st));
+        TRY(launch_lap(P, x, y, 1.0, 1.0, lambda2, 0, st));
+        TRY(dot(P, y, y, nu, kSlotPow, nullptr, 0, 0, 1, st));
+        TRY(vec(P, 3, x, y, nullptr, nullptr, nu, st));
+    }
+    DevScalars hs;
+    cudaError_t e = cudaMemcpyAsync(&hs, P->d_scal, sizeof(hs), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "power_norm: read");
+    *L = std::sqrt(std::sqrt(hs.lam));
+    return DR_OK;
+}
+
+template <typename S, typename T>
+static dr_status convert(const void *in, void *out, size_t n, cudaStream_t st) {
+    convert_kernel<S, T><<<vec_grid(n), kRedThreads, 0, st>>>((const S *)in, (T *)out, n);
+    return launched("convert_kernel");
+}
+
+static dr_status solve(dr_plan *P, const void *g_in, void *u_io, const dr_solve_params &prm) {
+    const cudaStream_t st = P->graph_stream;
+    Workspace &w = P->ws;
+    const size_t nu = nu_elems(P), ng = ng_elems(P), nf = nf_elems(P);
+    const size_t es = elem_size(P->prec), cs = calc_size(P->prec);
+    const bool bf = P->prec == DR_BF16_F32ACC;
+    const bool g_dev = is_device_ptr(g_in), u_dev = is_device_ptr(u_io);
+
+    DR_CUDA_TRY(cudaEventRecord(P->ev_a, P->stream));
+    DR_CUDA_TRY(cudaStreamWaitEvent(st, P->ev_a, 0));
+
+    // ---- bring g and u into compute-typed device buffers ----
+    const void *g = g_in;
+    void *u = u_io;
+    if (!g_dev || bf) {
+        void *src = (void *)g_in;
+        if (!g_dev) {
+            // host data: copy raw storage-typed bytes, then convert in place if needed
+            void *stage = bf ? w.gd : w.g_dev;  // gd is large enough (ng * cs >= ng * es)
+            DR_CUDA_TRY(cudaMemcpyAsync(stage, g_in, ng * es, cudaMemcpyHostToDevice, st));
+            src = stage;
+        }
+        if (bf) TRY(convert<bf16, float>(src, w.g_dev, ng, st));
+        g = w.g_dev;
+    }
+    if (!u_dev || bf) {
+        void *src = u_io;
+        if (!u_dev) {
+            void *stage = bf ? w.q : w.u_dev;
+            DR_CUDA_TRY(cudaMemcpyAsync(stage, u_io, nu * es, cudaMemcpyHostToDevice, st));
+            src = stage;
+        }
+        if (bf) TRY(convert<bf16, float>(src, w.u_dev, nu, st));
+        u = w.u_dev;
+    }
+
+    DR_CUDA_TRY(cudaMemsetAsync(P->d_scal, 0, sizeof(DevScalars), st));
+    DR_CUDA_TRY(cudaMemsetAsync(w.obj, 0, sizeof(double) * 3 * (size_t)(prm.iters + 1), st));
+    const bool want_obj = prm.objective_out != nullptr;
+    double rho = prm.rho > 0.0 ? prm.rho : (prm.lambda1 > 0.0 ? 10.0 * prm.lambda1 : 1.0);
+    double sigma = 0.0, tau = 0.0, L = 0.0;
+
+    if (prm.algo == DR_ADMM_CG) {
+        DR_CUDA_TRY(cudaMemsetAsync(w.mu, 0, nf * cs, st));
+        DR_CUDA_TRY(cudaMemsetAsync(w.w, 0, nf * cs, st));
+    } else {
+        DR_CUDA_TRY(cudaMemsetAsync(w.h1, 0, ng * cs, st));
+        DR_CUDA_TRY(cudaMemsetAsync(w.mu, 0, nf * cs, st));
+        const int pit = prm.power_iters > 0 ? prm.power_iters : 100;
+        TRY(power_norm(P, prm.lambda2, pit, &L, st));
+        if (!(L > 0.0) || !std::isfinite(L)) return fail(DR_EINVAL, "admm_solve: operator norm is zero");
+        sigma = tau = 0.99 / L;
+        if (prm.op_norm_out) *prm.op_norm_out = L;
+        DR_CUDA_TRY(cudaMemcpyAsync(w.ut, u, nu * cs, cudaMemcpyDeviceToDevice, st));
+        iter_kernel<<<1, 1, 0, st>>>(P->d_scal, 1, 0);
+        TRY(launched("iter_kernel"));
+    }
+
+    auto one = [&](cudaStream_t s) -> dr_status {
+        if (prm.algo == DR_ADMM_CG) return admm_iteration(P, u, g, prm, rho, s);
+        return cp_iteration(P, u, g, prm, sigma, tau, want_obj, s);
+    };
+    if (prm.iters > 0) {
+        // first iteration eagerly (sets kernel attributes), the rest as one graph
+        TRY(one(st));
+        if (prm.iters > 1) {
+            cudaGraph_t graph = nullptr;
+            cudaGraphExec_t exec = nullptr;
+            DR_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            dr_status cs_st = one(st);
+            cudaError_t ce = cudaStreamEndCapture(st, &graph);
+            if (cs_st != DR_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                return cs_st;
+            }
+            if (ce != cudaSuccess) return cuda_fail(ce, "admm_solve: graph capture");
+            ce = cudaGraphInstantiate(&exec, graph, 0);
+            if (ce != cudaSuccess) {
+                cudaGraphDestroy(graph);
+                return cuda_fail(ce, "admm_solve: graph instantiate");
+            }
+            for (int it = 1; it < prm.iters && ce == cudaSuccess; ++it) ce = cudaGraphLaunch(exec, st);
+            cudaGraphExecDestroy(exec);
+            cudaGraphDestroy(graph);
+            if (ce != cudaSuccess) return cuda_fail(ce, "admm_solve: graph launch");
+        }
+        if (prm.algo == DR_ADMM_CG && (want_obj)) {
+            // fidelity of the final u (row iters)
+            TRY(launch_fwd_calc(P, u, w.gd, g, 1, 0.0, st));
+            TRY(dot(P, w.gd, w.gd, ng, kSlotFid, w.obj, 0, 0, 0, st));
+        }
+    }
+
+    // ---- results back ----
+    if (!u_dev || bf) {
+        void *dst = u_io;
+        if (bf) {
+            void *tmp = u_dev ? u_io : (void *)w.q;
+            TRY(convert<float, bf16>(u, tmp, nu, st));
+            if (!u_dev) DR_CUDA_TRY(cudaMemcpyAsync(dst, tmp, nu * es, cudaMemcpyDeviceToHost, st));
+        } else {
+            DR_CUDA_TRY(cudaMemcpyAsync(dst, u, nu * cs, cudaMemcpyDeviceToHost, st));
+        }
+    }
+    std::vector<double> obj;
+    if (prm.iters > 0 && (want_obj || prm.primal_res_out)) {
+        obj.resize(3 * (size_t)(prm.iters + 1));
+        DR_CUDA_TRY(cudaMemcpyAsync(obj.data(), w.obj, sizeof(double) * obj.size(), cudaMemcpyDeviceToHost, st));
+    }
+    DR_CUDA_TRY(cudaEventRecord(P->ev_b, st));
+    DR_CUDA_TRY(cudaStreamWaitEvent(P->stream, P->ev_b, 0));
+    DR_CUDA_TRY(cudaStreamSynchronize(st));
+    int flag = 0;
+    DR_CUDA_TRY(cudaMemcpy(&flag, P->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+        cudaMemset(P->d_status, 0, sizeof(int));
+        return fail(DR_ETIMEOUT, "admm_solve: a bounded device-side wait gave up");
+    }
+    for (int it = 0; it < prm.iters && !obj.empty(); ++it) {
+        const double *row = &obj[3 * (size_t)(it + 1)];
+        if (want_obj) prm.objective_out[it] = 0.5 * row[0] + prm.lambda1 * row[1];
+        if (prm.primal_res_out) prm.primal_res_out[it] = std::sqrt(row[2]);
+    }
+    (void)rho;
+    return DR_OK;
+}
+
+}  // namespace dr
+
+using namespace dr;
+
+extern "C" {
+
+size_t dr_plan_workspace_bytes(const dr_plan *P, dr_algo algo) { return P ? ws_bytes(P, algo, 1) : 0; }
+
+dr_status admm_solve(dr_plan *P, const void *g, void *u, const dr_solve_params *prm) {
+    clear_error();
+    if (!P || !g || !u || !prm) return fail(DR_EINVAL, "admm_solve: NULL argument");
+    const dr_solve_params &p = *prm;
+    if (p.algo != DR_ADMM_CG && p.algo != DR_CHAMBOLLE_POCK) return fail(DR_EINVAL, "admm_solve: bad algo");
+    if (p.iters < 0 || (p.algo == DR_ADMM_CG && p.n_cg < 1)) return fail(DR_EINVAL, "admm_solve: bad iters/n_cg");
+    if (!(p.lambda1 >= 0.0) || !(p.lambda2 >= 0.0) || !std::isfinite(p.lambda1) || !std::isfinite(p.lambda2) ||
+        !std::isfinite(p.rho) || !std::isfinite(p.cp_theta))
+        return fail(DR_EINVAL, "admm_solve: lambdas must be finite and >= 0");
+    if (p.algo == DR_CHAMBOLLE_POCK && !(p.cp_theta >= 0.0 && p.cp_theta <= 1.0))
+        return fail(DR_EINVAL, "admm_solve: cp_theta must be in [0, 1]");
+    TRY(ensure_ws(P, p.algo, p.iters));
+    return solve(P, g, u, p);
+}
+
+}  // extern "C"

@@ -1,0 +1,606 @@
+// tv_impl.cuh -- 4D total-variation kernels on the synthesised frames.
+//
+// The regulariser of Eq. (TV1) acts on frames f(x, t_l) = sum_j phi_j(t_l)
+// u_j(x), l = 0..nt-1 (Sec. 4, Eq. discrt).  With D = nabla_{lambda2} o PhiF
+// (forward differences, zero across the last index of each dimension,
+// lambda2 on the time component) the kernels compute, per voxel, without
+// ever storing the frames:
+//   D u      : nabla along x,y,z of sum_j PhiF[l][j] u_j  =  sum_j PhiF[l][j] (u_j(x+e) - u_j(x));
+//              time part lambda2 sum_j (PhiF[l+1][j] - PhiF[l][j]) u_j(x)
+//   D^T p    : PhiF^T (-div p)  (Sec. 3, K_2^* = -div_{lambda2})
+//   D^T D x  : G (L_s x) + lambda2^2 Lt x with G = PhiF^T PhiF and
+//              Lt = PhiF^T L_t PhiF (m x m), L_s / L_t the Neumann Laplacians
+//              (the composition of the two stencils, exact up to rounding)
+//   ADMM shrink/dual update, CP projection and primal update (Sec. 3, Fig. 2)
+// All are HBM bound; each thread owns whole voxels (all m coefficients and
+// all nt frames), neighbours come through L1/L2.
+#include <algorithm>
+#include <cmath>
+
+#pragma once
+#include "dr_device.cuh"
+
+namespace dr {
+
+template <typename T>
+struct V4;
+template <>
+struct V4<float> {
+    typedef float4 type;
+};
+struct D4 {
+    double x, y, z, w;
+};
+template <>
+struct V4<double> {
+    typedef D4 type;
+};
+
+template <typename T>
+__device__ __forceinline__ typename V4<T>::type ld4(const T *p);
+template <>
+__device__ __forceinline__ float4 ld4<float>(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+template <>
+__device__ __forceinline__ D4 ld4<double>(const double *p) {
+    const double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
+    return D4{a.x, a.y, b.x, b.y};
+}
+template <typename T, typename V>
+__device__ __forceinline__ void st4(T *p, V v);
+template <>
+__device__ __forceinline__ void st4<float, float4>(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
+template <>
+__device__ __forceinline__ void st4<double, D4>(double *p, D4 v) {
+    reinterpret_cast<double2 *>(p)[0] = make_double2(v.x, v.y);
+    reinterpret_cast<double2 *>(p)[1] = make_double2(v.z, v.w);
+}
+
+struct Geo {
+    int nx, ny, nz, m, nt;
+};
+
+__device__ __forceinline__ void vox_xyz(size_t v, const Geo &g, int &x, int &y, int &z) {
+    x = (int)(v % g.nx);
+    const size_t r = v / g.nx;
+    y = (int)(r % g.ny);
+    z = (int)(r / g.ny);
+}
+
+// Shared-memory copies of PhiF / dPhiF ([nt][M]) and G / Lt ([M][M]).
+template <typename T, int M>
+__device__ __forceinline__ void load_tables(T *sm, const T *PhiF, const T *dPhiF, const T *G, const T *Lt, int nt,
+                                            bool want_gl) {
+    const int n1 = nt * M;
+    for (int i = threadIdx.x; i < n1; i += blockDim.x) {
+        sm[i] = PhiF[i];
+        sm[n1 + i] = dPhiF[i];
+    }
+    if (want_gl)
+        for (int i = threadIdx.x; i < M * M; i += blockDim.x) {
+            sm[2 * n1 + i] = G[i];
+            sm[2 * n1 + M * M + i] = Lt[i];
+        }
+    __syncthreads();
+}
+
+// Spatial forward differences of the coefficients at voxel v (Neumann).
+template <typename T, typename S, int M>
+__device__ __forceinline__ void coeff_diffs(const S *__restrict__ u, size_t v, int x, int y, int z, const Geo &g,
+                                            T (&uc)[M], T (&ex)[M], T (&ey)[M], T (&ez)[M]) {
+    load_coeffs<T, S, M>(u + v * g.m, g.m, uc);
+    if (x + 1 < g.nx) {
+        load_coeffs<T, S, M>(u + (v + 1) * g.m, g.m, ex);
+#pragma unroll
+        for (int j = 0; j < M; ++j) ex[j] -= uc[j];
+    } else {
+#pragma unroll
+        for (int j = 0; j < M; ++j) ex[j] = T(0);
+    }
+    if (y + 1 < g.ny) {
+        load_coeffs<T, S, M>(u + (v + g.nx) * g.m, g.m, ey);
+#pragma unroll
+        for (int j = 0; j < M; ++j) ey[j] -= uc[j];
+    } else {
+#pragma unroll
+        for (int j = 0; j < M; ++j) ey[j] = T(0);
+    }
+    if (z + 1 < g.nz) {
+        load_coeffs<T, S, M>(u + (v + (size_t)g.nx * g.ny) * g.m, g.m, ez);
+#pragma unroll
+        for (int j = 0; j < M; ++j) ez[j] -= uc[j];
+    } else {
+#pragma unroll
+        for (int j = 0; j < M; ++j) ez[j] = T(0);
+    }
+}
+
+// Spatial components of (D u)(x, t_l) from the coefficient differences.
+template <typename T, int M>
+__device__ __forceinline__ void grad_frame(const T *sm, int l, const T (&ex)[M], const T (&ey)[M],
+                                           const T (&ez)[M], T &gx, T &gy, T &gz) {
+    const T *ph = sm + l * M;
+    gx = gy = gz = T(0);
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+        gx = fma(ph[j], ex[j], gx);
+        gy = fma(ph[j], ey[j], gy);
+        gz = fma(ph[j], ez[j], gz);
+    }
+}
+
+// Time component lambda2 sum_j (PhiF[l+1][j] - PhiF[l][j]) u_j (zero for the last frame).
+template <typename T, int M>
+__device__ __forceinline__ T dt_frame(const T *dph_l, T lambda2, const T (&uc)[M]) {
+    T s = T(0);
+#pragma unroll
+    for (int j = 0; j < M; ++j) s = fma(dph_l[j], uc[j], s);
+    return lambda2 * s;
+}
+
+// ---------------------------------------------------------------------------
+// p = D u
+// ---------------------------------------------------------------------------
+template <typename T, typename S, int M>
+__global__ void __launch_bounds__(kRedThreads)
+    grad_kernel(const S *__restrict__ u, T *__restrict__ p, const T *PhiF, const T *dPhiF, Geo g, T lambda2) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sm = reinterpret_cast<T *>(smem_raw);
+    load_tables<T, M>(sm, PhiF, dPhiF, nullptr, nullptr, g.nt, false);
+    const T *dph = sm + g.nt * M;
+    const size_t nv = (size_t)g.nx * g.ny * g.nz;
+    for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < nv; v += (size_t)gridDim.x * blockDim.x) {
+        int x, y, z;
+        vox_xyz(v, g, x, y, z);
+        T uc[M], ex[M], ey[M], ez[M];
+        coeff_diffs<T, S, M>(u, v, x, y, z, g, uc, ex, ey, ez);
+        for (int l = 0; l < g.nt; ++l) {
+            T gx, gy, gz, gt;
+            grad_frame<T, M>(sm, l, ex, ey, ez, gx, gy, gz);
+            gt = dt_frame<T, M>(dph + l * M, lambda2, uc);
+            typename V4<T>::type o;
+            o.x = gx;
+            o.y = gy;
+            o.z = gz;
+            o.w = gt;
+            st4<T>(p + (v * g.nt + l) * 4, o);
+        }
+    }
+}
+
+// (D^T p)_j at voxel v (Neumann-matched backward differences, then PhiF^T).
+template <typename T, int M>
+__device__ __forceinline__ void gradT_voxel(const T *__restrict__ p, size_t v, int x, int y, int z, const Geo &g,
+                                            const T *sm, T lambda2, T (&outj)[M]) {
+    const T *dph = sm + g.nt * M;
+#pragma unroll
+    for (int j = 0; j < M; ++j) outj[j] = T(0);
+    const size_t sx = (size_t)g.nt * 4, sy = (size_t)g.nx * g.nt * 4, sz = (size_t)g.nx * g.ny * g.nt * 4;
+    const T *pv = p + v * g.nt * 4;
+    for (int l = 0; l < g.nt; ++l) {
+        const typename V4<T>::type q = ld4<T>(pv + l * 4);
+        T s = T(0);
+        if (x + 1 < g.nx) s -= q.x;
+        if (x > 0) s += (pv - sx)[l * 4 + 0];
+        if (y + 1 < g.ny) s -= q.y;
+        if (y > 0) s += (pv - sy)[l * 4 + 1];
+        if (z + 1 < g.nz) s -= q.z;
+        if (z > 0) s += (pv - sz)[l * 4 + 2];
+        const T qt = lambda2 * q.w;
+        const T *ph = sm + l * M;
+        const T *dp = dph + l * M;
+#pragma unroll
+        for (int j = 0; j < M; ++j) outj[j] = fma(ph[j], s, fma(dp[j], qt, outj[j]));
+    }
+}
+
+// u = beta u + alpha D^T p
+template <typename T, typename S, int M>
+__global__ void __launch_bounds__(kRedThreads)
+    gradT_kernel(const T *__restrict__ p, S *__restrict__ u_s, T *__restrict__ u_c, const T *PhiF, const T *dPhiF,
+                 Geo g, T lambda2, T alpha, T beta) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sm = reinterpret_cast<T *>(smem_raw);
+    load_tables<T, M>(sm, PhiF, dPhiF, nullptr, nullptr, g.nt, false);
+    const size_t nv = (size_t)g.nx * g.ny * g.nz;
+    for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < nv; v += (size_t)gridDim.x * blockDim.x) {
+        int x, y, z;
+        vox_xyz(v, g, x, y, z);
+        T o[M];
+        gradT_voxel<T, M>(p, v, x, y, z, g, sm, lambda2, o);
+#pragma unroll
+        for (int j = 0; j < M; ++j) {
+            if (j >= g.m) break;
+            const size_t i = v * g.m + j;
+            if (u_c) {
+                T r = alpha * o[j];
+                if (beta != T(0)) r += beta * u_c[i];
+                u_c[i] = r;
+            } else {
+                T r = alpha * o[j];
+                if (beta != T(0)) r += beta * ldc<T>(u_s + i);
+                stc<T>(u_s + i, r);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// ADMM prox: v = Du + mu/rho; psi = shrink(v, lambda1/rho); mu += rho (Du - psi);
+// w = psi - mu/rho.  Reduces sum |Du| and ||Du - psi||^2.
+// obj: destination row (tv, primal^2); when use_iter the row is obj + 3*iter + 1.
+// ---------------------------------------------------------------------------
+template <typename T, typename S, int M>
+__global__ void __launch_bounds__(kRedThreads)
+    prox_kernel(const S *__restrict__ u, T *__restrict__ mu, T *__restrict__ w, const T *PhiF, const T *dPhiF, Geo g,
+                T rho, T lambda1, T lambda2, double *partials, unsigned *counter, DevScalars *scal, double *obj,
+                int use_iter) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sm = reinterpret_cast<T *>(smem_raw);
+    load_tables<T, M>(sm, PhiF, dPhiF, nullptr, nullptr, g.nt, false);
+    const T *dph = sm + g.nt * M;
+    const T kappa = lambda1 / rho, irho = T(1) / rho;
+    double acc_tv = 0.0, acc_pr = 0.0;
+    const size_t nv = (size_t)g.nx * g.ny * g.nz;
+    for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < nv; v += (size_t)gridDim.x * blockDim.x) {
+        int x, y, z;
+        vox_xyz(v, g, x, y, z);
+        T uc[M], ex[M], ey[M], ez[M];
+        coeff_diffs<T, S, M>(u, v, x, y, z, g, uc, ex, ey, ez);
+        for (int l = 0; l < g.nt; ++l) {
+            T d[4];
+            grad_frame<T, M>(sm, l, ex, ey, ez, d[0], d[1], d[2]);
+            d[3] = dt_frame<T, M>(dph + l * M, lambda2, uc);
+            const size_t o = (v * g.nt + l) * 4;
+            const typename V4<T>::type mo = ld4<T>(mu + o);
+            const T mv[4] = {mo.x, mo.y, mo.z, mo.w};
+            T vv[4];
+            T n2 = T(0), dn2 = T(0);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                vv[c] = d[c] + mv[c] * irho;
+                n2 += vv[c] * vv[c];
+                dn2 += d[c] * d[c];
+            }
+            const T n = sqrt(n2);
+            const T f = (n > T(0)) ? fmax(T(0), T(1) - kappa / n) : T(0);
+            T mn[4], wn[4];
+            double pr = 0.0;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const T psi = vv[c] * f;
+                const T r = d[c] - psi;
+                pr += (double)r * (double)r;
+                mn[c] = mv[c] + rho * r;
+                wn[c] = psi - mn[c] * irho;
+            }
+            acc_tv += sqrt((double)dn2);
+            acc_pr += pr;
+            typename V4<T>::type a, b;
+            a.x = mn[0]; a.y = mn[1]; a.z = mn[2]; a.w = mn[3];
+            b.x = wn[0]; b.y = wn[1]; b.z = wn[2]; b.w = wn[3];
+            st4<T>(mu + o, a);
+            st4<T>(w + o, b);
+        }
+    }
+    double vals[2] = {acc_tv, acc_pr}, tot[2];
+    if (block_reduce_last<2>(vals, partials, counter, tot)) {
+        double *row = use_iter ? obj + 3 * (size_t)scal->iter : obj;
+        if (row) {
+            row[1] = tot[0];
+            row[2] = tot[1];
+        } else {
+            scal->acc1 = tot[0];
+            scal->acc2 = tot[1];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// out = beta out + alpha (G L_s x + lambda2^2 Lt x), G L_s + lambda2^2 Lt being
+// D^T D.  mode 0: reduce <x, out> into scal->pq.  mode 1 (CG step): the last
+// block turns <p, Ap> into the step alpha (stopping when <p,Ap> <= 0 or
+// <r,r> = 0).  mode 2 (ADMM right-hand side): also copy out into pdir and
+// reduce <out, out> into scal->rr, marking the CG active.
+// ---------------------------------------------------------------------------
+template <typename T, int M>
+__global__ void __launch_bounds__(kRedThreads)
+    lap_kernel(const T *__restrict__ xv, T *__restrict__ out, T *__restrict__ pdir, const T *PhiF,
+               const T *dPhiF, const T *G, const T *Lt, Geo g, T alpha, T beta, T lam2sq, double *partials,
+               unsigned *counter, DevScalars *scal, int mode) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sm = reinterpret_cast<T *>(smem_raw);
+    load_tables<T, M>(sm, PhiF, dPhiF, G, Lt, g.nt, true);
+    const T *Gs = sm + 2 * g.nt * M;
+    const T *Ls = Gs + M * M;
+    double acc = 0.0;
+    const size_t nv = (size_t)g.nx * g.ny * g.nz;
+    const size_t sy = g.nx, sz = (size_t)g.nx * g.ny;
+    for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < nv; v += (size_t)gridDim.x * blockDim.x) {
+        int x, y, z;
+        vox_xyz(v, g, x, y, z);
+        T xc[M], ls[M], nb[M];
+        load_coeffs<T, T, M>(xv + v * g.m, g.m, xc);
+#pragma unroll
+        for (int j = 0; j < M; ++j) ls[j] = T(0);
+        const bool has[6] = {x > 0, x + 1 < g.nx, y > 0, y + 1 < g.ny, z > 0, z + 1 < g.nz};
+        const long long off[6] = {-1, 1, -(long long)sy, (long long)sy, -(long long)sz, (long long)sz};
+#pragma unroll
+        for (int e = 0; e < 6; ++e) {
+            if (!has[e]) continue;
+            load_coeffs<T, T, M>(xv + (size_t)((long long)v + off[e]) * g.m, g.m, nb);
+#pragma unroll
+            for (int j = 0; j < M; ++j) ls[j] += xc[j] - nb[j];
+        }
+        double dotv = 0.0;
+#pragma unroll(M <= 16 ? M : 1)
+        for (int i = 0; i < M; ++i) {
+            if (i >= g.m) break;
+            T s = T(0);
+#pragma unroll
+            for (int j = 0; j < M; ++j) s = fma(Gs[i * M + j], ls[j], fma(lam2sq * Ls[i * M + j], xc[j], s));
+            const size_t idx = v * g.m + i;
+            T r = alpha * s;
+            if (beta != T(0)) r += beta * out[idx];
+            out[idx] = r;
+            if (mode == 2) {
+                pdir[idx] = r;
+                dotv += (double)r * (double)r;
+            } else {
+                dotv += (double)xv[idx] * (double)r;
+            }
+        }
+        acc += dotv;
+    }
+    double vals[1] = {acc}, tot[1];
+    if (block_reduce_last<1>(vals, partials, counter, tot)) {
+        if (mode == 1) {
+            const double pq = tot[0], rr = scal->rr;
+            scal->pq = pq;
+            if (scal->active && pq > 0.0 && rr > 0.0) {
+                scal->alpha = rr / pq;
+            } else {
+                scal->alpha = 0.0;
+                scal->active = 0;
+            }
+        } else if (mode == 2) {
+            scal->rr = tot[0];
+            scal->active = 1;
+        } else {
+            scal->pq = tot[0];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Chambolle-Pock (Fig. 2) step 4: h2 = project(h2 + sigma D ut, lambda1).
+// ---------------------------------------------------------------------------
+template <typename T, int M>
+__global__ void __launch_bounds__(kRedThreads)
+    cp_dual_kernel(const T *__restrict__ ut, T *__restrict__ h2, const T *PhiF, const T *dPhiF, Geo g, T sigma,
+                   T lambda1, T lambda2) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sm = reinterpret_cast<T *>(smem_raw);
+    load_tables<T, M>(sm, PhiF, dPhiF, nullptr, nullptr, g.nt, false);
+    const T *dph = sm + g.nt * M;
+    const size_t nv = (size_t)g.nx * g.ny * g.nz;
+    for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < nv; v += (size_t)gridDim.x * blockDim.x) {
+        int x, y, z;
+        vox_xyz(v, g, x, y, z);
+        T uc[M], ex[M], ey[M], ez[M];
+        coeff_diffs<T, T, M>(ut, v, x, y, z, g, uc, ex, ey, ez);
+        for (int l = 0; l < g.nt; ++l) {
+            T d[4];
+            grad_frame<T, M>(sm, l, ex, ey, ez, d[0], d[1], d[2]);
+            d[3] = dt_frame<T, M>(dph + l * M, lambda2, uc);
+            const size_t o = (v * g.nt + l) * 4;
+            typename V4<T>::type h = ld4<T>(h2 + o);
+            h.x += sigma * d[0];
+            h.y += sigma * d[1];
+            h.z += sigma * d[2];
+            h.w += sigma * d[3];
+            const T n = sqrt(h.x * h.x + h.y * h.y + h.z * h.z + h.w * h.w);
+            if (n > lambda1) {
+                const T f = lambda1 / n;
+                h.x *= f; h.y *= f; h.z *= f; h.w *= f;
+            }
+            st4<T>(h2 + o, h);
+        }
+    }
+}
+
+// Fig. 2 steps 5-6: u_new = u - tau (a + D^T h2); ut = u_new + theta (u_new - u).
+template <typename T, int M>
+__global__ void __launch_bounds__(kRedThreads)
+    cp_primal_kernel(T *__restrict__ u, T *__restrict__ ut, const T *__restrict__ a, const T *__restrict__ h2,
+                     const T *PhiF, const T *dPhiF, Geo g, T tau, T theta, T lambda2) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sm = reinterpret_cast<T *>(smem_raw);
+    load_tables<T, M>(sm, PhiF, dPhiF, nullptr, nullptr, g.nt, false);
+    const size_t nv = (size_t)g.nx * g.ny * g.nz;
+    for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < nv; v += (size_t)gridDim.x * blockDim.x) {
+        int x, y, z;
+        vox_xyz(v, g, x, y, z);
+        T dt[M];
+        gradT_voxel<T, M>(h2, v, x, y, z, g, sm, lambda2, dt);
+#pragma unroll
+        for (int j = 0; j < M; ++j) {
+            if (j >= g.m) break;
+            const size_t i = v * g.m + j;
+            const T uo = u[i];
+            const T un = uo - tau * (a[i] + dt[j]);
+            u[i] = un;
+            ut[i] = un + theta * (un - uo);
+        }
+    }
+}
+
+// sum |D u| (objective TV term) into obj row [1] (row = obj + 3*iter).
+template <typename T, int M>
+__global__ void __launch_bounds__(kRedThreads)
+    tvsum_kernel(const T *__restrict__ u, const T *PhiF, const T *dPhiF, Geo g, T lambda2, double *partials,
+                 unsigned *counter, DevScalars *scal, double *obj) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sm = reinterpret_cast<T *>(smem_raw);
+    load_tables<T, M>(sm, PhiF, dPhiF, nullptr, nullptr, g.nt, false);
+    const T *dph = sm + g.nt * M;
+    double acc = 0.0;
+    const size_t nv = (size_t)g.nx * g.ny * g.nz;
+    for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < nv; v += (size_t)gridDim.x * blockDim.x) {
+        int x, y, z;
+        vox_xyz(v, g, x, y, z);
+        T uc[M], ex[M], ey[M], ez[M];
+        coeff_diffs<T, T, M>(u, v, x, y, z, g, uc, ex, ey, ez);
+        for (int l = 0; l < g.nt; ++l) {
+            T d[4];
+            grad_frame<T, M>(sm, l, ex, ey, ez, d[0], d[1], d[2]);
+            d[3] = dt_frame<T, M>(dph + l * M, lambda2, uc);
+            acc += sqrt((double)(d[0] * d[0] + d[1] * d[1] + d[2] * d[2] + d[3] * d[3]));
+        }
+    }
+    double vals[1] = {acc}, tot[1];
+    if (block_reduce_last<1>(vals, partials, counter, tot)) obj[3 * (size_t)scal->iter + 1] = tot[0];
+}
+
+// ===========================================================================
+// Launchers (instantiated per precision in tv_ops_*.cu and tv_calc_*.cu)
+// ===========================================================================
+inline Geo geo(const dr_plan *P) { return Geo{P->nx, P->ny, P->nz, P->m, P->nt}; }
+
+template <typename T, int M>
+inline size_t tab_smem(const dr_plan *P, bool gl) {
+    return sizeof(T) * ((size_t)2 * P->nt * M + (gl ? 2 * M * M : 0));
+}
+
+template <typename K>
+inline dr_status prep_smem(K kern, size_t smem) {
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return cuda_fail(e, "tv: smem attribute");
+    }
+    return DR_OK;
+}
+
+inline dr_status tv_launched(const char *what) {
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? DR_OK : cuda_fail(e, what);
+}
+
+// TV template sizes: m rounded up to 4, 8, 16 or 32 (tables are padded).
+#define DR_TV_MT(...)                                      \
+    switch (P->MT) {                                       \
+        case 4: { constexpr int M = 4; __VA_ARGS__ }       \
+        case 8: { constexpr int M = 8; __VA_ARGS__ }       \
+        case 16: { constexpr int M = 16; __VA_ARGS__ }     \
+        case 32: { constexpr int M = 32; __VA_ARGS__ }     \
+    }                                                      \
+    return fail(DR_EINVAL, "tv: unsupported m");
+
+// Kernels whose coefficient input may be stored in S (bf16 for BF16 plans).
+template <typename T, typename S>
+struct TvOps {
+    static dr_status grad(dr_plan *P, const void *u, void *p, double lambda2, cudaStream_t st) {
+        DR_TV_MT({
+            auto kern = grad_kernel<T, S, M>;
+            const size_t smem = tab_smem<T, M>(P, false);
+            dr_status s = prep_smem(kern, smem);
+            if (s != DR_OK) return s;
+            kern<<<red_grid(nvox(P)), kRedThreads, smem, st>>>((const S *)u, (T *)p, (const T *)P->d_PhiF,
+                                                                (const T *)P->d_dPhiF, geo(P), (T)lambda2);
+            return tv_launched("grad_kernel");
+        })
+    }
+    static dr_status grad_adj(dr_plan *P, const void *p, void *u, bool calc, double lambda2, double alpha,
+                              double beta, cudaStream_t st) {
+        DR_TV_MT({
+            auto kern = gradT_kernel<T, S, M>;
+            const size_t smem = tab_smem<T, M>(P, false);
+            dr_status s = prep_smem(kern, smem);
+            if (s != DR_OK) return s;
+            kern<<<red_grid(nvox(P)), kRedThreads, smem, st>>>(
+                (const T *)p, calc ? nullptr : (S *)u, calc ? (T *)u : nullptr, (const T *)P->d_PhiF,
+                (const T *)P->d_dPhiF, geo(P), (T)lambda2, (T)alpha, (T)beta);
+            return tv_launched("gradT_kernel");
+        })
+    }
+    static dr_status prox(dr_plan *P, const void *u, void *mu, void *w, double rho, double lambda1, double lambda2,
+                          double *obj_row, cudaStream_t st) {
+        DR_TV_MT({
+            auto kern = prox_kernel<T, S, M>;
+            const size_t smem = tab_smem<T, M>(P, false);
+            dr_status s = prep_smem(kern, smem);
+            if (s != DR_OK) return s;
+            kern<<<red_grid(nvox(P)), kRedThreads, smem, st>>>(
+                (const S *)u, (T *)mu, (T *)w, (const T *)P->d_PhiF, (const T *)P->d_dPhiF, geo(P), (T)rho,
+                (T)lambda1, (T)lambda2, P->d_partials + kSlotProx * kRedSlotStride, P->d_counters + kSlotProx,
+                P->d_scal, obj_row, obj_row ? 1 : 0);
+            return tv_launched("prox_kernel");
+        })
+    }
+};
+
+// Kernels on compute-typed solver vectors only.
+template <typename T>
+struct TvCalc {
+    static dr_status lap(dr_plan *P, const void *x, void *out, void *pdir, double alpha, double beta,
+                         double lambda2, int mode, cudaStream_t st) {
+        DR_TV_MT({
+            auto kern = lap_kernel<T, M>;
+            const size_t smem = tab_smem<T, M>(P, true);
+            dr_status s = prep_smem(kern, smem);
+            if (s != DR_OK) return s;
+            const int slot = mode == 2 ? kSlotRhs : kSlotLap;
+            kern<<<red_grid(nvox(P)), kRedThreads, smem, st>>>(
+                (const T *)x, (T *)out, (T *)pdir, (const T *)P->d_PhiF, (const T *)P->d_dPhiF, (const T *)P->d_G,
+                (const T *)P->d_Lt, geo(P), (T)alpha, (T)beta, (T)(lambda2 * lambda2),
+                P->d_partials + slot * kRedSlotStride, P->d_counters + slot, P->d_scal, mode);
+            return tv_launched("lap_kernel");
+        })
+    }
+    static dr_status cp_dual(dr_plan *P, const void *ut, void *h2, double sigma, double lambda1, double lambda2,
+                             cudaStream_t st) {
+        DR_TV_MT({
+            auto kern = cp_dual_kernel<T, M>;
+            const size_t smem = tab_smem<T, M>(P, false);
+            dr_status s = prep_smem(kern, smem);
+            if (s != DR_OK) return s;
+            kern<<<red_grid(nvox(P)), kRedThreads, smem, st>>>((const T *)ut, (T *)h2, (const T *)P->d_PhiF,
+                                                                (const T *)P->d_dPhiF, geo(P), (T)sigma,
+                                                                (T)lambda1, (T)lambda2);
+            return tv_launched("cp_dual_kernel");
+        })
+    }
+    static dr_status cp_primal(dr_plan *P, void *u, void *ut, const void *a, const void *h2, double tau,
+                               double theta, double lambda2, cudaStream_t st) {
+        DR_TV_MT({
+            auto kern = cp_primal_kernel<T, M>;
+            const size_t smem = tab_smem<T, M>(P, false);
+            dr_status s = prep_smem(kern, smem);
+            if (s != DR_OK) return s;
+            kern<<<red_grid(nvox(P)), kRedThreads, smem, st>>>((T *)u, (T *)ut, (const T *)a, (const T *)h2,
+                                                                (const T *)P->d_PhiF, (const T *)P->d_dPhiF,
+                                                                geo(P), (T)tau, (T)theta, (T)lambda2);
+            return tv_launched("cp_primal_kernel");
+        })
+    }
+    static dr_status tv_sum(dr_plan *P, const void *u, double lambda2, double *obj, cudaStream_t st) {
+        DR_TV_MT({
+            auto kern = tvsum_kernel<T, M>;
+            const size_t smem = tab_smem<T, M>(P, false);
+            dr_status s = prep_smem(kern, smem);
+            if (s != DR_OK) return s;
+            kern<<<red_grid(nvox(P)), kRedThreads, smem, st>>>((const T *)u, (const T *)P->d_PhiF,
+                                                                (const T *)P->d_dPhiF, geo(P), (T)lambda2,
+                                                                P->d_partials + kSlotTv * kRedSlotStride,
+                                                                P->d_counters + kSlotTv, P->d_scal, obj);
+            return tv_launched("tvsum_kernel");
+        })
+    }
+};
+
+extern template struct TvOps<float, float>;
+extern template struct TvOps<float, bf16>;
+extern template struct TvOps<double, double>;
+extern template struct TvCalc<float>;
+extern template struct TvCalc<double>;
+
+}  // namespace dr

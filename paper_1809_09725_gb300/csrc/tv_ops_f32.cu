@@ -1,0 +1,6 @@
+// tv_ops_f32.cu -- explicit instantiation of the 4D TV kernels (see tv_impl.cuh).
+#include "tv_impl.cuh"
+
+namespace dr {
+template struct TvOps<float, float>;
+}  // namespace dr

@@ -1,0 +1,281 @@
+"""Thin Python binding of the dynrecon C ABI (``include/dynrecon.h``).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library ``libdynrecon.so``.  PyTorch supplies device memory and the stream;
+tensors are passed by pointer.  If the library is missing the import of the
+entry points fails loudly -- there is no CPU fallback.
+
+The entry points keep the C names: ``dyn_radon_fwd``, ``dyn_radon_adj``,
+``tv4d_grad``, ``tv4d_grad_adj``, ``tv4d_prox``, ``admm_solve``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdynrecon.so")
+
+DR_OK, DR_EINVAL, DR_ENOMEM, DR_ECUDA, DR_ETIMEOUT, DR_ENOTCONV, DR_ECANCELED = 0, -1, -2, -3, -4, -5, -6
+FOURIER, LEGENDRE = 0, 1
+F32, BF16, F64 = 0, 1, 2
+ADMM_CG, CHAMBOLLE_POCK = 0, 1
+
+_STATUS = {DR_EINVAL: "EINVAL", DR_ENOMEM: "ENOMEM", DR_ECUDA: "ECUDA", DR_ETIMEOUT: "ETIMEOUT",
+           DR_ENOTCONV: "ENOTCONV", DR_ECANCELED: "ECANCELED"}
+
+# Every symbol include/dynrecon.h declares.
+EXPORTS = ("dr_plan_create", "dr_plan_destroy", "dr_plan_set_stream", "dr_plan_device_bytes",
+           "dr_plan_workspace_bytes", "dr_plan_sync", "dyn_radon_fwd", "dyn_radon_adj", "tv4d_grad",
+           "tv4d_grad_adj", "tv4d_prox", "dr_solve_params_default", "admm_solve", "dr_last_error",
+           "dr_version")
+
+
+class DynreconError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s (%d): %s" % (_STATUS.get(status, "?"), status, msg))
+        self.status = status
+
+
+class SolveParams(ctypes.Structure):
+    _fields_ = [("algo", ctypes.c_int), ("iters", ctypes.c_int), ("n_cg", ctypes.c_int),
+                ("lambda1", ctypes.c_double), ("lambda2", ctypes.c_double), ("rho", ctypes.c_double),
+                ("cp_theta", ctypes.c_double), ("power_iters", ctypes.c_int),
+                ("objective_out", ctypes.POINTER(ctypes.c_double)),
+                ("primal_res_out", ctypes.POINTER(ctypes.c_double)),
+                ("op_norm_out", ctypes.POINTER(ctypes.c_double))]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load ``libdynrecon.so`` and declare the ABI (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError("libdynrecon.so not built (%s); run __graft_entry__.build()" % path)
+    lib = ctypes.CDLL(path)
+    vp, i, d, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+    pd = ctypes.POINTER(ctypes.c_double)
+    decl = {
+        "dr_plan_create": (i, [ctypes.POINTER(vp), i, i, i, i, i, pd, pd, i, i, i, i, vp]),
+        "dr_plan_destroy": (i, [vp]),
+        "dr_plan_set_stream": (i, [vp, vp]),
+        "dr_plan_device_bytes": (sz, [vp]),
+        "dr_plan_workspace_bytes": (sz, [vp, i]),
+        "dr_plan_sync": (i, [vp]),
+        "dyn_radon_fwd": (i, [vp, vp, vp]),
+        "dyn_radon_adj": (i, [vp, vp, vp, d]),
+        "tv4d_grad": (i, [vp, vp, vp, d]),
+        "tv4d_grad_adj": (i, [vp, vp, vp, d, d]),
+        "tv4d_prox": (i, [vp, vp, vp, vp, d, d, d, pd]),
+        "dr_solve_params_default": (None, [ctypes.POINTER(SolveParams)]),
+        "admm_solve": (i, [vp, vp, vp, ctypes.POINTER(SolveParams)]),
+        "dr_last_error": (ctypes.c_char_p, []),
+        "dr_version": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in decl.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(st: int):
+    if st != DR_OK:
+        raise DynreconError(st, load().dr_last_error().decode())
+
+
+def _torch():
+    import torch
+    return torch
+
+
+_DTYPES = {F32: "float32", BF16: "bfloat16", F64: "float64"}
+_CALC = {F32: "float32", BF16: "float32", F64: "float64"}
+
+
+def _ptr(x, want_dtype: str, shape, what: str):
+    """Device or host pointer of a torch tensor / numpy array after checks."""
+    if isinstance(x, np.ndarray):
+        if str(x.dtype) != want_dtype and not (want_dtype == "bfloat16" and x.dtype == np.uint16):
+            raise TypeError("%s: dtype %s, expected %s" % (what, x.dtype, want_dtype))
+        if not x.flags.c_contiguous:
+            raise ValueError("%s must be C-contiguous" % what)
+        if tuple(x.shape) != tuple(shape):
+            raise ValueError("%s: shape %s, expected %s" % (what, tuple(x.shape), tuple(shape)))
+        return ctypes.c_void_p(x.ctypes.data)
+    torch = _torch()
+    if x.dtype != getattr(torch, want_dtype):
+        raise TypeError("%s: dtype %s, expected %s" % (what, x.dtype, want_dtype))
+    if not x.is_contiguous():
+        raise ValueError("%s must be contiguous" % what)
+    if tuple(x.shape) != tuple(shape):
+        raise ValueError("%s: shape %s, expected %s" % (what, tuple(x.shape), tuple(shape)))
+    return ctypes.c_void_p(x.data_ptr())
+
+
+class Plan:
+    """A reconstruction geometry: grid (nz, ny, nx), detector bins ns, the
+    acquisition (theta_k, t_k), the temporal basis (kind, m) and the frame
+    count nt used by the time derivative.  Owns the device tables."""
+
+    def __init__(self, nx: int, ny: int, nz: int, ns: int, theta, t, basis: int = FOURIER, m: int = 4,
+                 nt: int = 4, prec: int = F32, stream=None):
+        lib = load()
+        self.nx, self.ny, self.nz, self.ns = int(nx), int(ny), int(nz), int(ns)
+        th = np.ascontiguousarray(theta, dtype=np.float64)
+        tt = np.ascontiguousarray(t, dtype=np.float64)
+        if th.shape != tt.shape or th.ndim != 1:
+            raise ValueError("theta and t must be 1-D of equal length")
+        self.K = th.size
+        self.basis, self.m, self.nt, self.prec = int(basis), int(m), int(nt), int(prec)
+        self._h = ctypes.c_void_p()
+        pd = ctypes.POINTER(ctypes.c_double)
+        _check(lib.dr_plan_create(ctypes.byref(self._h), self.nx, self.ny, self.nz, self.ns, self.K,
+                                  th.ctypes.data_as(pd), tt.ctypes.data_as(pd), self.basis, self.m,
+                                  self.nt, self.prec, ctypes.c_void_p(self._stream_handle(stream))))
+
+    @staticmethod
+    def _stream_handle(stream) -> int:
+        if stream is not None:
+            return int(getattr(stream, "cuda_stream", stream))
+        try:
+            torch = _torch()
+            if torch.cuda.is_available():
+                return int(torch.cuda.current_stream().cuda_stream)
+        except Exception:
+            pass
+        return 0
+
+    def use_current_stream(self):
+        _check(load().dr_plan_set_stream(self._h, ctypes.c_void_p(self._stream_handle(None))))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def u_shape(self):
+        return (self.nz, self.ny, self.nx, self.m)
+
+    def g_shape(self):
+        return (self.nz, self.K, self.ns)
+
+    def field_shape(self):
+        return (self.nz, self.ny, self.nx, self.nt, 4)
+
+    @property
+    def storage_dtype(self) -> str:
+        return _DTYPES[self.prec]
+
+    @property
+    def field_dtype(self) -> str:
+        return _CALC[self.prec]
+
+    def device_bytes(self) -> int:
+        return load().dr_plan_device_bytes(self._h)
+
+    def workspace_bytes(self, algo: int = ADMM_CG) -> int:
+        return load().dr_plan_workspace_bytes(self._h, int(algo))
+
+    def sync(self):
+        _check(load().dr_plan_sync(self._h))
+
+    def close(self):
+        if self._h:
+            load().dr_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def dyn_radon_fwd(plan: Plan, u, g):
+    """g = R u (Eq. radapr).  u [nz][ny][nx][m], g [nz][K][ns], device tensors."""
+    plan.use_current_stream()
+    _check(load().dyn_radon_fwd(plan.handle, _ptr(u, plan.storage_dtype, plan.u_shape(), "u"),
+                                _ptr(g, plan.storage_dtype, plan.g_shape(), "g")))
+    return g
+
+
+def dyn_radon_adj(plan: Plan, g, u, beta: float = 0.0):
+    """u = beta u + R* g (Eq. radadjapr)."""
+    plan.use_current_stream()
+    _check(load().dyn_radon_adj(plan.handle, _ptr(g, plan.storage_dtype, plan.g_shape(), "g"),
+                                _ptr(u, plan.storage_dtype, plan.u_shape(), "u"), float(beta)))
+    return u
+
+
+def tv4d_grad(plan: Plan, u, p, lambda2: float):
+    """p = D u = nabla_{lambda2} of the synthesised frames (Eq. TV1)."""
+    plan.use_current_stream()
+    _check(load().tv4d_grad(plan.handle, _ptr(u, plan.storage_dtype, plan.u_shape(), "u"),
+                            _ptr(p, plan.field_dtype, plan.field_shape(), "p"), float(lambda2)))
+    return p
+
+
+def tv4d_grad_adj(plan: Plan, p, u, lambda2: float, beta: float = 0.0):
+    """u = beta u + D^T p."""
+    plan.use_current_stream()
+    _check(load().tv4d_grad_adj(plan.handle, _ptr(p, plan.field_dtype, plan.field_shape(), "p"),
+                                _ptr(u, plan.storage_dtype, plan.u_shape(), "u"), float(lambda2),
+                                float(beta)))
+    return u
+
+
+def tv4d_prox(plan: Plan, u, mu, w, rho: float, lambda1: float, lambda2: float,
+              want_residual: bool = False) -> Optional[float]:
+    """ADMM shrink + dual update on psi = D u (in place on mu, w)."""
+    plan.use_current_stream()
+    res = ctypes.c_double(0.0)
+    _check(load().tv4d_prox(plan.handle, _ptr(u, plan.storage_dtype, plan.u_shape(), "u"),
+                            _ptr(mu, plan.field_dtype, plan.field_shape(), "mu"),
+                            _ptr(w, plan.field_dtype, plan.field_shape(), "w"), float(rho),
+                            float(lambda1), float(lambda2),
+                            ctypes.byref(res) if want_residual else None))
+    return res.value if want_residual else None
+
+
+def solve_params(algo: int = ADMM_CG, iters: int = 20, n_cg: int = 4, lambda1: float = 1e-3,
+                 lambda2: float = 1.0, rho: float = 0.0, cp_theta: float = 1.0,
+                 power_iters: int = 100) -> SolveParams:
+    p = SolveParams()
+    load().dr_solve_params_default(ctypes.byref(p))
+    p.algo, p.iters, p.n_cg = int(algo), int(iters), int(n_cg)
+    p.lambda1, p.lambda2, p.rho, p.cp_theta = float(lambda1), float(lambda2), float(rho), float(cp_theta)
+    p.power_iters = int(power_iters)
+    return p
+
+
+def admm_solve(plan: Plan, g, u, params: SolveParams, want_objective: bool = True,
+               want_primal: bool = False):
+    """Solve Eq. (lr12) in place on u; g and u may live on the host or the
+    device.  Returns dict(objective=..., primal_res=..., op_norm=...)."""
+    plan.use_current_stream()
+    n = max(int(params.iters), 1)
+    obj = np.zeros(n, dtype=np.float64)
+    pres = np.zeros(n, dtype=np.float64)
+    opn = ctypes.c_double(0.0)
+    pd = ctypes.POINTER(ctypes.c_double)
+    params.objective_out = obj.ctypes.data_as(pd) if want_objective else None
+    params.primal_res_out = pres.ctypes.data_as(pd) if want_primal else None
+    params.op_norm_out = ctypes.pointer(opn)
+    _check(load().admm_solve(plan.handle, _ptr(g, plan.storage_dtype, plan.g_shape(), "g"),
+                             _ptr(u, plan.storage_dtype, plan.u_shape(), "u"), ctypes.byref(params)))
+    it = int(params.iters)
+    return {"objective": obj[:it] if want_objective else None,
+            "primal_res": pres[:it] if want_primal else None,
+            "op_norm": opn.value}
+
+
+def version() -> str:
+    return load().dr_version().decode()

@@ -1,0 +1,180 @@
+"""GPU parity of the dynamic projector pair against the FP64 oracle.
+
+Forward g = R u (Eq. radapr) and adjoint u = R* g (Eq. radadjapr) through
+the C ABI, element by element against the oracle on the same seeded inputs:
+FP64 plans to 1e-12, FP32 plans to 1e-5 relative L2, BF16 storage against the
+oracle fed the same bf16-rounded inputs.  Sizes span several tiles with
+ragged tails, odd detector widths (plain-load staging instead of TMA), wide
+and narrow detectors, every template size of m, both bases, and the full
+16-slice 256^2 x 1800-projection workload the benchmark times.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1809_09725_gb300 import dynrecon as dr
+from paper_1809_09725_gb300 import synth
+
+from _common import dev_tensor, host_values, rel, to_bf16_f64
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+# name: nx, ny, nz, ns, K, half-turns, mod_pi, basis, m, nt
+CASES = {
+    "disks64": (64, 64, 1, 64, 256, 4, True, dr.FOURIER, 4, 4),
+    "ragged": (37, 29, 3, 45, 100, 3.3, False, dr.LEGENDRE, 5, 3),
+    "wide_det": (40, 40, 2, 70, 33, 2.0, False, dr.FOURIER, 3, 2),
+    "narrow_det": (48, 52, 2, 24, 65, 5.0, False, dr.FOURIER, 8, 5),
+    "single_proj": (20, 20, 1, 20, 1, 1.0, False, dr.FOURIER, 2, 1),
+    "m1_static": (33, 33, 2, 33, 47, 2.0, False, dr.FOURIER, 1, 2),
+    "m12": (24, 24, 2, 28, 40, 3.0, False, dr.LEGENDRE, 12, 4),
+    "m16": (24, 32, 1, 32, 70, 4.0, False, dr.FOURIER, 16, 8),
+    "m24": (20, 20, 2, 24, 36, 3.0, False, dr.FOURIER, 24, 6),
+    "m32": (16, 24, 1, 20, 50, 6.0, False, dr.LEGENDRE, 32, 6),
+}
+
+
+def _setup(case, seed=0):
+    nx, ny, nz, ns, K, ht, mp, basis, m, nt = CASES[case]
+    theta, t = synth.scan(K, ht, mp)
+    rng = synth.rng_for(1000 + seed + sum(map(ord, case)))
+    u = rng.standard_normal((nz, ny, nx, m))
+    g = rng.standard_normal((nz, K, ns))
+    P = oracle.Problem(nx, ny, nz, ns, theta, t, basis, m, nt)
+    return (nx, ny, nz, ns, theta, t, basis, m, nt), u, g, P
+
+
+def _plan(args, prec):
+    nx, ny, nz, ns, theta, t, basis, m, nt = args
+    return dr.Plan(nx, ny, nz, ns, theta, t, basis, m, nt, prec)
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+@pytest.mark.parametrize("prec,tol", [(dr.F64, 1e-12), (dr.F32, 1e-5)])
+def test_forward_matches_oracle(case, prec, tol):
+    args, u, _, P = _setup(case)
+    if prec == dr.F32:
+        u = u.astype(np.float32).astype(np.float64)
+    plan = _plan(args, prec)
+    g = torch.zeros(plan.g_shape(), dtype=getattr(torch, plan.storage_dtype), device="cuda")
+    dr.dyn_radon_fwd(plan, dev_tensor(u, prec), g)
+    plan.sync()
+    assert rel(host_values(g), P.fwd(u)) <= tol
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+@pytest.mark.parametrize("prec,tol", [(dr.F64, 1e-12), (dr.F32, 1e-5)])
+def test_adjoint_matches_oracle(case, prec, tol):
+    args, _, g, P = _setup(case)
+    if prec == dr.F32:
+        g = g.astype(np.float32).astype(np.float64)
+    plan = _plan(args, prec)
+    u = torch.zeros(plan.u_shape(), dtype=getattr(torch, plan.storage_dtype), device="cuda")
+    dr.dyn_radon_adj(plan, dev_tensor(g, prec), u)
+    plan.sync()
+    assert rel(host_values(u), P.adj(g)) <= tol
+
+
+@pytest.mark.parametrize("case", ["disks64", "ragged", "m16"])
+def test_adjoint_beta_accumulates(case):
+    args, u0, g, P = _setup(case, seed=3)
+    plan = _plan(args, dr.F64)
+    u = dev_tensor(u0, dr.F64)
+    dr.dyn_radon_adj(plan, dev_tensor(g, dr.F64), u, beta=-0.75)
+    plan.sync()
+    assert rel(host_values(u), -0.75 * u0 + P.adj(g)) <= 1e-12
+
+
+@pytest.mark.parametrize("case", ["disks64", "ragged", "m32"])
+def test_gpu_pair_is_adjoint(case):
+    """<R u, g> = <u, R* g> for the GPU pair itself (FP64 plan)."""
+    args, u, g, _ = _setup(case, seed=5)
+    plan = _plan(args, dr.F64)
+    gu = torch.zeros(plan.g_shape(), dtype=torch.float64, device="cuda")
+    ua = torch.zeros(plan.u_shape(), dtype=torch.float64, device="cuda")
+    dr.dyn_radon_fwd(plan, dev_tensor(u, dr.F64), gu)
+    dr.dyn_radon_adj(plan, dev_tensor(g, dr.F64), ua)
+    plan.sync()
+    lhs = float(np.vdot(host_values(gu), g))
+    rhs = float(np.vdot(u, host_values(ua)))
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+@pytest.mark.parametrize("case", ["disks64", "ragged", "narrow_det", "m16"])
+def test_bf16_storage(case):
+    """BF16 storage, FP32 accumulation: against the oracle fed the same
+    bf16-rounded inputs and rounded to bf16 the same way (1e-3), and the
+    end-to-end error including the output rounding (bounded by 2^-8)."""
+    args, u, g, P = _setup(case, seed=7)
+    ub, gb = to_bf16_f64(u), to_bf16_f64(g)
+    plan = _plan(args, dr.BF16)
+    go = torch.zeros(plan.g_shape(), dtype=torch.bfloat16, device="cuda")
+    uo = torch.zeros(plan.u_shape(), dtype=torch.bfloat16, device="cuda")
+    dr.dyn_radon_fwd(plan, dev_tensor(ub, dr.BF16), go)
+    dr.dyn_radon_adj(plan, dev_tensor(gb, dr.BF16), uo)
+    plan.sync()
+    ref_g, ref_u = P.fwd(ub), P.adj(gb)
+    assert rel(host_values(go), to_bf16_f64(ref_g)) <= 1e-3
+    assert rel(host_values(uo), to_bf16_f64(ref_u)) <= 1e-3
+    assert rel(host_values(go), ref_g) <= 2.0 ** -8
+    assert rel(host_values(uo), ref_u) <= 2.0 ** -8
+
+
+def test_half_turn_symmetry_on_gpu():
+    """Sec. 4: R f(theta + pi, s) = R f(theta, -s) for a static object."""
+    N, K = 48, 24
+    th0 = np.linspace(0.05, math.pi - 0.05, K // 2)
+    theta = np.concatenate([th0, th0 + math.pi])
+    t = np.zeros(K)
+    plan = dr.Plan(N, N, 1, N, theta, t, dr.FOURIER, 1, 1, dr.F64)
+    u = synth.rng_for(9).standard_normal((1, N, N, 1))
+    g = torch.zeros(plan.g_shape(), dtype=torch.float64, device="cuda")
+    dr.dyn_radon_fwd(plan, dev_tensor(u, dr.F64), g)
+    plan.sync()
+    gh = host_values(g)[0]
+    np.testing.assert_allclose(gh[K // 2:], gh[:K // 2, ::-1], atol=1e-11)
+
+
+def test_full_workload_256x16x1800_fp32():
+    """The benchmarked workload (16 slices of 256^2, 1800 projections over 10
+    half-turns, m = 8 Fourier) at full size, in the launch configuration the
+    benchmark uses, against the oracle on every output element."""
+    w = synth.WORKLOADS["ellipsoids256"]
+    theta, t = w.geometry()
+    rng = synth.rng_for(4242)
+    u = rng.standard_normal((w.nz, w.N, w.N, w.m)).astype(np.float32).astype(np.float64)
+    g = rng.standard_normal((w.nz, w.K, w.ns)).astype(np.float32).astype(np.float64)
+    plan = dr.Plan(w.N, w.N, w.nz, w.ns, theta, t, w.basis, w.m, w.nt, dr.F32)
+    P = oracle.Problem(w.N, w.N, w.nz, w.ns, theta, t, w.basis, w.m, w.nt)
+    go = torch.zeros(plan.g_shape(), dtype=torch.float32, device="cuda")
+    uo = torch.zeros(plan.u_shape(), dtype=torch.float32, device="cuda")
+    dr.dyn_radon_fwd(plan, dev_tensor(u, dr.F32), go)
+    dr.dyn_radon_adj(plan, dev_tensor(g, dr.F32), uo)
+    plan.sync()
+    assert rel(host_values(go), P.fwd(u)) <= 1e-5
+    assert rel(host_values(uo), P.adj(g)) <= 1e-5
+
+
+def test_invalid_arguments_raise():
+    theta, t = synth.scan(8, 1.0)
+    with pytest.raises(dr.DynreconError):
+        dr.Plan(0, 8, 1, 8, theta, t, dr.FOURIER, 2, 2, dr.F32)
+    with pytest.raises(dr.DynreconError):
+        dr.Plan(8, 8, 1, 8, theta, t, dr.FOURIER, 33, 2, dr.F32)
+    with pytest.raises(dr.DynreconError):
+        dr.Plan(8, 8, 1, 4096, theta, t, dr.FOURIER, 2, 2, dr.F32)
+    bad = theta.copy()
+    bad[3] = np.nan
+    with pytest.raises(dr.DynreconError):
+        dr.Plan(8, 8, 1, 8, bad, t, dr.FOURIER, 2, 2, dr.F32)
+    plan = dr.Plan(8, 8, 1, 8, theta, t, dr.FOURIER, 2, 2, dr.F32)
+    with pytest.raises(TypeError):
+        dr.dyn_radon_fwd(plan, torch.zeros(plan.u_shape(), dtype=torch.float64, device="cuda"),
+                         torch.zeros(plan.g_shape(), dtype=torch.float32, device="cuda"))
+    with pytest.raises(ValueError):
+        dr.dyn_radon_fwd(plan, torch.zeros((1, 8, 8, 3), dtype=torch.float32, device="cuda"),
+                         torch.zeros(plan.g_shape(), dtype=torch.float32, device="cuda"))

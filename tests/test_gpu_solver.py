@@ -1,0 +1,163 @@
+"""GPU parity of the solvers for Eq. (lr12) against the oracle, iteration by
+iteration from the same initial guess (the model can have several
+minimisers, so parity is defined per iteration of the same algorithm).
+
+ADMM-CG (the workload's solver) and Chambolle-Pock (Sec. 3, Fig. 2) on the
+single-slice disks workload (64^2, 256 projections over 4 half-turns, m = 4
+Fourier, 20 x 4 CG), FP64 and FP32 plans; a 2-slice cut of the 256^2 x 1800
+ellipsoid workload; host-buffer inputs; BF16 storage; degenerate inputs.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1809_09725_gb300 import dynrecon as dr
+from paper_1809_09725_gb300 import synth
+
+from _common import dev_tensor, host_values, rel, to_bf16_f64
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _disks():
+    w = synth.WORKLOADS["disks64"]
+    theta, t, g = synth.make_data(w)
+    P = oracle.Problem(w.N, w.N, w.nz, w.ns, theta, t, w.basis, w.m, w.nt)
+    return w, theta, t, g, P
+
+
+@pytest.fixture(scope="module")
+def disks():
+    return _disks()
+
+
+@pytest.fixture(scope="module")
+def disks_oracle_admm(disks):
+    w, theta, t, g, P = disks
+    u0 = np.zeros((w.nz, w.N, w.N, w.m))
+    g32 = g.astype(np.float32).astype(np.float64)
+    out = {}
+    out["f64"] = P.admm_cg(g, u0, w.iters, w.n_cg, w.lambda1, w.lambda2, w.rho, want_primal=True)
+    out["f32"] = P.admm_cg(g32, u0, w.iters, w.n_cg, w.lambda1, w.lambda2, w.rho, want_primal=True)
+    return out
+
+
+def _run(w, theta, t, g, prec, algo, iters=None, host=False, **kw):
+    plan = dr.Plan(w.N, w.N, w.nz, w.ns, theta, t, w.basis, w.m, w.nt, prec)
+    prm = dr.solve_params(algo, iters=w.iters if iters is None else iters, n_cg=w.n_cg, lambda1=w.lambda1,
+                          lambda2=w.lambda2, rho=w.rho, **kw)
+    if host:
+        dt = {dr.F32: np.float32, dr.F64: np.float64}[prec]
+        gd = np.ascontiguousarray(g, dtype=dt)
+        ud = np.zeros(plan.u_shape(), dtype=dt)
+    else:
+        gd = dev_tensor(g, prec)
+        ud = torch.zeros(plan.u_shape(), dtype=getattr(torch, plan.storage_dtype), device="cuda")
+    res = dr.admm_solve(plan, gd, ud, prm, want_primal=True)
+    u = ud.astype(np.float64) if host else host_values(ud)
+    return u, res
+
+
+def test_admm_f64_matches_oracle_every_iteration(disks, disks_oracle_admm):
+    w, theta, t, g, P = disks
+    uo, oo, po = disks_oracle_admm["f64"]
+    u, res = _run(w, theta, t, g, dr.F64, dr.ADMM_CG)
+    assert rel(res["objective"], oo) <= 1e-9
+    assert rel(res["primal_res"], po) <= 1e-8
+    assert rel(u, uo) <= 1e-8
+
+
+def test_admm_f32_matches_oracle(disks, disks_oracle_admm):
+    w, theta, t, g, P = disks
+    uo, oo, po = disks_oracle_admm["f32"]
+    g32 = g.astype(np.float32).astype(np.float64)
+    u, res = _run(w, theta, t, g32, dr.F32, dr.ADMM_CG)
+    assert rel(u, uo) <= 1e-4
+    assert np.max(np.abs(res["objective"] - oo) / np.abs(oo)) <= 1e-5
+
+
+def test_admm_host_buffers_equal_device_buffers(disks):
+    w, theta, t, g, P = disks
+    g32 = g.astype(np.float32).astype(np.float64)
+    ud, rd = _run(w, theta, t, g32, dr.F32, dr.ADMM_CG, iters=5)
+    uh, rh = _run(w, theta, t, g32, dr.F32, dr.ADMM_CG, iters=5, host=True)
+    np.testing.assert_array_equal(ud, uh)
+    np.testing.assert_array_equal(rd["objective"], rh["objective"])
+
+
+def test_admm_is_deterministic(disks):
+    w, theta, t, g, P = disks
+    a, ra = _run(w, theta, t, g, dr.F32, dr.ADMM_CG, iters=6)
+    b, rb = _run(w, theta, t, g, dr.F32, dr.ADMM_CG, iters=6)
+    np.testing.assert_array_equal(a, b)
+    np.testing.assert_array_equal(ra["objective"], rb["objective"])
+
+
+@pytest.mark.parametrize("prec,tol_u,tol_o", [(dr.F64, 1e-9, 1e-10), (dr.F32, 1e-4, 1e-5)])
+def test_chambolle_pock_matches_oracle(disks, prec, tol_u, tol_o):
+    w, theta, t, g, P = disks
+    if prec == dr.F32:
+        g = g.astype(np.float32).astype(np.float64)
+    u0 = np.zeros((w.nz, w.N, w.N, w.m))
+    L = P.power_norm(w.lambda2)
+    uo, oo = P.chambolle_pock(g, u0, w.iters, w.lambda1, w.lambda2, 1.0, L)
+    u, res = _run(w, theta, t, g, prec, dr.CHAMBOLLE_POCK)
+    assert abs(res["op_norm"] - L) <= (1e-10 if prec == dr.F64 else 1e-5) * L
+    assert rel(u, uo) <= tol_u
+    assert rel(res["objective"], oo) <= tol_o
+
+
+def test_ellipsoid_workload_two_slices_fp32():
+    """A 2-slice cut of the 256^2 x 1800-projection ellipsoid workload, 3 ADMM-CG iterations."""
+    w = synth.WORKLOADS["ellipsoids256"]
+    theta, t, g = synth.make_data(w, nz=2)
+    g = g.astype(np.float32).astype(np.float64)
+    P = oracle.Problem(w.N, w.N, 2, w.ns, theta, t, w.basis, w.m, w.nt)
+    uo, oo, _ = P.admm_cg(g, np.zeros((2, w.N, w.N, w.m)), 3, w.n_cg, w.lambda1, w.lambda2, w.rho)
+    plan = dr.Plan(w.N, w.N, 2, w.ns, theta, t, w.basis, w.m, w.nt, dr.F32)
+    ud = torch.zeros(plan.u_shape(), dtype=torch.float32, device="cuda")
+    prm = dr.solve_params(dr.ADMM_CG, iters=3, n_cg=w.n_cg, lambda1=w.lambda1, lambda2=w.lambda2, rho=w.rho)
+    res = dr.admm_solve(plan, dev_tensor(g, dr.F32), ud, prm)
+    assert rel(host_values(ud), uo) <= 1e-4
+    assert np.max(np.abs(res["objective"] - oo) / np.abs(oo)) <= 1e-5
+
+
+def test_bf16_storage_solve(disks):
+    """BF16 data and coefficients, FP32 state: error against the oracle run on
+    the bf16-rounded data (output rounding to bf16 included)."""
+    w, theta, t, g, P = disks
+    gb = to_bf16_f64(g)
+    uo, oo, _ = P.admm_cg(gb, np.zeros((w.nz, w.N, w.N, w.m)), 5, w.n_cg, w.lambda1, w.lambda2, w.rho)
+    plan = dr.Plan(w.N, w.N, w.nz, w.ns, theta, t, w.basis, w.m, w.nt, dr.BF16)
+    ud = torch.zeros(plan.u_shape(), dtype=torch.bfloat16, device="cuda")
+    prm = dr.solve_params(dr.ADMM_CG, iters=5, n_cg=w.n_cg, lambda1=w.lambda1, lambda2=w.lambda2, rho=w.rho)
+    res = dr.admm_solve(plan, dev_tensor(gb, dr.BF16), ud, prm)
+    assert rel(host_values(ud), uo) <= 2.0 ** -8
+    assert np.max(np.abs(res["objective"] - oo) / np.abs(oo)) <= 1e-4
+
+
+def test_zero_data_keeps_zero_solution(disks):
+    w, theta, t, g, P = disks
+    u, res = _run(w, theta, t, np.zeros_like(g), dr.F32, dr.ADMM_CG, iters=3)
+    assert np.all(u == 0.0)
+    assert np.all(res["objective"] == 0.0)
+
+
+def test_zero_iterations_leave_u_unchanged(disks):
+    w, theta, t, g, P = disks
+    plan = dr.Plan(w.N, w.N, w.nz, w.ns, theta, t, w.basis, w.m, w.nt, dr.F32)
+    u0 = synth.rng_for(3).standard_normal(plan.u_shape())
+    ud = dev_tensor(u0, dr.F32)
+    dr.admm_solve(plan, dev_tensor(g, dr.F32), ud, dr.solve_params(iters=0))
+    np.testing.assert_array_equal(host_values(ud), u0.astype(np.float32))
+
+
+def test_solver_rejects_bad_parameters(disks):
+    w, theta, t, g, P = disks
+    plan = dr.Plan(w.N, w.N, w.nz, w.ns, theta, t, w.basis, w.m, w.nt, dr.F32)
+    ud = torch.zeros(plan.u_shape(), dtype=torch.float32, device="cuda")
+    for bad in (dict(iters=-1), dict(n_cg=0), dict(lambda1=-1.0), dict(cp_theta=2.0, algo=dr.CHAMBOLLE_POCK)):
+        with pytest.raises(dr.DynreconError):
+            dr.admm_solve(plan, dev_tensor(g, dr.F32), ud, dr.solve_params(**bad))

@@ -1,0 +1,117 @@
+"""GPU parity of the 4D TV stencils and the ADMM prox against the oracle.
+
+D = nabla_{lambda2} o PhiF (Eq. TV1 on the synthesised frames), its adjoint
+(Sec. 3, K_2^* = -div), and the shrink/dual step of the ADMM split, through
+the C ABI on seeded inputs with ragged sizes, every TV template size of m,
+and nz = 1 (no z neighbours).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1809_09725_gb300 import dynrecon as dr
+from paper_1809_09725_gb300 import synth
+
+from _common import dev_tensor, host_values, rel, to_bf16_f64
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+# nx, ny, nz, basis, m, nt
+CASES = {
+    "c1like": (64, 64, 1, dr.FOURIER, 4, 4),
+    "ragged": (37, 29, 5, dr.LEGENDRE, 5, 3),
+    "m8": (33, 40, 4, dr.FOURIER, 8, 10),
+    "m1": (20, 17, 3, dr.FOURIER, 1, 2),
+    "m13": (16, 18, 3, dr.LEGENDRE, 13, 7),
+    "m32": (12, 10, 3, dr.FOURIER, 32, 5),
+    "nt1": (21, 22, 2, dr.FOURIER, 3, 1),
+}
+
+
+def _setup(case, seed=0):
+    nx, ny, nz, basis, m, nt = CASES[case]
+    K = 8
+    theta, t = synth.scan(K, 2.0)
+    plan_args = (nx, ny, nz, 9, theta, t, basis, m, nt)
+    P = oracle.Problem(nx, ny, nz, 9, theta, t, basis, m, nt)
+    rng = synth.rng_for(500 + seed + sum(map(ord, case)))
+    u = rng.standard_normal((nz, ny, nx, m))
+    p = rng.standard_normal((nz, ny, nx, nt, 4))
+    mu = rng.standard_normal((nz, ny, nx, nt, 4))
+    return plan_args, P, u, p, mu
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+@pytest.mark.parametrize("prec,tol", [(dr.F64, 1e-12), (dr.F32, 1e-5)])
+def test_grad_and_adjoint(case, prec, tol):
+    args, P, u, p, _ = _setup(case)
+    lam2 = 1.7
+    if prec == dr.F32:
+        u = u.astype(np.float32).astype(np.float64)
+        p = p.astype(np.float32).astype(np.float64)
+    plan = dr.Plan(*args, prec=prec)
+    fdt = getattr(torch, plan.field_dtype)
+    pg = torch.zeros(plan.field_shape(), dtype=fdt, device="cuda")
+    dr.tv4d_grad(plan, dev_tensor(u, prec), pg, lam2)
+    ua = torch.zeros(plan.u_shape(), dtype=getattr(torch, plan.storage_dtype), device="cuda")
+    dr.tv4d_grad_adj(plan, dev_tensor(p, prec), ua, lam2)
+    plan.sync()
+    assert rel(host_values(pg), P.D(u, lam2)) <= tol
+    assert rel(host_values(ua), P.DT(p, lam2)) <= tol
+
+
+@pytest.mark.parametrize("case", ["ragged", "m8"])
+def test_grad_adj_beta(case):
+    args, P, u, p, _ = _setup(case, seed=1)
+    plan = dr.Plan(*args, prec=dr.F64)
+    ut = dev_tensor(u, dr.F64)
+    dr.tv4d_grad_adj(plan, dev_tensor(p, dr.F64), ut, 0.6, beta=2.5)
+    plan.sync()
+    assert rel(host_values(ut), 2.5 * u + P.DT(p, 0.6)) <= 1e-12
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+@pytest.mark.parametrize("prec,tol", [(dr.F64, 1e-12), (dr.F32, 1e-5)])
+def test_prox_matches_oracle(case, prec, tol):
+    args, P, u, _, mu0 = _setup(case, seed=2)
+    rho, lam1, lam2 = 0.7, 0.4, 1.3
+    if prec == dr.F32:
+        u = u.astype(np.float32).astype(np.float64)
+        mu0 = mu0.astype(np.float32).astype(np.float64)
+    plan = dr.Plan(*args, prec=prec)
+    mu = dev_tensor(mu0, prec if prec != dr.BF16 else dr.F32)
+    w = torch.zeros_like(mu)
+    res = dr.tv4d_prox(plan, dev_tensor(u, prec), mu, w, rho, lam1, lam2, want_residual=True)
+    mu_o, w_o = mu0.copy(), np.zeros_like(mu0)
+    tv_o, pr_o = oracle.tv4d_prox(u, mu_o, w_o, P.PhiF, rho, lam1, lam2)
+    assert rel(host_values(mu), mu_o) <= tol
+    assert rel(host_values(w), w_o) <= tol
+    assert abs(res - np.sqrt(pr_o)) <= 10 * tol * np.sqrt(pr_o)
+
+
+def test_prox_bf16_coefficients():
+    args, P, u, _, mu0 = _setup("m8", seed=4)
+    ub = to_bf16_f64(u)
+    mu0 = mu0.astype(np.float32).astype(np.float64)
+    plan = dr.Plan(*args, prec=dr.BF16)
+    mu = dev_tensor(mu0, dr.F32)
+    w = torch.zeros_like(mu)
+    dr.tv4d_prox(plan, dev_tensor(ub, dr.BF16), mu, w, 0.7, 0.4, 1.3)
+    plan.sync()
+    mu_o, w_o = mu0.copy(), np.zeros_like(mu0)
+    oracle.tv4d_prox(ub, mu_o, w_o, P.PhiF, 0.7, 0.4, 1.3)
+    assert rel(host_values(mu), mu_o) <= 1e-5
+    assert rel(host_values(w), w_o) <= 1e-5
+
+
+def test_prox_rejects_bad_parameters():
+    args, _, u, _, mu0 = _setup("m1")
+    plan = dr.Plan(*args, prec=dr.F32)
+    mu = dev_tensor(mu0, dr.F32)
+    w = torch.zeros_like(mu)
+    with pytest.raises(dr.DynreconError):
+        dr.tv4d_prox(plan, dev_tensor(u, dr.F32), mu, w, 0.0, 0.4, 1.3)
+    with pytest.raises(dr.DynreconError):
+        dr.tv4d_prox(plan, dev_tensor(u, dr.F32), mu, w, 1.0, -0.4, 1.3)
