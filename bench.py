@@ -123,13 +123,19 @@ def barrier_max(tdist, value: float, device):
     return float(t.item())
 
 
-def roofline_entry(kind, P, w, t_ms):
-    """ALU roofline of a projector launch: algorithmic FP32 flops = 2 (m + 2)
-    per voxel-projection pair (m FMAs of the basis combine + 2 of the
-    interpolation / footprint), K V pairs per launch."""
-    flops = 2.0 * (w.m + 2) * w.K * w.voxels()
-    achieved = flops / (t_ms * 1e-3) / 1e12
-    return flops, achieved
+def algorithmic_flops(w, variant, U):
+    """FP32 flops of one projector application (FMA = 2 flops).
+
+    direct (every projection at its own angle): per voxel-projection pair m
+    FMAs of the basis combine + 2 of the interpolation / footprint:
+        2 (m + 2) K V.
+    half-turn fold (Sec. 4): per voxel and distinct angle mod pi, 2 FMAs of
+    the interpolation for each of the m coefficients, plus m FMAs per
+    detector sample to distribute (fold) over the K projections:
+        2 (2 m U V + m K ns nz)."""
+    if variant == 1:
+        return 2.0 * (2 * w.m * U * w.voxels() + w.m * w.K * w.ns * w.nz)
+    return 2.0 * (w.m + 2) * w.K * w.voxels()
 
 
 def run_ours(a):
@@ -150,9 +156,13 @@ def run_ours(a):
     units_per_iter = 2 * (w.n_cg + 1) * w.K * w.voxels()  # projector applications x K V
 
     if a.profile_small:
-        # a few plain operator launches (fwd, adj) for profiler captures
-        for _ in range(2):
-            dr.dyn_radon_fwd(plan, u, g)
+        # one forward and one adjoint of each variant (direct, half-turn fold)
+        # on the benchmark workload, for profiler captures
+        uin = torch.randn(plan.u_shape(), dtype=torch.float32, device=dev)
+        gout = torch.empty_like(g)
+        for var in (dr.DIRECT, dr.FOLD):
+            plan.set_variant(var, var)
+            dr.dyn_radon_fwd(plan, uin, gout)
             dr.dyn_radon_adj(plan, g, u)
         torch.cuda.synchronize()
         print(json.dumps({"profile_small": True}))
@@ -183,7 +193,10 @@ def run_ours(a):
     value = total_units / (ms * 1e-3)
     obj = res["objective"]
 
-    # dominant kernels: time the projector pair alone on the same stream
+    # dominant kernels: time the projector pair alone on the same stream, in
+    # the variant the solver selected (autotuned inside admm_solve)
+    info = plan.info()
+    tune = plan.autotune()
     p_in = torch.randn(plan.u_shape(), dtype=torch.float32, device=dev)
     gbuf = torch.empty(plan.g_shape(), dtype=torch.float32, device=dev)
     ubuf = torch.empty(plan.u_shape(), dtype=torch.float32, device=dev)
@@ -191,7 +204,7 @@ def run_ours(a):
         dr.dyn_radon_fwd(plan, p_in, gbuf)
         dr.dyn_radon_adj(plan, gbuf, ubuf)
     reps = 10
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     torch.cuda.synchronize()
     ev[0].record(stream)
     for _ in range(reps):
@@ -203,11 +216,20 @@ def run_ours(a):
     torch.cuda.synchronize()
     fwd_ms = ev[0].elapsed_time(ev[1]) / reps
     adj_ms = ev[1].elapsed_time(ev[2]) / reps
-    kern = ("fwd_kernel", fwd_ms) if fwd_ms >= adj_ms else ("adj_kernel", adj_ms)
-    flops, achieved = roofline_entry(kern[0], plan, w, kern[1])
+    U = info["unique_angles"]
+    if fwd_ms >= adj_ms:
+        variant = info["fwd_variant"]
+        kname = "fold_fwd_kernel" if variant == 1 else "fwd_kernel"
+        launch_ms = fwd_ms
+    else:
+        variant = info["adj_variant"]
+        kname = "fold_adj_kernel+fold_data_kernel" if variant == 1 else "adj_kernel"
+        launch_ms = adj_ms
+    flops = algorithmic_flops(w, variant, U)
+    achieved = flops / (launch_ms * 1e-3) / 1e12
     clocks = clk.summary()
     peak = fp32_peak_tflops()
-    traffic = load_traffic(kern[0])
+    traffic = load_traffic(kname)
 
     # end to end through the public call with host buffers (one full job per call)
     e2e = None
@@ -255,10 +277,12 @@ def run_ours(a):
             "clocks": clocks,
             "e2e": e2e,
             "gpu_launches": launches_per_iter * a.steps + 2,
-            "roofline": {"bound": "alu", "kernel": kern[0], "achieved": achieved, "peak": peak,
+            "roofline": {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
-                         "launch_ms": kern[1], "fwd_ms": fwd_ms, "adj_ms": adj_ms,
+                         "launch_ms": launch_ms, "fwd_ms": fwd_ms, "adj_ms": adj_ms,
                          "algorithmic_flops_per_launch": flops,
+                         "variants": {"unique_angles": U, "fwd": info["fwd_variant"], "adj": info["adj_variant"],
+                                      "autotune_ms_fwd_direct_fold_adj_direct_fold": tune},
                          "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz max SM clock"},
             "cpu_baseline": cpu,
         }

@@ -103,6 +103,41 @@ size_t dr_plan_device_bytes(const dr_plan *plan);
 size_t dr_plan_workspace_bytes(const dr_plan *plan, dr_algo algo);
 
 /*
+ * Projector variants.  0 = direct: every projection uses its own angle
+ * (Eqs. radapr / radadjapr as written).  1 = half-turn fold (Sec. 4): with
+ * theta_k = n_k pi + theta0_k, R f(theta_k, s) = R f(theta0_k, (-1)^n_k s), so
+ * the static transform of each coefficient volume is computed once per
+ * distinct theta0 (angles equal within 1e-11 rad) and distributed with the
+ * weights phi_j(t_k); the adjoint first folds the data per theta0
+ *     gt_j(theta0, s) = sum_{k: theta0_k = theta0} phi_j(t_k) g_k((-1)^n_k s)
+ * and back-projects the m folded sinograms.  Same operator up to rounding;
+ * the fold is offered for F32 and BF16 plans.  -1 = automatic (a cost model
+ * until dr_plan_autotune or admm_solve has timed both).  Returns DR_EINVAL
+ * if the fold is requested but unavailable.
+ */
+dr_status dr_plan_set_variant(dr_plan *plan, int fwd_variant, int adj_variant);
+
+/*
+ * Time both variants of both projectors on this plan's geometry (allocates
+ * and frees scratch; synchronises) and keep the faster ones for automatic
+ * selection.  times_ms: HOST [4] nullable: forward direct, forward fold,
+ * adjoint direct, adjoint fold (-1 where a variant is unavailable).
+ */
+dr_status dr_plan_autotune(dr_plan *plan, double *times_ms);
+
+typedef struct {
+    int unique_angles;   /* distinct theta mod pi (0: the fold is unavailable) */
+    int max_group;       /* most projections sharing one theta mod pi */
+    int fwd_variant;     /* variant the forward uses now (0 direct, 1 fold) */
+    int adj_variant;     /* variant the adjoint uses now */
+    int tuned;           /* 1 once the variants have been timed */
+    size_t device_bytes; /* device memory held by the plan */
+} dr_plan_info_t;
+
+/* Describe the plan (host struct filled in). */
+dr_status dr_plan_info(const dr_plan *plan, dr_plan_info_t *info);
+
+/*
  * Wait for the plan's stream, then report any failure recorded by its
  * kernels (DR_ETIMEOUT if a bounded wait gave up) or by the CUDA runtime.
  * Clears the plan's device status word.

@@ -143,6 +143,22 @@ struct dr_plan {
     void *d_dPhiF = nullptr;  // [nt][MT] T, row l = PhiF[l+1] - PhiF[l] (0 for the last)
     void *d_G = nullptr;      // [MT][MT] T, PhiF^T PhiF
     void *d_Lt = nullptr;     // [MT][MT] T, PhiF^T Lt PhiF (Lt = 1D Neumann Laplacian in l)
+    // half-turn fold (Sec. 4): projections grouped by theta mod pi
+    int fold_U = 0;                   // unique angles (0: the fold is unavailable for this plan)
+    int fold_maxgrp = 0;              // largest group
+    dr::FwdProj *d_fold_fwd = nullptr;  // [U] Joseph constants of the unique angles
+    dr::AdjProj *d_fold_adj = nullptr;  // [U]
+    int *d_fold_start = nullptr;      // [U+1] member ranges
+    int *d_fold_member = nullptr;     // [K] 2*k + (1 if theta_k = theta0 + odd multiple of pi)
+    int *d_fold_blocks = nullptr;     // [n_fold_blocks][fold_P] unique angles grouped by stepping axis
+    int n_fold_blocks = 0, fold_P = 0, fold_R = 0, fold_nchunk = 1;
+    bool fold_fwd_ok = false;         // the forward strip fits in shared memory
+    void *d_gt = nullptr;             // folded data [nz][U][ns][MS] float (allocated on first use)
+    size_t gt_bytes = 0;
+    int var_fwd = -1, var_adj = -1;   // -1 automatic, 0 direct, 1 fold (explicit choice)
+    int sel_fwd = 0, sel_adj = 0;     // variant in use
+    bool tuned = false;
+    double tune_ms[4] = {0, 0, 0, 0}; // fwd direct, fwd fold, adj direct, adj fold
     double *d_partials = nullptr;
     unsigned *d_counters = nullptr;
     dr::DevScalars *d_scal = nullptr;
@@ -209,5 +225,16 @@ dr_status launch_dot_to(dr_plan *P, const void *a, const void *b, size_t n, bool
 // Host-side tensor-map encoder (driver entry point, resolved once).
 bool encode_tensor_map_2d(CUtensorMap *map, CUtensorMapDataType dt, void *base, uint64_t dim0,
                           uint64_t dim1, uint64_t stride1_bytes, uint32_t box0, uint32_t box1);
+// rank-dimensional tiled map: dims[rank], strides[rank-1] (bytes, dims 1..), box[rank]
+bool encode_tensor_map(CUtensorMap *map, CUtensorMapDataType dt, int rank, void *base, const uint64_t *dims,
+                       const uint64_t *strides, const uint32_t *box);
+
+// Direct and folded projector variants; selection per plan (projector.cu).
+dr_status launch_fwd_variant(dr_plan *P, int variant, bool calc, const void *u, void *out, const void *gm,
+                             int mode, double sigma, cudaStream_t st);
+dr_status launch_adj_variant(dr_plan *P, int variant, bool calc, const void *g, void *u, double alpha,
+                             double beta, bool u_calc, cudaStream_t st);
+dr_status ensure_fold_scratch(dr_plan *P);
+dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch);
 
 }  // namespace dr

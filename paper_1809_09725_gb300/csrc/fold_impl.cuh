@@ -1,0 +1,512 @@
+// fold_impl.cuh -- half-turn folded projector pair (Sec. 4).
+//
+// With theta = n pi + theta0, theta0 in [0, pi), the static transform obeys
+// R f(n pi + theta0, s) = R f(theta0, (-1)^n s) (exact for the Joseph
+// discretisation on the symmetric bin grid).  Projections that share theta0
+// (one per half-turn in a continuous scan) therefore need the static
+// transform of each coefficient volume only once:
+//
+//   forward  g[k](s) = sum_j phi_j(t_k) (R u_j)(theta0_k, (-1)^{n_k} s)
+//   adjoint  u_j = sum_{theta0} R*( gt_j(theta0) ),
+//            gt_j(theta0, s) = sum_{k: theta0_k = theta0} phi_j(t_k) g[k]((-1)^{n_k} s)
+//
+// The forward marches the Joseph rays of each unique angle through a strip
+// of the m-vector image staged in shared memory (all m coefficient sums per
+// ray in registers) and distributes every ray to all projections of its
+// angle in the epilogue.  The adjoint first folds the data per unique angle
+// (fold_data_kernel, HBM bound), then back-projects the m folded sinograms
+// with the voxel-driven exact transpose: per unique angle a TMA tile load of
+// the footprint window (Wb bins x MS coefficients), mbarrier pipeline.
+// Work per application drops from K (m + c) to U (2m + c') per voxel, U the
+// number of unique angles.
+#pragma once
+#include "dr_device.cuh"
+
+namespace dr {
+
+constexpr int kFoldThreads = 256;
+constexpr int kFoldAdjP = 8;       // unique angles per adjoint pipeline stage
+constexpr int kFoldAdjStages = 3;
+
+// Padded coefficient stride in shared memory and in the folded data:
+// multiples of 4 floats (16-byte vectors, TMA rows) whose pattern of
+// 16-byte slots repeats only every 8 pixels (no bank conflicts between
+// neighbouring pixels).
+__host__ __device__ constexpr int fold_ms(int M) { return M <= 4 ? 4 : ((M % 8 == 0) ? M + 4 : M); }
+__host__ __device__ constexpr int fold_rpt(int M) { return M <= 4 ? 8 : 32 / M; }
+
+template <typename T, int M>
+__device__ __forceinline__ void load_vec(const T *p, T (&v)[M]) {
+    if constexpr (sizeof(T) == 4 && (M % 4) == 0) {
+#pragma unroll
+        for (int j = 0; j < M / 4; ++j) {
+            const float4 a = reinterpret_cast<const float4 *>(p)[j];
+            v[4 * j] = a.x;
+            v[4 * j + 1] = a.y;
+            v[4 * j + 2] = a.z;
+            v[4 * j + 3] = a.w;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < M; ++j) v[j] = p[j];
+    }
+}
+
+// ===========================================================================
+// Forward
+// ===========================================================================
+template <typename S, typename T, int M>
+__global__ void __launch_bounds__(kFoldThreads)
+    fold_fwd_kernel(const S *__restrict__ u, S *__restrict__ out, const S *__restrict__ gm,
+                    const FwdProj *__restrict__ uproj, const int *__restrict__ start, const int *__restrict__ member,
+                    const T *__restrict__ phip, const int *__restrict__ blocks, int nx, int ny, int ns, int K,
+                    int m, int MP, int P, int R, int nchunk, int mode, T sigma) {
+    constexpr int MS = fold_ms(M);
+    constexpr int RPT = fold_rpt(M);
+    extern __shared__ __align__(16) unsigned char fold_smem[];
+    T *scale_s = reinterpret_cast<T *>(fold_smem);                       // [64]
+    long long *bfx_s = reinterpret_cast<long long *>(fold_smem + 256);   // [64]
+    T *strip = reinterpret_cast<T *>(fold_smem + 768);                   // [R][wpad][MS]
+
+    const int tid = threadIdx.x;
+    const int z = blockIdx.y;
+    const int blk_id = blockIdx.x / nchunk, chunk = blockIdx.x - blk_id * nchunk;
+    const int *blk = blocks + (size_t)blk_id * P;
+    const int branch = uproj[blk[0]].branch;
+    const int W = branch ? ny : nx;
+    const int H = branch ? nx : ny;
+    const int wpad = W + 2 * kFwdGuard;
+
+    for (int p = tid; p < P; p += kFoldThreads) {
+        const int a = blk[p];
+        const FwdProj f = uproj[a >= 0 ? a : blk[0]];
+        scale_s[p] = (T)f.scale;
+        bfx_s[p] = f.B_fx;
+    }
+    for (int i = tid; i < R * wpad * MS; i += kFoldThreads) strip[i] = T(0);
+
+    const int rays_per_cta = kFoldThreads * RPT;
+    const int b_base = chunk * rays_per_cta;
+    long long x0fx[RPT];
+    int lo[RPT], hi[RPT];
+    T acc[RPT][M];
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+        lo[q] = 1;
+        hi[q] = 0;
+        x0fx[q] = 0;
+#pragma unroll
+        for (int j = 0; j < M; ++j) acc[q][j] = T(0);
+        const int rid = b_base + tid + q * kFoldThreads;
+        const int p = (nchunk > 1) ? 0 : rid / ns;
+        const int b = (nchunk > 1) ? rid : rid - p * ns;
+        if (p < P && b < ns) {
+            const int a = blk[p];
+            if (a >= 0) {
+                const FwdProj f = uproj[a];
+                x0fx[q] = f.C_fx + (long long)b * f.A_fx;
+                const float xf = f.Cf + (float)b * f.Af;
+                const float Bf = f.Bf;
+                if (fabsf(Bf) < 1e-2f) {
+                    lo[q] = 0;
+                    hi[q] = H - 1;
+                } else {
+                    const float r1 = (-1.0f - xf) / Bf, r2 = ((float)W - xf) / Bf;
+                    float rmin = fminf(r1, r2), rmax = fmaxf(r1, r2);
+                    rmin = fmaxf(rmin, -4.0f);
+                    rmax = fminf(rmax, (float)H + 4.0f);
+                    lo[q] = max(0, (int)floorf(rmin) - 1);
+                    hi[q] = min(H - 1, (int)ceilf(rmax) + 1);
+                }
+            }
+        }
+    }
+    __syncthreads();
+
+    const size_t zoff = (size_t)z * ny * nx;
+    for (int r0 = 0; r0 < H; r0 += R) {
+        const int nl = min(R, H - r0);
+        // ---- stage lines [r0, r0+nl) of the m-vector image ----
+        const int npx = nl * W;
+        for (int qq = tid; qq < npx; qq += kFoldThreads) {
+            int rl, i;
+            size_t pix;
+            if (branch == 0) {
+                rl = qq / W;
+                i = qq - rl * W;
+                pix = zoff + (size_t)(r0 + rl) * nx + i;
+            } else {
+                i = qq / nl;
+                rl = qq - i * nl;
+                pix = zoff + (size_t)i * nx + (r0 + rl);
+            }
+            T v[M];
+            load_coeffs<T, S, M>(u + pix * m, m, v);
+            T *dst = strip + ((size_t)rl * wpad + kFwdGuard + i) * MS;
+            if constexpr (sizeof(T) == 4 && (M % 4) == 0) {
+#pragma unroll
+                for (int j = 0; j < M / 4; ++j)
+                    reinterpret_cast<float4 *>(dst)[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < M; ++j) dst[j] = v[j];
+            }
+        }
+        __syncthreads();
+        // ---- march the rays: all m coefficient sums per ray ----
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) {
+            const int rs = max(lo[q], r0), re = min(hi[q], r0 + nl - 1);
+            if (rs > re) continue;
+            const int rid = b_base + tid + q * kFoldThreads;
+            const int p = (nchunk > 1) ? 0 : rid / ns;
+            const long long bfx = bfx_s[p];
+            long long x = x0fx[q] + (long long)rs * bfx;
+            const T *row = strip + ((size_t)(rs - r0) * wpad + kFwdGuard) * MS;
+            for (int r = rs; r <= re; ++r) {
+                int i0 = (int)(x >> 32);
+                i0 = min(max(i0, -2), W);
+                const float w = __uint_as_float(0x3F800000u | ((unsigned)x >> 9)) - 1.0f;
+                const float w1m = 1.0f - w;
+                T t0[M], t1[M];
+                load_vec<T, M>(row + i0 * MS, t0);
+                load_vec<T, M>(row + (i0 + 1) * MS, t1);
+#pragma unroll
+                for (int j = 0; j < M; ++j) acc[q][j] = fmaf(w, t1[j], fmaf(w1m, t0[j], acc[q][j]));
+                x += bfx;
+                row += (size_t)wpad * MS;
+            }
+        }
+        __syncthreads();
+    }
+
+    // ---- epilogue: distribute each ray to every projection of its angle ----
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+        const int rid = b_base + tid + q * kFoldThreads;
+        const int p = (nchunk > 1) ? 0 : rid / ns;
+        const int b = (nchunk > 1) ? rid : rid - p * ns;
+        if (p >= P || b >= ns) continue;
+        const int a = blk[p];
+        if (a < 0) continue;
+        const T sc = scale_s[p];
+        const int e = start[a + 1];
+        for (int idx = start[a]; idx < e; ++idx) {
+            const int mem = member[idx];
+            const int k = mem >> 1;
+            const int bb = (mem & 1) ? (ns - 1 - b) : b;
+            const T *ph = phip + (size_t)k * MP;
+            T val = T(0);
+#pragma unroll
+            for (int j = 0; j < M; ++j) val = fmaf(__ldg(ph + j), acc[q][j], val);
+            val *= sc;
+            const size_t o = ((size_t)z * K + k) * ns + bb;
+            if (mode == 0) {
+                stc<T>(out + o, val);
+            } else if (mode == 1) {
+                stc<T>(out + o, val - ldc<T>(gm + o));
+            } else {
+                const T h = ldc<T>(out + o);
+                stc<T>(out + o, (h + sigma * val - sigma * ldc<T>(gm + o)) / (T(1) + sigma));
+            }
+        }
+    }
+}
+
+// ===========================================================================
+// Adjoint, step 1: fold the data per unique angle
+//   gt[z][a][b][j] = sum_{k in group(a)} phi_j(t_k) g[z][k][flip_k(b)]
+// ===========================================================================
+template <typename S, typename T, int M>
+__global__ void __launch_bounds__(kRedThreads)
+    fold_data_kernel(const S *__restrict__ g, T *__restrict__ gt, const int *__restrict__ start,
+                     const int *__restrict__ member, const T *__restrict__ phip, int nz, int U, int ns, int K, int MP) {
+    constexpr int MS = fold_ms(M);
+    const size_t n = (size_t)nz * U * ns;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int b = (int)(i % ns);
+        const size_t r = i / ns;
+        const int a = (int)(r % U);
+        const int z = (int)(r / U);
+        T acc[M];
+#pragma unroll
+        for (int j = 0; j < M; ++j) acc[j] = T(0);
+        const int e = start[a + 1];
+        for (int idx = start[a]; idx < e; ++idx) {
+            const int mem = __ldg(member + idx);
+            const int k = mem >> 1;
+            const int bb = (mem & 1) ? (ns - 1 - b) : b;
+            const T gv = ldc<T>(g + ((size_t)z * K + k) * ns + bb);
+            const T *ph = phip + (size_t)k * MP;
+#pragma unroll
+            for (int j = 0; j < M; ++j) acc[j] = fmaf(__ldg(ph + j), gv, acc[j]);
+        }
+        T *dst = gt + i * MS;
+        if constexpr ((MS % 4) == 0 && sizeof(T) == 4) {
+            float v[MS];
+#pragma unroll
+            for (int j = 0; j < MS; ++j) v[j] = j < M ? acc[j] : 0.0f;
+#pragma unroll
+            for (int j = 0; j < MS / 4; ++j)
+                reinterpret_cast<float4 *>(dst)[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < MS; ++j) dst[j] = j < M ? acc[j] : T(0);
+        }
+    }
+}
+
+// ===========================================================================
+// Adjoint, step 2: voxel-driven exact transpose of the folded sinograms
+// ===========================================================================
+struct alignas(16) FoldPrm {
+    float c, s, c8, qb;   // cos, sin, 8 cos, window-relative origin position - 1/2
+    float e0, inv_c2;     // 1/c - 1/(2c^2), 1/c^2
+    int idx_base, pad_;   // integer origin position minus the float magic
+};
+
+template <int M>
+struct FoldAdjShape {
+    static constexpr int VPT = (M <= 8) ? 4 : ((M <= 16) ? 2 : 1);
+    static constexpr int TX = 8 * VPT;
+};
+
+template <typename S, typename T, int M>
+__global__ void __launch_bounds__(kAdjThreads)
+    fold_adj_kernel(const __grid_constant__ CUtensorMap tm_gt, const AdjProj *__restrict__ uproj,
+                    S *__restrict__ u_s, T *__restrict__ u_c, int nx, int ny, int U, int m, int Wb, T alpha, T beta,
+                    int *status) {
+    constexpr int VPT = FoldAdjShape<M>::VPT;
+    constexpr int TX = FoldAdjShape<M>::TX;
+    constexpr int TY = kAdjTY;
+    constexpr int PP = kFoldAdjP;
+    constexpr int NST = kFoldAdjStages;
+    constexpr int MS = fold_ms(M);
+    constexpr float kMag = 12582912.0f;
+    constexpr int kMagI = 0x4B400000;
+
+    extern __shared__ __align__(128) unsigned char fadj_smem_raw[];
+    unsigned char *smem_raw =
+        reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(fadj_smem_raw) + 127) & ~uintptr_t(127));
+    const size_t row_bytes = ((size_t)Wb * MS * sizeof(T) + 127) & ~(size_t)127;
+    const size_t win_bytes = PP * row_bytes;
+    const size_t stage_bytes = win_bytes + 128 * ((PP * sizeof(FoldPrm) + 127) / 128);
+    __shared__ __align__(8) uint64_t full[NST];
+    auto win_s = [&](int st, int p) { return reinterpret_cast<T *>(smem_raw + st * stage_bytes + p * row_bytes); };
+    auto prm_s = [&](int st) { return reinterpret_cast<FoldPrm *>(smem_raw + st * stage_bytes + win_bytes); };
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int ntx = (nx + TX - 1) / TX;
+    const int x0 = (blockIdx.x % ntx) * TX, y0 = (blockIdx.x / ntx) * TY;
+    const int z = blockIdx.y;
+    const int xo = x0 + TX / 2, yo = y0 + TY / 2;
+    const int tx = tid & 7, ty = tid >> 3;
+    const int dx0 = x0 + tx - xo, dy = y0 + ty - yo;
+    const int nkb = (U + PP - 1) / PP;
+
+    auto issue = [&](int st, int kb) {
+        int wb0 = 0, row = 0;
+        if (lane < PP) {
+            const int a = kb * PP + lane;
+            const int aa = a < U ? a : U - 1;
+            const AdjProj pj = uproj[aa];
+            const double posO = xo * pj.c + yo * pj.s + pj.C0;
+            const double emin = posO + fmin((-TX / 2) * pj.c, (TX / 2 - 1) * pj.c) +
+                                fmin((-TY / 2) * pj.s, (TY / 2 - 1) * pj.s);
+            wb0 = (int)floor(emin) - 1;
+            const double rel = posO - wb0;
+            const double ri = floor(rel);
+            FoldPrm pr;
+            pr.c = (float)pj.c;
+            pr.s = (float)pj.s;
+            pr.c8 = (float)(8.0 * pj.c);
+            pr.qb = (float)(rel - ri) - 0.5f;
+            pr.inv_c2 = (float)(pj.inv_c * pj.inv_c);
+            pr.e0 = (float)(pj.inv_c - 0.5 * pj.inv_c * pj.inv_c);
+            pr.idx_base = (int)ri - kMagI;
+            pr.pad_ = 0;
+            prm_s(st)[lane] = pr;
+            row = z * U + aa;
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive_expect_tx(&full[st], (unsigned)(PP * Wb * MS * sizeof(T)));
+        __syncwarp();
+        if (lane < PP) tma_load_3d(win_s(st, lane), &tm_gt, 0, wb0, row, &full[st]);
+        if (lane != 0) mbar_arrive(&full[st]);
+    };
+
+    if (tid == 0) {
+        for (int s = 0; s < NST; ++s) mbar_init(&full[s], 32);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (warp == 0)
+        for (int s = 0; s < NST && s < nkb; ++s) issue(s, s);
+
+    T acc[VPT][M];
+#pragma unroll
+    for (int v = 0; v < VPT; ++v)
+#pragma unroll
+        for (int j = 0; j < M; ++j) acc[v][j] = T(0);
+
+    const float dxf = (float)dx0, dyf = (float)dy;
+    for (int kb = 0; kb < nkb; ++kb) {
+        const int st = kb % NST;
+        const bool bad = !mbar_wait_bounded(&full[st], (unsigned)((kb / NST) & 1), status, 2000000000ull);
+        if (!bad) {
+            const FoldPrm *prm = prm_s(st);
+            const int np = min(PP, U - kb * PP);
+            for (int p = 0; p < np; ++p) {
+                const FoldPrm a = prm[p];
+                const T *w = win_s(st, p);
+                float q = fmaf(dyf, a.s, fmaf(dxf, a.c, a.qb));
+#pragma unroll
+                for (int v = 0; v < VPT; ++v) {
+                    const float t = q + kMag;
+                    const float fl = t - kMag;
+                    const float d = q - fl;
+                    const int idx = __float_as_int(t) + a.idx_base;
+                    const float w0 = fmaxf(0.0f, fmaf(-d, a.inv_c2, a.e0));
+                    const float w1 = fmaxf(0.0f, fmaf(d, a.inv_c2, a.e0));
+                    T t0[M], t1[M];
+                    load_vec<T, M>(w + idx * MS, t0);
+                    load_vec<T, M>(w + (idx + 1) * MS, t1);
+#pragma unroll
+                    for (int j = 0; j < M; ++j) acc[v][j] = fmaf(w1, t1[j], fmaf(w0, t0[j], acc[v][j]));
+                    q += a.c8;
+                }
+            }
+        }
+        if (__syncthreads_or(bad)) {
+            if (tid == 0)
+                for (int s = kb; s < nkb && s < kb + NST; ++s)
+                    mbar_wait_bounded(&full[s % NST], (unsigned)((s / NST) & 1), status, 100000000ull);
+            return;
+        }
+        if (warp == 0 && kb + NST < nkb) issue(st, kb + NST);
+    }
+
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) {
+        const int x = x0 + tx + 8 * v, y = y0 + ty;
+        if (x >= nx || y >= ny) continue;
+        const size_t base = (((size_t)z * ny + y) * nx + x) * m;
+#pragma unroll
+        for (int j = 0; j < M; ++j)
+            if (j < m) {
+                if (u_c) {
+                    T r = alpha * acc[v][j];
+                    if (beta != T(0)) r += beta * u_c[base + j];
+                    u_c[base + j] = r;
+                } else {
+                    T r = alpha * acc[v][j];
+                    if (beta != T(0)) r += beta * ldc<T>(u_s + base + j);
+                    stc<T>(u_s + base + j, r);
+                }
+            }
+    }
+}
+
+// ===========================================================================
+// Host launchers
+// ===========================================================================
+inline int fold_adj_wb(int M) {
+    const int VPT = (M <= 8) ? 4 : ((M <= 16) ? 2 : 1);
+    const int TX = 8 * VPT;
+    const double ext = std::sqrt((double)(TX - 1) * (TX - 1) + (double)(kAdjTY - 1) * (kAdjTY - 1));
+    return (int)std::ceil(ext) + 6;
+}
+
+template <typename S, typename T, int M>
+dr_status fold_fwd_launch_t(dr_plan *P, const void *u, void *out, const void *gm, int mode, double sigma,
+                            cudaStream_t st) {
+    constexpr int MS = fold_ms(M);
+    const int Wmax = std::max(P->nx, P->ny);
+    const int wpad = Wmax + 2 * kFwdGuard;
+    const size_t smem = 768 + sizeof(T) * (size_t)P->fold_R * wpad * MS;
+    auto kern = fold_fwd_kernel<S, T, M>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return cuda_fail(e, "fold fwd: smem attribute");
+    }
+    dim3 grid(P->n_fold_blocks * P->fold_nchunk, P->nz);
+    kern<<<grid, kFoldThreads, smem, st>>>((const S *)u, (S *)out, (const S *)gm, P->d_fold_fwd, P->d_fold_start,
+                                           P->d_fold_member, (const T *)P->d_PhiP, P->d_fold_blocks, P->nx, P->ny,
+                                           P->ns, P->K, P->m, P->MP, P->fold_P, P->fold_R, P->fold_nchunk, mode,
+                                           (T)sigma);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? DR_OK : cuda_fail(e, "fold_fwd_kernel launch");
+}
+
+template <typename S, typename T, int M>
+dr_status fold_adj_launch_t(dr_plan *P, const void *g, void *u, double alpha, double beta, bool u_calc,
+                            cudaStream_t st) {
+    constexpr int MS = fold_ms(M);
+    // step 1: fold the data into the plan's scratch buffer
+    fold_data_kernel<S, T, M><<<red_grid((size_t)P->nz * P->fold_U * P->ns), kRedThreads, 0, st>>>(
+        (const S *)g, (T *)P->d_gt, P->d_fold_start, P->d_fold_member, (const T *)P->d_PhiP, P->nz, P->fold_U, P->ns,
+        P->K, P->MP);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "fold_data_kernel launch");
+    // step 2: back-project the folded sinograms
+    const int Wb = fold_adj_wb(M);
+    CUtensorMap tm{};
+    const uint64_t dims[3] = {(uint64_t)MS, (uint64_t)P->ns, (uint64_t)P->nz * P->fold_U};
+    const uint64_t strides[2] = {(uint64_t)MS * sizeof(T), (uint64_t)P->ns * MS * sizeof(T)};
+    const uint32_t box[3] = {(uint32_t)MS, (uint32_t)Wb, 1};
+    if (!encode_tensor_map(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, P->d_gt, dims, strides, box))
+        return fail(DR_ECUDA, "fold adj: tensor map encode failed");
+    const size_t row_bytes = ((size_t)Wb * MS * sizeof(T) + 127) & ~(size_t)127;
+    const size_t stage = kFoldAdjP * row_bytes + 128 * ((kFoldAdjP * sizeof(FoldPrm) + 127) / 128);
+    const size_t smem = stage * kFoldAdjStages + 128;
+    auto kern = fold_adj_kernel<S, T, M>;
+    if (smem > 48 * 1024) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return cuda_fail(e, "fold adj: smem attribute");
+    }
+    constexpr int TX = FoldAdjShape<M>::TX;
+    const int ntx = (P->nx + TX - 1) / TX, nty = (P->ny + kAdjTY - 1) / kAdjTY;
+    dim3 grid(ntx * nty, P->nz);
+    kern<<<grid, kAdjThreads, smem, st>>>(tm, P->d_fold_adj, u_calc ? nullptr : (S *)u, u_calc ? (T *)u : nullptr,
+                                          P->nx, P->ny, P->fold_U, P->m, Wb, (T)alpha, (T)beta, P->d_status);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? DR_OK : cuda_fail(e, "fold_adj_kernel launch");
+}
+
+template <typename S, typename T>
+struct FoldOps {
+    static dr_status fwd(dr_plan *P, const void *u, void *out, const void *gm, int mode, double sigma,
+                         cudaStream_t st);
+    static dr_status adj(dr_plan *P, const void *g, void *u, double alpha, double beta, bool u_calc,
+                         cudaStream_t st);
+};
+
+#define DR_FOLD_DISPATCH(FN, S, T, ...)                   \
+    switch (P->M) {                                       \
+        case 1: return FN<S, T, 1>(__VA_ARGS__);          \
+        case 2: return FN<S, T, 2>(__VA_ARGS__);          \
+        case 4: return FN<S, T, 4>(__VA_ARGS__);          \
+        case 8: return FN<S, T, 8>(__VA_ARGS__);          \
+        case 12: return FN<S, T, 12>(__VA_ARGS__);        \
+        case 16: return FN<S, T, 16>(__VA_ARGS__);        \
+        case 24: return FN<S, T, 24>(__VA_ARGS__);        \
+        case 32: return FN<S, T, 32>(__VA_ARGS__);        \
+        default: return fail(DR_EINVAL, "unsupported m"); \
+    }
+
+template <typename S, typename T>
+dr_status FoldOps<S, T>::fwd(dr_plan *P, const void *u, void *out, const void *gm, int mode, double sigma,
+                             cudaStream_t st) {
+    DR_FOLD_DISPATCH(fold_fwd_launch_t, S, T, P, u, out, gm, mode, sigma, st)
+}
+
+template <typename S, typename T>
+dr_status FoldOps<S, T>::adj(dr_plan *P, const void *g, void *u, double alpha, double beta, bool u_calc,
+                             cudaStream_t st) {
+    DR_FOLD_DISPATCH(fold_adj_launch_t, S, T, P, g, u, alpha, beta, u_calc, st)
+}
+
+extern template struct FoldOps<float, float>;
+extern template struct FoldOps<bf16, float>;
+
+}  // namespace dr

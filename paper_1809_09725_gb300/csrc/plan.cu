@@ -63,8 +63,7 @@ static void eval_basis(dr_basis kind, int m, double t, double *row) {
 static std::once_flag g_tmap_once;
 static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
-bool encode_tensor_map_2d(CUtensorMap *map, CUtensorMapDataType dt, void *base, uint64_t dim0,
-                          uint64_t dim1, uint64_t stride1_bytes, uint32_t box0, uint32_t box1) {
+static void resolve_encoder() {
     std::call_once(g_tmap_once, [] {
         void *fn = nullptr;
         cudaDriverEntryPointQueryResult q;
@@ -73,6 +72,29 @@ bool encode_tensor_map_2d(CUtensorMap *map, CUtensorMapDataType dt, void *base, 
             q == cudaDriverEntryPointSuccess)
             g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
     });
+}
+
+bool encode_tensor_map(CUtensorMap *map, CUtensorMapDataType dt, int rank, void *base, const uint64_t *dims,
+                       const uint64_t *strides, const uint32_t *box) {
+    resolve_encoder();
+    if (!g_encode || rank < 1 || rank > 5) return false;
+    cuuint64_t gdim[5], gstr[4];
+    cuuint32_t bx[5], es[5];
+    for (int i = 0; i < rank; ++i) {
+        gdim[i] = dims[i];
+        bx[i] = box[i];
+        es[i] = 1;
+        if (i + 1 < rank) gstr[i] = strides[i];
+    }
+    CUresult r = g_encode(map, dt, (cuuint32_t)rank, base, gdim, gstr, bx, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+bool encode_tensor_map_2d(CUtensorMap *map, CUtensorMapDataType dt, void *base, uint64_t dim0,
+                          uint64_t dim1, uint64_t stride1_bytes, uint32_t box0, uint32_t box1) {
+    resolve_encoder();
     if (!g_encode) return false;
     cuuint64_t gdim[2] = {dim0, dim1};
     cuuint64_t gstride[1] = {stride1_bytes};
@@ -216,6 +238,112 @@ static dr_status build_tables(dr_plan *P) {
     if (!blocks.empty())
         DR_CUDA_TRY(cudaMemcpy(P->d_fwd_blocks, blocks.data(), sizeof(int) * blocks.size(), cudaMemcpyHostToDevice));
 
+    // ---- half-turn fold (Sec. 4): group projections by theta mod pi ----
+    if (P->prec != DR_F64) {
+        struct Ent { double th0; int k, flip; };
+        std::vector<Ent> ent(K);
+        for (int k = 0; k < K; ++k) {
+            const double n = std::floor(P->theta[k] / M_PI);
+            double th0 = P->theta[k] - n * M_PI;
+            long long ni = (long long)n;
+            if (th0 >= M_PI) { th0 -= M_PI; ++ni; }
+            if (th0 < 0.0) { th0 += M_PI; --ni; }
+            ent[k] = Ent{th0, k, (int)(((ni % 2) + 2) % 2)};
+        }
+        std::sort(ent.begin(), ent.end(), [](const Ent &a, const Ent &b) {
+            return a.th0 < b.th0 || (a.th0 == b.th0 && a.k < b.k);
+        });
+        // angles within 1e-11 rad of the group's first member share it; an angle
+        // just below pi joins the group of 0 with the opposite parity
+        const double tol = 1e-11;
+        std::vector<int> start{0};
+        std::vector<double> rep{ent.empty() ? 0.0 : ent[0].th0};
+        for (int i = 1; i < K; ++i)
+            if (ent[i].th0 - rep.back() > tol) {
+                start.push_back(i);
+                rep.push_back(ent[i].th0);
+            }
+        start.push_back(K);
+        std::vector<int> member(K);
+        for (int i = 0; i < K; ++i) member[i] = 2 * ent[i].k + ent[i].flip;
+        if (rep.size() > 1 && M_PI - rep.back() <= tol) {
+            // merge the last group into the first with flipped parity
+            const int s0 = start[start.size() - 2];
+            std::vector<int> merged;
+            for (int i = s0; i < K; ++i) merged.push_back(member[i] ^ 1);
+            std::vector<int> rest(member.begin(), member.begin() + s0);
+            member.assign(merged.begin(), merged.end());
+            member.insert(member.end(), rest.begin(), rest.end());
+            const int shift = K - s0;
+            std::vector<int> ns2{0};
+            for (size_t g = 1; g + 1 < start.size() - 1; ++g) ns2.push_back(start[g] + shift);
+            ns2.push_back(K);
+            start = ns2;
+            rep.pop_back();
+        }
+        const int U = (int)rep.size();
+        int maxg = 0;
+        for (int a = 0; a < U; ++a) maxg = std::max(maxg, start[a + 1] - start[a]);
+        std::vector<FwdProj> ufw(U);
+        std::vector<AdjProj> uad(U);
+        std::vector<int> ub0, ub1;
+        for (int a = 0; a < U; ++a) {
+            const double c = std::cos(rep[a]), s = std::sin(rep[a]);
+            FwdProj f{};
+            if (std::fabs(c) >= std::fabs(s)) {
+                f.branch = 0; f.A = 1.0 / c; f.B = -s / c; f.C = (-hs + hy * s) / c + hx; f.scale_d = 1.0 / std::fabs(c);
+                ub0.push_back(a);
+            } else {
+                f.branch = 1; f.A = 1.0 / s; f.B = -c / s; f.C = (-hs + hx * c) / s + hy; f.scale_d = 1.0 / std::fabs(s);
+                ub1.push_back(a);
+            }
+            f.A_fx = std::llround(f.A * two32); f.B_fx = std::llround(f.B * two32); f.C_fx = std::llround(f.C * two32);
+            f.Af = (float)f.A; f.Bf = (float)f.B; f.Cf = (float)f.C; f.scale = (float)f.scale_d;
+            ufw[a] = f;
+            uad[a] = AdjProj{c, s, -hx * c - hy * s + hs, 1.0 / std::max(std::fabs(c), std::fabs(s))};
+        }
+        // forward work lists over unique angles
+        const int M = P->M;
+        const int rpt = M <= 4 ? 8 : 32 / M;
+        const int rays = 256 * rpt;
+        int Pf, nchunk;
+        if (P->ns <= rays) { Pf = std::min(64, rays / P->ns); nchunk = 1; }
+        else { Pf = 1; nchunk = (P->ns + rays - 1) / rays; }
+        const int MS = M <= 4 ? 4 : ((M % 8 == 0) ? M + 4 : M);
+        const size_t line = sizeof(float) * (size_t)(std::max(P->nx, P->ny) + 2 * kFwdGuard) * MS;
+        int R = (int)((56 * 1024) / line);
+        if (R < 1 && line + 768 <= 200 * 1024) R = 1;
+        R = std::min(R, 16);
+        P->fold_fwd_ok = R >= 1;
+        std::vector<int> fb;
+        for (const std::vector<int> *grp : {&ub0, &ub1})
+            for (size_t i = 0; i < grp->size(); i += Pf)
+                for (int q = 0; q < Pf; ++q) fb.push_back(i + q < grp->size() ? (*grp)[i + q] : -1);
+        P->fold_U = U;
+        P->fold_maxgrp = maxg;
+        P->fold_P = Pf;
+        P->fold_R = std::max(R, 1);
+        P->fold_nchunk = nchunk;
+        P->n_fold_blocks = (int)(fb.size() / Pf);
+        DR_CUDA_TRY(cudaMalloc(&P->d_fold_fwd, sizeof(FwdProj) * U));
+        DR_CUDA_TRY(cudaMalloc(&P->d_fold_adj, sizeof(AdjProj) * U));
+        DR_CUDA_TRY(cudaMalloc(&P->d_fold_start, sizeof(int) * (U + 1)));
+        DR_CUDA_TRY(cudaMalloc(&P->d_fold_member, sizeof(int) * K));
+        DR_CUDA_TRY(cudaMalloc(&P->d_fold_blocks, sizeof(int) * std::max<size_t>(fb.size(), 1)));
+        bytes += (sizeof(FwdProj) + sizeof(AdjProj) + sizeof(int)) * U + sizeof(int) * (K + 1 + fb.size());
+        DR_CUDA_TRY(cudaMemcpy(P->d_fold_fwd, ufw.data(), sizeof(FwdProj) * U, cudaMemcpyHostToDevice));
+        DR_CUDA_TRY(cudaMemcpy(P->d_fold_adj, uad.data(), sizeof(AdjProj) * U, cudaMemcpyHostToDevice));
+        DR_CUDA_TRY(cudaMemcpy(P->d_fold_start, start.data(), sizeof(int) * (U + 1), cudaMemcpyHostToDevice));
+        DR_CUDA_TRY(cudaMemcpy(P->d_fold_member, member.data(), sizeof(int) * K, cudaMemcpyHostToDevice));
+        if (!fb.empty())
+            DR_CUDA_TRY(cudaMemcpy(P->d_fold_blocks, fb.data(), sizeof(int) * fb.size(), cudaMemcpyHostToDevice));
+        P->gt_bytes = sizeof(float) * (size_t)P->nz * U * P->ns * MS;
+        // cost model until measured: fold when the unique angles carry the work
+        const double direct = (double)K * (P->m + 16), fold = (double)U * (3.0 * P->m + 12) + 0.05 * K * P->m;
+        P->sel_fwd = (P->fold_fwd_ok && fold < 0.8 * direct) ? 1 : 0;
+        P->sel_adj = (fold < 0.8 * direct) ? 1 : 0;
+    }
+
     // reductions, scalars, status
     DR_CUDA_TRY(cudaMalloc(&P->d_partials, sizeof(double) * kRedSlots * kRedSlotStride));
     DR_CUDA_TRY(cudaMalloc(&P->d_counters, sizeof(unsigned) * kRedSlots));
@@ -310,8 +438,10 @@ dr_status dr_plan_destroy(dr_plan *P) {
     if (!P) return DR_OK;
     if (P->stream || P->graph_stream) cudaDeviceSynchronize();
     free_workspace(P);
-    void *ptrs[] = {P->d_fwd, P->d_adj, P->d_PhiP, P->d_fwd_blocks, P->d_PhiF, P->d_dPhiF, P->d_G, P->d_Lt,
-                    P->d_partials, P->d_counters, P->d_scal, P->d_status};
+    void *ptrs[] = {P->d_fwd,        P->d_adj,       P->d_PhiP,       P->d_fwd_blocks,  P->d_PhiF,
+                    P->d_dPhiF,      P->d_G,         P->d_Lt,         P->d_partials,    P->d_counters,
+                    P->d_scal,       P->d_status,    P->d_fold_fwd,   P->d_fold_adj,    P->d_fold_start,
+                    P->d_fold_member, P->d_fold_blocks, P->d_gt};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (P->graph_stream) cudaStreamDestroy(P->graph_stream);
@@ -327,7 +457,7 @@ dr_status dr_plan_set_stream(dr_plan *P, void *s) {
     return DR_OK;
 }
 
-size_t dr_plan_device_bytes(const dr_plan *P) { return P ? P->table_bytes + P->ws.bytes : 0; }
+size_t dr_plan_device_bytes(const dr_plan *P) { return P ? P->table_bytes + P->ws.bytes + (P->d_gt ? P->gt_bytes : 0) : 0; }
 
 dr_status dr_plan_sync(dr_plan *P) {
     if (!P) return fail(DR_EINVAL, "dr_plan_sync: NULL plan");

@@ -4,40 +4,130 @@
 #include <cmath>
 
 #include "projector_impl.cuh"
+#include "fold_impl.cuh"
 
 namespace dr {
 
-dr_status launch_fwd(dr_plan *P, const void *u, void *out, const void *gm, int mode, double sigma,
-                     cudaStream_t st) {
+dr_status ensure_fold_scratch(dr_plan *P) {
+    if (P->d_gt) return DR_OK;
+    cudaError_t e = cudaMalloc(&P->d_gt, std::max<size_t>(P->gt_bytes, 16));
+    if (e != cudaSuccess) {
+        P->d_gt = nullptr;
+        return cuda_fail(e, "folded-data scratch allocation");
+    }
+    return DR_OK;
+}
+
+// variant 0: direct (every projection at its own angle); 1: half-turn fold.
+// calc: buffers are compute typed (float for F32/BF16 plans, double for F64).
+dr_status launch_fwd_variant(dr_plan *P, int variant, bool calc, const void *u, void *out, const void *gm,
+                             int mode, double sigma, cudaStream_t st) {
+    if (variant == 1 && P->fold_U > 0 && P->fold_fwd_ok) {
+        if (P->prec == DR_BF16_F32ACC && !calc) return FoldOps<bf16, float>::fwd(P, u, out, gm, mode, sigma, st);
+        return FoldOps<float, float>::fwd(P, u, out, gm, mode, sigma, st);
+    }
     switch (P->prec) {
         case DR_F32: return ProjOps<float, float>::fwd(P, u, out, gm, mode, sigma, st);
-        case DR_BF16_F32ACC: return ProjOps<bf16, float>::fwd(P, u, out, gm, mode, sigma, st);
+        case DR_BF16_F32ACC:
+            if (calc) return ProjOps<float, float>::fwd(P, u, out, gm, mode, sigma, st);
+            return ProjOps<bf16, float>::fwd(P, u, out, gm, mode, sigma, st);
         case DR_F64: return ProjOps<double, double>::fwd(P, u, out, gm, mode, sigma, st);
     }
     return fail(DR_EINVAL, "bad precision");
 }
 
-dr_status launch_adj(dr_plan *P, const void *g, void *u, double alpha, double beta, bool u_calc,
-                     cudaStream_t st) {
+dr_status launch_adj_variant(dr_plan *P, int variant, bool calc, const void *g, void *u, double alpha,
+                             double beta, bool u_calc, cudaStream_t st) {
+    if (variant == 1 && P->fold_U > 0) {
+        dr_status s = ensure_fold_scratch(P);
+        if (s != DR_OK) return s;
+        if (P->prec == DR_BF16_F32ACC && !calc)
+            return FoldOps<bf16, float>::adj(P, g, u, alpha, beta, u_calc, st);
+        return FoldOps<float, float>::adj(P, g, u, alpha, beta, u_calc, st);
+    }
     switch (P->prec) {
         case DR_F32: return ProjOps<float, float>::adj(P, g, u, alpha, beta, u_calc, st);
-        case DR_BF16_F32ACC: return ProjOps<bf16, float>::adj(P, g, u, alpha, beta, u_calc, st);
+        case DR_BF16_F32ACC:
+            if (calc) return ProjOps<float, float>::adj(P, g, u, alpha, beta, u_calc, st);
+            return ProjOps<bf16, float>::adj(P, g, u, alpha, beta, u_calc, st);
         case DR_F64: return ProjOps<double, double>::adj(P, g, u, alpha, beta, u_calc, st);
     }
     return fail(DR_EINVAL, "bad precision");
+}
+
+static int fwd_choice(const dr_plan *P) { return P->var_fwd >= 0 ? P->var_fwd : P->sel_fwd; }
+static int adj_choice(const dr_plan *P) { return P->var_adj >= 0 ? P->var_adj : P->sel_adj; }
+
+dr_status launch_fwd(dr_plan *P, const void *u, void *out, const void *gm, int mode, double sigma,
+                     cudaStream_t st) {
+    return launch_fwd_variant(P, fwd_choice(P), false, u, out, gm, mode, sigma, st);
+}
+
+dr_status launch_adj(dr_plan *P, const void *g, void *u, double alpha, double beta, bool u_calc,
+                     cudaStream_t st) {
+    return launch_adj_variant(P, adj_choice(P), false, g, u, alpha, beta, u_calc, st);
 }
 
 // Compute-typed variants for the solvers: all buffers are float (F32 and
 // BF16 plans) or double (F64 plans).
 dr_status launch_fwd_calc(dr_plan *P, const void *u, void *out, const void *gm, int mode, double sigma,
                           cudaStream_t st) {
-    if (P->prec == DR_F64) return ProjOps<double, double>::fwd(P, u, out, gm, mode, sigma, st);
-    return ProjOps<float, float>::fwd(P, u, out, gm, mode, sigma, st);
+    return launch_fwd_variant(P, fwd_choice(P), true, u, out, gm, mode, sigma, st);
 }
 
 dr_status launch_adj_calc(dr_plan *P, const void *g, void *u, double alpha, double beta, cudaStream_t st) {
-    if (P->prec == DR_F64) return ProjOps<double, double>::adj(P, g, u, alpha, beta, true, st);
-    return ProjOps<float, float>::adj(P, g, u, alpha, beta, true, st);
+    return launch_adj_variant(P, adj_choice(P), true, g, u, alpha, beta, true, st);
+}
+
+// Autotuner: time the direct and folded variants of both projectors on the
+// plan's own geometry (compute-typed scratch buffers supplied by the
+// caller, contents overwritten) and keep the faster of each.  Explicit
+// choices made with dr_plan_set_variant are left alone.
+dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
+    if (P->fold_U == 0) {
+        P->tuned = true;
+        return DR_OK;
+    }
+    cudaStream_t st = P->graph_stream;
+    cudaEvent_t e0, e1;
+    DR_CUDA_TRY(cudaEventCreate(&e0));
+    DR_CUDA_TRY(cudaEventCreate(&e1));
+    const size_t cs = calc_size(P->prec);
+    DR_CUDA_TRY(cudaMemsetAsync(u_scratch, 0, nu_elems(P) * cs, st));
+    DR_CUDA_TRY(cudaMemsetAsync(g_scratch, 0, ng_elems(P) * cs, st));
+    double ms[4] = {1e30, 1e30, 1e30, 1e30};
+    for (int v = 0; v < 2; ++v) {
+        if (v == 1 && !P->fold_fwd_ok) continue;
+        for (int rep = 0; rep < 3; ++rep) {
+            DR_CUDA_TRY(cudaEventRecord(e0, st));
+            dr_status s = launch_fwd_variant(P, v, true, u_scratch, g_scratch, nullptr, 0, 0.0, st);
+            if (s != DR_OK) return s;
+            DR_CUDA_TRY(cudaEventRecord(e1, st));
+            DR_CUDA_TRY(cudaEventSynchronize(e1));
+            float t = 0.f;
+            DR_CUDA_TRY(cudaEventElapsedTime(&t, e0, e1));
+            if (rep > 0) ms[v] = std::min(ms[v], (double)t);
+        }
+    }
+    for (int v = 0; v < 2; ++v) {
+        for (int rep = 0; rep < 3; ++rep) {
+            DR_CUDA_TRY(cudaEventRecord(e0, st));
+            dr_status s = launch_adj_variant(P, v, true, g_scratch, u_scratch, 1.0, 0.0, true, st);
+            if (s != DR_OK) return s;
+            DR_CUDA_TRY(cudaEventRecord(e1, st));
+            DR_CUDA_TRY(cudaEventSynchronize(e1));
+            float t = 0.f;
+            DR_CUDA_TRY(cudaEventElapsedTime(&t, e0, e1));
+            if (rep > 0) ms[2 + v] = std::min(ms[2 + v], (double)t);
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    for (int i = 0; i < 4; ++i) P->tune_ms[i] = ms[i] < 1e29 ? ms[i] : -1.0;
+    P->sel_fwd = ms[1] < ms[0] ? 1 : 0;
+    P->sel_adj = ms[3] < ms[2] ? 1 : 0;
+    P->tuned = true;
+    return DR_OK;
 }
 
 }  // namespace dr
@@ -57,6 +147,53 @@ dr_status dyn_radon_adj(dr_plan *P, const void *g, void *u, double beta) {
     if (!P || !u || !g) return fail(DR_EINVAL, "dyn_radon_adj: NULL argument");
     if (!std::isfinite(beta)) return fail(DR_EINVAL, "dyn_radon_adj: beta must be finite");
     return launch_adj(P, g, u, 1.0, beta, false, P->stream);
+}
+
+dr_status dr_plan_set_variant(dr_plan *P, int fwd_variant, int adj_variant) {
+    clear_error();
+    if (!P) return fail(DR_EINVAL, "dr_plan_set_variant: NULL plan");
+    if (fwd_variant < -1 || fwd_variant > 1 || adj_variant < -1 || adj_variant > 1)
+        return fail(DR_EINVAL, "dr_plan_set_variant: variants are -1 (auto), 0 (direct) or 1 (fold)");
+    if ((fwd_variant == 1 && !(P->fold_U > 0 && P->fold_fwd_ok)) || (adj_variant == 1 && P->fold_U == 0))
+        return fail(DR_EINVAL, "dr_plan_set_variant: the half-turn fold is unavailable for this plan");
+    P->var_fwd = fwd_variant;
+    P->var_adj = adj_variant;
+    return DR_OK;
+}
+
+dr_status dr_plan_autotune(dr_plan *P, double *times_ms) {
+    clear_error();
+    if (!P) return fail(DR_EINVAL, "dr_plan_autotune: NULL plan");
+    if (!P->tuned) {
+        const size_t cs = calc_size(P->prec);
+        void *us = nullptr, *gs = nullptr;
+        DR_CUDA_TRY(cudaMalloc(&us, std::max<size_t>(nu_elems(P) * cs, 16)));
+        cudaError_t e = cudaMalloc(&gs, std::max<size_t>(ng_elems(P) * cs, 16));
+        if (e != cudaSuccess) {
+            cudaFree(us);
+            return cuda_fail(e, "dr_plan_autotune: scratch");
+        }
+        dr_status s = autotune(P, us, gs);
+        cudaStreamSynchronize(P->graph_stream);
+        cudaFree(us);
+        cudaFree(gs);
+        if (s != DR_OK) return s;
+    }
+    if (times_ms)
+        for (int i = 0; i < 4; ++i) times_ms[i] = P->tune_ms[i];
+    return DR_OK;
+}
+
+dr_status dr_plan_info(const dr_plan *P, dr_plan_info_t *info) {
+    clear_error();
+    if (!P || !info) return fail(DR_EINVAL, "dr_plan_info: NULL argument");
+    info->unique_angles = P->fold_U;
+    info->max_group = P->fold_maxgrp;
+    info->fwd_variant = P->var_fwd >= 0 ? P->var_fwd : P->sel_fwd;
+    info->adj_variant = P->var_adj >= 0 ? P->var_adj : P->sel_adj;
+    info->tuned = P->tuned ? 1 : 0;
+    info->device_bytes = P->table_bytes + P->ws.bytes + (P->d_gt ? P->gt_bytes : 0);
+    return DR_OK;
 }
 
 }  // extern "C"

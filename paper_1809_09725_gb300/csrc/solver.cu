@@ -308,6 +308,8 @@ static dr_status solve(dr_plan *P, const void *g_in, void *u_io, const dr_solve_
 
     DR_CUDA_TRY(cudaEventRecord(P->ev_a, P->stream));
     DR_CUDA_TRY(cudaStreamWaitEvent(st, P->ev_a, 0));
+    // pick the faster projector variants once per plan (scratch: q, gd)
+    if (!P->tuned) TRY(autotune(P, w.q, w.gd));
 
     // ---- bring g and u into compute-typed device buffers ----
     const void *g = g_in;

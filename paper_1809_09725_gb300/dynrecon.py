@@ -29,15 +29,22 @@ _STATUS = {DR_EINVAL: "EINVAL", DR_ENOMEM: "ENOMEM", DR_ECUDA: "ECUDA", DR_ETIME
 
 # Every symbol include/dynrecon.h declares.
 EXPORTS = ("dr_plan_create", "dr_plan_destroy", "dr_plan_set_stream", "dr_plan_device_bytes",
-           "dr_plan_workspace_bytes", "dr_plan_sync", "dyn_radon_fwd", "dyn_radon_adj", "tv4d_grad",
-           "tv4d_grad_adj", "tv4d_prox", "dr_solve_params_default", "admm_solve", "dr_last_error",
-           "dr_version")
+           "dr_plan_workspace_bytes", "dr_plan_sync", "dr_plan_set_variant", "dr_plan_autotune", "dr_plan_info",
+           "dyn_radon_fwd", "dyn_radon_adj", "tv4d_grad", "tv4d_grad_adj", "tv4d_prox",
+           "dr_solve_params_default", "admm_solve", "dr_last_error", "dr_version")
+
+DIRECT, FOLD, AUTO = 0, 1, -1
 
 
 class DynreconError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__("%s (%d): %s" % (_STATUS.get(status, "?"), status, msg))
         self.status = status
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("unique_angles", ctypes.c_int), ("max_group", ctypes.c_int), ("fwd_variant", ctypes.c_int),
+                ("adj_variant", ctypes.c_int), ("tuned", ctypes.c_int), ("device_bytes", ctypes.c_size_t)]
 
 
 class SolveParams(ctypes.Structure):
@@ -69,6 +76,9 @@ def load(path: str = LIB_PATH):
         "dr_plan_device_bytes": (sz, [vp]),
         "dr_plan_workspace_bytes": (sz, [vp, i]),
         "dr_plan_sync": (i, [vp]),
+        "dr_plan_set_variant": (i, [vp, i, i]),
+        "dr_plan_autotune": (i, [vp, pd]),
+        "dr_plan_info": (i, [vp, ctypes.POINTER(PlanInfo)]),
         "dyn_radon_fwd": (i, [vp, vp, vp]),
         "dyn_radon_adj": (i, [vp, vp, vp, d]),
         "tv4d_grad": (i, [vp, vp, vp, d]),
@@ -186,6 +196,22 @@ class Plan:
 
     def sync(self):
         _check(load().dr_plan_sync(self._h))
+
+    def set_variant(self, fwd: int = AUTO, adj: int = AUTO):
+        """0 direct, 1 half-turn fold (Sec. 4), -1 automatic."""
+        _check(load().dr_plan_set_variant(self._h, int(fwd), int(adj)))
+
+    def autotune(self):
+        """Time both projector variants; returns [fwd direct, fwd fold, adj direct, adj fold] ms."""
+        self.use_current_stream()
+        t = (ctypes.c_double * 4)()
+        _check(load().dr_plan_autotune(self._h, t))
+        return list(t)
+
+    def info(self) -> dict:
+        inf = PlanInfo()
+        _check(load().dr_plan_info(self._h, ctypes.byref(inf)))
+        return {f: getattr(inf, f) for f, _ in PlanInfo._fields_}
 
     def close(self):
         if self._h:

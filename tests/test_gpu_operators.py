@@ -60,6 +60,7 @@ def test_forward_matches_oracle(case, prec, tol):
     if prec == dr.F32:
         u = u.astype(np.float32).astype(np.float64)
     plan = _plan(args, prec)
+    plan.set_variant(dr.DIRECT, dr.DIRECT)
     g = torch.zeros(plan.g_shape(), dtype=getattr(torch, plan.storage_dtype), device="cuda")
     dr.dyn_radon_fwd(plan, dev_tensor(u, prec), g)
     plan.sync()
@@ -73,6 +74,7 @@ def test_adjoint_matches_oracle(case, prec, tol):
     if prec == dr.F32:
         g = g.astype(np.float32).astype(np.float64)
     plan = _plan(args, prec)
+    plan.set_variant(dr.DIRECT, dr.DIRECT)
     u = torch.zeros(plan.u_shape(), dtype=getattr(torch, plan.storage_dtype), device="cuda")
     dr.dyn_radon_adj(plan, dev_tensor(g, prec), u)
     plan.sync()
@@ -112,6 +114,7 @@ def test_bf16_storage(case):
     args, u, g, P = _setup(case, seed=7)
     ub, gb = to_bf16_f64(u), to_bf16_f64(g)
     plan = _plan(args, dr.BF16)
+    plan.set_variant(dr.DIRECT, dr.DIRECT)
     go = torch.zeros(plan.g_shape(), dtype=torch.bfloat16, device="cuda")
     uo = torch.zeros(plan.u_shape(), dtype=torch.bfloat16, device="cuda")
     dr.dyn_radon_fwd(plan, dev_tensor(ub, dr.BF16), go)
@@ -149,6 +152,7 @@ def test_full_workload_256x16x1800_fp32():
     u = rng.standard_normal((w.nz, w.N, w.N, w.m)).astype(np.float32).astype(np.float64)
     g = rng.standard_normal((w.nz, w.K, w.ns)).astype(np.float32).astype(np.float64)
     plan = dr.Plan(w.N, w.N, w.nz, w.ns, theta, t, w.basis, w.m, w.nt, dr.F32)
+    plan.set_variant(dr.DIRECT, dr.DIRECT)
     P = oracle.Problem(w.N, w.N, w.nz, w.ns, theta, t, w.basis, w.m, w.nt)
     go = torch.zeros(plan.g_shape(), dtype=torch.float32, device="cuda")
     uo = torch.zeros(plan.u_shape(), dtype=torch.float32, device="cuda")
@@ -178,3 +182,92 @@ def test_invalid_arguments_raise():
     with pytest.raises(ValueError):
         dr.dyn_radon_fwd(plan, torch.zeros((1, 8, 8, 3), dtype=torch.float32, device="cuda"),
                          torch.zeros(plan.g_shape(), dtype=torch.float32, device="cuda"))
+
+
+# --------------------------------------------------------------------------- #
+# Half-turn fold (Sec. 4): same operator as the direct form, up to rounding
+# --------------------------------------------------------------------------- #
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_fold_variant_matches_oracle(case):
+    args, u, g, P = _setup(case, seed=11)
+    u = u.astype(np.float32).astype(np.float64)
+    g = g.astype(np.float32).astype(np.float64)
+    plan = _plan(args, dr.F32)
+    plan.set_variant(dr.FOLD, dr.FOLD)
+    go = torch.zeros(plan.g_shape(), dtype=torch.float32, device="cuda")
+    uo = torch.zeros(plan.u_shape(), dtype=torch.float32, device="cuda")
+    dr.dyn_radon_fwd(plan, dev_tensor(u, dr.F32), go)
+    dr.dyn_radon_adj(plan, dev_tensor(g, dr.F32), uo)
+    plan.sync()
+    assert rel(host_values(go), P.fwd(u)) <= 1e-5
+    assert rel(host_values(uo), P.adj(g)) <= 1e-5
+
+
+@pytest.mark.parametrize("case", ["disks64", "narrow_det", "m16"])
+def test_fold_variant_bf16(case):
+    args, u, g, P = _setup(case, seed=13)
+    ub, gb = to_bf16_f64(u), to_bf16_f64(g)
+    plan = _plan(args, dr.BF16)
+    plan.set_variant(dr.FOLD, dr.FOLD)
+    go = torch.zeros(plan.g_shape(), dtype=torch.bfloat16, device="cuda")
+    uo = torch.zeros(plan.u_shape(), dtype=torch.bfloat16, device="cuda")
+    dr.dyn_radon_fwd(plan, dev_tensor(ub, dr.BF16), go)
+    dr.dyn_radon_adj(plan, dev_tensor(gb, dr.BF16), uo, beta=0.0)
+    plan.sync()
+    assert rel(host_values(go), to_bf16_f64(P.fwd(ub))) <= 1e-3
+    assert rel(host_values(uo), to_bf16_f64(P.adj(gb))) <= 1e-3
+
+
+def test_fold_groups_angles_across_pi():
+    """Angles a hair below pi fold onto 0 with reversed bins; repeated
+    half-turns fold onto their base angle."""
+    base = np.array([0.0, 0.3, 1.2, 2.5])
+    theta = np.concatenate([base, base + np.pi, base + 2 * np.pi, [np.pi - 1e-13, 3 * np.pi - 2e-13]])
+    K = theta.size
+    t = np.linspace(0.0, 0.99, K)
+    args = (30, 26, 2, 33, theta, t, dr.FOURIER, 3, 3)
+    plan = _plan(args, dr.F32)
+    info = plan.info()
+    assert info["unique_angles"] == 4 and info["max_group"] == 5
+    rng = synth.rng_for(21)
+    u = rng.standard_normal((2, 26, 30, 3)).astype(np.float32).astype(np.float64)
+    g = rng.standard_normal((2, K, 33)).astype(np.float32).astype(np.float64)
+    P = oracle.Problem(30, 26, 2, 33, theta, t, dr.FOURIER, 3, 3)
+    plan.set_variant(dr.FOLD, dr.FOLD)
+    go = torch.zeros(plan.g_shape(), dtype=torch.float32, device="cuda")
+    uo = torch.zeros(plan.u_shape(), dtype=torch.float32, device="cuda")
+    dr.dyn_radon_fwd(plan, dev_tensor(u, dr.F32), go)
+    dr.dyn_radon_adj(plan, dev_tensor(g, dr.F32), uo)
+    plan.sync()
+    assert rel(host_values(go), P.fwd(u)) <= 1e-5
+    assert rel(host_values(uo), P.adj(g)) <= 1e-5
+
+
+def test_fold_full_workload_and_autotune():
+    w = synth.WORKLOADS["ellipsoids256"]
+    theta, t = w.geometry()
+    plan = dr.Plan(w.N, w.N, w.nz, w.ns, theta, t, w.basis, w.m, w.nt, dr.F32)
+    info = plan.info()
+    assert info["unique_angles"] == 180 and info["max_group"] == 10
+    times = plan.autotune()
+    assert plan.info()["tuned"] == 1 and all(x > 0 for x in times)
+    rng = synth.rng_for(4243)
+    u = rng.standard_normal((w.nz, w.N, w.N, w.m)).astype(np.float32).astype(np.float64)
+    g = rng.standard_normal((w.nz, w.K, w.ns)).astype(np.float32).astype(np.float64)
+    P = oracle.Problem(w.N, w.N, w.nz, w.ns, theta, t, w.basis, w.m, w.nt)
+    plan.set_variant(dr.FOLD, dr.FOLD)
+    go = torch.zeros(plan.g_shape(), dtype=torch.float32, device="cuda")
+    uo = torch.zeros(plan.u_shape(), dtype=torch.float32, device="cuda")
+    dr.dyn_radon_fwd(plan, dev_tensor(u, dr.F32), go)
+    dr.dyn_radon_adj(plan, dev_tensor(g, dr.F32), uo)
+    plan.sync()
+    assert rel(host_values(go), P.fwd(u)) <= 1e-5
+    assert rel(host_values(uo), P.adj(g)) <= 1e-5
+
+
+def test_fold_is_unavailable_for_f64_plans():
+    args, _, _, _ = _setup("disks64")
+    plan = _plan(args, dr.F64)
+    assert plan.info()["unique_angles"] == 0
+    with pytest.raises(dr.DynreconError):
+        plan.set_variant(dr.FOLD, dr.FOLD)
