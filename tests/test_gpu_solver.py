@@ -150,7 +150,8 @@ def test_bf16_storage_solve(disks):
     prm = dr.solve_params(dr.ADMM_CG, iters=5, n_cg=w.n_cg, lambda1=w.lambda1, lambda2=w.lambda2, rho=w.rho)
     res = dr.admm_solve(plan, dev_tensor(gb, dr.BF16), ud, prm)
     assert rel(host_values(ud), uo) <= 2.0 ** -8
-    assert np.max(np.abs(res["objective"] - oo) / np.abs(oo)) <= 1e-4
+    # state and arithmetic are FP32: the FP32 solve gate applies to the objective
+    assert np.max(np.abs(res["objective"] - oo) / np.abs(oo)) <= F32_SOLVE_TOL_OBJ
 
 
 def test_zero_data_keeps_zero_solution(disks):
