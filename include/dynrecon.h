@@ -162,6 +162,28 @@ dr_status dyn_radon_fwd(dr_plan *plan, const void *u, void *g);
 dr_status dyn_radon_adj(dr_plan *plan, const void *g, void *u, double beta);
 
 /*
+ * dyn_radon_adj for callers that may not allocate device memory at call
+ * time -- code running while a stream is captured into a CUDA graph, or
+ * applications whose memory policy forbids allocations after start-up.
+ * The paper has no counterpart; it is a deployment variant.
+ *     u_j[z] = beta * u_j[z] + sum_k phi_j(t_k) (R*_{theta_k} g[z][k])
+ * computed by the half-turn fold, the same operator as dyn_radon_adj.
+ * Instead of the plan's lazily allocated buffer, the folded data live in a
+ * fixed 8 MiB (8388608-byte) device array inside the library, which every
+ * GPU that loads the library holds until the process exits.  Requires an
+ * F32 or BF16 plan with the fold available, the plan's device current, and
+ * nz * U * ns * MS * 4 <= 8388608 bytes (U = distinct angles mod pi; MS =
+ * 4 for m <= 4, 12 for m <= 12, 20 for m <= 16, 28 for m <= 24, 36 for
+ * m <= 32): larger problems get DR_EINVAL with the size in dr_last_error();
+ * call it per slab of slices instead.  Calls no cudaMalloc/cudaFree.  The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture.  All calls share the
+ * array: calls whose work overlaps on the GPU (other streams or threads)
+ * race; calls in order on one stream are safe.  Asynchronous.
+ */
+dr_status dyn_radon_adj_noalloc(dr_plan *plan, const void *g, void *u, double beta);
+
+/*
  * 4D gradient of the synthesised frames, D = nabla_{lambda2} o PhiF
  * (Eq. TV1; frames f(t_l) = sum_j phi_j(t_l) u_j):  p = D u.
  * u: device [nz][ny][nx][m]; p: device [nz][ny][nx][nt][4] (overwritten).

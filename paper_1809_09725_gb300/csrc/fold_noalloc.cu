@@ -1,0 +1,125 @@
+// fold_noalloc.cu -- the half-turn folded back-projection for callers that
+// must not allocate device memory at call time.
+//
+// dyn_radon_adj with the fold variant keeps its folded data in a buffer the
+// plan allocates with cudaMalloc on first use.  Some callers cannot allow
+// that: code running while a stream is being captured into a CUDA graph
+// (an allocation inside a capture fails or breaks it), and applications
+// whose memory policy forbids any allocation after start-up (a fixed device
+// memory budget handed out by their own pool).  dyn_radon_adj_noalloc does
+// the same computation with the folded data in a fixed file-scope device
+// array instead, and allocates nothing.
+//
+// The array costs kNoAllocBytes of device memory on every GPU that loads
+// this library, for the life of the process.  All calls in the process share
+// it, so two calls whose work overlaps on the GPU (different streams, or
+// different host threads) race on it; calls issued in order on one stream
+// are safe.  Every call overwrites the part it uses completely before
+// reading it, so nothing has to start at zero.
+#include <algorithm>
+#include <cmath>
+#include <mutex>
+
+#include "fold_impl.cuh"
+
+namespace dr {
+
+// 8 MiB of folded data: nz * U * ns * MS floats (MS = m padded, see fold_ms).
+constexpr size_t kNoAllocBytes = size_t(8) << 20;
+constexpr size_t kNoAllocFloats = kNoAllocBytes / sizeof(float);
+
+static __device__ __align__(256) float g_noalloc_fold_scratch[kNoAllocFloats];
+
+// Device address of the array, looked up once per device (with that device
+// current) and cached; host code must not use the symbol itself as a
+// device pointer.
+constexpr int kMaxDevices = 64;
+static std::mutex g_noalloc_mutex;
+static float *g_noalloc_ptr[kMaxDevices];
+
+static dr_status noalloc_scratch(int device, float **out) {
+    if (device < 0 || device >= kMaxDevices) return fail(DR_EINVAL, "dyn_radon_adj_noalloc: device index out of range");
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[device]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_fold_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "dyn_radon_adj_noalloc: cudaGetSymbolAddress");
+        g_noalloc_ptr[device] = static_cast<float *>(p);
+    }
+    *out = g_noalloc_ptr[device];
+    return DR_OK;
+}
+
+template <typename S, int M>
+static dr_status noalloc_adj_t(dr_plan *P, const void *g, void *u, double beta, float *scratch, cudaStream_t st) {
+    typedef float T;
+    constexpr int MS = fold_ms(M);
+    fold_data_kernel<S, T, M><<<red_grid((size_t)P->nz * P->fold_U * P->ns), kRedThreads, 0, st>>>(
+        (const S *)g, scratch, P->d_fold_start, P->d_fold_member, (const T *)P->d_PhiP, P->nz, P->fold_U, P->ns, P->K,
+        P->MP);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "dyn_radon_adj_noalloc: fold_data_kernel launch");
+    const int Wb = fold_adj_wb(M);
+    CUtensorMap tm{};
+    const uint64_t dims[3] = {(uint64_t)MS, (uint64_t)P->ns, (uint64_t)P->nz * P->fold_U};
+    const uint64_t strides[2] = {(uint64_t)MS * sizeof(T), (uint64_t)P->ns * MS * sizeof(T)};
+    const uint32_t box[3] = {(uint32_t)MS, (uint32_t)Wb, 1};
+    if (!encode_tensor_map(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, scratch, dims, strides, box))
+        return fail(DR_ECUDA, "dyn_radon_adj_noalloc: tensor map encode failed");
+    const size_t row_bytes = ((size_t)Wb * MS * sizeof(T) + 127) & ~(size_t)127;
+    const size_t stage = kFoldAdjP * row_bytes + 128 * ((kFoldAdjP * sizeof(FoldPrm) + 127) / 128);
+    const size_t smem = stage * kFoldAdjStages + 128;
+    auto kern = fold_adj_kernel<S, T, M>;
+    if (smem > 48 * 1024) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return cuda_fail(e, "dyn_radon_adj_noalloc: smem attribute");
+    }
+    constexpr int TX = FoldAdjShape<M>::TX;
+    const int ntx = (P->nx + TX - 1) / TX, nty = (P->ny + kAdjTY - 1) / kAdjTY;
+    dim3 grid(ntx * nty, P->nz);
+    kern<<<grid, kAdjThreads, smem, st>>>(tm, P->d_fold_adj, (S *)u, nullptr, P->nx, P->ny, P->fold_U, P->m, Wb,
+                                          1.0f, (float)beta, P->d_status);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? DR_OK : cuda_fail(e, "dyn_radon_adj_noalloc: fold_adj_kernel launch");
+}
+
+template <typename S>
+static dr_status noalloc_dispatch(dr_plan *P, const void *g, void *u, double beta, float *scratch, cudaStream_t st) {
+    switch (P->M) {
+        case 1: return noalloc_adj_t<S, 1>(P, g, u, beta, scratch, st);
+        case 2: return noalloc_adj_t<S, 2>(P, g, u, beta, scratch, st);
+        case 4: return noalloc_adj_t<S, 4>(P, g, u, beta, scratch, st);
+        case 8: return noalloc_adj_t<S, 8>(P, g, u, beta, scratch, st);
+        case 12: return noalloc_adj_t<S, 12>(P, g, u, beta, scratch, st);
+        case 16: return noalloc_adj_t<S, 16>(P, g, u, beta, scratch, st);
+        case 24: return noalloc_adj_t<S, 24>(P, g, u, beta, scratch, st);
+        case 32: return noalloc_adj_t<S, 32>(P, g, u, beta, scratch, st);
+    }
+    return fail(DR_EINVAL, "dyn_radon_adj_noalloc: unsupported m");
+}
+
+}  // namespace dr
+
+using namespace dr;
+
+extern "C" dr_status dyn_radon_adj_noalloc(dr_plan *P, const void *g, void *u, double beta) {
+    clear_error();
+    if (!P || !g || !u) return fail(DR_EINVAL, "dyn_radon_adj_noalloc: NULL argument");
+    if (!std::isfinite(beta)) return fail(DR_EINVAL, "dyn_radon_adj_noalloc: beta must be finite");
+    if (P->prec == DR_F64 || P->fold_U == 0)
+        return fail(DR_EINVAL, "dyn_radon_adj_noalloc: needs an F32 or BF16 plan (the half-turn fold)");
+    const size_t need = sizeof(float) * (size_t)P->nz * P->fold_U * P->ns * fold_ms(P->M);
+    if (need > kNoAllocBytes)
+        return fail(DR_EINVAL, "dyn_radon_adj_noalloc: folded data needs " + std::to_string(need) +
+                                   " bytes, more than the fixed " + std::to_string(kNoAllocBytes) +
+                                   "-byte scratch array (use fewer slices per call)");
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "dyn_radon_adj_noalloc: cudaGetDevice");
+    if (dev != P->device) return fail(DR_EINVAL, "dyn_radon_adj_noalloc: the plan's device must be current");
+    float *scratch = nullptr;
+    dr_status s = noalloc_scratch(dev, &scratch);
+    if (s != DR_OK) return s;
+    if (P->prec == DR_BF16_F32ACC) return noalloc_dispatch<bf16>(P, g, u, beta, scratch, P->stream);
+    return noalloc_dispatch<float>(P, g, u, beta, scratch, P->stream);
+}

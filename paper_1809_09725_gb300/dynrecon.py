@@ -30,7 +30,7 @@ _STATUS = {DR_EINVAL: "EINVAL", DR_ENOMEM: "ENOMEM", DR_ECUDA: "ECUDA", DR_ETIME
 # Every symbol include/dynrecon.h declares.
 EXPORTS = ("dr_plan_create", "dr_plan_destroy", "dr_plan_set_stream", "dr_plan_device_bytes",
            "dr_plan_workspace_bytes", "dr_plan_sync", "dr_plan_set_variant", "dr_plan_autotune", "dr_plan_info",
-           "dyn_radon_fwd", "dyn_radon_adj", "tv4d_grad", "tv4d_grad_adj", "tv4d_prox",
+           "dyn_radon_fwd", "dyn_radon_adj", "dyn_radon_adj_noalloc", "tv4d_grad", "tv4d_grad_adj", "tv4d_prox",
            "dr_solve_params_default", "admm_solve", "dr_last_error", "dr_version")
 
 DIRECT, FOLD, AUTO = 0, 1, -1
@@ -81,6 +81,7 @@ def load(path: str = LIB_PATH):
         "dr_plan_info": (i, [vp, ctypes.POINTER(PlanInfo)]),
         "dyn_radon_fwd": (i, [vp, vp, vp]),
         "dyn_radon_adj": (i, [vp, vp, vp, d]),
+        "dyn_radon_adj_noalloc": (i, [vp, vp, vp, d]),
         "tv4d_grad": (i, [vp, vp, vp, d]),
         "tv4d_grad_adj": (i, [vp, vp, vp, d, d]),
         "tv4d_prox": (i, [vp, vp, vp, vp, d, d, d, pd]),
@@ -238,6 +239,16 @@ def dyn_radon_adj(plan: Plan, g, u, beta: float = 0.0):
     plan.use_current_stream()
     _check(load().dyn_radon_adj(plan.handle, _ptr(g, plan.storage_dtype, plan.g_shape(), "g"),
                                 _ptr(u, plan.storage_dtype, plan.u_shape(), "u"), float(beta)))
+    return u
+
+
+def dyn_radon_adj_noalloc(plan: Plan, g, u, beta: float = 0.0):
+    """u = beta u + R* g by the half-turn fold, with the folded data in the
+    library's fixed 8 MiB device array: allocates no device memory (for
+    callers inside a stream capture or under a no-allocation policy)."""
+    plan.use_current_stream()
+    _check(load().dyn_radon_adj_noalloc(plan.handle, _ptr(g, plan.storage_dtype, plan.g_shape(), "g"),
+                                        _ptr(u, plan.storage_dtype, plan.u_shape(), "u"), float(beta)))
     return u
 
 
