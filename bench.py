@@ -53,6 +53,10 @@ def parse():
     ap.add_argument("--workload", default="ellipsoids256")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-jobs", type=int, default=24)
+    ap.add_argument("--variant", default=None,
+                    help="force projector variants 'fwd,adj' (0 direct, 1 fold); default: autotuned")
     ap.add_argument("--profile-small", action="store_true",
                     help="run only a few operator launches of a 2-slice cut (for ncu captures)")
     return ap.parse_args()
@@ -154,6 +158,9 @@ def run_ours(a):
     g = torch.from_numpy(g_np.astype(np.float32)).to(dev)
     u = torch.zeros(plan.u_shape(), dtype=torch.float32, device=dev)
     units_per_iter = 2 * (w.n_cg + 1) * w.K * w.voxels()  # projector applications x K V
+    if a.variant:
+        fv, av = (int(x) for x in a.variant.split(","))
+        plan.set_variant(fv, av)
 
     if a.profile_small:
         # one forward and one adjoint of each variant (direct, half-turn fold)
@@ -196,7 +203,7 @@ def run_ours(a):
     # dominant kernels: time the projector pair alone on the same stream, in
     # the variant the solver selected (autotuned inside admm_solve)
     info = plan.info()
-    tune = plan.autotune()
+    tune = plan.autotune() if not a.variant else None
     p_in = torch.randn(plan.u_shape(), dtype=torch.float32, device=dev)
     gbuf = torch.empty(plan.g_shape(), dtype=torch.float32, device=dev)
     ubuf = torch.empty(plan.u_shape(), dtype=torch.float32, device=dev)
@@ -256,6 +263,10 @@ def run_ours(a):
                "step": "one %d-iteration reconstruction job via admm_solve on pinned host buffers" % w.iters,
                "jobs": jobs, "s_per_job": el / jobs}
 
+    serving = None
+    if not a.no_serving:
+        serving = {name: run_serving(a, local, prec) for name, prec in (("fp32", dr.F32), ("bf16", dr.BF16))}
+
     cpu = None
     if rank == 0 and not a.no_cpu_baseline:
         cpu = cpu_baseline(w, theta, t, g_np)
@@ -285,8 +296,73 @@ def run_ours(a):
                                       "autotune_ms_fwd_direct_fold_adj_direct_fold": tune},
                          "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz max SM clock"},
             "cpu_baseline": cpu,
+            "serving": serving,
         }
         print(json.dumps(line))
+
+
+def serving_jobs(n, seed=180905):
+    """A stream of uneven reconstruction requests: Poisson arrivals at 4 jobs/s;
+    grid 128 or 256, 4-16 slices, 4-20 continuous half-turns at 90 or 180
+    projections per half-turn, m in {4, 8, 16}, Fourier or Legendre, 30
+    ADMM-CG iterations; data are exact line integrals of 5 moving disks."""
+    from paper_1809_09725_gb300 import synth
+    rng = synth.rng_for(seed)
+    t_arr = np.cumsum(rng.exponential(1.0 / 4.0, size=n))
+    jobs = []
+    for i in range(n):
+        N = int(rng.choice([128, 256]))
+        nz = int(rng.integers(4, 17))
+        ht = int(rng.integers(4, 21))
+        per = int(rng.choice([90, 180]))
+        K = ht * per
+        m = int(rng.choice([4, 8, 16]))
+        basis = int(rng.integers(0, 2))
+        theta, t = synth.scan(K, ht)
+        blobs = synth.disks(rng, N, 5)
+        g = np.repeat(synth.sinogram(blobs, theta, t, N, 1), nz, axis=0)
+        jobs.append(dict(arrival=float(t_arr[i]), N=N, nz=nz, K=K, m=m, basis=basis, nt=ht, theta=theta, t=t,
+                         g=g))
+    return jobs
+
+
+def run_serving(a, device, prec):
+    """Submit the request stream to the serving loop in real time; report
+    latency percentiles and aggregate projector throughput."""
+    from paper_1809_09725_gb300 import dynrecon as dr
+    jobs = serving_jobs(a.serving_jobs)
+    descs = []
+    for j in jobs:
+        if prec == dr.BF16:
+            import torch
+            gh = torch.from_numpy(j["g"]).to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16)
+            uh = np.zeros((j["nz"], j["N"], j["N"], j["m"]), dtype=np.uint16)
+        else:
+            gh = j["g"].astype(np.float32)
+            uh = np.zeros((j["nz"], j["N"], j["N"], j["m"]), dtype=np.float32)
+        prm = dr.solve_params(dr.ADMM_CG, iters=30, n_cg=4, lambda1=1e-3, lambda2=1.0, rho=1e-2)
+        descs.append(dr.job_desc(j["N"], j["N"], j["nz"], j["N"], j["theta"], j["t"], j["basis"], j["m"], j["nt"],
+                                 prec, prm, gh, uh))
+    srv = dr.Server(device=device, budget_bytes=150 * 10 ** 9, slots=8)
+    t0 = time.perf_counter()
+    ids = []
+    for j, d in zip(jobs, descs):
+        dt = j["arrival"] - (time.perf_counter() - t0)
+        if dt > 0:
+            time.sleep(dt)
+        ids.append(srv.submit(d))
+    res = [srv.wait(i, timeout_s=600.0) for i in ids]
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    units = sum(2 * 5 * 30 * j["K"] * j["N"] * j["N"] * j["nz"] for j in jobs)
+    return {"jobs": len(jobs), "completed": st["completed"], "failed": st["failed"],
+            "p50_latency_s": st["p50_latency_s"], "p99_latency_s": st["p99_latency_s"],
+            "voxel_projection_per_s": units / wall, "wall_s": wall,
+            "peak_device_gb": st["peak_device_bytes"] / 1e9, "budget_gb": 150,
+            "stream": "Poisson 4 jobs/s, first %d arrivals; N in {128,256}, nz 4-16, K 360-3600 over 4-20 "
+                      "half-turns, m in {4,8,16}, 30 ADMM-CG iterations" % len(jobs),
+            "max_queue_s": max(r["queue_s"] for r in res)}
 
 
 def load_traffic(kernel):

@@ -243,6 +243,87 @@ void dr_solve_params_default(dr_solve_params *params);
  */
 dr_status admm_solve(dr_plan *plan, const void *g, void *u, const dr_solve_params *params);
 
+/*
+ * Several independent reconstructions at once (uneven sizes, bases,
+ * precisions and iteration counts allowed).  Job j solves Eq. (lr12) for
+ * plans[j], g[j], u[j], params[j] exactly as admm_solve would; the first
+ * iteration of every job runs eagerly, then each iteration of all jobs still
+ * running is replayed as ONE CUDA graph with one branch per job (forked from
+ * a root stream and joined back), so the jobs' kernels overlap on the
+ * device.  Each job keeps its own plan workspace, scalars and reduction
+ * order, so its result is bit-for-bit that of a separate admm_solve call.
+ * Plans must be distinct and on the same device; arrays have njobs entries.
+ * Synchronises before returning.
+ */
+dr_status admm_solve_batch(int njobs, dr_plan *const *plans, const void *const *g, void *const *u,
+                           const dr_solve_params *params);
+
+/* ------------------------------------------------------------------------ */
+/* Serving: a request loop with device-memory-budget admission.             */
+/* ------------------------------------------------------------------------ */
+typedef struct dr_server dr_server;
+
+enum { DR_JOB_QUEUED = 0, DR_JOB_RUNNING = 1, DR_JOB_DONE = 2, DR_JOB_FAILED = 3, DR_JOB_CANCELED = 4 };
+
+/* One reconstruction request.  theta and t are copied at submission; g, u
+ * and the output pointers inside params (host or device memory) are the
+ * caller's and must stay valid until the job has finished. */
+typedef struct {
+    int nx, ny, nz, ns, K;
+    const double *theta;    /* [K] radians */
+    const double *t;        /* [K] in [0, 1) */
+    dr_basis basis;
+    int m, nt;
+    dr_precision prec;
+    dr_solve_params params;
+    const void *g;          /* [nz][K][ns] data */
+    void *u;                /* [nz][ny][nx][m] initial guess in, result out */
+} dr_job_desc;
+
+typedef struct {
+    int state;              /* DR_JOB_* */
+    dr_status status;
+    double latency_s;       /* completion - submission */
+    double queue_s;         /* start - submission */
+    size_t device_bytes;    /* memory the job was admitted with */
+} dr_job_result;
+
+typedef struct {
+    int64_t completed, failed, canceled, queued;
+    int active;
+    double p50_latency_s, p99_latency_s;
+    size_t peak_device_bytes, budget_bytes;
+    double voxel_projection_per_s;  /* projector work of completed jobs / busy span */
+} dr_server_stats_t;
+
+/* Device bytes a job is admitted with (host arithmetic only, no CUDA call):
+ * plan tables, reduction slots, folded-data scratch, solver workspace and
+ * the staging copies of host inputs. */
+size_t dr_job_device_bytes(const dr_job_desc *desc);
+
+/* Start a server on `device` with `slots` worker threads (jobs that may run
+ * at once) and a device-memory budget in bytes for all running jobs. */
+dr_status dr_server_create(dr_server **out, int device, size_t budget_bytes, int slots);
+
+/* Queue a job; returns its id.  DR_ENOMEM if it cannot fit the budget even
+ * alone.  Queued jobs are admitted in order, a later job that fits may pass
+ * a head job that does not (backfill); admitted jobs keep all their state on
+ * the device and run concurrently, each with its own plan and stream. */
+dr_status dr_server_submit(dr_server *server, const dr_job_desc *desc, int64_t *job_id);
+
+/* Cancel a job that has not started (DR_EINVAL once it runs). */
+dr_status dr_server_cancel(dr_server *server, int64_t job_id);
+
+/* Wait up to timeout_s seconds (< 0: no limit) for a job; fills res
+ * (nullable) and returns the job's status (DR_ETIMEOUT if still running). */
+dr_status dr_server_wait(dr_server *server, int64_t job_id, double timeout_s, dr_job_result *res);
+
+/* Counters and latency percentiles of completed jobs. */
+dr_status dr_server_stats(dr_server *server, dr_server_stats_t *stats);
+
+/* Finish all queued and running jobs, stop the workers, free the server. */
+dr_status dr_server_destroy(dr_server *server);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char *dr_last_error(void);
 

@@ -26,7 +26,7 @@ namespace dr {
 
 constexpr int kFoldThreads = 256;
 constexpr int kFoldAdjP = 8;       // unique angles per adjoint pipeline stage
-constexpr int kFoldAdjStages = 3;
+constexpr int kFoldAdjStages = 2;
 
 // Padded coefficient stride in shared memory and in the folded data:
 // multiples of 4 floats (16-byte vectors, TMA rows) whose pattern of

@@ -298,13 +298,32 @@ static dr_status convert(const void *in, void *out, size_t n, cudaStream_t st) {
     return launched("convert_kernel");
 }
 
-static dr_status solve(dr_plan *P, const void *g_in, void *u_io, const dr_solve_params &prm) {
+// Per-call solver state: which device buffers hold g and u, step sizes.
+struct SolveCtx {
+    dr_solve_params prm;
+    const void *g_in = nullptr;
+    void *u_io = nullptr;
+    const void *g = nullptr;  // compute-typed device copy or the caller's buffer
+    void *u = nullptr;
+    bool g_dev = false, u_dev = false, bf = false, want_obj = false;
+    double rho = 0.0, sigma = 0.0, tau = 0.0, L = 0.0;
+    int done = 0;             // iterations issued
+};
+
+// Stage inputs, reset the state, run the Chambolle-Pock power iteration.
+static dr_status solve_begin(dr_plan *P, const void *g_in, void *u_io, const dr_solve_params &prm, SolveCtx &c) {
     const cudaStream_t st = P->graph_stream;
     Workspace &w = P->ws;
     const size_t nu = nu_elems(P), ng = ng_elems(P), nf = nf_elems(P);
     const size_t es = elem_size(P->prec), cs = calc_size(P->prec);
-    const bool bf = P->prec == DR_BF16_F32ACC;
-    const bool g_dev = is_device_ptr(g_in), u_dev = is_device_ptr(u_io);
+    c.prm = prm;
+    c.g_in = g_in;
+    c.u_io = u_io;
+    c.bf = P->prec == DR_BF16_F32ACC;
+    c.g_dev = is_device_ptr(g_in);
+    c.u_dev = is_device_ptr(u_io);
+    c.want_obj = prm.objective_out != nullptr;
+    c.done = 0;
 
     DR_CUDA_TRY(cudaEventRecord(P->ev_a, P->stream));
     DR_CUDA_TRY(cudaStreamWaitEvent(st, P->ev_a, 0));
@@ -312,35 +331,33 @@ static dr_status solve(dr_plan *P, const void *g_in, void *u_io, const dr_solve_
     if (!P->tuned) TRY(autotune(P, w.q, w.gd));
 
     // ---- bring g and u into compute-typed device buffers ----
-    const void *g = g_in;
-    void *u = u_io;
-    if (!g_dev || bf) {
+    c.g = g_in;
+    c.u = u_io;
+    if (!c.g_dev || c.bf) {
         void *src = (void *)g_in;
-        if (!g_dev) {
-            // host data: copy raw storage-typed bytes, then convert in place if needed
-            void *stage = bf ? w.gd : w.g_dev;  // gd is large enough (ng * cs >= ng * es)
+        if (!c.g_dev) {
+            // host data: copy raw storage-typed bytes, then convert if needed
+            void *stage = c.bf ? w.gd : w.g_dev;  // gd is large enough (ng * cs >= ng * es)
             DR_CUDA_TRY(cudaMemcpyAsync(stage, g_in, ng * es, cudaMemcpyHostToDevice, st));
             src = stage;
         }
-        if (bf) TRY(convert<bf16, float>(src, w.g_dev, ng, st));
-        g = w.g_dev;
+        if (c.bf) TRY(convert<bf16, float>(src, w.g_dev, ng, st));
+        c.g = w.g_dev;
     }
-    if (!u_dev || bf) {
+    if (!c.u_dev || c.bf) {
         void *src = u_io;
-        if (!u_dev) {
-            void *stage = bf ? w.q : w.u_dev;
+        if (!c.u_dev) {
+            void *stage = c.bf ? w.q : w.u_dev;
             DR_CUDA_TRY(cudaMemcpyAsync(stage, u_io, nu * es, cudaMemcpyHostToDevice, st));
             src = stage;
         }
-        if (bf) TRY(convert<bf16, float>(src, w.u_dev, nu, st));
-        u = w.u_dev;
+        if (c.bf) TRY(convert<bf16, float>(src, w.u_dev, nu, st));
+        c.u = w.u_dev;
     }
 
     DR_CUDA_TRY(cudaMemsetAsync(P->d_scal, 0, sizeof(DevScalars), st));
     DR_CUDA_TRY(cudaMemsetAsync(w.obj, 0, sizeof(double) * 3 * (size_t)(prm.iters + 1), st));
-    const bool want_obj = prm.objective_out != nullptr;
-    double rho = prm.rho > 0.0 ? prm.rho : (prm.lambda1 > 0.0 ? 10.0 * prm.lambda1 : 1.0);
-    double sigma = 0.0, tau = 0.0, L = 0.0;
+    c.rho = prm.rho > 0.0 ? prm.rho : (prm.lambda1 > 0.0 ? 10.0 * prm.lambda1 : 1.0);
 
     if (prm.algo == DR_ADMM_CG) {
         DR_CUDA_TRY(cudaMemsetAsync(w.mu, 0, nf * cs, st));
@@ -349,66 +366,52 @@ static dr_status solve(dr_plan *P, const void *g_in, void *u_io, const dr_solve_
         DR_CUDA_TRY(cudaMemsetAsync(w.h1, 0, ng * cs, st));
         DR_CUDA_TRY(cudaMemsetAsync(w.mu, 0, nf * cs, st));
         const int pit = prm.power_iters > 0 ? prm.power_iters : 100;
-        TRY(power_norm(P, prm.lambda2, pit, &L, st));
-        if (!(L > 0.0) || !std::isfinite(L)) return fail(DR_EINVAL, "admm_solve: operator norm is zero");
-        sigma = tau = 0.99 / L;
-        if (prm.op_norm_out) *prm.op_norm_out = L;
-        DR_CUDA_TRY(cudaMemcpyAsync(w.ut, u, nu * cs, cudaMemcpyDeviceToDevice, st));
+        TRY(power_norm(P, prm.lambda2, pit, &c.L, st));
+        if (!(c.L > 0.0) || !std::isfinite(c.L)) return fail(DR_EINVAL, "admm_solve: operator norm is zero");
+        c.sigma = c.tau = 0.99 / c.L;
+        if (prm.op_norm_out) *prm.op_norm_out = c.L;
+        DR_CUDA_TRY(cudaMemcpyAsync(w.ut, c.u, nu * cs, cudaMemcpyDeviceToDevice, st));
         iter_kernel<<<1, 1, 0, st>>>(P->d_scal, 1, 0);
         TRY(launched("iter_kernel"));
     }
+    return DR_OK;
+}
 
-    auto one = [&](cudaStream_t s) -> dr_status {
-        if (prm.algo == DR_ADMM_CG) return admm_iteration(P, u, g, prm, rho, s);
-        return cp_iteration(P, u, g, prm, sigma, tau, want_obj, s);
-    };
-    if (prm.iters > 0) {
-        // first iteration eagerly (sets kernel attributes), the rest as one graph
-        TRY(one(st));
-        if (prm.iters > 1) {
-            cudaGraph_t graph = nullptr;
-            cudaGraphExec_t exec = nullptr;
-            DR_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-            dr_status cs_st = one(st);
-            cudaError_t ce = cudaStreamEndCapture(st, &graph);
-            if (cs_st != DR_OK) {
-                if (graph) cudaGraphDestroy(graph);
-                return cs_st;
-            }
-            if (ce != cudaSuccess) return cuda_fail(ce, "admm_solve: graph capture");
-            ce = cudaGraphInstantiate(&exec, graph, 0);
-            if (ce != cudaSuccess) {
-                cudaGraphDestroy(graph);
-                return cuda_fail(ce, "admm_solve: graph instantiate");
-            }
-            for (int it = 1; it < prm.iters && ce == cudaSuccess; ++it) ce = cudaGraphLaunch(exec, st);
-            cudaGraphExecDestroy(exec);
-            cudaGraphDestroy(graph);
-            if (ce != cudaSuccess) return cuda_fail(ce, "admm_solve: graph launch");
-        }
-        if (prm.algo == DR_ADMM_CG && (want_obj)) {
-            // fidelity of the final u (row iters)
-            TRY(launch_fwd_calc(P, u, w.gd, g, 1, 0.0, st));
-            TRY(dot(P, w.gd, w.gd, ng, kSlotFid, w.obj, 0, 0, 0, st));
-        }
+// Launch one iteration of the chosen algorithm on stream s.
+static dr_status solve_iter(dr_plan *P, SolveCtx &c, cudaStream_t s) {
+    if (c.prm.algo == DR_ADMM_CG) return admm_iteration(P, c.u, c.g, c.prm, c.rho, s);
+    return cp_iteration(P, c.u, c.g, c.prm, c.sigma, c.tau, c.want_obj, s);
+}
+
+// Final objective row, results back to the caller's buffers, status check.
+static dr_status solve_end(dr_plan *P, SolveCtx &c) {
+    const cudaStream_t st = P->graph_stream;
+    Workspace &w = P->ws;
+    const dr_solve_params &prm = c.prm;
+    const size_t nu = nu_elems(P), ng = ng_elems(P);
+    const size_t es = elem_size(P->prec), cs = calc_size(P->prec);
+    if (prm.iters > 0 && prm.algo == DR_ADMM_CG && c.want_obj) {
+        // fidelity of the final u (row iters)
+        TRY(launch_fwd_calc(P, c.u, w.gd, c.g, 1, 0.0, st));
+        TRY(dot(P, w.gd, w.gd, ng, kSlotFid, w.obj, 0, 0, 0, st));
     }
-
-    // ---- results back ----
-    if (!u_dev || bf) {
-        void *dst = u_io;
-        if (bf) {
-            void *tmp = u_dev ? u_io : (void *)w.q;
-            TRY(convert<float, bf16>(u, tmp, nu, st));
-            if (!u_dev) DR_CUDA_TRY(cudaMemcpyAsync(dst, tmp, nu * es, cudaMemcpyDeviceToHost, st));
+    if (!c.u_dev || c.bf) {
+        void *dst = c.u_io;
+        if (c.bf) {
+            void *tmp = c.u_dev ? c.u_io : (void *)w.q;
+            TRY(convert<float, bf16>(c.u, tmp, nu, st));
+            if (!c.u_dev) DR_CUDA_TRY(cudaMemcpyAsync(dst, tmp, nu * es, cudaMemcpyDeviceToHost, st));
         } else {
-            DR_CUDA_TRY(cudaMemcpyAsync(dst, u, nu * cs, cudaMemcpyDeviceToHost, st));
+            DR_CUDA_TRY(cudaMemcpyAsync(dst, c.u, nu * cs, cudaMemcpyDeviceToHost, st));
         }
     }
     std::vector<double> obj;
-    if (prm.iters > 0 && (want_obj || prm.primal_res_out)) {
+    if (prm.iters > 0 && (c.want_obj || prm.primal_res_out)) {
         obj.resize(3 * (size_t)(prm.iters + 1));
         DR_CUDA_TRY(cudaMemcpyAsync(obj.data(), w.obj, sizeof(double) * obj.size(), cudaMemcpyDeviceToHost, st));
     }
+    DevScalars hs;
+    DR_CUDA_TRY(cudaMemcpyAsync(&hs, P->d_scal, sizeof(hs), cudaMemcpyDeviceToHost, st));
     DR_CUDA_TRY(cudaEventRecord(P->ev_b, st));
     DR_CUDA_TRY(cudaStreamWaitEvent(P->stream, P->ev_b, 0));
     DR_CUDA_TRY(cudaStreamSynchronize(st));
@@ -418,12 +421,132 @@ static dr_status solve(dr_plan *P, const void *g_in, void *u_io, const dr_solve_
         cudaMemset(P->d_status, 0, sizeof(int));
         return fail(DR_ETIMEOUT, "admm_solve: a bounded device-side wait gave up");
     }
+    bool finite = std::isfinite(hs.rr) && std::isfinite(hs.alpha) && std::isfinite(hs.beta);
     for (int it = 0; it < prm.iters && !obj.empty(); ++it) {
         const double *row = &obj[3 * (size_t)(it + 1)];
-        if (want_obj) prm.objective_out[it] = 0.5 * row[0] + prm.lambda1 * row[1];
+        if (c.want_obj) prm.objective_out[it] = 0.5 * row[0] + prm.lambda1 * row[1];
         if (prm.primal_res_out) prm.primal_res_out[it] = std::sqrt(row[2]);
+        if (c.want_obj && !std::isfinite(prm.objective_out[it])) finite = false;
     }
-    (void)rho;
+    if (!finite) return fail(DR_ENOTCONV, "admm_solve: non-finite values (check the data for NaN/Inf)");
+    return DR_OK;
+}
+
+// Capture `body` (launches on per-job streams) as one graph on stream `root`.
+template <typename F>
+static dr_status capture_graph(cudaStream_t root, F body, cudaGraphExec_t *exec) {
+    cudaGraph_t graph = nullptr;
+    DR_CUDA_TRY(cudaStreamBeginCapture(root, cudaStreamCaptureModeThreadLocal));
+    dr_status st = body();
+    cudaError_t ce = cudaStreamEndCapture(root, &graph);
+    if (st != DR_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    if (ce != cudaSuccess) return cuda_fail(ce, "graph capture");
+    ce = cudaGraphInstantiate(exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) return cuda_fail(ce, "graph instantiate");
+    return DR_OK;
+}
+
+static dr_status solve(dr_plan *P, const void *g_in, void *u_io, const dr_solve_params &prm) {
+    SolveCtx c;
+    TRY(solve_begin(P, g_in, u_io, prm, c));
+    const cudaStream_t st = P->graph_stream;
+    if (prm.iters > 0) {
+        // first iteration eagerly (sets kernel attributes, allocates lazily), the rest as one graph
+        TRY(solve_iter(P, c, st));
+        if (prm.iters > 1) {
+            cudaGraphExec_t exec = nullptr;
+            TRY(capture_graph(st, [&]() { return solve_iter(P, c, st); }, &exec));
+            cudaError_t ce = cudaSuccess;
+            for (int it = 1; it < prm.iters && ce == cudaSuccess; ++it) ce = cudaGraphLaunch(exec, st);
+            cudaGraphExecDestroy(exec);
+            if (ce != cudaSuccess) return cuda_fail(ce, "admm_solve: graph launch");
+        }
+    }
+    return solve_end(P, c);
+}
+
+// Several independent reconstructions: each iteration of all active jobs is
+// one CUDA graph with one branch per job (fork from a root stream, join back),
+// so the jobs' kernels overlap on the device.  Every job keeps its own plan,
+// workspace, scalars and reduction slots, so its result is the same as alone.
+static dr_status solve_batch(int n, dr_plan *const *plans, const void *const *g, void *const *u,
+                             const dr_solve_params *prm) {
+    std::vector<SolveCtx> c(n);
+    for (int j = 0; j < n; ++j) TRY(solve_begin(plans[j], g[j], u[j], prm[j], c[j]));
+    for (int j = 0; j < n; ++j)
+        if (prm[j].iters > 0) {
+            TRY(solve_iter(plans[j], c[j], plans[j]->graph_stream));
+            c[j].done = 1;
+        }
+    cudaStream_t root = nullptr;
+    DR_CUDA_TRY(cudaStreamCreateWithFlags(&root, cudaStreamNonBlocking));
+    std::vector<cudaEvent_t> ev(n + 1, nullptr);
+    dr_status result = DR_OK;
+    for (auto &e : ev)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) result = fail(DR_ECUDA, "batch events");
+    // the root stream starts after every job's eager iteration
+    for (int j = 0; j < n && result == DR_OK; ++j) {
+        if (cudaEventRecord(ev[j + 1], plans[j]->graph_stream) != cudaSuccess ||
+            cudaStreamWaitEvent(root, ev[j + 1], 0) != cudaSuccess)
+            result = fail(DR_ECUDA, "batch: join eager iterations");
+    }
+    while (result == DR_OK) {
+        std::vector<int> act;
+        int reps = 1 << 30;
+        for (int j = 0; j < n; ++j)
+            if (c[j].done < prm[j].iters) {
+                act.push_back(j);
+                reps = std::min(reps, prm[j].iters - c[j].done);
+            }
+        if (act.empty()) break;
+        cudaGraphExec_t exec = nullptr;
+        result = capture_graph(
+            root,
+            [&]() -> dr_status {
+                DR_CUDA_TRY(cudaEventRecord(ev[0], root));
+                for (int j : act) {
+                    DR_CUDA_TRY(cudaStreamWaitEvent(plans[j]->graph_stream, ev[0], 0));
+                    TRY(solve_iter(plans[j], c[j], plans[j]->graph_stream));
+                    DR_CUDA_TRY(cudaEventRecord(ev[j + 1], plans[j]->graph_stream));
+                    DR_CUDA_TRY(cudaStreamWaitEvent(root, ev[j + 1], 0));
+                }
+                return DR_OK;
+            },
+            &exec);
+        if (result != DR_OK) break;
+        cudaError_t ce = cudaSuccess;
+        for (int r = 0; r < reps && ce == cudaSuccess; ++r) ce = cudaGraphLaunch(exec, root);
+        cudaGraphExecDestroy(exec);
+        if (ce != cudaSuccess) {
+            result = cuda_fail(ce, "admm_solve_batch: graph launch");
+            break;
+        }
+        for (int j : act) c[j].done += reps;
+    }
+    // the jobs' own streams continue after the root stream's replays
+    if (result == DR_OK && cudaEventRecord(ev[0], root) != cudaSuccess) result = fail(DR_ECUDA, "batch: join");
+    for (int j = 0; j < n && result == DR_OK; ++j)
+        if (cudaStreamWaitEvent(plans[j]->graph_stream, ev[0], 0) != cudaSuccess) result = fail(DR_ECUDA, "batch: join");
+    for (int j = 0; j < n && result == DR_OK; ++j) result = solve_end(plans[j], c[j]);
+    cudaStreamSynchronize(root);
+    for (auto &e : ev)
+        if (e) cudaEventDestroy(e);
+    cudaStreamDestroy(root);
+    return result;
+}
+
+static dr_status check_params(const dr_solve_params &p) {
+    if (p.algo != DR_ADMM_CG && p.algo != DR_CHAMBOLLE_POCK) return fail(DR_EINVAL, "admm_solve: bad algo");
+    if (p.iters < 0 || (p.algo == DR_ADMM_CG && p.n_cg < 1)) return fail(DR_EINVAL, "admm_solve: bad iters/n_cg");
+    if (!(p.lambda1 >= 0.0) || !(p.lambda2 >= 0.0) || !std::isfinite(p.lambda1) || !std::isfinite(p.lambda2) ||
+        !std::isfinite(p.rho) || !std::isfinite(p.cp_theta))
+        return fail(DR_EINVAL, "admm_solve: lambdas must be finite and >= 0");
+    if (p.algo == DR_CHAMBOLLE_POCK && !(p.cp_theta >= 0.0 && p.cp_theta <= 1.0))
+        return fail(DR_EINVAL, "admm_solve: cp_theta must be in [0, 1]");
     return DR_OK;
 }
 
@@ -438,16 +561,24 @@ size_t dr_plan_workspace_bytes(const dr_plan *P, dr_algo algo) { return P ? ws_b
 dr_status admm_solve(dr_plan *P, const void *g, void *u, const dr_solve_params *prm) {
     clear_error();
     if (!P || !g || !u || !prm) return fail(DR_EINVAL, "admm_solve: NULL argument");
-    const dr_solve_params &p = *prm;
-    if (p.algo != DR_ADMM_CG && p.algo != DR_CHAMBOLLE_POCK) return fail(DR_EINVAL, "admm_solve: bad algo");
-    if (p.iters < 0 || (p.algo == DR_ADMM_CG && p.n_cg < 1)) return fail(DR_EINVAL, "admm_solve: bad iters/n_cg");
-    if (!(p.lambda1 >= 0.0) || !(p.lambda2 >= 0.0) || !std::isfinite(p.lambda1) || !std::isfinite(p.lambda2) ||
-        !std::isfinite(p.rho) || !std::isfinite(p.cp_theta))
-        return fail(DR_EINVAL, "admm_solve: lambdas must be finite and >= 0");
-    if (p.algo == DR_CHAMBOLLE_POCK && !(p.cp_theta >= 0.0 && p.cp_theta <= 1.0))
-        return fail(DR_EINVAL, "admm_solve: cp_theta must be in [0, 1]");
-    TRY(ensure_ws(P, p.algo, p.iters));
-    return solve(P, g, u, p);
+    TRY(check_params(*prm));
+    TRY(ensure_ws(P, prm->algo, prm->iters));
+    return solve(P, g, u, *prm);
+}
+
+dr_status admm_solve_batch(int njobs, dr_plan *const *plans, const void *const *g, void *const *u,
+                           const dr_solve_params *params) {
+    clear_error();
+    if (njobs < 1 || !plans || !g || !u || !params) return fail(DR_EINVAL, "admm_solve_batch: bad arguments");
+    for (int j = 0; j < njobs; ++j) {
+        if (!plans[j] || !g[j] || !u[j]) return fail(DR_EINVAL, "admm_solve_batch: NULL job entry");
+        if (plans[j]->device != plans[0]->device) return fail(DR_EINVAL, "admm_solve_batch: plans on different devices");
+        for (int i = 0; i < j; ++i)
+            if (plans[i] == plans[j]) return fail(DR_EINVAL, "admm_solve_batch: a plan appears twice");
+        TRY(check_params(params[j]));
+    }
+    for (int j = 0; j < njobs; ++j) TRY(ensure_ws(plans[j], params[j].algo, params[j].iters));
+    return solve_batch(njobs, plans, g, u, params);
 }
 
 }  // extern "C"

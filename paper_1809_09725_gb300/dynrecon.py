@@ -31,7 +31,11 @@ _STATUS = {DR_EINVAL: "EINVAL", DR_ENOMEM: "ENOMEM", DR_ECUDA: "ECUDA", DR_ETIME
 EXPORTS = ("dr_plan_create", "dr_plan_destroy", "dr_plan_set_stream", "dr_plan_device_bytes",
            "dr_plan_workspace_bytes", "dr_plan_sync", "dr_plan_set_variant", "dr_plan_autotune", "dr_plan_info",
            "dyn_radon_fwd", "dyn_radon_adj", "dyn_radon_adj_noalloc", "tv4d_grad", "tv4d_grad_adj", "tv4d_prox",
-           "dr_solve_params_default", "admm_solve", "dr_last_error", "dr_version")
+           "dr_solve_params_default", "admm_solve", "admm_solve_batch", "dr_job_device_bytes", "dr_server_create",
+           "dr_server_submit", "dr_server_cancel", "dr_server_wait", "dr_server_stats", "dr_server_destroy",
+           "dr_last_error", "dr_version")
+
+JOB_QUEUED, JOB_RUNNING, JOB_DONE, JOB_FAILED, JOB_CANCELED = 0, 1, 2, 3, 4
 
 DIRECT, FOLD, AUTO = 0, 1, -1
 
@@ -54,6 +58,26 @@ class SolveParams(ctypes.Structure):
                 ("objective_out", ctypes.POINTER(ctypes.c_double)),
                 ("primal_res_out", ctypes.POINTER(ctypes.c_double)),
                 ("op_norm_out", ctypes.POINTER(ctypes.c_double))]
+
+
+class JobDesc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("ns", ctypes.c_int),
+                ("K", ctypes.c_int), ("theta", ctypes.POINTER(ctypes.c_double)),
+                ("t", ctypes.POINTER(ctypes.c_double)), ("basis", ctypes.c_int), ("m", ctypes.c_int),
+                ("nt", ctypes.c_int), ("prec", ctypes.c_int), ("params", SolveParams), ("g", ctypes.c_void_p),
+                ("u", ctypes.c_void_p)]
+
+
+class JobResult(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int), ("status", ctypes.c_int), ("latency_s", ctypes.c_double),
+                ("queue_s", ctypes.c_double), ("device_bytes", ctypes.c_size_t)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_int64), ("failed", ctypes.c_int64), ("canceled", ctypes.c_int64),
+                ("queued", ctypes.c_int64), ("active", ctypes.c_int), ("p50_latency_s", ctypes.c_double),
+                ("p99_latency_s", ctypes.c_double), ("peak_device_bytes", ctypes.c_size_t),
+                ("budget_bytes", ctypes.c_size_t), ("voxel_projection_per_s", ctypes.c_double)]
 
 
 _lib = None
@@ -87,6 +111,15 @@ def load(path: str = LIB_PATH):
         "tv4d_prox": (i, [vp, vp, vp, vp, d, d, d, pd]),
         "dr_solve_params_default": (None, [ctypes.POINTER(SolveParams)]),
         "admm_solve": (i, [vp, vp, vp, ctypes.POINTER(SolveParams)]),
+        "admm_solve_batch": (i, [i, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                 ctypes.POINTER(SolveParams)]),
+        "dr_job_device_bytes": (sz, [ctypes.POINTER(JobDesc)]),
+        "dr_server_create": (i, [ctypes.POINTER(vp), i, sz, i]),
+        "dr_server_submit": (i, [vp, ctypes.POINTER(JobDesc), ctypes.POINTER(ctypes.c_int64)]),
+        "dr_server_cancel": (i, [vp, ctypes.c_int64]),
+        "dr_server_wait": (i, [vp, ctypes.c_int64, d, ctypes.POINTER(JobResult)]),
+        "dr_server_stats": (i, [vp, ctypes.POINTER(ServerStats)]),
+        "dr_server_destroy": (i, [vp]),
         "dr_last_error": (ctypes.c_char_p, []),
         "dr_version": (ctypes.c_char_p, []),
     }
@@ -316,3 +349,81 @@ def admm_solve(plan: Plan, g, u, params: SolveParams, want_objective: bool = Tru
 
 def version() -> str:
     return load().dr_version().decode()
+
+
+def admm_solve_batch(plans, gs, us, params_list):
+    """Solve several independent jobs together: one CUDA graph per iteration
+    with one branch per job (results equal separate admm_solve calls)."""
+    n = len(plans)
+    for p in plans:
+        p.use_current_stream()
+    hp = (ctypes.c_void_p * n)(*[p.handle.value for p in plans])
+    hg = (ctypes.c_void_p * n)(*[_ptr(g, p.storage_dtype, p.g_shape(), "g").value for p, g in zip(plans, gs)])
+    hu = (ctypes.c_void_p * n)(*[_ptr(u, p.storage_dtype, p.u_shape(), "u").value for p, u in zip(plans, us)])
+    prm = (SolveParams * n)(*params_list)
+    _check(load().admm_solve_batch(n, hp, hg, hu, prm))
+
+
+def job_desc(nx, ny, nz, ns, theta, t, basis, m, nt, prec, params: SolveParams, g, u) -> JobDesc:
+    """Describe a reconstruction request (g, u: host numpy arrays or device tensors,
+    kept alive by the caller until the job finishes)."""
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    tt = np.ascontiguousarray(t, dtype=np.float64)
+    pd = ctypes.POINTER(ctypes.c_double)
+    d = JobDesc()
+    d.nx, d.ny, d.nz, d.ns, d.K = int(nx), int(ny), int(nz), int(ns), th.size
+    d.theta, d.t = th.ctypes.data_as(pd), tt.ctypes.data_as(pd)
+    d.basis, d.m, d.nt, d.prec = int(basis), int(m), int(nt), int(prec)
+    d.params = params
+    dt = _DTYPES[int(prec)]
+    d.g = _ptr(g, dt, (nz, th.size, ns), "g").value
+    d.u = _ptr(u, dt, (nz, ny, nx, m), "u").value
+    d._keep = (th, tt, g, u)
+    return d
+
+
+def job_device_bytes(desc: JobDesc) -> int:
+    return load().dr_job_device_bytes(ctypes.byref(desc))
+
+
+class Server:
+    """Request loop: jobs are admitted under a device-memory budget and run
+    concurrently (one worker thread, plan and stream per running job)."""
+
+    def __init__(self, device: int = 0, budget_bytes: int = 1 << 30, slots: int = 4):
+        self._h = ctypes.c_void_p()
+        _check(load().dr_server_create(ctypes.byref(self._h), int(device), int(budget_bytes), int(slots)))
+        self._descs = {}
+
+    def submit(self, desc: JobDesc) -> int:
+        jid = ctypes.c_int64(0)
+        _check(load().dr_server_submit(self._h, ctypes.byref(desc), ctypes.byref(jid)))
+        self._descs[jid.value] = desc
+        return jid.value
+
+    def cancel(self, job_id: int):
+        _check(load().dr_server_cancel(self._h, ctypes.c_int64(job_id)))
+
+    def wait(self, job_id: int, timeout_s: float = -1.0) -> dict:
+        r = JobResult()
+        st = load().dr_server_wait(self._h, ctypes.c_int64(job_id), float(timeout_s), ctypes.byref(r))
+        out = {f: getattr(r, f) for f, _ in JobResult._fields_}
+        out["error"] = load().dr_last_error().decode() if st != DR_OK else ""
+        out["rc"] = st
+        return out
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        _check(load().dr_server_stats(self._h, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in ServerStats._fields_}
+
+    def close(self):
+        if self._h:
+            load().dr_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -51,3 +51,30 @@ def test_oracle_and_library_share_no_code():
     for f in ("dynrecon.py", "__init__.py", "build.py"):
         txt = open(os.path.join(ROOT, "paper_1809_09725_gb300", f)).read()
         assert "import oracle" not in txt and "from oracle" not in txt, f
+
+
+def test_job_admission_estimate_is_host_only_and_monotone(lib):
+    """dr_job_device_bytes is plain host arithmetic (callable without a GPU):
+    it grows with the volume, the projection count and the precision."""
+    import numpy as np
+    from paper_1809_09725_gb300 import dynrecon as dr
+
+    def est(nz=2, K=100, prec=dr.F32, algo=dr.ADMM_CG, N=64, m=4):
+        theta = np.linspace(0, 3, K)
+        t = np.linspace(0, 0.99, K)
+        dt = np.float64 if prec == dr.F64 else np.float32
+        g = np.zeros((nz, K, N), dtype=dt)
+        u = np.zeros((nz, N, N, m), dtype=dt)
+        prm = dr.SolveParams()
+        lib.dr_solve_params_default(prm)
+        prm.algo = algo
+        return dr.job_device_bytes(dr.job_desc(N, N, nz, N, theta, t, dr.FOURIER, m, 4, prec, prm, g, u))
+
+    base = est()
+    assert base > 0
+    assert est(nz=4) > 1.8 * base - 4 * (1 << 20)
+    assert est(K=400) > est(K=100)
+    assert est(prec=dr.F64) > base
+    assert est(m=16) > base
+    # a 16 x 256^2, 1800-projection, m = 8 job needs well under 2 GB
+    assert est(nz=16, K=1800, N=256, m=8) < 2 * 1024 ** 3
