@@ -110,21 +110,32 @@ class ClockSampler:
 
 
 def dist_init(n):
+    """One process per GPU under torchrun (NCCL); gloo when no GPU is present.
+    Replicas only exchange the timing maximum, never data."""
     if n <= 1 and "RANK" not in os.environ:
         return 0, 1, None
+    import torch
     import torch.distributed as tdist
-    backend = "nccl"
-    tdist.init_process_group(backend=backend)
+    backend = "nccl" if torch.cuda.is_available() else "gloo"
+    if not tdist.is_initialized():
+        tdist.init_process_group(backend=backend)
     return tdist.get_rank(), tdist.get_world_size(), tdist
 
 
 def barrier_max(tdist, value: float, device):
+    """Maximum of a per-rank value over all ranks (the job's wall time)."""
     if tdist is None:
         return value
     import torch
-    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dev = device if tdist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
     tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_units(units_per_rank: float, world: int) -> float:
+    """Whole-job work of N independent replicas (weak scaling)."""
+    return units_per_rank * world
 
 
 def algorithmic_flops(w, variant, U):
@@ -196,7 +207,7 @@ def run_ours(a):
             tdist.barrier()
     ms = e0.elapsed_time(e1)
     ms = barrier_max(tdist, ms, dev)
-    total_units = units_per_iter * a.steps * world
+    total_units = replica_units(units_per_iter * a.steps, world)
     value = total_units / (ms * 1e-3)
     obj = res["objective"]
 
@@ -366,13 +377,17 @@ def run_serving(a, device, prec):
 
 
 def load_traffic(kernel):
-    """DRAM bytes per launch from the committed ncu summary, if present."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+    """DRAM bytes per launch of `kernel` from the committed ncu summary
+    (profiles/traffic.txt), or None if that kernel was not captured."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
     try:
-        d = json.load(open(path))
-        return d.get(kernel)
-    except Exception:
-        return None
+        for line in open(path):
+            parts = line.split()
+            if len(parts) == 2 and not line.startswith("#") and parts[0] == kernel:
+                return int(parts[1])
+    except OSError:
+        pass
+    return None
 
 
 def cpu_baseline(w, theta, t, g_np, sample_slices=None):

@@ -328,7 +328,7 @@ static dr_status solve_begin(dr_plan *P, const void *g_in, void *u_io, const dr_
     DR_CUDA_TRY(cudaEventRecord(P->ev_a, P->stream));
     DR_CUDA_TRY(cudaStreamWaitEvent(st, P->ev_a, 0));
     // pick the faster projector variants once per plan (scratch: q, gd)
-    if (!P->tuned) TRY(autotune(P, w.q, w.gd));
+    if (!P->tuned && (P->var_fwd < 0 || P->var_adj < 0)) TRY(autotune(P, w.q, w.gd));
 
     // ---- bring g and u into compute-typed device buffers ----
     c.g = g_in;
