@@ -120,7 +120,9 @@ dr_status dr_plan_set_variant(dr_plan *plan, int fwd_variant, int adj_variant);
 /*
  * Time both variants of both projectors on this plan's geometry (allocates
  * and frees scratch; synchronises) and keep the faster ones for automatic
- * selection.  times_ms: HOST [4] nullable: forward direct, forward fold,
+ * selection.  The decision is cached for the process, keyed by the sizes,
+ * basis, precision, angles and times, so later plans of the same problem
+ * reuse it (same kernels, bit-identical results) without timing again.  times_ms: HOST [4] nullable: forward direct, forward fold,
  * adjoint direct, adjoint fold (-1 where a variant is unavailable).
  */
 dr_status dr_plan_autotune(dr_plan *plan, double *times_ms);

@@ -40,6 +40,9 @@ _lib = None
 
 FOURIER = 0
 LEGENDRE = 1
+HAAR = 2
+HEAVISIDE = 3
+ORTHONORMAL = 0x100  # flag: Gram-Schmidt orthonormalise over the acquisition times
 
 _dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
 _i = ctypes.c_int
@@ -71,6 +74,7 @@ def _load():
         lib = ctypes.CDLL(build())
         sig = {
             "or_basis_table": (_i, [_i, _i, _dp, _i64, _dp]),
+            "or_orthonormalise": (_i, [_dp, _i64, _i, _dp, _i64]),
             "or_joseph_fwd_slice": (None, [_dp, _i, _i, _d, _i, _dp]),
             "or_joseph_adj_slice": (None, [_dp, _i, _d, _i, _i, _dp]),
             "or_dyn_fwd": (None, [_dp, _i, _i, _i, _i, _i, _dp, _dp, _i, _dp]),
@@ -262,8 +266,12 @@ class Problem:
         self.t = _c(t)
         self.K = self.theta.size
         self.basis, self.m, self.nt = int(basis), int(m), int(nt)
-        self.Phi = basis_table(basis, m, self.t)
-        self.PhiF = frame_table(basis, m, nt)
+        kind = int(basis) & 0xff
+        self.Phi = basis_table(kind, m, self.t)
+        self.PhiF = frame_table(kind, m, nt)
+        if int(basis) & ORTHONORMAL:
+            if _load().or_orthonormalise(self.Phi, self.K, self.m, self.PhiF, self.nt) != 0:
+                raise ValueError("basis columns are linearly dependent over the acquisition times")
 
     def _head(self):
         return (self.nx, self.ny, self.nz, self.ns, self.K, self.m, self.nt, self.theta, self.Phi,

@@ -31,19 +31,40 @@
 typedef int64_t i64;
 
 /* ------------------------------------------------------------------------- */
-/* Temporal bases (Sec. 4, Eq. repr; Sec. 5 uses a Fourier basis).           */
+/* Temporal bases (Sec. 4, Eq. repr; Sec. 5 uses a Fourier basis; Sec. 4     */
+/* and Sec. 8 name Haar wavelets and Heaviside step functions).              */
 /* kind 0: real Fourier  phi_0 = 1, phi_{2i-1} = cos(2 pi i t),              */
 /*                       phi_{2i} = sin(2 pi i t)                            */
 /* kind 1: shifted Legendre  phi_j(t) = P_j(2t - 1), three-term recurrence   */
 /*         (n+1) P_{n+1}(x) = (2n+1) x P_n(x) - n P_{n-1}(x).                */
+/* kind 2: Haar  phi_0 = 1; for j >= 1 write j = 2^lev + pos (0 <= pos <    */
+/*         2^lev): phi_j(t) = +1 on [pos, pos + 1/2) / 2^lev, -1 on          */
+/*         [pos + 1/2, pos + 1) / 2^lev, 0 elsewhere (unnormalised).          */
+/* kind 3: Heaviside  phi_0 = 1, phi_j(t) = 1 if t >= j/m else 0.            */
 /* out[n][m] = phi_j(t[i]).                                                  */
 /* ------------------------------------------------------------------------- */
+static double haar(int j, double t)
+{
+    if (j == 0) return 1.0;
+    int lev = 0;
+    while ((2 << lev) <= j) ++lev;
+    int pos = j - (1 << lev);
+    double x = t * (double)(1 << lev) - (double)pos; /* position inside the support */
+    if (x >= 0.0 && x < 0.5) return 1.0;
+    if (x >= 0.5 && x < 1.0) return -1.0;
+    return 0.0;
+}
+
 int or_basis_table(int kind, int m, const double *t, i64 n, double *out)
 {
-    if (m < 1 || (kind != 0 && kind != 1)) return -1;
+    if (m < 1 || kind < 0 || kind > 3) return -1;
     for (i64 i = 0; i < n; ++i) {
         double *row = out + i * m;
-        if (kind == 0) {
+        if (kind == 2) {
+            for (int j = 0; j < m; ++j) row[j] = haar(j, t[i]);
+        } else if (kind == 3) {
+            for (int j = 0; j < m; ++j) row[j] = (j == 0 || t[i] >= (double)j / (double)m) ? 1.0 : 0.0;
+        } else if (kind == 0) {
             row[0] = 1.0;
             for (int j = 1; j < m; ++j) {
                 int freq = (j + 1) / 2;
@@ -58,6 +79,47 @@ int or_basis_table(int kind, int m, const double *t, i64 n, double *out)
                 row[j + 1] = ((2.0 * j + 1.0) * x * row[j] - (double)j * row[j - 1]) / (double)(j + 1);
         }
     }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Gram-Schmidt orthonormalisation of a basis over the acquisition times     */
+/* (Sec. 4 suggests it to make a basis orthonormal): modified Gram-Schmidt   */
+/* on the columns of Phi[K][m] (samples phi_j(t_k)) gives Phi = Q Rm with Q  */
+/* orthonormal over the samples; the new basis is phi~ = phi Rm^{-1},        */
+/* applied to Phi (becomes Q) and to any other table of the same functions   */
+/* (PhiF[nt][m]).  Returns -1 if a column is dependent on the previous ones. */
+/* ------------------------------------------------------------------------- */
+int or_orthonormalise(double *Phi, i64 K, int m, double *PhiF, i64 nt)
+{
+    double *Rm = (double *)calloc((size_t)m * m, sizeof(double));
+    for (int j = 0; j < m; ++j) {
+        for (int i = 0; i < j; ++i) {
+            double d = 0.0;
+            for (i64 k = 0; k < K; ++k) d += Phi[k * m + i] * Phi[k * m + j];
+            Rm[i * m + j] = d;
+            for (i64 k = 0; k < K; ++k) Phi[k * m + j] -= d * Phi[k * m + i];
+        }
+        double nrm = 0.0;
+        for (i64 k = 0; k < K; ++k) nrm += Phi[k * m + j] * Phi[k * m + j];
+        nrm = sqrt(nrm);
+        if (!(nrm > 1e-12)) {
+            free(Rm);
+            return -1;
+        }
+        Rm[j * m + j] = nrm;
+        for (i64 k = 0; k < K; ++k) Phi[k * m + j] /= nrm;
+    }
+    /* PhiF <- PhiF Rm^{-1}: solve X Rm = PhiF row by row (Rm upper triangular) */
+    for (i64 l = 0; l < nt; ++l) {
+        double *row = PhiF + l * m;
+        for (int j = 0; j < m; ++j) {
+            double v = row[j];
+            for (int i = 0; i < j; ++i) v -= row[i] * Rm[i * m + j];
+            row[j] = v / Rm[j * m + j];
+        }
+    }
+    free(Rm);
     return 0;
 }
 

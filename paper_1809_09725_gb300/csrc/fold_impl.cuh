@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(kFoldThreads)
     fold_fwd_kernel(const S *__restrict__ u, S *__restrict__ out, const S *__restrict__ gm,
                     const FwdProj *__restrict__ uproj, const int *__restrict__ start, const int *__restrict__ member,
                     const T *__restrict__ phip, const int *__restrict__ blocks, int nx, int ny, int ns, int K,
-                    int m, int MP, int P, int R, int nchunk, int mode, T sigma) {
+                    int m, int MP, int P, int R, int nchunk, int mode, T sigma, int async_stage) {
     constexpr int MS = fold_ms(M);
     constexpr int RPT = fold_rpt(M);
     extern __shared__ __align__(16) unsigned char fold_smem[];
@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(kFoldThreads)
         scale_s[p] = (T)f.scale;
         bfx_s[p] = f.B_fx;
     }
-    for (int i = tid; i < R * wpad * MS; i += kFoldThreads) strip[i] = T(0);
+    for (int i = tid; i < (async_stage ? 2 : 1) * R * wpad * MS; i += kFoldThreads) strip[i] = T(0);
 
     const int rays_per_cta = kFoldThreads * RPT;
     const int b_base = chunk * rays_per_cta;
@@ -124,9 +124,10 @@ __global__ void __launch_bounds__(kFoldThreads)
     __syncthreads();
 
     const size_t zoff = (size_t)z * ny * nx;
-    for (int r0 = 0; r0 < H; r0 += R) {
-        const int nl = min(R, H - r0);
-        // ---- stage lines [r0, r0+nl) of the m-vector image ----
+    // Stage lines [r0, r0+nl) of the m-vector image into buffer `buf`:
+    // asynchronously (cp.async, 16-byte chunks) when the coefficients are
+    // 16-byte float vectors, else through registers.
+    auto stage = [&](T *buf, int r0, int nl) {
         const int npx = nl * W;
         for (int qq = tid; qq < npx; qq += kFoldThreads) {
             int rl, i;
@@ -140,9 +141,16 @@ __global__ void __launch_bounds__(kFoldThreads)
                 rl = qq - i * nl;
                 pix = zoff + (size_t)i * nx + (r0 + rl);
             }
+            T *dst = buf + ((size_t)rl * wpad + kFwdGuard + i) * MS;
+            if constexpr (sizeof(S) == 4 && (M % 4) == 0) {
+                if (async_stage) {
+#pragma unroll
+                    for (int j = 0; j < M / 4; ++j) cp_async_16(dst + 4 * j, u + pix * m + 4 * j);
+                    continue;
+                }
+            }
             T v[M];
             load_coeffs<T, S, M>(u + pix * m, m, v);
-            T *dst = strip + ((size_t)rl * wpad + kFwdGuard + i) * MS;
             if constexpr (sizeof(T) == 4 && (M % 4) == 0) {
 #pragma unroll
                 for (int j = 0; j < M / 4; ++j)
@@ -152,7 +160,32 @@ __global__ void __launch_bounds__(kFoldThreads)
                 for (int j = 0; j < M; ++j) dst[j] = v[j];
             }
         }
-        __syncthreads();
+    };
+    T *bufs[2] = {strip, strip + (size_t)R * wpad * MS};
+    if (async_stage) {
+        stage(bufs[0], 0, min(R, H));
+        cp_async_commit();
+    }
+    int s_idx = 0;
+    for (int r0 = 0; r0 < H; r0 += R, ++s_idx) {
+        const int nl = min(R, H - r0);
+        T *cur;
+        if (async_stage) {
+            // prefetch the next strip into the other buffer, then wait for this one
+            if (r0 + R < H) {
+                stage(bufs[(s_idx + 1) & 1], r0 + R, min(R, H - r0 - R));
+                cp_async_commit();
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
+            }
+            __syncthreads();
+            cur = bufs[s_idx & 1];
+        } else {
+            stage(bufs[0], r0, nl);
+            __syncthreads();
+            cur = bufs[0];
+        }
         // ---- march the rays: all m coefficient sums per ray ----
 #pragma unroll
         for (int q = 0; q < RPT; ++q) {
@@ -162,7 +195,8 @@ __global__ void __launch_bounds__(kFoldThreads)
             const int p = (nchunk > 1) ? 0 : rid / ns;
             const long long bfx = bfx_s[p];
             long long x = x0fx[q] + (long long)rs * bfx;
-            const T *row = strip + ((size_t)(rs - r0) * wpad + kFwdGuard) * MS;
+            const T *row = cur + ((size_t)(rs - r0) * wpad + kFwdGuard) * MS;
+#pragma unroll 1
             for (int r = rs; r <= re; ++r) {
                 int i0 = (int)(x >> 32);
                 i0 = min(max(i0, -2), W);
@@ -286,8 +320,9 @@ __global__ void __launch_bounds__(kAdjThreads)
     constexpr int kMagI = 0x4B400000;
 
     extern __shared__ __align__(128) unsigned char fadj_smem_raw[];
-    unsigned char *smem_raw =
-        reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(fadj_smem_raw) + 127) & ~uintptr_t(127));
+    // round up to 128 B by pointer arithmetic on the __shared__ array, so the
+    // compiler keeps addressing it as shared memory (LDS, not generic loads)
+    unsigned char *smem_raw = fadj_smem_raw + ((128u - (smem_u32(fadj_smem_raw) & 127u)) & 127u);
     const size_t row_bytes = ((size_t)Wb * MS * sizeof(T) + 127) & ~(size_t)127;
     const size_t win_bytes = PP * row_bytes;
     const size_t stage_bytes = win_bytes + 128 * ((PP * sizeof(FoldPrm) + 127) / 128);
@@ -423,7 +458,10 @@ dr_status fold_fwd_launch_t(dr_plan *P, const void *u, void *out, const void *gm
     constexpr int MS = fold_ms(M);
     const int Wmax = std::max(P->nx, P->ny);
     const int wpad = Wmax + 2 * kFwdGuard;
-    const size_t smem = 768 + sizeof(T) * (size_t)P->fold_R * wpad * MS;
+    // double-buffered cp.async staging for 16-byte float coefficient vectors
+    const int async_stage = (sizeof(S) == 4 && (M % 4) == 0 && P->m == M) ? 1 : 0;
+    const int R = async_stage ? std::max(1, P->fold_R / 2) : P->fold_R;
+    const size_t smem = 768 + sizeof(T) * (size_t)(async_stage ? 2 : 1) * R * wpad * MS;
     auto kern = fold_fwd_kernel<S, T, M>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -432,8 +470,8 @@ dr_status fold_fwd_launch_t(dr_plan *P, const void *u, void *out, const void *gm
     dim3 grid(P->n_fold_blocks * P->fold_nchunk, P->nz);
     kern<<<grid, kFoldThreads, smem, st>>>((const S *)u, (S *)out, (const S *)gm, P->d_fold_fwd, P->d_fold_start,
                                            P->d_fold_member, (const T *)P->d_PhiP, P->d_fold_blocks, P->nx, P->ny,
-                                           P->ns, P->K, P->m, P->MP, P->fold_P, P->fold_R, P->fold_nchunk, mode,
-                                           (T)sigma);
+                                           P->ns, P->K, P->m, P->MP, P->fold_P, R, P->fold_nchunk, mode,
+                                           (T)sigma, async_stage);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? DR_OK : cuda_fail(e, "fold_fwd_kernel launch");
 }

@@ -2,6 +2,10 @@
 // projector pair (Sec. 4, Eqs. radapr and radadjapr).  The kernels live in
 // projector_impl.cuh and are instantiated per precision in projector_*.cu.
 #include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "projector_impl.cuh"
 #include "fold_impl.cuh"
@@ -83,10 +87,52 @@ dr_status launch_adj_calc(dr_plan *P, const void *g, void *u, double alpha, doub
 // plan's own geometry (compute-typed scratch buffers supplied by the
 // caller, contents overwritten) and keep the faster of each.  Explicit
 // choices made with dr_plan_set_variant are left alone.
+// Process-wide cache of autotuner decisions, keyed by everything that
+// defines the operators (sizes, basis, precision, and the acquisition
+// angles and times), so every plan of the same problem runs the same
+// kernels and produces bit-identical results.
+struct TuneKey {
+    int nx, ny, nz, ns, K, m, nt, basis, prec;
+    uint64_t hash;
+    bool operator<(const TuneKey &o) const {
+        return std::tie(nx, ny, nz, ns, K, m, nt, basis, prec, hash) <
+               std::tie(o.nx, o.ny, o.nz, o.ns, o.K, o.m, o.nt, o.basis, o.prec, o.hash);
+    }
+};
+struct TuneVal {
+    int fwd, adj;
+    double ms[4];
+};
+static std::mutex g_tune_mutex;
+static std::map<TuneKey, TuneVal> g_tune_cache;
+
+static TuneKey tune_key(const dr_plan *P) {
+    uint64_t h = 1469598103934665603ull;  // FNV-1a over the bytes of theta and t
+    auto mix = [&h](const std::vector<double> &v) {
+        const unsigned char *b = reinterpret_cast<const unsigned char *>(v.data());
+        for (size_t i = 0; i < v.size() * sizeof(double); ++i) h = (h ^ b[i]) * 1099511628211ull;
+    };
+    mix(P->theta);
+    mix(P->t);
+    return TuneKey{P->nx, P->ny, P->nz, P->ns, P->K, P->m, P->nt, (int)P->basis, (int)P->prec, h};
+}
+
 dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
     if (P->fold_U == 0) {
         P->tuned = true;
         return DR_OK;
+    }
+    const TuneKey key = tune_key(P);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mutex);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            P->sel_fwd = it->second.fwd;
+            P->sel_adj = it->second.adj;
+            for (int i = 0; i < 4; ++i) P->tune_ms[i] = it->second.ms[i];
+            P->tuned = true;
+            return DR_OK;
+        }
     }
     cudaStream_t st = P->graph_stream;
     cudaEvent_t e0, e1;
@@ -127,6 +173,14 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
     P->sel_fwd = ms[1] < ms[0] ? 1 : 0;
     P->sel_adj = ms[3] < ms[2] ? 1 : 0;
     P->tuned = true;
+    std::lock_guard<std::mutex> lk(g_tune_mutex);
+    auto ins = g_tune_cache.emplace(key, TuneVal{P->sel_fwd, P->sel_adj, {0, 0, 0, 0}});
+    if (ins.second) {
+        for (int i = 0; i < 4; ++i) ins.first->second.ms[i] = P->tune_ms[i];
+    } else {  // another thread tuned the same problem first: follow its choice
+        P->sel_fwd = ins.first->second.fwd;
+        P->sel_adj = ins.first->second.adj;
+    }
     return DR_OK;
 }
 

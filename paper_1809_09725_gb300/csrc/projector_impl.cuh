@@ -276,8 +276,9 @@ __global__ void __launch_bounds__(kAdjThreads)
 
     extern __shared__ __align__(128) unsigned char adj_smem_raw[];
     // the launch adds 128 bytes so the base can be rounded up to 128 B (TMA destination alignment)
-    unsigned char *smem_raw =
-        reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(adj_smem_raw) + 127) & ~uintptr_t(127));
+    // round up to 128 B by pointer arithmetic on the __shared__ array, so the
+    // compiler keeps addressing it as shared memory (LDS, not generic loads)
+    unsigned char *smem_raw = adj_smem_raw + ((128u - (smem_u32(adj_smem_raw) & 127u)) & 127u);
     // per stage: window [PP][wbs] S (rows 128-B aligned), phi [PP][MP] T, prm [PP]
     const size_t win_bytes = (size_t)PP * wbs * sizeof(S);
     const size_t phi_bytes = (((size_t)PP * MP * sizeof(T)) + 127) & ~(size_t)127;

@@ -170,3 +170,36 @@ def test_disk_line_integrals_converge():
     assert errs[0] < 0.05
     assert errs[1] < 0.75 * errs[0]
     assert errs[2] < 0.75 * errs[1]
+
+
+def test_haar_values_and_orthogonality():
+    # phi_0 = 1; phi_1 = psi(t); phi_2 = psi(2t); phi_3 = psi(2t - 1); psi = +1 on [0,1/2), -1 on [1/2,1)
+    P = oracle.basis_table(oracle.HAAR, 4, [0.1, 0.3, 0.6, 0.9])
+    np.testing.assert_array_equal(P, [[1, 1, 1, 0], [1, 1, -1, 0], [1, -1, 0, 1], [1, -1, 0, -1]])
+    K = 64
+    Pk = oracle.basis_table(oracle.HAAR, 8, (np.arange(K) + 0.5) / K)
+    G = Pk.T @ Pk
+    # levels 0 (j=1), 1 (j=2,3), 2 (j=4..7): supports of length 1, 1/2, 1/4
+    np.testing.assert_allclose(G, np.diag([64, 64, 32, 32, 16, 16, 16, 16]), atol=0)
+
+
+def test_heaviside_values():
+    P = oracle.basis_table(oracle.HEAVISIDE, 4, [0.0, 0.249, 0.25, 0.6, 0.99])
+    np.testing.assert_array_equal(P, [[1, 0, 0, 0], [1, 0, 0, 0], [1, 1, 0, 0], [1, 1, 1, 0], [1, 1, 1, 1]])
+
+
+@pytest.mark.parametrize("kind", [oracle.FOURIER, oracle.LEGENDRE, oracle.HEAVISIDE])
+def test_orthonormalised_basis(kind):
+    """Gram-Schmidt over the acquisition times: Phi^T Phi = I, and the new
+    functions span the same space (same frames up to the triangular change)."""
+    theta, t = synth.scan(40, 3.0)
+    P = oracle.Problem(6, 6, 1, 7, theta, t, kind | oracle.ORTHONORMAL, 4, 5)
+    np.testing.assert_allclose(P.Phi.T @ P.Phi, np.eye(4), atol=1e-13)
+    raw = oracle.basis_table(kind, 4, t)
+    # raw = Phi Rm with Rm upper triangular: Phi^T raw = Rm
+    M = P.Phi.T @ raw
+    assert np.max(np.abs(np.tril(M, -1))) < 1e-12
+    # the frame table transforms with the same matrix
+    rawF = oracle.frame_table(kind, 4, 5)
+    Rm = np.linalg.lstsq(P.Phi, raw, rcond=None)[0]
+    np.testing.assert_allclose(P.PhiF @ Rm, rawF, atol=1e-11)
