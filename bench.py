@@ -304,6 +304,7 @@ def run_ours(a):
                          "launch_ms": launch_ms, "fwd_ms": fwd_ms, "adj_ms": adj_ms,
                          "algorithmic_flops_per_launch": flops,
                          "variants": {"unique_angles": U, "fwd": info["fwd_variant"], "adj": info["adj_variant"],
+                                      "fold_lines": info["fold_lines"], "fold_async": info["fold_async"],
                                       "autotune_ms_fwd_direct_fold_adj_direct_fold": tune},
                          "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz max SM clock"},
             "cpu_baseline": cpu,

@@ -58,7 +58,13 @@ typedef enum {
 
 typedef enum {
     DR_FOURIER_REAL = 0, /* phi_0 = 1, phi_{2i-1} = cos(2 pi i t), phi_{2i} = sin(2 pi i t) */
-    DR_LEGENDRE = 1      /* phi_j(t) = P_j(2t - 1), Legendre polynomials, unnormalised */
+    DR_LEGENDRE = 1,     /* phi_j(t) = P_j(2t - 1), Legendre polynomials, unnormalised */
+    DR_HAAR = 2,         /* phi_0 = 1; j = 2^l + p: +1 on [p, p+1/2)/2^l, -1 on [p+1/2, p+1)/2^l (Sec. 8) */
+    DR_HEAVISIDE = 3,    /* phi_0 = 1, phi_j(t) = 1 for t >= j/m, else 0 (Sec. 4) */
+    /* Flag OR-ed into the kind: orthonormalise the basis over the acquisition
+     * times (Gram-Schmidt, Sec. 4): phi~ = phi R^{-1} with sum_k phi~_i(t_k)
+     * phi~_j(t_k) = delta_ij; the frames use the same transformed functions. */
+    DR_BASIS_ORTHONORMAL = 0x100
 } dr_basis;
 
 typedef enum { DR_F32 = 0, DR_BF16_F32ACC = 1, DR_F64 = 2 } dr_precision;
@@ -77,7 +83,9 @@ typedef struct dr_plan dr_plan;
  *   K           number of projections, >= 1
  *   theta       host [K] projection angles in radians (any real value)
  *   t           host [K] acquisition times in [0, 1) (scan-normalised)
- *   basis, m    temporal basis kind and size, 1 <= m <= 32 (Sec. 4, Eq. repr)
+ *   basis, m    temporal basis kind (optionally | DR_BASIS_ORTHONORMAL) and size,
+ *               1 <= m <= 32 (Sec. 4, Eq. repr); DR_EINVAL if orthonormalisation
+ *               finds the functions dependent over the acquisition times
  *   nt_frames   number of reconstruction frames for the time derivative (<= 256),
  *               frame l at t = l / nt_frames, >= 1
  *   prec        storage/arithmetic precision (see above)
@@ -120,7 +128,8 @@ dr_status dr_plan_set_variant(dr_plan *plan, int fwd_variant, int adj_variant);
 /*
  * Time both variants of both projectors on this plan's geometry (allocates
  * and frees scratch; synchronises) and keep the faster ones for automatic
- * selection.  The decision is cached for the process, keyed by the sizes,
+ * selection; for the folded forward also choose the strip height and
+ * staging mode (neither changes the result).  The decision is cached for the process, keyed by the sizes,
  * basis, precision, angles and times, so later plans of the same problem
  * reuse it (same kernels, bit-identical results) without timing again.  times_ms: HOST [4] nullable: forward direct, forward fold,
  * adjoint direct, adjoint fold (-1 where a variant is unavailable).
@@ -134,6 +143,8 @@ typedef struct {
     int adj_variant;     /* variant the adjoint uses now */
     int tuned;           /* 1 once the variants have been timed */
     size_t device_bytes; /* device memory held by the plan */
+    int fold_lines;      /* folded forward: image lines staged per shared-memory strip */
+    int fold_async;      /* folded forward: 1 if strips are double-buffered with cp.async */
 } dr_plan_info_t;
 
 /* Describe the plan (host struct filled in). */

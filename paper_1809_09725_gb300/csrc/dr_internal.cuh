@@ -122,6 +122,7 @@ struct dr_plan {
     int MP;  // padded row length of the projection basis table (multiple of 4)
     int MT;  // TV template size >= m (4, 8, 16 or 32): row stride of the frame tables
     dr_basis basis;
+    bool orthonormal = false;
     dr_precision prec;
     cudaStream_t stream;
     cudaStream_t graph_stream;
@@ -152,6 +153,7 @@ struct dr_plan {
     int *d_fold_member = nullptr;     // [K] 2*k + (1 if theta_k = theta0 + odd multiple of pi)
     int *d_fold_blocks = nullptr;     // [n_fold_blocks][fold_P] unique angles grouped by stepping axis
     int n_fold_blocks = 0, fold_P = 0, fold_R = 0, fold_nchunk = 1;
+    int fold_lines = 0, fold_async = 0;  // folded forward: strip lines per buffer, cp.async double buffering
     bool fold_fwd_ok = false;         // the forward strip fits in shared memory
     void *d_gt = nullptr;             // folded data [nz][U][ns][MS] float (allocated on first use)
     size_t gt_bytes = 0;

@@ -458,9 +458,11 @@ dr_status fold_fwd_launch_t(dr_plan *P, const void *u, void *out, const void *gm
     constexpr int MS = fold_ms(M);
     const int Wmax = std::max(P->nx, P->ny);
     const int wpad = Wmax + 2 * kFwdGuard;
-    // double-buffered cp.async staging for 16-byte float coefficient vectors
-    const int async_stage = (sizeof(S) == 4 && (M % 4) == 0 && P->m == M) ? 1 : 0;
-    const int R = async_stage ? std::max(1, P->fold_R / 2) : P->fold_R;
+    // strip height and staging mode: the autotuned choice (cp.async double
+    // buffering needs 16-byte float coefficient vectors)
+    const int async_ok = (sizeof(S) == 4 && (M % 4) == 0 && P->m == M) ? 1 : 0;
+    const int async_stage = async_ok && P->fold_async;
+    const int R = std::max(1, P->fold_lines);
     const size_t smem = 768 + sizeof(T) * (size_t)(async_stage ? 2 : 1) * R * wpad * MS;
     auto kern = fold_fwd_kernel<S, T, M>;
     if (smem > 48 * 1024) {

@@ -39,6 +39,21 @@ int template_m(int m) {
 // Shifted Legendre: phi_j(t) = P_j(2t - 1) by Bonnet's recurrence.
 // ---------------------------------------------------------------------------
 static void eval_basis(dr_basis kind, int m, double t, double *row) {
+    if (kind == DR_HAAR) {
+        row[0] = 1.0;
+        for (int j = 1; j < m; ++j) {
+            int level = 31 - __builtin_clz((unsigned)j);  // j = 2^level + pos
+            const int pos = j - (1 << level);
+            const double x = std::ldexp(t, level) - pos;
+            row[j] = (x >= 0.0 && x < 0.5) ? 1.0 : ((x >= 0.5 && x < 1.0) ? -1.0 : 0.0);
+        }
+        return;
+    }
+    if (kind == DR_HEAVISIDE) {
+        row[0] = 1.0;
+        for (int j = 1; j < m; ++j) row[j] = (t >= (double)j / (double)m) ? 1.0 : 0.0;
+        return;
+    }
     if (kind == DR_FOURIER_REAL) {
         row[0] = 1.0;
         for (int j = 1; j < m; ++j) {
@@ -106,6 +121,17 @@ bool encode_tensor_map_2d(CUtensorMap *map, CUtensorMapDataType dt, void *base, 
     return r == CUDA_SUCCESS;
 }
 
+// Adjoint constants of one angle: pixel (i, j) lies at bin position
+// i*c + j*s + C0; the footprint half-width is max(|c|, |s|).
+static AdjProj make_adj(double c, double s, double C0) {
+    AdjProj a{};
+    a.c = c;
+    a.s = s;
+    a.C0 = C0;
+    a.inv_c = 1.0 / std::max(std::fabs(c), std::fabs(s));
+    return a;
+}
+
 template <typename T>
 static dr_status upload(void **dst, const std::vector<double> &src, size_t &bytes) {
     std::vector<T> tmp(src.size());
@@ -127,6 +153,40 @@ static dr_status build_tables(dr_plan *P) {
     for (int k = 0; k < K; ++k) eval_basis(P->basis, m, P->t[k], &P->Phi[(size_t)k * m]);
     P->PhiF.assign((size_t)nt * m, 0.0);
     for (int l = 0; l < nt; ++l) eval_basis(P->basis, m, (double)l / nt, &P->PhiF[(size_t)l * m]);
+    if (P->orthonormal) {
+        // Gram matrix of the sampled functions, its Cholesky factor R (G = R^T R,
+        // R upper with positive diagonal), then phi~ = phi R^{-1} for both tables.
+        std::vector<double> G((size_t)m * m, 0.0), R((size_t)m * m, 0.0);
+        for (int i = 0; i < m; ++i)
+            for (int j = 0; j < m; ++j) {
+                double a = 0.0;
+                for (int k = 0; k < K; ++k) a += P->Phi[(size_t)k * m + i] * P->Phi[(size_t)k * m + j];
+                G[(size_t)i * m + j] = a;
+            }
+        for (int j = 0; j < m; ++j) {
+            double d = G[(size_t)j * m + j];
+            for (int q = 0; q < j; ++q) d -= R[(size_t)q * m + j] * R[(size_t)q * m + j];
+            if (!(d > 1e-24 * std::max(1.0, G[0]))) return fail(DR_EINVAL, "basis functions are dependent over the acquisition times");
+            R[(size_t)j * m + j] = std::sqrt(d);
+            for (int i = j + 1; i < m; ++i) {
+                double e = G[(size_t)j * m + i];
+                for (int q = 0; q < j; ++q) e -= R[(size_t)q * m + j] * R[(size_t)q * m + i];
+                R[(size_t)j * m + i] = e / R[(size_t)j * m + j];
+            }
+        }
+        auto apply = [&](std::vector<double> &tab, int rows) {
+            for (int r = 0; r < rows; ++r) {
+                double *row = &tab[(size_t)r * m];
+                for (int j = 0; j < m; ++j) {  // solve x R = row (forward substitution over columns)
+                    double v = row[j];
+                    for (int q = 0; q < j; ++q) v -= row[q] * R[(size_t)q * m + j];
+                    row[j] = v / R[(size_t)j * m + j];
+                }
+            }
+        };
+        apply(P->Phi, K);
+        apply(P->PhiF, nt);
+    }
 
     std::vector<double> phip((size_t)K * MP, 0.0);
     for (int k = 0; k < K; ++k)
@@ -201,12 +261,7 @@ static dr_status build_tables(dr_plan *P) {
         f.Cf = (float)f.C;
         f.scale = (float)f.scale_d;
         fw[k] = f;
-        AdjProj a{};
-        a.c = c;
-        a.s = s;
-        a.C0 = -hx * c - hy * s + hs;
-        a.inv_c = 1.0 / std::max(std::fabs(c), std::fabs(s));
-        ad[k] = a;
+        ad[k] = make_adj(c, s, -hx * c - hy * s + hs);
     }
     DR_CUDA_TRY(cudaMalloc(&P->d_fwd, sizeof(FwdProj) * K));
     DR_CUDA_TRY(cudaMalloc(&P->d_adj, sizeof(AdjProj) * K));
@@ -300,12 +355,12 @@ static dr_status build_tables(dr_plan *P) {
             f.A_fx = std::llround(f.A * two32); f.B_fx = std::llround(f.B * two32); f.C_fx = std::llround(f.C * two32);
             f.Af = (float)f.A; f.Bf = (float)f.B; f.Cf = (float)f.C; f.scale = (float)f.scale_d;
             ufw[a] = f;
-            uad[a] = AdjProj{c, s, -hx * c - hy * s + hs, 1.0 / std::max(std::fabs(c), std::fabs(s))};
+            uad[a] = make_adj(c, s, -hx * c - hy * s + hs);
         }
         // forward work lists over unique angles
         const int M = P->M;
-        const int rpt = M <= 4 ? 8 : 32 / M;
-        const int rays = 256 * rpt;
+        const int rpt = M <= 4 ? 8 : 32 / M;  // rays per thread of the folded forward
+        const int rays = 256 * rpt;            // 256-thread CTAs
         int Pf, nchunk;
         if (P->ns <= rays) { Pf = std::min(64, rays / P->ns); nchunk = 1; }
         else { Pf = 1; nchunk = (P->ns + rays - 1) / rays; }
@@ -322,7 +377,9 @@ static dr_status build_tables(dr_plan *P) {
         P->fold_U = U;
         P->fold_maxgrp = maxg;
         P->fold_P = Pf;
-        P->fold_R = std::max(R, 1);
+        P->fold_R = std::max(R, 1);  // lines of one strip buffer that fit the 56 KB shared-memory budget
+        P->fold_lines = P->fold_R;   // in use (the autotuner may choose fewer)
+        P->fold_async = 0;
         P->fold_nchunk = nchunk;
         P->n_fold_blocks = (int)(fb.size() / Pf);
         DR_CUDA_TRY(cudaMalloc(&P->d_fold_fwd, sizeof(FwdProj) * U));
@@ -395,7 +452,9 @@ dr_status dr_plan_create(dr_plan **out, int nx, int ny, int nz, int ns, int K, c
     if (nx > 65536 || ny > 65536 || nz > 65535 || K > (1 << 24))
         return fail(DR_EINVAL, "dr_plan_create: size out of range");
     if (m < 1 || m > 32) return fail(DR_EINVAL, "dr_plan_create: m must be in [1, 32]");
-    if (basis != DR_FOURIER_REAL && basis != DR_LEGENDRE) return fail(DR_EINVAL, "dr_plan_create: bad basis");
+    const int kind = (int)basis & 0xff, flags = (int)basis & ~0xff;
+    if (kind < DR_FOURIER_REAL || kind > DR_HEAVISIDE || (flags & ~DR_BASIS_ORTHONORMAL))
+        return fail(DR_EINVAL, "dr_plan_create: bad basis");
     if (prec != DR_F32 && prec != DR_BF16_F32ACC && prec != DR_F64)
         return fail(DR_EINVAL, "dr_plan_create: bad precision");
     if (!theta || !t) return fail(DR_EINVAL, "dr_plan_create: theta/t are NULL");
@@ -409,7 +468,8 @@ dr_status dr_plan_create(dr_plan **out, int nx, int ny, int nz, int ns, int K, c
     P->M = template_m(m);
     P->MP = (P->M + 3) / 4 * 4;
     P->MT = m <= 4 ? 4 : (m <= 8 ? 8 : (m <= 16 ? 16 : 32));
-    P->basis = basis;
+    P->basis = (dr_basis)kind;
+    P->orthonormal = (flags & DR_BASIS_ORTHONORMAL) != 0;
     P->prec = prec;
     P->stream = (cudaStream_t)cuda_stream;
     P->theta.assign(theta, theta + K);

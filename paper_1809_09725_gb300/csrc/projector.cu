@@ -100,7 +100,7 @@ struct TuneKey {
     }
 };
 struct TuneVal {
-    int fwd, adj;
+    int fwd, adj, lines, async;
     double ms[4];
 };
 static std::mutex g_tune_mutex;
@@ -129,6 +129,8 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
         if (it != g_tune_cache.end()) {
             P->sel_fwd = it->second.fwd;
             P->sel_adj = it->second.adj;
+            P->fold_lines = it->second.lines;
+            P->fold_async = it->second.async;
             for (int i = 0; i < 4; ++i) P->tune_ms[i] = it->second.ms[i];
             P->tuned = true;
             return DR_OK;
@@ -142,8 +144,7 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
     DR_CUDA_TRY(cudaMemsetAsync(u_scratch, 0, nu_elems(P) * cs, st));
     DR_CUDA_TRY(cudaMemsetAsync(g_scratch, 0, ng_elems(P) * cs, st));
     double ms[4] = {1e30, 1e30, 1e30, 1e30};
-    for (int v = 0; v < 2; ++v) {
-        if (v == 1 && !P->fold_fwd_ok) continue;
+    auto time_fwd = [&](int v, double &best) -> dr_status {
         for (int rep = 0; rep < 3; ++rep) {
             DR_CUDA_TRY(cudaEventRecord(e0, st));
             dr_status s = launch_fwd_variant(P, v, true, u_scratch, g_scratch, nullptr, 0, 0.0, st);
@@ -152,8 +153,39 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
             DR_CUDA_TRY(cudaEventSynchronize(e1));
             float t = 0.f;
             DR_CUDA_TRY(cudaEventElapsedTime(&t, e0, e1));
-            if (rep > 0) ms[v] = std::min(ms[v], (double)t);
+            if (rep > 0) best = std::min(best, (double)t);
         }
+        return DR_OK;
+    };
+    {
+        dr_status s = time_fwd(0, ms[0]);
+        if (s != DR_OK) return s;
+    }
+    if (P->fold_fwd_ok) {
+        // folded forward: strip lines per buffer and staging mode
+        // (every choice marches each ray over the same lines in the same order,
+        // so the result does not depend on it)
+        int best_lines = P->fold_R, best_async = 0;
+        const int async_ok = P->prec == DR_F32 && P->M % 4 == 0 && P->m == P->M;
+        const int cand[] = {1, 2, 3, 4, 6, 8, 12, 16};
+        for (int as = 0; as <= async_ok; ++as)
+            for (int c : cand) {
+                const int lines = c;
+                // both buffers of the double-buffered mode share the strip budget
+                if ((as ? 2 : 1) * lines > P->fold_R) continue;
+                P->fold_lines = lines;
+                P->fold_async = as;
+                double t = 1e30;
+                dr_status s = time_fwd(1, t);
+                if (s != DR_OK) return s;
+                if (t < ms[1]) {
+                    ms[1] = t;
+                    best_lines = lines;
+                    best_async = as;
+                }
+            }
+        P->fold_lines = best_lines;
+        P->fold_async = best_async;
     }
     for (int v = 0; v < 2; ++v) {
         for (int rep = 0; rep < 3; ++rep) {
@@ -174,12 +206,14 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
     P->sel_adj = ms[3] < ms[2] ? 1 : 0;
     P->tuned = true;
     std::lock_guard<std::mutex> lk(g_tune_mutex);
-    auto ins = g_tune_cache.emplace(key, TuneVal{P->sel_fwd, P->sel_adj, {0, 0, 0, 0}});
+    auto ins = g_tune_cache.emplace(key, TuneVal{P->sel_fwd, P->sel_adj, P->fold_lines, P->fold_async, {0, 0, 0, 0}});
     if (ins.second) {
         for (int i = 0; i < 4; ++i) ins.first->second.ms[i] = P->tune_ms[i];
     } else {  // another thread tuned the same problem first: follow its choice
         P->sel_fwd = ins.first->second.fwd;
         P->sel_adj = ins.first->second.adj;
+        P->fold_lines = ins.first->second.lines;
+        P->fold_async = ins.first->second.async;
     }
     return DR_OK;
 }
@@ -247,6 +281,8 @@ dr_status dr_plan_info(const dr_plan *P, dr_plan_info_t *info) {
     info->adj_variant = P->var_adj >= 0 ? P->var_adj : P->sel_adj;
     info->tuned = P->tuned ? 1 : 0;
     info->device_bytes = P->table_bytes + P->ws.bytes + (P->d_gt ? P->gt_bytes : 0);
+    info->fold_lines = P->fold_lines;
+    info->fold_async = P->fold_async;
     return DR_OK;
 }
 

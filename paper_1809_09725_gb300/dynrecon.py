@@ -20,7 +20,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libdynrecon.so")
 
 DR_OK, DR_EINVAL, DR_ENOMEM, DR_ECUDA, DR_ETIMEOUT, DR_ENOTCONV, DR_ECANCELED = 0, -1, -2, -3, -4, -5, -6
-FOURIER, LEGENDRE = 0, 1
+FOURIER, LEGENDRE, HAAR, HEAVISIDE = 0, 1, 2, 3
+ORTHONORMAL = 0x100  # flag OR-ed into the basis kind
 F32, BF16, F64 = 0, 1, 2
 ADMM_CG, CHAMBOLLE_POCK = 0, 1
 
@@ -48,7 +49,8 @@ class DynreconError(RuntimeError):
 
 class PlanInfo(ctypes.Structure):
     _fields_ = [("unique_angles", ctypes.c_int), ("max_group", ctypes.c_int), ("fwd_variant", ctypes.c_int),
-                ("adj_variant", ctypes.c_int), ("tuned", ctypes.c_int), ("device_bytes", ctypes.c_size_t)]
+                ("adj_variant", ctypes.c_int), ("tuned", ctypes.c_int), ("device_bytes", ctypes.c_size_t),
+                ("fold_lines", ctypes.c_int), ("fold_async", ctypes.c_int)]
 
 
 class SolveParams(ctypes.Structure):

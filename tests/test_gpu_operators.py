@@ -35,6 +35,9 @@ CASES = {
     "m16": (24, 32, 1, 32, 70, 4.0, False, dr.FOURIER, 16, 8),
     "m24": (20, 20, 2, 24, 36, 3.0, False, dr.FOURIER, 24, 6),
     "m32": (16, 24, 1, 20, 50, 6.0, False, dr.LEGENDRE, 32, 6),
+    "haar": (30, 28, 2, 33, 120, 4.0, False, dr.HAAR, 6, 4),
+    "heaviside": (26, 26, 2, 29, 90, 3.0, False, dr.HEAVISIDE, 5, 5),
+    "orthonormal": (32, 32, 1, 32, 128, 4.0, True, dr.FOURIER | dr.ORTHONORMAL, 4, 4),
 }
 
 
@@ -271,3 +274,12 @@ def test_fold_is_unavailable_for_f64_plans():
     assert plan.info()["unique_angles"] == 0
     with pytest.raises(dr.DynreconError):
         plan.set_variant(dr.FOLD, dr.FOLD)
+
+
+def test_dependent_basis_is_rejected():
+    """Orthonormalising Heaviside steps sampled only on [0, 1/2): the steps at
+    t >= 1/2 vanish on every acquisition, so the basis is dependent there."""
+    theta, t = synth.scan(40, 2.0)
+    t = t * 0.5
+    with pytest.raises(dr.DynreconError):
+        dr.Plan(16, 16, 1, 16, theta, t, dr.HEAVISIDE | dr.ORTHONORMAL, 8, 4, dr.F32)

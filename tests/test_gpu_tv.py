@@ -27,6 +27,8 @@ CASES = {
     "m13": (16, 18, 3, dr.LEGENDRE, 13, 7),
     "m32": (12, 10, 3, dr.FOURIER, 32, 5),
     "nt1": (21, 22, 2, dr.FOURIER, 3, 1),
+    "haar": (20, 18, 3, dr.HAAR, 4, 8),
+    "orthonormal": (18, 20, 2, dr.LEGENDRE | dr.ORTHONORMAL, 5, 6),
 }
 
 
