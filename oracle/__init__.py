@@ -95,6 +95,9 @@ def _load():
             "or_power_norm_flat": (_d, [_i, _i, _i, _i, _i, _i, _i, _dp, _dp, _dp, _d, _i]),
             "or_splitmix_uniform": (_d, [ctypes.c_uint64, ctypes.c_uint64]),
             "or_objective_flat": (_d, [_i, _i, _i, _i, _i, _i, _i, _dp, _dp, _dp, _dp, _dp, _d, _d]),
+            "or_shepp_logan_tap": (_d, [_i64]),
+            "or_shepp_logan_filter": (None, [_dp, _i64, _i, _dp]),
+            "or_fbp_windows": (_i, [_dp, _i, _i, _i, _i, _dp, _dp, _i, _i, _dp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -255,6 +258,52 @@ def tv4d_prox(u, mu, w, PhiF, rho: float, lambda1: float, lambda2: float):
 
 
 # --------------------------------------------------------------------------- #
+# FBP initial guess (Sec. 5)
+# --------------------------------------------------------------------------- #
+def shepp_logan_tap(n: int) -> float:
+    """Discrete Shepp-Logan kernel h(n) = -2 / (pi^2 (4 n^2 - 1)), unit spacing."""
+    return _load().or_shepp_logan_tap(int(n))
+
+
+def shepp_logan_filter(g) -> np.ndarray:
+    """Linear convolution of every row of g[..., ns] with h along the last axis."""
+    g = _c(g)
+    ns = g.shape[-1]
+    q = np.zeros_like(g)
+    _load().or_shepp_logan_filter(g, g.size // ns, ns, q)
+    return q
+
+
+def fbp_windows(g, theta, t, nx: int, ny: int, n_windows: int) -> np.ndarray:
+    """FBP image of every time window: f[nz][nw][ny][nx] (see or_fbp_windows)."""
+    g = _c(g)
+    nz, K, ns = g.shape
+    f = np.zeros((nz, n_windows, ny, nx))
+    rc = _load().or_fbp_windows(g, nx, ny, nz, K, _c(theta), _c(t), ns, int(n_windows), f)
+    if rc != 0:
+        raise MemoryError("oracle fbp_windows failed (%d)" % rc)
+    return f
+
+
+def fbp_init(g, theta, t, Phi, nx: int, ny: int, n_windows: int) -> np.ndarray:
+    """Initial coefficients from windowed FBP images (Sec. 5 starts the
+    iterations from an FBP reconstruction).  The target at acquisition time
+    t_k is the FBP image of the window k falls in; the coefficients are the
+    least-squares fit over the acquisition times,
+        u = argmin sum_k || sum_j phi_j(t_k) u_j - f_{w(k)} ||^2,
+    i.e. u_j = sum_w A[j, w] f_w with A = (Phi^T Phi)^{-1} Phi^T S and
+    S[k, w] = 1 if projection k is in window w.  Returns u[nz][ny][nx][m]."""
+    Phi = _c(Phi)
+    K, m = Phi.shape
+    f = fbp_windows(g, theta, t, nx, ny, n_windows)
+    w = np.clip(np.floor(_c(t) * n_windows), 0, n_windows - 1).astype(int)
+    S = np.zeros((K, n_windows))
+    S[np.arange(K), w] = 1.0
+    A = np.linalg.solve(Phi.T @ Phi, Phi.T @ S)
+    return np.einsum("jw,zwyx->zyxj", A, f)
+
+
+# --------------------------------------------------------------------------- #
 # Problem + solvers
 # --------------------------------------------------------------------------- #
 class Problem:
@@ -291,6 +340,9 @@ class Problem:
 
     def objective(self, g, u, lambda1, lambda2) -> float:
         return _load().or_objective_flat(*self._head(), _c(g), _c(u), float(lambda1), float(lambda2))
+
+    def fbp_init(self, g, n_windows: int = 1):
+        return fbp_init(g, self.theta, self.t, self.Phi, self.nx, self.ny, n_windows)
 
     def power_norm(self, lambda2, iters: int = 100) -> float:
         return _load().or_power_norm_flat(*self._head(), float(lambda2), int(iters))

@@ -661,3 +661,81 @@ double or_objective_flat(int nx, int ny, int nz, int ns, int K, int m, int nt,
     or_problem P = mk(nx, ny, nz, ns, K, m, nt, theta, Phi, PhiF);
     return or_objective(&P, g, u, lambda1, lambda2);
 }
+
+/* ------------------------------------------------------------------------- */
+/* FBP initial guess (Sec. 5: the iterations start from the filtered         */
+/* back-projection reconstruction, with the Shepp-Logan filter).             */
+/*                                                                           */
+/* Filter: the discrete Shepp-Logan kernel at unit bin spacing,              */
+/*     h(n) = -2 / (pi^2 (4 n^2 - 1)),                                       */
+/* applied as a linear (zero-padded) convolution along s:                    */
+/*     q[b] = sum_{b'} h(b - b') g[b'].                                      */
+/* Its frequency response is |sin(w/2)| / pi, the ramp |w| / (2 pi) of the   */
+/* continuous inversion formula rolled off towards the Nyquist frequency.    */
+/* ------------------------------------------------------------------------- */
+double or_shepp_logan_tap(i64 n)
+{
+    double nn = (double)n;
+    return -2.0 / (M_PI * M_PI * (4.0 * nn * nn - 1.0));
+}
+
+void or_shepp_logan_filter(const double *g, i64 rows, int ns, double *q)
+{
+#pragma omp parallel for schedule(static)
+    for (i64 r = 0; r < rows; ++r) {
+        const double *gr = g + r * ns;
+        double *qr = q + r * ns;
+        for (int b = 0; b < ns; ++b) {
+            double acc = 0.0;
+            for (int bp = 0; bp < ns; ++bp) acc += or_shepp_logan_tap((i64)b - bp) * gr[bp];
+            qr[b] = acc;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Windowed FBP images.  Projection k belongs to time window                 */
+/*     w(k) = min(nw - 1, max(0, floor(t_k nw)))                             */
+/* (one window per half-turn when nw is the number of half-turns, as the FBP */
+/* frames of Sec. 5 are formed from the projections of one interval of       */
+/* length pi).  With K_w projections in window w spread evenly over whole    */
+/* half-turns, the angular integral over [0, pi) of the inversion formula is */
+/* (pi / K_w) times the sum over the window, so                              */
+/*     f[z][w] = (pi / K_w) sum_{k in w} R*_{theta_k} q[z][k]                */
+/* with R* the exact Joseph transpose above; empty windows give 0.           */
+/* f [nz][nw][ny][nx].                                                       */
+/* ------------------------------------------------------------------------- */
+int or_fbp_windows(const double *g, int nx, int ny, int nz, int K, const double *theta,
+                   const double *t, int ns, int nw, double *f)
+{
+    i64 npix = (i64)nx * ny;
+    double *q = (double *)malloc(sizeof(double) * (size_t)nz * K * ns);
+    int *win = (int *)malloc(sizeof(int) * (size_t)K);
+    i64 *cnt = (i64 *)calloc((size_t)nw, sizeof(i64));
+    if (!q || !win || !cnt) return -2;
+    or_shepp_logan_filter(g, (i64)nz * K, ns, q);
+    for (int k = 0; k < K; ++k) {
+        double x = floor(t[k] * nw);
+        int w = x < 0.0 ? 0 : (x > nw - 1 ? nw - 1 : (int)x);
+        win[k] = w;
+        cnt[w] += 1;
+    }
+    memset(f, 0, sizeof(double) * (size_t)nz * nw * npix);
+#pragma omp parallel for schedule(dynamic)
+    for (int z = 0; z < nz; ++z) {
+        double *tmp = (double *)malloc(sizeof(double) * npix);
+        for (int k = 0; k < K; ++k) {
+            or_joseph_adj_slice(q + ((i64)z * K + k) * ns, ns, theta[k], nx, ny, tmp);
+            double *fw = f + ((i64)z * nw + win[k]) * npix;
+            for (i64 p = 0; p < npix; ++p) fw[p] += tmp[p];
+        }
+        for (int w = 0; w < nw; ++w) {
+            double sc = cnt[w] > 0 ? M_PI / (double)cnt[w] : 0.0;
+            double *fw = f + ((i64)z * nw + w) * npix;
+            for (i64 p = 0; p < npix; ++p) fw[p] *= sc;
+        }
+        free(tmp);
+    }
+    free(q); free(win); free(cnt);
+    return 0;
+}
