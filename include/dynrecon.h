@@ -197,6 +197,28 @@ dr_status dyn_radon_adj(dr_plan *plan, const void *g, void *u, double beta);
 dr_status dyn_radon_adj_noalloc(dr_plan *plan, const void *g, void *u, double beta);
 
 /*
+ * Initial guess from filtered back-projection (Sec. 5 starts the iterations
+ * from an FBP reconstruction with the Shepp-Logan filter).
+ *   1. every projection row is filtered along s with the discrete Shepp-Logan
+ *      kernel h(n) = -2 / (pi^2 (4 n^2 - 1)) (unit bin spacing, zero padded);
+ *   2. projection k belongs to window w(k) = min(nw-1, max(0, floor(t_k nw)));
+ *      the FBP image of window w is f_w = (pi / K_w) sum_{k in w} R*_k q_k
+ *      (K_w projections spread over whole half-turns);
+ *   3. u is the least-squares fit over the acquisition times:
+ *      u = argmin sum_k || sum_j phi_j(t_k) u_j - f_{w(k)} ||^2.
+ * n_windows = 1 gives the static FBP of all projections spread over the
+ * basis (the constant function's coefficients when it is in the span); one
+ * window per half-turn gives the per-half-turn FBP frames of Sec. 5.
+ * g: device [nz][K][ns] (storage precision), u: device [nz][ny][nx][m]
+ * (overwritten).  The plan keeps scratch for the filtered data (nz K ns
+ * compute-typed values, plus nx ny nz m floats for BF16 plans) until it is
+ * destroyed.  Waits for the plan's stream before uploading its table, then
+ * runs asynchronously.  DR_EINVAL if n_windows is outside [1, K] or the basis
+ * functions are dependent over the acquisition times.
+ */
+dr_status dr_fbp_init(dr_plan *plan, const void *g, void *u, int n_windows);
+
+/*
  * 4D gradient of the synthesised frames, D = nabla_{lambda2} o PhiF
  * (Eq. TV1; frames f(t_l) = sum_j phi_j(t_l) u_j):  p = D u.
  * u: device [nz][ny][nx][m]; p: device [nz][ny][nx][nt][4] (overwritten).

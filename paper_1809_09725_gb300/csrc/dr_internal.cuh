@@ -166,6 +166,12 @@ struct dr_plan {
     dr::DevScalars *d_scal = nullptr;
     int *d_status = nullptr;
     size_t table_bytes = 0;
+    // FBP initial guess scratch (allocated on first use, fbp.cu)
+    void *d_fbp_taps = nullptr;  // [2 ns - 1] T, Shepp-Logan taps
+    void *d_fbp_phi = nullptr;   // [K][MP] T, window least-squares table used in place of PhiP
+    void *d_fbp_q = nullptr;     // [nz][K][ns] T, filtered data
+    void *d_fbp_u = nullptr;     // [V][m] float, result before BF16 rounding (BF16 plans)
+    size_t fbp_bytes = 0;
 
     dr::Workspace ws;
 };

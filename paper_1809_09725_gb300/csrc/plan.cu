@@ -501,7 +501,8 @@ dr_status dr_plan_destroy(dr_plan *P) {
     void *ptrs[] = {P->d_fwd,        P->d_adj,       P->d_PhiP,       P->d_fwd_blocks,  P->d_PhiF,
                     P->d_dPhiF,      P->d_G,         P->d_Lt,         P->d_partials,    P->d_counters,
                     P->d_scal,       P->d_status,    P->d_fold_fwd,   P->d_fold_adj,    P->d_fold_start,
-                    P->d_fold_member, P->d_fold_blocks, P->d_gt};
+                    P->d_fold_member, P->d_fold_blocks, P->d_gt, P->d_fbp_taps, P->d_fbp_phi, P->d_fbp_q,
+                    P->d_fbp_u};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (P->graph_stream) cudaStreamDestroy(P->graph_stream);
@@ -517,7 +518,9 @@ dr_status dr_plan_set_stream(dr_plan *P, void *s) {
     return DR_OK;
 }
 
-size_t dr_plan_device_bytes(const dr_plan *P) { return P ? P->table_bytes + P->ws.bytes + (P->d_gt ? P->gt_bytes : 0) : 0; }
+size_t dr_plan_device_bytes(const dr_plan *P) {
+    return P ? P->table_bytes + P->ws.bytes + (P->d_gt ? P->gt_bytes : 0) + P->fbp_bytes : 0;
+}
 
 dr_status dr_plan_sync(dr_plan *P) {
     if (!P) return fail(DR_EINVAL, "dr_plan_sync: NULL plan");

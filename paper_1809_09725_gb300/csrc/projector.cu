@@ -280,7 +280,7 @@ dr_status dr_plan_info(const dr_plan *P, dr_plan_info_t *info) {
     info->fwd_variant = P->var_fwd >= 0 ? P->var_fwd : P->sel_fwd;
     info->adj_variant = P->var_adj >= 0 ? P->var_adj : P->sel_adj;
     info->tuned = P->tuned ? 1 : 0;
-    info->device_bytes = P->table_bytes + P->ws.bytes + (P->d_gt ? P->gt_bytes : 0);
+    info->device_bytes = P->table_bytes + P->ws.bytes + (P->d_gt ? P->gt_bytes : 0) + P->fbp_bytes;
     info->fold_lines = P->fold_lines;
     info->fold_async = P->fold_async;
     return DR_OK;

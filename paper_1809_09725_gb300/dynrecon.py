@@ -31,7 +31,7 @@ _STATUS = {DR_EINVAL: "EINVAL", DR_ENOMEM: "ENOMEM", DR_ECUDA: "ECUDA", DR_ETIME
 # Every symbol include/dynrecon.h declares.
 EXPORTS = ("dr_plan_create", "dr_plan_destroy", "dr_plan_set_stream", "dr_plan_device_bytes",
            "dr_plan_workspace_bytes", "dr_plan_sync", "dr_plan_set_variant", "dr_plan_autotune", "dr_plan_info",
-           "dyn_radon_fwd", "dyn_radon_adj", "dyn_radon_adj_noalloc", "tv4d_grad", "tv4d_grad_adj", "tv4d_prox",
+           "dyn_radon_fwd", "dyn_radon_adj", "dyn_radon_adj_noalloc", "dr_fbp_init", "tv4d_grad", "tv4d_grad_adj", "tv4d_prox",
            "dr_solve_params_default", "admm_solve", "admm_solve_batch", "dr_job_device_bytes", "dr_server_create",
            "dr_server_submit", "dr_server_cancel", "dr_server_wait", "dr_server_stats", "dr_server_destroy",
            "dr_last_error", "dr_version")
@@ -108,6 +108,7 @@ def load(path: str = LIB_PATH):
         "dyn_radon_fwd": (i, [vp, vp, vp]),
         "dyn_radon_adj": (i, [vp, vp, vp, d]),
         "dyn_radon_adj_noalloc": (i, [vp, vp, vp, d]),
+        "dr_fbp_init": (i, [vp, vp, vp, i]),
         "tv4d_grad": (i, [vp, vp, vp, d]),
         "tv4d_grad_adj": (i, [vp, vp, vp, d, d]),
         "tv4d_prox": (i, [vp, vp, vp, vp, d, d, d, pd]),
@@ -284,6 +285,15 @@ def dyn_radon_adj_noalloc(plan: Plan, g, u, beta: float = 0.0):
     plan.use_current_stream()
     _check(load().dyn_radon_adj_noalloc(plan.handle, _ptr(g, plan.storage_dtype, plan.g_shape(), "g"),
                                         _ptr(u, plan.storage_dtype, plan.u_shape(), "u"), float(beta)))
+    return u
+
+
+def fbp_init(plan: Plan, g, u, n_windows: int = 1):
+    """u = least-squares fit over the acquisition times of the Shepp-Logan FBP
+    images of ``n_windows`` time windows (the initial guess of Sec. 5)."""
+    plan.use_current_stream()
+    _check(load().dr_fbp_init(plan.handle, _ptr(g, plan.storage_dtype, plan.g_shape(), "g"),
+                              _ptr(u, plan.storage_dtype, plan.u_shape(), "u"), int(n_windows)))
     return u
 
 
