@@ -255,6 +255,7 @@ typedef struct {
     double *objective_out;  /* HOST [iters], nullable: Eq. (lr12) at u after each iteration */
     double *primal_res_out; /* HOST [iters], nullable: ADMM ||D u - psi|| after each iteration */
     double *op_norm_out;    /* HOST, nullable: Chambolle-Pock operator norm estimate used */
+    double op_norm;         /* Chambolle-Pock: > 0 uses this ||[R; D]|| instead of the power iteration */
 } dr_solve_params;
 
 /* Fill params with defaults: ADMM-CG, 20 iterations, 4 CG steps, lambda1 = lambda2 = 1e-3... */
@@ -293,6 +294,38 @@ dr_status admm_solve(dr_plan *plan, const void *g, void *u, const dr_solve_param
 dr_status admm_solve_batch(int njobs, dr_plan *const *plans, const void *const *g, void *const *u,
                            const dr_solve_params *params);
 
+/*
+ * Chambolle-Pock (Sec. 3, Fig. 2) for a volume kept in HOST memory and
+ * streamed through the GPU in slabs of slab_nz slices, the scheme of Sec. 6:
+ * each slab is copied in with the slice above it (for the forward z
+ * difference of D), steps 3-6 run on it, and it is copied out, with the
+ * copies of the neighbouring slabs overlapping the computation on separate
+ * streams.  The updated dual on the slice below a slab is carried over on the
+ * device from the previous slab.  With the same operator norm (params->op_norm
+ * > 0) the result is bit-identical to admm_solve with DR_CHAMBOLLE_POCK and
+ * the same projector variants; otherwise the norm comes from a streamed power
+ * iteration (params->power_iters passes over the volume), equal to the
+ * in-core estimate up to rounding.
+ *   plan     the whole volume's plan (nz = all slices); its stream is
+ *            synchronised first and the plan must not be used concurrently
+ *   g        HOST [nz][K][ns] storage precision (copied to pinned memory once
+ *            if it is pageable)
+ *   u        HOST [nz][ny][nx][m] storage precision: initial guess in, result out
+ *   params   algo must be DR_CHAMBOLLE_POCK (ADMM-CG needs whole-volume inner
+ *            products inside every CG step); objective_out / op_norm_out as
+ *            for admm_solve
+ *   slab_nz  slices per slab (>= 1; device memory grows with it)
+ * Host memory: pinned copies of u, u~, h1 and h2 (compute precision) for the
+ * whole volume.  Device memory: cp_solve_slabs_device_bytes().  Synchronous.
+ * DR_EINVAL for device pointers or bad parameters, DR_ENOMEM if the slab
+ * buffers do not fit, DR_ENOTCONV for non-finite results.
+ */
+dr_status cp_solve_slabs(dr_plan *plan, const void *g, void *u, const dr_solve_params *params, int slab_nz);
+
+/* Device bytes cp_solve_slabs allocates for this plan, slab thickness and
+ * parameters (0 on bad arguments). */
+size_t cp_solve_slabs_device_bytes(dr_plan *plan, int slab_nz, const dr_solve_params *params);
+
 /* ------------------------------------------------------------------------ */
 /* Serving: a request loop with device-memory-budget admission.             */
 /* ------------------------------------------------------------------------ */
@@ -321,6 +354,8 @@ typedef struct {
     double latency_s;       /* completion - submission */
     double queue_s;         /* start - submission */
     size_t device_bytes;    /* memory the job was admitted with */
+    int slab_nz;            /* 0: whole volume on the device; > 0: streamed through
+                             * the GPU in slabs of this many slices (cp_solve_slabs) */
 } dr_job_result;
 
 typedef struct {
@@ -336,14 +371,21 @@ typedef struct {
  * the staging copies of host inputs. */
 size_t dr_job_device_bytes(const dr_job_desc *desc);
 
+/* Device bytes of the same job streamed in slabs of slab_nz slices
+ * (cp_solve_slabs; host arithmetic only, an upper bound). */
+size_t dr_job_slab_device_bytes(const dr_job_desc *desc, int slab_nz);
+
 /* Start a server on `device` with `slots` worker threads (jobs that may run
  * at once) and a device-memory budget in bytes for all running jobs. */
 dr_status dr_server_create(dr_server **out, int device, size_t budget_bytes, int slots);
 
-/* Queue a job; returns its id.  DR_ENOMEM if it cannot fit the budget even
- * alone.  Queued jobs are admitted in order, a later job that fits may pass
- * a head job that does not (backfill); admitted jobs keep all their state on
- * the device and run concurrently, each with its own plan and stream. */
+/* Queue a job; returns its id.  A Chambolle-Pock job on host buffers whose
+ * whole-volume state does not fit the budget is streamed through the GPU in
+ * the thickest slabs that fit (Sec. 6); DR_ENOMEM if even one-slice slabs (or,
+ * for other jobs, the whole volume) cannot fit the budget alone.  Queued jobs
+ * are admitted in order, a later job that fits may pass a head job that does
+ * not (backfill); admitted jobs keep their state on the device (or stream it)
+ * and run concurrently, each with its own plan and stream. */
 dr_status dr_server_submit(dr_server *server, const dr_job_desc *desc, int64_t *job_id);
 
 /* Cancel a job that has not started (DR_EINVAL once it runs). */

@@ -7,6 +7,16 @@
 
 namespace dr {
 
+// Counter-based SplitMix64 (Steele, Lea, Flood, OOPSLA 2014): output i of the
+// stream with seed s is the finaliser applied to s + (i+1) * golden gamma.
+__device__ __forceinline__ double splitmix_uniform(unsigned long long seed, unsigned long long i) {
+    unsigned long long z = seed + (i + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+}
+
 // ---------------------------------------------------------------------------
 // Storage <-> compute conversions
 // ---------------------------------------------------------------------------

@@ -118,6 +118,9 @@ struct Workspace {
 // The opaque plan.
 struct dr_plan {
     int nx, ny, nz, ns, K, m, nt;
+    // slab launches (slabs.cu): the TV stencils treat the slice below local
+    // z = 0 / above local z = nz-1 as present; 0 for whole-volume launches
+    int z_open_lo = 0, z_open_hi = 0;
     int M;   // template size >= m
     int MP;  // padded row length of the projection basis table (multiple of 4)
     int MT;  // TV template size >= m (4, 8, 16 or 32): row stride of the frame tables

@@ -37,6 +37,7 @@ struct Job {
     dr_job_desc desc{};
     std::vector<double> theta, t;
     size_t bytes = 0;
+    int slab = 0;  // > 0: streamed in slabs of this many slices
     int state = DR_JOB_QUEUED;
     dr_status status = DR_OK;
     std::string error;
@@ -68,16 +69,51 @@ namespace dr {
 
 // Device bytes a job holds while it runs: plan tables, reduction slots,
 // folded-data scratch, solver workspace with its staging copies.
-static size_t job_bytes(const dr_job_desc &d) {
+static size_t plan_table_bytes(const dr_job_desc &d) {
     const int M = template_m(d.m) > 0 ? template_m(d.m) : 32;
     const int MP = (M + 3) / 4 * 4, MT = d.m <= 4 ? 4 : (d.m <= 8 ? 8 : (d.m <= 16 ? 16 : 32));
     const size_t cs = d.prec == DR_F64 ? 8 : 4;
-    const size_t V = (size_t)d.nx * d.ny * d.nz, nu = V * d.m, ng = (size_t)d.nz * d.K * d.ns;
-    const size_t nf = V * d.nt * 4;
     size_t b = 0;
     b += (size_t)d.K * (MP * cs + sizeof(FwdProj) + sizeof(AdjProj) + 4 * sizeof(int));  // projection tables
     b += (size_t)d.nt * MT * 2 * cs + 2 * (size_t)MT * MT * cs;                           // frame tables
     b += sizeof(double) * kRedSlots * kRedSlotStride + 4096;                                // reductions, scalars
+    return b;
+}
+
+// Device bytes of the job streamed in slabs of S slices (cp_solve_slabs):
+// two stages of slab buffers with halos, the compute temporaries, folded-data
+// scratch for S slices (at most one distinct angle per projection) and the
+// power-iteration buffers when no operator norm is given.
+static size_t job_slab_bytes(const dr_job_desc &d, int S) {
+    S = std::max(1, std::min(S, d.nz));
+    const int M = template_m(d.m) > 0 ? template_m(d.m) : 32;
+    const size_t cs = d.prec == DR_F64 ? 8 : 4;
+    const size_t um = (size_t)d.nx * d.ny * d.m, gk = (size_t)d.K * d.ns, f4 = (size_t)d.nx * d.ny * d.nt * 4;
+    const size_t s = (size_t)S;
+    size_t b = plan_table_bytes(d);
+    b += 2 * ((s + 1) * um * cs * 2 + s * gk * cs * 2 + (s + 1) * f4 * cs);
+    if (d.prec == DR_BF16_F32ACC) b += 2 * s * gk * 2;
+    b += s * um * cs + s * gk * cs + f4 * cs + um * cs;
+    if (d.prec != DR_F64) {
+        const int MS = M <= 4 ? 4 : ((M % 8 == 0) ? M + 4 : M);
+        b += sizeof(float) * s * gk * MS;
+    }
+    const bool power = !(d.params.op_norm > 0.0);
+    if (power) b += 2 * ((s + 2) * um * cs + s * um * cs);
+    const size_t nslab = ((size_t)d.nz + s - 1) / s;
+    const size_t pit = d.params.power_iters > 0 ? d.params.power_iters : 100;
+    const size_t rows = std::max((size_t)std::max(d.params.iters, 0) * nslab, power ? (pit + 1) * nslab : 0);
+    b += sizeof(double) * 3 * (rows + 1);
+    b += b / 64 + (1u << 20);
+    return b;
+}
+
+static size_t job_bytes(const dr_job_desc &d) {
+    const int M = template_m(d.m) > 0 ? template_m(d.m) : 32;
+    const size_t cs = d.prec == DR_F64 ? 8 : 4;
+    const size_t V = (size_t)d.nx * d.ny * d.nz, nu = V * d.m, ng = (size_t)d.nz * d.K * d.ns;
+    const size_t nf = V * d.nt * 4;
+    size_t b = plan_table_bytes(d);
     if (d.prec != DR_F64) {
         const int MS = M <= 4 ? 4 : ((M % 8 == 0) ? M + 4 : M);
         b += sizeof(float) * ng * MS;  // folded data (at most one distinct angle per projection)
@@ -89,6 +125,15 @@ static size_t job_bytes(const dr_job_desc &d) {
     b += sizeof(double) * 3 * (size_t)(d.params.iters + 1);
     b += b / 64 + (1u << 20);                                      // allocation granularity slack
     return b;
+}
+
+static bool is_device_buffer(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
 static void worker_loop(dr_server *S) {
@@ -132,7 +177,8 @@ static void worker_loop(dr_server *S) {
             if (st != DR_OK) err = dr_last_error();
         }
         if (st == DR_OK) {
-            st = admm_solve(plan, d.g, d.u, &d.params);
+            st = job->slab > 0 ? cp_solve_slabs(plan, d.g, d.u, &d.params, job->slab)
+                               : admm_solve(plan, d.g, d.u, &d.params);
             if (st != DR_OK) err = dr_last_error();
         }
         if (plan) dr_plan_destroy(plan);
@@ -178,6 +224,10 @@ extern "C" {
 
 size_t dr_job_device_bytes(const dr_job_desc *desc) { return desc ? job_bytes(*desc) : 0; }
 
+size_t dr_job_slab_device_bytes(const dr_job_desc *desc, int slab_nz) {
+    return desc && slab_nz >= 1 ? job_slab_bytes(*desc, slab_nz) : 0;
+}
+
 dr_status dr_server_create(dr_server **out, int device, size_t budget_bytes, int slots) {
     clear_error();
     if (!out || slots < 1 || slots > 256 || budget_bytes == 0) return fail(DR_EINVAL, "dr_server_create: bad arguments");
@@ -204,6 +254,16 @@ dr_status dr_server_submit(dr_server *S, const dr_job_desc *d, int64_t *job_id) 
     job->theta.assign(d->theta, d->theta + d->K);
     job->t.assign(d->t, d->t + d->K);
     job->bytes = job_bytes(*d);
+    if (job->bytes > S->budget && d->params.algo == DR_CHAMBOLLE_POCK && !is_device_buffer(d->g) &&
+        !is_device_buffer(d->u)) {
+        // stream the volume through the GPU: the thickest slab that fits
+        for (int s = d->nz - 1; s >= 1; --s)
+            if (job_slab_bytes(*d, s) <= S->budget) {
+                job->slab = s;
+                job->bytes = job_slab_bytes(*d, s);
+                break;
+            }
+    }
     {
         std::lock_guard<std::mutex> lk(S->mu);
         if (S->stop) return fail(DR_ECANCELED, "dr_server_submit: server is shutting down");
@@ -254,6 +314,7 @@ dr_status dr_server_wait(dr_server *S, int64_t id, double timeout_s, dr_job_resu
         res->latency_s = job->t_done - job->t_submit;
         res->queue_s = (job->t_start > 0 ? job->t_start : job->t_done) - job->t_submit;
         res->device_bytes = job->bytes;
+        res->slab_nz = job->slab;
     }
     if (job->status != DR_OK) return fail(job->status, job->error.empty() ? "job failed" : job->error);
     return DR_OK;

@@ -14,16 +14,6 @@
 
 namespace dr {
 
-// Counter-based SplitMix64 (Steele, Lea, Flood, OOPSLA 2014): output i of the
-// stream with seed s is the finaliser applied to s + (i+1) * golden gamma.
-__device__ __forceinline__ double splitmix_uniform(unsigned long long seed, unsigned long long i) {
-    unsigned long long z = seed + (i + 1ull) * 0x9E3779B97F4A7C15ull;
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    z ^= z >> 31;
-    return (double)(z >> 11) * (1.0 / 9007199254740992.0);
-}
-
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads)
     dot_kernel(const T *__restrict__ a, const T *__restrict__ b, size_t n, double *partials, unsigned *counter,
@@ -70,10 +60,12 @@ __global__ void cg_dir_kernel(T *__restrict__ p, const T *__restrict__ r, size_t
         p[i] = r[i] + b * p[i];
 }
 
+// Power-iteration start x_i = 0.5 + U_i (SplitMix64 stream, seed 1809) for
+// global indices i = first .. first + n - 1.
 template <typename T>
-__global__ void pow_init_kernel(T *__restrict__ x, size_t n) {
+__global__ void pow_init_kernel(T *__restrict__ x, size_t n, size_t first) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-        x[i] = (T)(0.5 + splitmix_uniform(1809ull, (unsigned long long)i));
+        x[i] = (T)(0.5 + splitmix_uniform(1809ull, (unsigned long long)(first + i)));
 }
 
 // x = y / sqrt(scal->lam) (normalise by the norm just reduced).
@@ -199,7 +191,7 @@ static dr_status vec_launches(dr_plan *P, int which, void *a, void *b, void *c, 
             cg_dir_kernel<T><<<vec_grid(n), kRedThreads, 0, st>>>((T *)a, (const T *)b, n, P->d_scal);
             return launched("cg_dir_kernel");
         case 2:
-            pow_init_kernel<T><<<vec_grid(n), kRedThreads, 0, st>>>((T *)a, n);
+            pow_init_kernel<T><<<vec_grid(n), kRedThreads, 0, st>>>((T *)a, n, (size_t)0);
             return launched("pow_init_kernel");
         case 3:
             pow_scale_kernel<T><<<vec_grid(n), kRedThreads, 0, st>>>((T *)a, (const T *)b, n, P->d_scal);
@@ -217,6 +209,30 @@ static dr_status dot(dr_plan *P, const void *a, const void *b, size_t n, int slo
                      int to_lam, cudaStream_t st) {
     return P->prec == DR_F64 ? dot_t<double>(P, a, b, n, slot, obj, row_off, col, to_lam, st)
                              : dot_t<float>(P, a, b, n, slot, obj, row_off, col, to_lam, st);
+}
+
+// Helpers for the slab-streamed solver (slabs.cu).
+dr_status launch_dot_obj(dr_plan *P, const void *a, const void *b, size_t n, double *obj, int row_off, int col,
+                         cudaStream_t st) {
+    return dot(P, a, b, n, kSlotFid, obj, row_off, col, 0, st);
+}
+
+dr_status launch_set_iter(dr_plan *P, int value, cudaStream_t st) {
+    iter_kernel<<<1, 1, 0, st>>>(P->d_scal, 1, value);
+    return launched("iter_kernel");
+}
+
+dr_status launch_pow_init(dr_plan *P, void *x, size_t n, size_t first, cudaStream_t st) {
+    if (P->prec == DR_F64) pow_init_kernel<double><<<vec_grid(n), kRedThreads, 0, st>>>((double *)x, n, first);
+    else pow_init_kernel<float><<<vec_grid(n), kRedThreads, 0, st>>>((float *)x, n, first);
+    return launched("pow_init_kernel");
+}
+
+dr_status launch_convert_bf16(dr_plan *P, const void *in, void *out, size_t n, bool to_bf16, cudaStream_t st) {
+    (void)P;
+    if (to_bf16) convert_kernel<float, bf16><<<vec_grid(n), kRedThreads, 0, st>>>((const float *)in, (bf16 *)out, n);
+    else convert_kernel<bf16, float><<<vec_grid(n), kRedThreads, 0, st>>>((const bf16 *)in, (float *)out, n);
+    return launched("convert_kernel");
 }
 
 #define TRY(...)                       \
@@ -365,8 +381,12 @@ static dr_status solve_begin(dr_plan *P, const void *g_in, void *u_io, const dr_
     } else {
         DR_CUDA_TRY(cudaMemsetAsync(w.h1, 0, ng * cs, st));
         DR_CUDA_TRY(cudaMemsetAsync(w.mu, 0, nf * cs, st));
-        const int pit = prm.power_iters > 0 ? prm.power_iters : 100;
-        TRY(power_norm(P, prm.lambda2, pit, &c.L, st));
+        if (prm.op_norm > 0.0) {
+            c.L = prm.op_norm;
+        } else {
+            const int pit = prm.power_iters > 0 ? prm.power_iters : 100;
+            TRY(power_norm(P, prm.lambda2, pit, &c.L, st));
+        }
         if (!(c.L > 0.0) || !std::isfinite(c.L)) return fail(DR_EINVAL, "admm_solve: operator norm is zero");
         c.sigma = c.tau = 0.99 / c.L;
         if (prm.op_norm_out) *prm.op_norm_out = c.L;
@@ -543,7 +563,7 @@ static dr_status check_params(const dr_solve_params &p) {
     if (p.algo != DR_ADMM_CG && p.algo != DR_CHAMBOLLE_POCK) return fail(DR_EINVAL, "admm_solve: bad algo");
     if (p.iters < 0 || (p.algo == DR_ADMM_CG && p.n_cg < 1)) return fail(DR_EINVAL, "admm_solve: bad iters/n_cg");
     if (!(p.lambda1 >= 0.0) || !(p.lambda2 >= 0.0) || !std::isfinite(p.lambda1) || !std::isfinite(p.lambda2) ||
-        !std::isfinite(p.rho) || !std::isfinite(p.cp_theta))
+        !std::isfinite(p.rho) || !std::isfinite(p.cp_theta) || !std::isfinite(p.op_norm))
         return fail(DR_EINVAL, "admm_solve: lambdas must be finite and >= 0");
     if (p.algo == DR_CHAMBOLLE_POCK && !(p.cp_theta >= 0.0 && p.cp_theta <= 1.0))
         return fail(DR_EINVAL, "admm_solve: cp_theta must be in [0, 1]");

@@ -55,8 +55,12 @@ __device__ __forceinline__ void st4<double, D4>(double *p, D4 v) {
     reinterpret_cast<double2 *>(p)[1] = make_double2(v.z, v.w);
 }
 
+// zlo / zhi: the slice below local z = 0 / above local z = nz-1 exists in
+// memory (a halo of a slab of a larger volume), so the z differences there
+// are interior ones instead of the Neumann boundary.
 struct Geo {
     int nx, ny, nz, m, nt;
+    int zlo, zhi;
 };
 
 __device__ __forceinline__ void vox_xyz(size_t v, const Geo &g, int &x, int &y, int &z) {
@@ -104,7 +108,7 @@ __device__ __forceinline__ void coeff_diffs(const S *__restrict__ u, size_t v, i
 #pragma unroll
         for (int j = 0; j < M; ++j) ey[j] = T(0);
     }
-    if (z + 1 < g.nz) {
+    if (z + 1 < g.nz || g.zhi) {
         load_coeffs<T, S, M>(u + (v + (size_t)g.nx * g.ny) * g.m, g.m, ez);
 #pragma unroll
         for (int j = 0; j < M; ++j) ez[j] -= uc[j];
@@ -183,8 +187,8 @@ __device__ __forceinline__ void gradT_voxel(const T *__restrict__ p, size_t v, i
         if (x > 0) s += (pv - sx)[l * 4 + 0];
         if (y + 1 < g.ny) s -= q.y;
         if (y > 0) s += (pv - sy)[l * 4 + 1];
-        if (z + 1 < g.nz) s -= q.z;
-        if (z > 0) s += (pv - sz)[l * 4 + 2];
+        if (z + 1 < g.nz || g.zhi) s -= q.z;
+        if (z > 0 || g.zlo) s += (pv - sz)[l * 4 + 2];
         const T qt = lambda2 * q.w;
         const T *ph = sm + l * M;
         const T *dp = dph + l * M;
@@ -322,7 +326,7 @@ __global__ void __launch_bounds__(kRedThreads)
         load_coeffs<T, T, M>(xv + v * g.m, g.m, xc);
 #pragma unroll
         for (int j = 0; j < M; ++j) ls[j] = T(0);
-        const bool has[6] = {x > 0, x + 1 < g.nx, y > 0, y + 1 < g.ny, z > 0, z + 1 < g.nz};
+        const bool has[6] = {x > 0, x + 1 < g.nx, y > 0, y + 1 < g.ny, z > 0 || g.zlo != 0, z + 1 < g.nz || g.zhi != 0};
         const long long off[6] = {-1, 1, -(long long)sy, (long long)sy, -(long long)sz, (long long)sz};
 #pragma unroll
         for (int e = 0; e < 6; ++e) {
@@ -464,7 +468,7 @@ __global__ void __launch_bounds__(kRedThreads)
 // ===========================================================================
 // Launchers (instantiated per precision in tv_ops_*.cu and tv_calc_*.cu)
 // ===========================================================================
-inline Geo geo(const dr_plan *P) { return Geo{P->nx, P->ny, P->nz, P->m, P->nt}; }
+inline Geo geo(const dr_plan *P) { return Geo{P->nx, P->ny, P->nz, P->m, P->nt, P->z_open_lo, P->z_open_hi}; }
 
 template <typename T, int M>
 inline size_t tab_smem(const dr_plan *P, bool gl) {

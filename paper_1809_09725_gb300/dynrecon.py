@@ -32,7 +32,8 @@ _STATUS = {DR_EINVAL: "EINVAL", DR_ENOMEM: "ENOMEM", DR_ECUDA: "ECUDA", DR_ETIME
 EXPORTS = ("dr_plan_create", "dr_plan_destroy", "dr_plan_set_stream", "dr_plan_device_bytes",
            "dr_plan_workspace_bytes", "dr_plan_sync", "dr_plan_set_variant", "dr_plan_autotune", "dr_plan_info",
            "dyn_radon_fwd", "dyn_radon_adj", "dyn_radon_adj_noalloc", "dr_fbp_init", "tv4d_grad", "tv4d_grad_adj", "tv4d_prox",
-           "dr_solve_params_default", "admm_solve", "admm_solve_batch", "dr_job_device_bytes", "dr_server_create",
+           "dr_solve_params_default", "admm_solve", "admm_solve_batch", "cp_solve_slabs",
+           "cp_solve_slabs_device_bytes", "dr_job_device_bytes", "dr_job_slab_device_bytes", "dr_server_create",
            "dr_server_submit", "dr_server_cancel", "dr_server_wait", "dr_server_stats", "dr_server_destroy",
            "dr_last_error", "dr_version")
 
@@ -59,7 +60,7 @@ class SolveParams(ctypes.Structure):
                 ("cp_theta", ctypes.c_double), ("power_iters", ctypes.c_int),
                 ("objective_out", ctypes.POINTER(ctypes.c_double)),
                 ("primal_res_out", ctypes.POINTER(ctypes.c_double)),
-                ("op_norm_out", ctypes.POINTER(ctypes.c_double))]
+                ("op_norm_out", ctypes.POINTER(ctypes.c_double)), ("op_norm", ctypes.c_double)]
 
 
 class JobDesc(ctypes.Structure):
@@ -72,7 +73,7 @@ class JobDesc(ctypes.Structure):
 
 class JobResult(ctypes.Structure):
     _fields_ = [("state", ctypes.c_int), ("status", ctypes.c_int), ("latency_s", ctypes.c_double),
-                ("queue_s", ctypes.c_double), ("device_bytes", ctypes.c_size_t)]
+                ("queue_s", ctypes.c_double), ("device_bytes", ctypes.c_size_t), ("slab_nz", ctypes.c_int)]
 
 
 class ServerStats(ctypes.Structure):
@@ -116,7 +117,10 @@ def load(path: str = LIB_PATH):
         "admm_solve": (i, [vp, vp, vp, ctypes.POINTER(SolveParams)]),
         "admm_solve_batch": (i, [i, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
                                  ctypes.POINTER(SolveParams)]),
+        "cp_solve_slabs": (i, [vp, vp, vp, ctypes.POINTER(SolveParams), i]),
+        "cp_solve_slabs_device_bytes": (sz, [vp, i, ctypes.POINTER(SolveParams)]),
         "dr_job_device_bytes": (sz, [ctypes.POINTER(JobDesc)]),
+        "dr_job_slab_device_bytes": (sz, [ctypes.POINTER(JobDesc), i]),
         "dr_server_create": (i, [ctypes.POINTER(vp), i, sz, i]),
         "dr_server_submit": (i, [vp, ctypes.POINTER(JobDesc), ctypes.POINTER(ctypes.c_int64)]),
         "dr_server_cancel": (i, [vp, ctypes.c_int64]),
@@ -329,12 +333,13 @@ def tv4d_prox(plan: Plan, u, mu, w, rho: float, lambda1: float, lambda2: float,
 
 def solve_params(algo: int = ADMM_CG, iters: int = 20, n_cg: int = 4, lambda1: float = 1e-3,
                  lambda2: float = 1.0, rho: float = 0.0, cp_theta: float = 1.0,
-                 power_iters: int = 100) -> SolveParams:
+                 power_iters: int = 100, op_norm: float = 0.0) -> SolveParams:
     p = SolveParams()
     load().dr_solve_params_default(ctypes.byref(p))
     p.algo, p.iters, p.n_cg = int(algo), int(iters), int(n_cg)
     p.lambda1, p.lambda2, p.rho, p.cp_theta = float(lambda1), float(lambda2), float(rho), float(cp_theta)
     p.power_iters = int(power_iters)
+    p.op_norm = float(op_norm)
     return p
 
 
@@ -357,6 +362,29 @@ def admm_solve(plan: Plan, g, u, params: SolveParams, want_objective: bool = Tru
     return {"objective": obj[:it] if want_objective else None,
             "primal_res": pres[:it] if want_primal else None,
             "op_norm": opn.value}
+
+
+def cp_solve_slabs(plan: Plan, g: np.ndarray, u: np.ndarray, params: SolveParams, slab_nz: int,
+                   want_objective: bool = True):
+    """Chambolle-Pock on host-resident g and u, streamed through the GPU in
+    slabs of ``slab_nz`` slices (in place on u).  Returns dict(objective, op_norm)."""
+    plan.use_current_stream()
+    n = max(int(params.iters), 1)
+    obj = np.zeros(n, dtype=np.float64)
+    opn = ctypes.c_double(0.0)
+    pd = ctypes.POINTER(ctypes.c_double)
+    params.objective_out = obj.ctypes.data_as(pd) if want_objective else None
+    params.primal_res_out = None
+    params.op_norm_out = ctypes.pointer(opn)
+    _check(load().cp_solve_slabs(plan.handle, _ptr(g, plan.storage_dtype, plan.g_shape(), "g"),
+                                 _ptr(u, plan.storage_dtype, plan.u_shape(), "u"), ctypes.byref(params),
+                                 int(slab_nz)))
+    it = int(params.iters)
+    return {"objective": obj[:it] if want_objective else None, "op_norm": opn.value}
+
+
+def cp_solve_slabs_device_bytes(plan: Plan, slab_nz: int, params: SolveParams) -> int:
+    return int(load().cp_solve_slabs_device_bytes(plan.handle, int(slab_nz), ctypes.byref(params)))
 
 
 def version() -> str:
@@ -396,6 +424,10 @@ def job_desc(nx, ny, nz, ns, theta, t, basis, m, nt, prec, params: SolveParams, 
 
 def job_device_bytes(desc: JobDesc) -> int:
     return load().dr_job_device_bytes(ctypes.byref(desc))
+
+
+def job_slab_device_bytes(desc: JobDesc, slab_nz: int) -> int:
+    return load().dr_job_slab_device_bytes(ctypes.byref(desc), int(slab_nz))
 
 
 class Server:

@@ -78,3 +78,28 @@ def test_job_admission_estimate_is_host_only_and_monotone(lib):
     assert est(m=16) > base
     # a 16 x 256^2, 1800-projection, m = 8 job needs well under 2 GB
     assert est(nz=16, K=1800, N=256, m=8) < 2 * 1024 ** 3
+
+
+def test_slab_estimate_lets_the_largest_serving_job_fit(lib):
+    """The largest job of the serving mix (2048^2 x 128 slices, K = 7200,
+    m = 32, 20 frames, BF16) needs several hundred GB with its whole volume on
+    the device, but streamed in slabs it fits a 150 GB budget; the slab
+    estimate grows with the slab thickness (host arithmetic only)."""
+    import numpy as np
+    from paper_1809_09725_gb300 import dynrecon as dr
+
+    K = 7200
+    theta = np.linspace(0.0, 20 * np.pi, K, endpoint=False)
+    t = np.arange(K) / K
+    prm = dr.SolveParams()
+    lib.dr_solve_params_default(prm)
+    prm.algo, prm.iters = dr.CHAMBOLLE_POCK, 30
+    d = dr.JobDesc()
+    d.nx = d.ny = d.ns = 2048
+    d.nz, d.K, d.m, d.nt, d.prec, d.basis = 128, K, 32, 20, dr.BF16, dr.FOURIER
+    d.params = prm
+    budget = 150 * 10 ** 9
+    assert dr.job_device_bytes(d) > 3 * budget
+    sizes = [dr.job_slab_device_bytes(d, s) for s in (1, 2, 4, 8, 16)]
+    assert all(a < b for a, b in zip(sizes, sizes[1:]))
+    assert sizes[3] < budget  # slabs of 8 slices
