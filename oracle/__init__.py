@@ -42,6 +42,7 @@ FOURIER = 0
 LEGENDRE = 1
 HAAR = 2
 HEAVISIDE = 3
+COMPLEX_FOURIER = 4  # exp(2 pi i t (j - M/2)) as 2M real channels (Re, Im of each u_j)
 ORTHONORMAL = 0x100  # flag: Gram-Schmidt orthonormalise over the acquisition times
 
 _dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
@@ -122,7 +123,8 @@ def _optbuf(n: int, want: bool):
 # Bases and single-slice Joseph pair
 # --------------------------------------------------------------------------- #
 def basis_table(kind: int, m: int, t) -> np.ndarray:
-    """``out[i, j] = phi_j(t[i])``; kind FOURIER (real) or LEGENDRE (shifted)."""
+    """``out[i, j] = phi_j(t[i])``; kind FOURIER (real), LEGENDRE (shifted), HAAR,
+    HEAVISIDE or COMPLEX_FOURIER (m = 2M real channels)."""
     t = _c(np.atleast_1d(t))
     out = np.zeros((t.size, m), dtype=np.float64)
     if _load().or_basis_table(int(kind), int(m), t, t.size, out) != 0:
@@ -291,15 +293,17 @@ def fbp_init(g, theta, t, Phi, nx: int, ny: int, n_windows: int) -> np.ndarray:
     t_k is the FBP image of the window k falls in; the coefficients are the
     least-squares fit over the acquisition times,
         u = argmin sum_k || sum_j phi_j(t_k) u_j - f_{w(k)} ||^2,
-    i.e. u_j = sum_w A[j, w] f_w with A = (Phi^T Phi)^{-1} Phi^T S and
-    S[k, w] = 1 if projection k is in window w.  Returns u[nz][ny][nx][m]."""
+    i.e. u_j = sum_w A[j, w] f_w with A = Phi^+ S (the minimum-norm
+    least-squares solution; (Phi^T Phi)^{-1} Phi^T S when the functions are
+    independent over the acquisition times) and S[k, w] = 1 if projection k
+    is in window w.  Returns u[nz][ny][nx][m]."""
     Phi = _c(Phi)
     K, m = Phi.shape
     f = fbp_windows(g, theta, t, nx, ny, n_windows)
     w = np.clip(np.floor(_c(t) * n_windows), 0, n_windows - 1).astype(int)
     S = np.zeros((K, n_windows))
     S[np.arange(K), w] = 1.0
-    A = np.linalg.solve(Phi.T @ Phi, Phi.T @ S)
+    A = np.linalg.lstsq(Phi, S, rcond=1e-6)[0]
     return np.einsum("jw,zwyx->zyxj", A, f)
 
 

@@ -41,6 +41,11 @@ typedef int64_t i64;
 /*         2^lev): phi_j(t) = +1 on [pos, pos + 1/2) / 2^lev, -1 on          */
 /*         [pos + 1/2, pos + 1) / 2^lev, 0 elsewhere (unnormalised).          */
 /* kind 3: Heaviside  phi_0 = 1, phi_j(t) = 1 if t >= j/m else 0.            */
+/* kind 4: complex Fourier of Sec. 5, phi_j(t) = exp(2 pi i t (j - M/2)),    */
+/*         j = 0..M-1, carried as m = 2M real channels: the object           */
+/*         f(t) = Re sum_j u_j phi_j(t) with u_j = a_j + i b_j is            */
+/*         sum_j a_j cos(w_j t) - b_j sin(w_j t), w_j = 2 pi (j - M/2), so   */
+/*         channel 2j = cos(w_j t), channel 2j+1 = -sin(w_j t).              */
 /* out[n][m] = phi_j(t[i]).                                                  */
 /* ------------------------------------------------------------------------- */
 static double haar(int j, double t)
@@ -57,10 +62,17 @@ static double haar(int j, double t)
 
 int or_basis_table(int kind, int m, const double *t, i64 n, double *out)
 {
-    if (m < 1 || kind < 0 || kind > 3) return -1;
+    if (m < 1 || kind < 0 || kind > 4 || (kind == 4 && m % 2 != 0)) return -1;
     for (i64 i = 0; i < n; ++i) {
         double *row = out + i * m;
-        if (kind == 2) {
+        if (kind == 4) {
+            int M = m / 2;
+            for (int j = 0; j < M; ++j) {
+                double w = 2.0 * M_PI * (double)(j - M / 2);
+                row[2 * j] = cos(w * t[i]);
+                row[2 * j + 1] = -sin(w * t[i]);
+            }
+        } else if (kind == 2) {
             for (int j = 0; j < m; ++j) row[j] = haar(j, t[i]);
         } else if (kind == 3) {
             for (int j = 0; j < m; ++j) row[j] = (j == 0 || t[i] >= (double)j / (double)m) ? 1.0 : 0.0;

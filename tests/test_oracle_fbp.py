@@ -162,3 +162,21 @@ def test_fbp_init_least_squares_normal_equations():
     proj = np.einsum("kj,zkyx->zyxj", P.Phi, resid)
     assert np.max(np.abs(proj)) < 1e-9 * max(1.0, np.max(np.abs(f)))
     assert np.max(np.abs(resid)) > 1e-3  # the fit is not exact
+
+
+def test_fbp_init_minimum_norm_for_a_redundant_basis():
+    """The complex Fourier basis of Sec. 5 is redundant as a real basis
+    (cos(-w t) = cos(w t), and the zero-frequency sine vanishes): the fit is
+    the minimum-norm least-squares solution, so for one window the constant
+    channel holds the image and every other channel is zero."""
+    N, K, M = 24, 96, 4
+    rng = synth.rng_for(34)
+    theta, t = synth.scan(K, 2.0)
+    g = rng.standard_normal((1, K, N))
+    f = oracle.fbp_windows(g, theta, t, N, N, 1)
+    P = oracle.Problem(N, N, 1, N, theta, t, oracle.COMPLEX_FOURIER, 2 * M, 2)
+    u = P.fbp_init(g, 1)
+    const = 2 * (M // 2)  # channel of cos(0 t) = 1
+    np.testing.assert_allclose(u[..., const], f[:, 0], atol=1e-10)
+    others = np.delete(u, const, axis=-1)
+    assert np.max(np.abs(others)) < 1e-10

@@ -203,3 +203,48 @@ def test_orthonormalised_basis(kind):
     rawF = oracle.frame_table(kind, 4, 5)
     Rm = np.linalg.lstsq(P.Phi, raw, rcond=None)[0]
     np.testing.assert_allclose(P.PhiF @ Rm, rawF, atol=1e-11)
+
+
+def _complex_coeffs(u_real):
+    """u[..., 2j] + i u[..., 2j+1]: the complex coefficients of the channels."""
+    return u_real[..., 0::2] + 1j * u_real[..., 1::2]
+
+
+def test_complex_fourier_channels_against_complex_arithmetic():
+    """Sec. 5 basis phi_j(t) = exp(2 pi i t (j - M/2)): the real channel table
+    reproduces Re sum_j u_j phi_j(t) computed with complex numbers, and its
+    transpose is the paper's adjoint weight conj(phi_j) (Eq. radadjapr)."""
+    M = 6
+    rng = synth.rng_for(40)
+    t = rng.uniform(0.0, 1.0, 50)
+    Phi = oracle.basis_table(oracle.COMPLEX_FOURIER, 2 * M, t)
+    a = rng.standard_normal(2 * M)
+    uc = _complex_coeffs(a)
+    freqs = np.arange(M) - M // 2
+    E = np.exp(2j * np.pi * np.outer(t, freqs))  # [K][M]
+    np.testing.assert_allclose(Phi @ a, (E @ uc).real, atol=1e-13)
+    x = rng.standard_normal(t.size)
+    adj = E.conj().T @ x  # sum_k conj(phi_j(t_k)) x_k
+    back = Phi.T @ x
+    np.testing.assert_allclose(back[0::2], adj.real, atol=1e-12)
+    np.testing.assert_allclose(back[1::2], adj.imag, atol=1e-12)
+    with pytest.raises(ValueError):
+        oracle.basis_table(oracle.COMPLEX_FOURIER, 5, t)
+
+
+def test_complex_fourier_dynamic_projection():
+    """R applied to the complex-basis object equals Re of the complex sum of
+    the Radon transforms of the coefficient images (linearity, Eq. radapr)."""
+    M, n, ns = 4, 9, 11
+    rng = synth.rng_for(41)
+    theta, t = synth.scan(12, 2.0)
+    u = rng.standard_normal((1, n, n, 2 * M))
+    Phi = oracle.basis_table(oracle.COMPLEX_FOURIER, 2 * M, t)
+    g = oracle.dyn_fwd(u, theta, Phi, ns)[0]
+    uc = _complex_coeffs(u[0])
+    freqs = np.arange(M) - M // 2
+    for k in range(theta.size):
+        Rre = np.stack([oracle.joseph_fwd_slice(uc[..., j].real, theta[k], ns) for j in range(M)], axis=-1)
+        Rim = np.stack([oracle.joseph_fwd_slice(uc[..., j].imag, theta[k], ns) for j in range(M)], axis=-1)
+        ph = np.exp(2j * np.pi * t[k] * freqs)
+        np.testing.assert_allclose(g[k], ((Rre + 1j * Rim) @ ph).real, atol=1e-12)
