@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-jobs", type=int, default=24)
+    ap.add_argument("--no-slabs", action="store_true", help="skip the slab-streaming measurement")
     ap.add_argument("--variant", default=None,
                     help="force projector variants 'fwd,adj' (0 direct, 1 fold); default: autotuned")
     ap.add_argument("--profile-small", action="store_true",
@@ -295,6 +296,10 @@ def run_ours(a):
     if not a.no_serving:
         serving = {name: run_serving(a, local, prec) for name, prec in (("fp32", dr.F32), ("bf16", dr.BF16))}
 
+    slabs = None
+    if rank == 0 and not a.no_slabs:
+        slabs = run_slabs(w, theta, t, g_np, dev)
+
     cpu = None
     if rank == 0 and not a.no_cpu_baseline:
         cpu = cpu_baseline(w, theta, t, g_np)
@@ -327,6 +332,7 @@ def run_ours(a):
             "cpu_baseline": cpu,
             "serving": serving,
             "fbp_init": fbp,
+            "slab_streaming": slabs,
         }
         print(json.dumps(line))
 
@@ -393,6 +399,57 @@ def run_serving(a, device, prec):
             "stream": "Poisson 4 jobs/s, first %d arrivals; N in {128,256}, nz 4-16, K 360-3600 over 4-20 "
                       "half-turns, m in {4,8,16}, 30 ADMM-CG iterations" % len(jobs),
             "max_queue_s": max(r["queue_s"] for r in res)}
+
+
+def run_slabs(w, theta, t, g_np, dev, slab=4, iters=10):
+    """Chambolle-Pock with the volume in pinned host memory, streamed in slabs
+    (cp_solve_slabs), against the same iterations with the volume resident on
+    the device; the same operator norm for both."""
+    import torch
+
+    from paper_1809_09725_gb300 import dynrecon as dr
+
+    plan = dr.Plan(w.N, w.N, w.nz, w.ns, theta, t, w.basis, w.m, w.nt, dr.F32)
+    g = torch.from_numpy(g_np.astype(np.float32)).to(dev)
+    u = torch.zeros(plan.u_shape(), dtype=torch.float32, device=dev)
+    prm = dr.solve_params(dr.CHAMBOLLE_POCK, iters=1, lambda1=w.lambda1, lambda2=w.lambda2)
+    L = dr.admm_solve(plan, g, u, prm, want_objective=False)["op_norm"]
+    prm = dr.solve_params(dr.CHAMBOLLE_POCK, iters=iters, lambda1=w.lambda1, lambda2=w.lambda2, op_norm=L)
+    u.zero_()
+    dr.admm_solve(plan, g, u, prm, want_objective=False)
+    u.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    dr.admm_solve(plan, g, u, prm, want_objective=False)
+    torch.cuda.synchronize()
+    t_in = time.perf_counter() - t0
+    gh = torch.from_numpy(g_np.astype(np.float32)).pin_memory().numpy()
+    uh = np.zeros(plan.u_shape(), dtype=np.float32)
+    dr.cp_solve_slabs(plan, gh, uh, dr.solve_params(dr.CHAMBOLLE_POCK, iters=1, lambda1=w.lambda1,
+                                                    lambda2=w.lambda2, op_norm=L), slab, want_objective=False)
+    # per-iteration cost = difference of two runs (removes the per-call set-up:
+    # pinned host state, device buffers, first-touch of the host arrays)
+    times = []
+    for n_it in (iters, 3 * iters):
+        uh[...] = 0.0
+        prm_n = dr.solve_params(dr.CHAMBOLLE_POCK, iters=n_it, lambda1=w.lambda1, lambda2=w.lambda2, op_norm=L)
+        t0 = time.perf_counter()
+        dr.cp_solve_slabs(plan, gh, uh, prm_n, slab, want_objective=False)
+        times.append(time.perf_counter() - t0)
+    t_sl = (times[1] - times[0]) / 2.0
+    setup_s = times[0] - t_sl
+    V = w.voxels()
+    per_slice = (w.N * w.N * w.m * 4, w.K * w.ns * 4, w.N * w.N * w.nt * 16)  # u, data, dual field
+    nslab = (w.nz + slab - 1) // slab
+    h2d = w.nz * (2 * per_slice[0] + 2 * per_slice[1] + per_slice[2]) + (nslab - 1) * per_slice[0]
+    d2h = w.nz * (2 * per_slice[0] + per_slice[1] + per_slice[2])
+    return {"slab_nz": slab, "iters": iters, "ms_per_iter_streamed": 1e3 * t_sl / iters,
+            "ms_per_iter_in_core": 1e3 * t_in / iters,
+            "streamed_voxel_projection_per_s": 2.0 * w.K * V * iters / t_sl,
+            "h2d_bytes_per_iter": int(h2d), "d2h_bytes_per_iter": int(d2h),
+            "copy_gbs": (h2d + d2h) * iters / t_sl / 1e9, "setup_s_per_call": setup_s,
+            "note": "Chambolle-Pock, same operator norm; streamed = volume in pinned host memory, per-iteration "
+                    "time from the difference of a %d- and a %d-iteration call" % (iters, 3 * iters)}
 
 
 def load_traffic(kernel):

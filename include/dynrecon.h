@@ -61,6 +61,14 @@ typedef enum {
     DR_LEGENDRE = 1,     /* phi_j(t) = P_j(2t - 1), Legendre polynomials, unnormalised */
     DR_HAAR = 2,         /* phi_0 = 1; j = 2^l + p: +1 on [p, p+1/2)/2^l, -1 on [p+1/2, p+1)/2^l (Sec. 8) */
     DR_HEAVISIDE = 3,    /* phi_0 = 1, phi_j(t) = 1 for t >= j/m, else 0 (Sec. 4) */
+    /* Complex Fourier basis of Sec. 5, phi_j(t) = exp(2 pi i t (j - M/2)),
+     * j = 0..M-1 (M/2 rounded down), carried as m = 2M real channels: channel
+     * 2j holds Re u_j with function cos(w_j t), channel 2j+1 holds Im u_j with
+     * -sin(w_j t), w_j = 2 pi (j - M/2), so the object is Re sum_j u_j phi_j(t)
+     * and the adjoint weights are conj(phi_j) as in Eq. (radadjapr).  m must
+     * be even.  As a real basis it is redundant (cos(-w t) = cos(w t), sin 0 =
+     * 0), so DR_BASIS_ORTHONORMAL rejects it. */
+    DR_FOURIER_COMPLEX = 4,
     /* Flag OR-ed into the kind: orthonormalise the basis over the acquisition
      * times (Gram-Schmidt, Sec. 4): phi~ = phi R^{-1} with sum_k phi~_i(t_k)
      * phi~_j(t_k) = delta_ij; the frames use the same transformed functions. */
@@ -205,7 +213,9 @@ dr_status dyn_radon_adj_noalloc(dr_plan *plan, const void *g, void *u, double be
  *      the FBP image of window w is f_w = (pi / K_w) sum_{k in w} R*_k q_k
  *      (K_w projections spread over whole half-turns);
  *   3. u is the least-squares fit over the acquisition times:
- *      u = argmin sum_k || sum_j phi_j(t_k) u_j - f_{w(k)} ||^2.
+ *      u = argmin sum_k || sum_j phi_j(t_k) u_j - f_{w(k)} ||^2,
+ *      the minimum-norm one when the functions are dependent over the times
+ *      (singular values of Phi below 1e-6 of the largest count as zero).
  * n_windows = 1 gives the static FBP of all projections spread over the
  * basis (the constant function's coefficients when it is in the span); one
  * window per half-turn gives the per-half-turn FBP frames of Sec. 5.
@@ -213,8 +223,8 @@ dr_status dyn_radon_adj_noalloc(dr_plan *plan, const void *g, void *u, double be
  * (overwritten).  The plan keeps scratch for the filtered data (nz K ns
  * compute-typed values, plus nx ny nz m floats for BF16 plans) until it is
  * destroyed.  Waits for the plan's stream before uploading its table, then
- * runs asynchronously.  DR_EINVAL if n_windows is outside [1, K] or the basis
- * functions are dependent over the acquisition times.
+ * runs asynchronously.  DR_EINVAL if n_windows is outside [1, K] or every
+ * basis function vanishes at every acquisition time.
  */
 dr_status dr_fbp_init(dr_plan *plan, const void *g, void *u, int n_windows);
 

@@ -8,7 +8,8 @@
 //      image of window w is f_w = (pi / K_w) sum_{k in w} R*_k q_k.  The
 //      coefficients are the least-squares fit over the acquisition times,
 //      u = argmin sum_k || sum_j phi_j(t_k) u_j - f_{w(k)} ||^2, i.e.
-//      u_j = sum_w A[j][w] f_w with A = (Phi^T Phi)^{-1} Phi^T S.
+//      u_j = sum_w A[j][w] f_w with A = Phi^+ S (minimum-norm least squares,
+//      (Phi^T Phi)^{-1} Phi^T S for functions independent over the times).
 //      Both steps are linear in q, so u_j = sum_k Psi[k][j] R*_k q_k with
 //      Psi[k][j] = (pi / K_{w(k)}) A[j][w(k)]: one dynamic back-projection
 //      with the table Psi in place of Phi (either projector variant).
@@ -79,8 +80,48 @@ static dr_status upload_as(void *dst, const std::vector<double> &src) {
     return DR_OK;
 }
 
-// Psi[k][j] (row stride MP, zero padded) for nw windows; DR_EINVAL if the
-// basis functions are dependent over the acquisition times.
+// Eigen-decomposition of a symmetric n x n matrix by cyclic Jacobi rotations
+// (Jacobi's method; Golub and Van Loan, Matrix Computations, Sec. 8.5):
+// A = V diag(lam) V^T, V[i][e] = component i of eigenvector e.
+static void sym_eig(std::vector<double> A, int n, std::vector<double> &V, std::vector<double> &lam) {
+    V.assign((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) V[(size_t)i * n + i] = 1.0;
+    for (int sweep = 0; sweep < 64; ++sweep) {
+        double off = 0.0, diag = 0.0;
+        for (int p = 0; p < n; ++p) {
+            diag += A[(size_t)p * n + p] * A[(size_t)p * n + p];
+            for (int q = p + 1; q < n; ++q) off += A[(size_t)p * n + q] * A[(size_t)p * n + q];
+        }
+        if (off <= 1e-32 * diag) break;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                const double apq = A[(size_t)p * n + q];
+                if (apq == 0.0) continue;
+                const double th = (A[(size_t)q * n + q] - A[(size_t)p * n + p]) / (2.0 * apq);
+                const double t = (th >= 0.0 ? 1.0 : -1.0) / (std::fabs(th) + std::sqrt(th * th + 1.0));
+                const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < n; ++k) {  // columns p, q
+                    const double akp = A[(size_t)k * n + p], akq = A[(size_t)k * n + q];
+                    A[(size_t)k * n + p] = c * akp - s * akq;
+                    A[(size_t)k * n + q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < n; ++k) {  // rows p, q
+                    const double apk = A[(size_t)p * n + k], aqk = A[(size_t)q * n + k];
+                    A[(size_t)p * n + k] = c * apk - s * aqk;
+                    A[(size_t)q * n + k] = s * apk + c * aqk;
+                }
+                for (int k = 0; k < n; ++k) {
+                    const double vkp = V[(size_t)k * n + p], vkq = V[(size_t)k * n + q];
+                    V[(size_t)k * n + p] = c * vkp - s * vkq;
+                    V[(size_t)k * n + q] = s * vkp + c * vkq;
+                }
+            }
+    }
+    lam.assign(n, 0.0);
+    for (int i = 0; i < n; ++i) lam[i] = A[(size_t)i * n + i];
+}
+
+// Psi[k][j] (row stride MP, zero padded) for nw windows.
 static dr_status fbp_table(const dr_plan *P, int nw, std::vector<double> &psi) {
     const int K = P->K, m = P->m;
     std::vector<int> win(K);
@@ -91,39 +132,33 @@ static dr_status fbp_table(const dr_plan *P, int nw, std::vector<double> &psi) {
         win[k] = w;
         ++cnt[w];
     }
-    // Gram matrix Phi^T Phi and its Cholesky factor L (G = L L^T)
-    std::vector<double> G((size_t)m * m, 0.0), L((size_t)m * m, 0.0);
+    // Gram matrix Phi^T Phi = V diag(lam) V^T (cyclic Jacobi rotations)
+    std::vector<double> G((size_t)m * m, 0.0), V, lam;
     for (int k = 0; k < K; ++k)
         for (int i = 0; i < m; ++i)
             for (int j = 0; j < m; ++j) G[(size_t)i * m + j] += P->Phi[(size_t)k * m + i] * P->Phi[(size_t)k * m + j];
-    for (int j = 0; j < m; ++j) {
-        double d = G[(size_t)j * m + j];
-        for (int q = 0; q < j; ++q) d -= L[(size_t)j * m + q] * L[(size_t)j * m + q];
-        if (!(d > 1e-24 * std::max(1.0, G[0])))
-            return fail(DR_EINVAL, "dr_fbp_init: basis functions are dependent over the acquisition times");
-        L[(size_t)j * m + j] = std::sqrt(d);
-        for (int i = j + 1; i < m; ++i) {
-            double e = G[(size_t)i * m + j];
-            for (int q = 0; q < j; ++q) e -= L[(size_t)i * m + q] * L[(size_t)j * m + q];
-            L[(size_t)i * m + j] = e / L[(size_t)j * m + j];
-        }
-    }
-    // A[:, w] = G^{-1} (sum_{k in w} Phi[k][:])
+    sym_eig(G, m, V, lam);
+    double lmax = 0.0;
+    for (double l : lam) lmax = std::max(lmax, l);
+    if (!(lmax > 0.0)) return fail(DR_EINVAL, "dr_fbp_init: the basis vanishes at every acquisition time");
+    // A[:, w] = G^+ (sum_{k in w} Phi[k][:]): the minimum-norm least-squares
+    // fit; eigenvalues below 1e-12 lam_max (singular values of Phi below
+    // 1e-6 of the largest) count as zero
     std::vector<double> A((size_t)m * nw, 0.0), y(m);
     for (int w = 0; w < nw; ++w) {
         std::vector<double> rhs(m, 0.0);
         for (int k = 0; k < K; ++k)
             if (win[k] == w)
                 for (int j = 0; j < m; ++j) rhs[j] += P->Phi[(size_t)k * m + j];
-        for (int i = 0; i < m; ++i) {  // L y = rhs
-            double v = rhs[i];
-            for (int q = 0; q < i; ++q) v -= L[(size_t)i * m + q] * y[q];
-            y[i] = v / L[(size_t)i * m + i];
+        for (int e = 0; e < m; ++e) {  // y = diag(1/lam) V^T rhs
+            double v = 0.0;
+            for (int j = 0; j < m; ++j) v += V[(size_t)j * m + e] * rhs[j];
+            y[e] = lam[e] > 1e-12 * lmax ? v / lam[e] : 0.0;
         }
-        for (int i = m - 1; i >= 0; --i) {  // L^T a = y
-            double v = y[i];
-            for (int q = i + 1; q < m; ++q) v -= L[(size_t)q * m + i] * A[(size_t)q * nw + w];
-            A[(size_t)i * nw + w] = v / L[(size_t)i * m + i];
+        for (int i = 0; i < m; ++i) {
+            double v = 0.0;
+            for (int e = 0; e < m; ++e) v += V[(size_t)i * m + e] * y[e];
+            A[(size_t)i * nw + w] = v;
         }
     }
     psi.assign((size_t)K * P->MP, 0.0);

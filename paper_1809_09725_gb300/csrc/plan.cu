@@ -36,9 +36,20 @@ int template_m(int m) {
 // ---------------------------------------------------------------------------
 // Temporal basis evaluation (Sec. 4, Eq. repr).  Real Fourier:
 // phi_0 = 1, phi_{2i-1} = cos(2 pi i t), phi_{2i} = sin(2 pi i t).
-// Shifted Legendre: phi_j(t) = P_j(2t - 1) by Bonnet's recurrence.
+// Shifted Legendre: phi_j(t) = P_j(2t - 1) by Bonnet's recurrence.  Haar,
+// Heaviside steps, and the complex Fourier basis of Sec. 5 as real channel
+// pairs (cos(w_j t), -sin(w_j t)), w_j = 2 pi (j - M/2).
 // ---------------------------------------------------------------------------
 static void eval_basis(dr_basis kind, int m, double t, double *row) {
+    if (kind == DR_FOURIER_COMPLEX) {
+        const int M = m / 2;
+        for (int j = 0; j < M; ++j) {
+            const double w = 2.0 * M_PI * (double)(j - M / 2);
+            row[2 * j] = std::cos(w * t);
+            row[2 * j + 1] = -std::sin(w * t);
+        }
+        return;
+    }
     if (kind == DR_HAAR) {
         row[0] = 1.0;
         for (int j = 1; j < m; ++j) {
@@ -453,8 +464,10 @@ dr_status dr_plan_create(dr_plan **out, int nx, int ny, int nz, int ns, int K, c
         return fail(DR_EINVAL, "dr_plan_create: size out of range");
     if (m < 1 || m > 32) return fail(DR_EINVAL, "dr_plan_create: m must be in [1, 32]");
     const int kind = (int)basis & 0xff, flags = (int)basis & ~0xff;
-    if (kind < DR_FOURIER_REAL || kind > DR_HEAVISIDE || (flags & ~DR_BASIS_ORTHONORMAL))
+    if (kind < DR_FOURIER_REAL || kind > DR_FOURIER_COMPLEX || (flags & ~DR_BASIS_ORTHONORMAL))
         return fail(DR_EINVAL, "dr_plan_create: bad basis");
+    if (kind == DR_FOURIER_COMPLEX && m % 2 != 0)
+        return fail(DR_EINVAL, "dr_plan_create: the complex Fourier basis needs an even m (2 real channels per function)");
     if (prec != DR_F32 && prec != DR_BF16_F32ACC && prec != DR_F64)
         return fail(DR_EINVAL, "dr_plan_create: bad precision");
     if (!theta || !t) return fail(DR_EINVAL, "dr_plan_create: theta/t are NULL");

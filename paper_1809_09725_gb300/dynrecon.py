@@ -20,7 +20,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libdynrecon.so")
 
 DR_OK, DR_EINVAL, DR_ENOMEM, DR_ECUDA, DR_ETIMEOUT, DR_ENOTCONV, DR_ECANCELED = 0, -1, -2, -3, -4, -5, -6
-FOURIER, LEGENDRE, HAAR, HEAVISIDE = 0, 1, 2, 3
+FOURIER, LEGENDRE, HAAR, HEAVISIDE, COMPLEX_FOURIER = 0, 1, 2, 3, 4
 ORTHONORMAL = 0x100  # flag OR-ed into the basis kind
 F32, BF16, F64 = 0, 1, 2
 ADMM_CG, CHAMBOLLE_POCK = 0, 1

@@ -4,9 +4,10 @@ starting point of the iterations) against the oracle.
 dr_fbp_init filters every projection row with the discrete Shepp-Logan
 kernel and back-projects once with the windowed least-squares table in place
 of the basis table; the oracle filters, back-projects window by window and
-fits the coefficients with a dense solve.  Cases: several bases and window
-counts, ragged sizes, both projector variants, FP64 / FP32 / BF16 plans, a
-two-slice cut of the 256^2 x 1800 workload, and bad arguments.
+fits the coefficients by a dense minimum-norm least-squares solve.  Cases:
+several bases and window counts (one of them redundant), ragged sizes, both
+projector variants, FP64 / FP32 / BF16 plans, a two-slice cut of the 256^2 x
+1800 workload, and bad arguments.
 """
 import numpy as np
 import pytest
@@ -29,6 +30,7 @@ CASES = {
     "heaviside": (40, 40, 2, 40, 160, 4.0, dr.HEAVISIDE, 4, 4, 4),
     "m16_orthonormal": (24, 26, 2, 31, 200, 5.0, dr.LEGENDRE | dr.ORTHONORMAL, 16, 5, 5),
     "wide_det": (20, 20, 1, 300, 64, 2.0, dr.FOURIER, 3, 2, 2),
+    "complex_redundant": (30, 30, 2, 32, 128, 4.0, dr.COMPLEX_FOURIER, 8, 4, 4),
 }
 
 
@@ -144,11 +146,15 @@ def test_fbp_init_rejects_bad_arguments():
         with pytest.raises(dr.DynreconError) as err:
             dr.fbp_init(plan, gd, u, bad)
         assert err.value.status == dr.DR_EINVAL
-    # m = 4 Legendre functions sampled at only 3 distinct times are dependent
+
+
+def test_fbp_init_dependent_basis_takes_minimum_norm_fit():
+    """m = 4 Legendre functions sampled at only 3 distinct times are dependent:
+    the fit is the minimum-norm least-squares one, as in the oracle."""
     theta = np.linspace(0.0, np.pi, 12, endpoint=False)
     t = np.repeat([0.1, 0.5, 0.9], 4)
-    p2 = dr.Plan(16, 16, 1, 16, theta, t, dr.LEGENDRE, 4, 2, dr.F32)
-    u2 = torch.zeros(p2.u_shape(), dtype=torch.float32, device="cuda")
-    with pytest.raises(dr.DynreconError) as err:
-        dr.fbp_init(p2, torch.zeros(p2.g_shape(), dtype=torch.float32, device="cuda"), u2, 1)
-    assert err.value.status == dr.DR_EINVAL
+    rng = synth.rng_for(777)
+    g = rng.standard_normal((1, 12, 16))
+    P = oracle.Problem(16, 16, 1, 16, theta, t, oracle.LEGENDRE, 4, 2)
+    u = _run((16, 16, 1, 16, theta, t, dr.LEGENDRE, 4, 2), g, dr.F64, 3)
+    assert rel(u, P.fbp_init(g, 3)) <= 1e-9

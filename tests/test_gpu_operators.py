@@ -38,6 +38,8 @@ CASES = {
     "haar": (30, 28, 2, 33, 120, 4.0, False, dr.HAAR, 6, 4),
     "heaviside": (26, 26, 2, 29, 90, 3.0, False, dr.HEAVISIDE, 5, 5),
     "orthonormal": (32, 32, 1, 32, 128, 4.0, True, dr.FOURIER | dr.ORTHONORMAL, 4, 4),
+    "complex_m8": (36, 30, 2, 40, 160, 8.0, False, dr.COMPLEX_FOURIER, 16, 8),
+    "complex_m4": (28, 28, 1, 28, 96, 4.0, True, dr.COMPLEX_FOURIER, 8, 4),
 }
 
 
@@ -283,3 +285,11 @@ def test_dependent_basis_is_rejected():
     t = t * 0.5
     with pytest.raises(dr.DynreconError):
         dr.Plan(16, 16, 1, 16, theta, t, dr.HEAVISIDE | dr.ORTHONORMAL, 8, 4, dr.F32)
+
+
+def test_complex_basis_rejects_odd_m_and_orthonormalisation():
+    theta, t = synth.scan(40, 2.0)
+    with pytest.raises(dr.DynreconError):
+        dr.Plan(16, 16, 1, 16, theta, t, dr.COMPLEX_FOURIER, 5, 2, dr.F32)
+    with pytest.raises(dr.DynreconError):
+        dr.Plan(16, 16, 1, 16, theta, t, dr.COMPLEX_FOURIER | dr.ORTHONORMAL, 8, 2, dr.F32)

@@ -29,6 +29,7 @@ CASES = {
     "nt1": (21, 22, 2, dr.FOURIER, 3, 1),
     "haar": (20, 18, 3, dr.HAAR, 4, 8),
     "orthonormal": (18, 20, 2, dr.LEGENDRE | dr.ORTHONORMAL, 5, 6),
+    "complex": (19, 17, 3, dr.COMPLEX_FOURIER, 8, 6),
 }
 
 
