@@ -250,6 +250,32 @@ def run_ours(a):
     peak = fp32_peak_tflops()
     traffic = load_traffic(kname)
 
+    # the projector pair on BF16 storage (FP32 accumulation) next to FP32
+    bf16_ops = None
+    if rank == 0:
+        pb = dr.Plan(w.N, w.N, w.nz, w.ns, theta, t, w.basis, w.m, w.nt, dr.BF16)
+        pb.autotune()
+        ub = p_in.to(torch.bfloat16)
+        gb = torch.empty(pb.g_shape(), dtype=torch.bfloat16, device=dev)
+        uab = torch.empty_like(ub)
+        for _ in range(3):
+            dr.dyn_radon_fwd(pb, ub, gb)
+            dr.dyn_radon_adj(pb, gb, uab)
+        bev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        torch.cuda.synchronize()
+        bev[0].record(stream)
+        for _ in range(reps):
+            dr.dyn_radon_fwd(pb, ub, gb)
+        bev[1].record(stream)
+        for _ in range(reps):
+            dr.dyn_radon_adj(pb, gb, uab)
+        bev[2].record(stream)
+        torch.cuda.synchronize()
+        bf16_ops = {"fwd_ms": bev[0].elapsed_time(bev[1]) / reps, "adj_ms": bev[1].elapsed_time(bev[2]) / reps,
+                    "fp32_fwd_ms": fwd_ms, "fp32_adj_ms": adj_ms,
+                    "note": "dyn_radon_fwd / dyn_radon_adj on bf16 u and g (FP32 accumulation), same workload"}
+        del pb, ub, gb, uab
+
     # FBP initial guess (Sec. 5), one window per half-turn: filter + one back-projection
     ufbp = torch.empty(plan.u_shape(), dtype=torch.float32, device=dev)
     n_win = int(round(w.n_halfturns))
@@ -332,6 +358,7 @@ def run_ours(a):
             "cpu_baseline": cpu,
             "serving": serving,
             "fbp_init": fbp,
+            "bf16_operators": bf16_ops,
             "slab_streaming": slabs,
         }
         print(json.dumps(line))
@@ -398,7 +425,8 @@ def run_serving(a, device, prec):
             "peak_device_gb": st["peak_device_bytes"] / 1e9, "budget_gb": 150,
             "stream": "Poisson 4 jobs/s, first %d arrivals; N in {128,256}, nz 4-16, K 360-3600 over 4-20 "
                       "half-turns, m in {4,8,16}, 30 ADMM-CG iterations" % len(jobs),
-            "max_queue_s": max(r["queue_s"] for r in res)}
+            "max_queue_s": max(r["queue_s"] for r in res),
+            "errors": [{"job": i, "rc": r["rc"], "error": r["error"]} for i, r in enumerate(res) if r["rc"] != 0]}
 
 
 def run_slabs(w, theta, t, g_np, dev, slab=4, iters=10):

@@ -144,6 +144,17 @@ dr_status dr_plan_set_variant(dr_plan *plan, int fwd_variant, int adj_variant);
  */
 dr_status dr_plan_autotune(dr_plan *plan, double *times_ms);
 
+/*
+ * Fix the folded forward's strip: `lines` image lines staged in shared memory
+ * per step (1 <= lines; lines (x 2 with async) within the plan's 110 KB strip
+ * budget) and async = 1 for cp.async double buffering (F32 plans with m a
+ * multiple of 4, BF16 plans with m a multiple of 8).  Every choice marches
+ * each ray over the same lines in the same order, so results are identical;
+ * only the time changes.  A later autotune may replace the choice.  DR_EINVAL
+ * if the fold is unavailable or the choice does not fit.
+ */
+dr_status dr_plan_set_fold_strip(dr_plan *plan, int lines, int async);
+
 typedef struct {
     int unique_angles;   /* distinct theta mod pi (0: the fold is unavailable) */
     int max_group;       /* most projections sharing one theta mod pi */

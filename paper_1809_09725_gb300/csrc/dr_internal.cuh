@@ -69,6 +69,9 @@ constexpr int kAdjStages = 3;  // TMA pipeline depth
 constexpr int kFwdThreads = 256;
 constexpr int kFwdRPT = 8;   // rays per thread
 constexpr int kFwdGuard = 4; // zero cells on each side of a staged line
+// Shared-memory budget of the folded forward's strip (float lines; both
+// buffers when double-buffered): two CTAs of 256 threads still fit an SM.
+constexpr int kFoldStripBudget = 110 * 1024;
 
 constexpr int kRedThreads = 256;
 constexpr int kRedBlocksMax = 1024;
@@ -157,6 +160,7 @@ struct dr_plan {
     int *d_fold_blocks = nullptr;     // [n_fold_blocks][fold_P] unique angles grouped by stepping axis
     int n_fold_blocks = 0, fold_P = 0, fold_R = 0, fold_nchunk = 1;
     int fold_lines = 0, fold_async = 0;  // folded forward: strip lines per buffer, cp.async double buffering
+    int fold_lines_st = 0, fold_async_st = 0;  // the same for the bf16-strip kernel of BF16 plans
     bool fold_fwd_ok = false;         // the forward strip fits in shared memory
     void *d_gt = nullptr;             // folded data [nz][U][ns][MS] float (allocated on first use)
     size_t gt_bytes = 0;
@@ -232,6 +236,13 @@ dr_status launch_tv_sum(dr_plan *P, const void *u, double lambda2, double *obj_r
 // Vector kernels (solver.cu).
 dr_status launch_dot_to(dr_plan *P, const void *a, const void *b, size_t n, bool storage, double *dst,
                         cudaStream_t st);
+
+// Allow `smem` bytes of dynamic shared memory for kernel `fn` on the current
+// device.  The attribute is process-wide per kernel while plans on several
+// threads launch it with different sizes, so it is raised once per kernel and
+// device to the device's opt-in maximum (never set to one launch's size,
+// which another thread could undercut between its set and its launch).
+dr_status allow_dynamic_smem(const void *fn, size_t smem);
 
 // Host-side tensor-map encoder (driver entry point, resolved once).
 bool encode_tensor_map_2d(CUtensorMap *map, CUtensorMapDataType dt, void *base, uint64_t dim0,

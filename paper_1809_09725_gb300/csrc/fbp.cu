@@ -63,7 +63,10 @@ static dr_status launch_filter(dr_plan *P, const void *g, cudaStream_t st) {
     const long long rows = (long long)P->nz * P->K;
     const size_t smem = sizeof(T) * (size_t)(3 * P->ns - 1);
     auto kern = shepp_logan_kernel<S, T>;
-    if (smem > 48 * 1024) DR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    {
+        dr_status s = allow_dynamic_smem((const void *)kern, smem);
+        if (s != DR_OK) return s;
+    }
     int per_sm = 0;
     DR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kFbpThreads, smem));
     const long long grid = std::min<long long>(rows, (long long)P->num_sms * std::max(per_sm, 1));

@@ -20,6 +20,8 @@
 // Work per application drops from K (m + c) to U (2m + c') per voxel, U the
 // number of unique angles.
 #pragma once
+#include <type_traits>
+
 #include "dr_device.cuh"
 
 namespace dr {
@@ -34,6 +36,42 @@ constexpr int kFoldAdjStages = 2;
 // neighbouring pixels).
 __host__ __device__ constexpr int fold_ms(int M) { return M <= 4 ? 4 : ((M % 8 == 0) ? M + 4 : M); }
 __host__ __device__ constexpr int fold_rpt(int M) { return M <= 4 ? 8 : 32 / M; }
+
+// Element stride of one pixel's coefficient vector in the forward strip.
+// Float strips use fold_ms.  BF16 plans stage the stored bf16 values as they
+// are (exact; the march widens them to float in registers), which halves the
+// shared-memory bytes per ray step: 8-byte vectors for M <= 4, otherwise an
+// odd number of 16-byte slots per pixel (no bank conflicts between
+// neighbouring pixels).
+__host__ __device__ constexpr int fold_bf16_ps(int M) {
+    return M <= 4 ? 4 : 8 * (((M + 7) / 8) % 2 == 1 ? (M + 7) / 8 : (M + 7) / 8 + 1);
+}
+template <typename S, typename T, int M>
+__host__ __device__ constexpr int fold_strip_ps() {
+    return sizeof(S) == 2 ? fold_bf16_ps(M) : fold_ms(M);
+}
+
+// M bf16 coefficients of one strip pixel (PS-element slots), widened to float.
+template <int M, int PS>
+__device__ __forceinline__ void load_vec_bf16(const bf16 *p, float (&v)[M]) {
+    if constexpr (PS == 4) {
+        const uint2 a = *reinterpret_cast<const uint2 *>(p);
+        const unsigned w[2] = {a.x, a.y};
+#pragma unroll
+        for (int j = 0; j < M; ++j) v[j] = __uint_as_float((j & 1) ? (w[j >> 1] & 0xffff0000u) : (w[j >> 1] << 16));
+    } else {
+#pragma unroll
+        for (int c = 0; c < (M + 7) / 8; ++c) {
+            const uint4 a = reinterpret_cast<const uint4 *>(p)[c];
+            const unsigned w[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+            for (int h = 0; h < 8; ++h) {
+                const int j = 8 * c + h;
+                if (j < M) v[j] = __uint_as_float((h & 1) ? (w[h >> 1] & 0xffff0000u) : (w[h >> 1] << 16));
+            }
+        }
+    }
+}
 
 template <typename T, int M>
 __device__ __forceinline__ void load_vec(const T *p, T (&v)[M]) {
@@ -55,18 +93,23 @@ __device__ __forceinline__ void load_vec(const T *p, T (&v)[M]) {
 // ===========================================================================
 // Forward
 // ===========================================================================
+// Resident CTAs per SM the folded forward asks the compiler for: the march is
+// latency bound, and at M = 8 three CTAs (<= 85 registers) beat two.
+__host__ __device__ constexpr int fold_fwd_min_blocks(int M) { return M == 8 ? 3 : 1; }
+
 template <typename S, typename T, int M>
-__global__ void __launch_bounds__(kFoldThreads)
+__global__ void __launch_bounds__(kFoldThreads, fold_fwd_min_blocks(M))
     fold_fwd_kernel(const S *__restrict__ u, S *__restrict__ out, const S *__restrict__ gm,
                     const FwdProj *__restrict__ uproj, const int *__restrict__ start, const int *__restrict__ member,
                     const T *__restrict__ phip, const int *__restrict__ blocks, int nx, int ny, int ns, int K,
                     int m, int MP, int P, int R, int nchunk, int mode, T sigma, int async_stage) {
-    constexpr int MS = fold_ms(M);
+    using ST = std::conditional_t<sizeof(S) == 2, S, T>;  // strip element: stored bf16, else the compute type
+    constexpr int MS = fold_strip_ps<S, T, M>();
     constexpr int RPT = fold_rpt(M);
     extern __shared__ __align__(16) unsigned char fold_smem[];
     T *scale_s = reinterpret_cast<T *>(fold_smem);                       // [64]
     long long *bfx_s = reinterpret_cast<long long *>(fold_smem + 256);   // [64]
-    T *strip = reinterpret_cast<T *>(fold_smem + 768);                   // [R][wpad][MS]
+    ST *strip = reinterpret_cast<ST *>(fold_smem + 768);                 // [R][wpad][MS]
 
     const int tid = threadIdx.x;
     const int z = blockIdx.y;
@@ -83,7 +126,7 @@ __global__ void __launch_bounds__(kFoldThreads)
         scale_s[p] = (T)f.scale;
         bfx_s[p] = f.B_fx;
     }
-    for (int i = tid; i < (async_stage ? 2 : 1) * R * wpad * MS; i += kFoldThreads) strip[i] = T(0);
+    for (int i = tid; i < (async_stage ? 2 : 1) * R * wpad * MS; i += kFoldThreads) strip[i] = ST(0.0f);
 
     const int rays_per_cta = kFoldThreads * RPT;
     const int b_base = chunk * rays_per_cta;
@@ -127,7 +170,7 @@ __global__ void __launch_bounds__(kFoldThreads)
     // Stage lines [r0, r0+nl) of the m-vector image into buffer `buf`:
     // asynchronously (cp.async, 16-byte chunks) when the coefficients are
     // 16-byte float vectors, else through registers.
-    auto stage = [&](T *buf, int r0, int nl) {
+    auto stage = [&](ST *buf, int r0, int nl) {
         const int npx = nl * W;
         for (int qq = tid; qq < npx; qq += kFoldThreads) {
             int rl, i;
@@ -141,7 +184,26 @@ __global__ void __launch_bounds__(kFoldThreads)
                 rl = qq - i * nl;
                 pix = zoff + (size_t)i * nx + (r0 + rl);
             }
-            T *dst = buf + ((size_t)rl * wpad + kFwdGuard + i) * MS;
+            ST *dst = buf + ((size_t)rl * wpad + kFwdGuard + i) * MS;
+            if constexpr (sizeof(S) == 2) {
+                // bf16 strip: the stored values as they are
+                if constexpr ((M % 8) == 0) {
+                    if (m == M) {
+                        if (async_stage) {
+#pragma unroll
+                            for (int j = 0; j < M / 8; ++j) cp_async_16(dst + 8 * j, u + pix * m + 8 * j);
+                        } else {
+#pragma unroll
+                            for (int j = 0; j < M / 8; ++j)
+                                reinterpret_cast<uint4 *>(dst)[j] = __ldg(reinterpret_cast<const uint4 *>(u + pix * m) + j);
+                        }
+                        continue;
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < M; ++j) dst[j] = j < m ? u[pix * m + j] : S(0.0f);
+                continue;
+            } else {
             if constexpr (sizeof(S) == 4 && (M % 4) == 0) {
                 if (async_stage) {
 #pragma unroll
@@ -159,32 +221,33 @@ __global__ void __launch_bounds__(kFoldThreads)
 #pragma unroll
                 for (int j = 0; j < M; ++j) dst[j] = v[j];
             }
+            }
         }
     };
-    T *bufs[2] = {strip, strip + (size_t)R * wpad * MS};
+    const size_t buf_elems = (size_t)R * wpad * MS;  // buffer b starts at strip + b * buf_elems
     if (async_stage) {
-        stage(bufs[0], 0, min(R, H));
+        stage(strip, 0, min(R, H));
         cp_async_commit();
     }
     int s_idx = 0;
     for (int r0 = 0; r0 < H; r0 += R, ++s_idx) {
         const int nl = min(R, H - r0);
-        T *cur;
+        ST *cur;
         if (async_stage) {
             // prefetch the next strip into the other buffer, then wait for this one
             if (r0 + R < H) {
-                stage(bufs[(s_idx + 1) & 1], r0 + R, min(R, H - r0 - R));
+                stage(strip + ((s_idx + 1) & 1) * buf_elems, r0 + R, min(R, H - r0 - R));
                 cp_async_commit();
                 cp_async_wait<1>();
             } else {
                 cp_async_wait<0>();
             }
             __syncthreads();
-            cur = bufs[s_idx & 1];
+            cur = strip + (s_idx & 1) * buf_elems;
         } else {
-            stage(bufs[0], r0, nl);
+            stage(strip, r0, nl);
             __syncthreads();
-            cur = bufs[0];
+            cur = strip;
         }
         // ---- march the rays: all m coefficient sums per ray ----
 #pragma unroll
@@ -195,7 +258,7 @@ __global__ void __launch_bounds__(kFoldThreads)
             const int p = (nchunk > 1) ? 0 : rid / ns;
             const long long bfx = bfx_s[p];
             long long x = x0fx[q] + (long long)rs * bfx;
-            const T *row = cur + ((size_t)(rs - r0) * wpad + kFwdGuard) * MS;
+            const ST *row = cur + ((size_t)(rs - r0) * wpad + kFwdGuard) * MS;
 #pragma unroll 1
             for (int r = rs; r <= re; ++r) {
                 int i0 = (int)(x >> 32);
@@ -203,8 +266,13 @@ __global__ void __launch_bounds__(kFoldThreads)
                 const float w = __uint_as_float(0x3F800000u | ((unsigned)x >> 9)) - 1.0f;
                 const float w1m = 1.0f - w;
                 T t0[M], t1[M];
-                load_vec<T, M>(row + i0 * MS, t0);
-                load_vec<T, M>(row + (i0 + 1) * MS, t1);
+                if constexpr (sizeof(S) == 2) {
+                    load_vec_bf16<M, MS>(row + i0 * MS, t0);
+                    load_vec_bf16<M, MS>(row + (i0 + 1) * MS, t1);
+                } else {
+                    load_vec<T, M>(row + i0 * MS, t0);
+                    load_vec<T, M>(row + (i0 + 1) * MS, t1);
+                }
 #pragma unroll
                 for (int j = 0; j < M; ++j) acc[q][j] = fmaf(w, t1[j], fmaf(w1m, t0[j], acc[q][j]));
                 x += bfx;
@@ -455,19 +523,21 @@ inline int fold_adj_wb(int M) {
 template <typename S, typename T, int M>
 dr_status fold_fwd_launch_t(dr_plan *P, const void *u, void *out, const void *gm, int mode, double sigma,
                             cudaStream_t st) {
-    constexpr int MS = fold_ms(M);
+    using ST = std::conditional_t<sizeof(S) == 2, S, T>;
+    constexpr int MS = fold_strip_ps<S, T, M>();
     const int Wmax = std::max(P->nx, P->ny);
     const int wpad = Wmax + 2 * kFwdGuard;
     // strip height and staging mode: the autotuned choice (cp.async double
-    // buffering needs 16-byte float coefficient vectors)
-    const int async_ok = (sizeof(S) == 4 && (M % 4) == 0 && P->m == M) ? 1 : 0;
-    const int async_stage = async_ok && P->fold_async;
-    const int R = std::max(1, P->fold_lines);
-    const size_t smem = 768 + sizeof(T) * (size_t)(async_stage ? 2 : 1) * R * wpad * MS;
+    // buffering needs whole 16-byte coefficient vectors)
+    const int async_ok = (P->m == M && ((sizeof(S) == 4 && (M % 4) == 0) || (sizeof(S) == 2 && (M % 8) == 0))) ? 1 : 0;
+    const bool bf16_strip = sizeof(S) == 2;
+    const int async_stage = async_ok && (bf16_strip ? P->fold_async_st : P->fold_async);
+    const int R = std::max(1, bf16_strip ? P->fold_lines_st : P->fold_lines);
+    const size_t smem = 768 + sizeof(ST) * (size_t)(async_stage ? 2 : 1) * R * wpad * MS;
     auto kern = fold_fwd_kernel<S, T, M>;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return cuda_fail(e, "fold fwd: smem attribute");
+    {
+        dr_status s = allow_dynamic_smem((const void *)kern, smem);
+        if (s != DR_OK) return s;
     }
     dim3 grid(P->n_fold_blocks * P->fold_nchunk, P->nz);
     kern<<<grid, kFoldThreads, smem, st>>>((const S *)u, (S *)out, (const S *)gm, P->d_fold_fwd, P->d_fold_start,
@@ -500,9 +570,9 @@ dr_status fold_adj_launch_t(dr_plan *P, const void *g, void *u, double alpha, do
     const size_t stage = kFoldAdjP * row_bytes + 128 * ((kFoldAdjP * sizeof(FoldPrm) + 127) / 128);
     const size_t smem = stage * kFoldAdjStages + 128;
     auto kern = fold_adj_kernel<S, T, M>;
-    if (smem > 48 * 1024) {
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return cuda_fail(e, "fold adj: smem attribute");
+    {
+        dr_status s = allow_dynamic_smem((const void *)kern, smem);
+        if (s != DR_OK) return s;
     }
     constexpr int TX = FoldAdjShape<M>::TX;
     const int ntx = (P->nx + TX - 1) / TX, nty = (P->ny + kAdjTY - 1) / kAdjTY;

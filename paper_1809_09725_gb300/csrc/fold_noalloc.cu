@@ -70,9 +70,9 @@ static dr_status noalloc_adj_t(dr_plan *P, const void *g, void *u, double beta, 
     const size_t stage = kFoldAdjP * row_bytes + 128 * ((kFoldAdjP * sizeof(FoldPrm) + 127) / 128);
     const size_t smem = stage * kFoldAdjStages + 128;
     auto kern = fold_adj_kernel<S, T, M>;
-    if (smem > 48 * 1024) {
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return cuda_fail(e, "dyn_radon_adj_noalloc: smem attribute");
+    {
+        dr_status s = allow_dynamic_smem((const void *)kern, smem);
+        if (s != DR_OK) return s;
     }
     constexpr int TX = FoldAdjShape<M>::TX;
     const int ntx = (P->nx + TX - 1) / TX, nty = (P->ny + kAdjTY - 1) / kAdjTY;

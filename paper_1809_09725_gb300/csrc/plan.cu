@@ -6,7 +6,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <string>
 
 #include "dr_internal.cuh"
 
@@ -31,6 +33,25 @@ int template_m(int m) {
     for (int s : sizes)
         if (m <= s) return s;
     return -1;
+}
+
+dr_status allow_dynamic_smem(const void *fn, size_t smem) {
+    if (smem <= 48 * 1024) return DR_OK;
+    static std::mutex mu;
+    static std::map<std::pair<const void *, int>, int> done;  // (kernel, device) -> allowed bytes
+    int dev = 0;
+    DR_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = done.find({fn, dev});
+    if (it == done.end()) {
+        int optin = 0;
+        DR_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        DR_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+        it = done.emplace(std::make_pair(fn, dev), optin).first;
+    }
+    if (smem > (size_t)it->second)
+        return fail(DR_EINVAL, "a kernel needs " + std::to_string(smem) + " bytes of shared memory, more than the device allows");
+    return DR_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -377,7 +398,7 @@ static dr_status build_tables(dr_plan *P) {
         else { Pf = 1; nchunk = (P->ns + rays - 1) / rays; }
         const int MS = M <= 4 ? 4 : ((M % 8 == 0) ? M + 4 : M);
         const size_t line = sizeof(float) * (size_t)(std::max(P->nx, P->ny) + 2 * kFwdGuard) * MS;
-        int R = (int)((56 * 1024) / line);
+        int R = (int)((kFoldStripBudget) / line);
         if (R < 1 && line + 768 <= 200 * 1024) R = 1;
         R = std::min(R, 16);
         P->fold_fwd_ok = R >= 1;
@@ -388,9 +409,11 @@ static dr_status build_tables(dr_plan *P) {
         P->fold_U = U;
         P->fold_maxgrp = maxg;
         P->fold_P = Pf;
-        P->fold_R = std::max(R, 1);  // lines of one strip buffer that fit the 56 KB shared-memory budget
+        P->fold_R = std::max(R, 1);  // lines of one strip buffer that fit the shared-memory strip budget
         P->fold_lines = P->fold_R;   // in use (the autotuner may choose fewer)
         P->fold_async = 0;
+        P->fold_lines_st = P->fold_R;
+        P->fold_async_st = 0;
         P->fold_nchunk = nchunk;
         P->n_fold_blocks = (int)(fb.size() / Pf);
         DR_CUDA_TRY(cudaMalloc(&P->d_fold_fwd, sizeof(FwdProj) * U));

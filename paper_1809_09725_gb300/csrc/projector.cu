@@ -5,6 +5,7 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <string>
 #include <tuple>
 
 #include "projector_impl.cuh"
@@ -100,7 +101,7 @@ struct TuneKey {
     }
 };
 struct TuneVal {
-    int fwd, adj, lines, async;
+    int fwd, adj, lines, async, lines_st, async_st;
     double ms[4];
 };
 static std::mutex g_tune_mutex;
@@ -131,6 +132,8 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
             P->sel_adj = it->second.adj;
             P->fold_lines = it->second.lines;
             P->fold_async = it->second.async;
+            P->fold_lines_st = it->second.lines_st;
+            P->fold_async_st = it->second.async_st;
             for (int i = 0; i < 4; ++i) P->tune_ms[i] = it->second.ms[i];
             P->tuned = true;
             return DR_OK;
@@ -144,10 +147,10 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
     DR_CUDA_TRY(cudaMemsetAsync(u_scratch, 0, nu_elems(P) * cs, st));
     DR_CUDA_TRY(cudaMemsetAsync(g_scratch, 0, ng_elems(P) * cs, st));
     double ms[4] = {1e30, 1e30, 1e30, 1e30};
-    auto time_fwd = [&](int v, double &best) -> dr_status {
+    auto time_fwd = [&](int v, double &best, bool calc = true) -> dr_status {
         for (int rep = 0; rep < 3; ++rep) {
             DR_CUDA_TRY(cudaEventRecord(e0, st));
-            dr_status s = launch_fwd_variant(P, v, true, u_scratch, g_scratch, nullptr, 0, 0.0, st);
+            dr_status s = launch_fwd_variant(P, v, calc, u_scratch, g_scratch, nullptr, 0, 0.0, st);
             if (s != DR_OK) return s;
             DR_CUDA_TRY(cudaEventRecord(e1, st));
             DR_CUDA_TRY(cudaEventSynchronize(e1));
@@ -166,7 +169,8 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
         // (every choice marches each ray over the same lines in the same order,
         // so the result does not depend on it)
         int best_lines = P->fold_R, best_async = 0;
-        const int async_ok = P->prec == DR_F32 && P->M % 4 == 0 && P->m == P->M;
+        const int async_ok = P->m == P->M && ((P->prec == DR_F32 && P->M % 4 == 0) ||
+                                              (P->prec == DR_BF16_F32ACC && P->M % 8 == 0));
         const int cand[] = {1, 2, 3, 4, 6, 8, 12, 16};
         for (int as = 0; as <= async_ok; ++as)
             for (int c : cand) {
@@ -186,6 +190,29 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
             }
         P->fold_lines = best_lines;
         P->fold_async = best_async;
+        if (P->prec == DR_BF16_F32ACC) {
+            // the storage-typed (bf16 strip) kernel of the operator calls: its own choice
+            // (the scratch buffers are float sized, large enough for bf16 data)
+            const int async_st_ok = P->m == P->M && P->M % 8 == 0;
+            double best_t = 1e30;
+            int bl = P->fold_R, ba = 0;
+            for (int as = 0; as <= async_st_ok; ++as)
+                for (int c : cand) {
+                    if ((as ? 2 : 1) * c > P->fold_R) continue;
+                    P->fold_lines_st = c;
+                    P->fold_async_st = as;
+                    double t = 1e30;
+                    dr_status s = time_fwd(1, t, false);
+                    if (s != DR_OK) return s;
+                    if (t < best_t) {
+                        best_t = t;
+                        bl = c;
+                        ba = as;
+                    }
+                }
+            P->fold_lines_st = bl;
+            P->fold_async_st = ba;
+        }
     }
     for (int v = 0; v < 2; ++v) {
         for (int rep = 0; rep < 3; ++rep) {
@@ -206,7 +233,8 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
     P->sel_adj = ms[3] < ms[2] ? 1 : 0;
     P->tuned = true;
     std::lock_guard<std::mutex> lk(g_tune_mutex);
-    auto ins = g_tune_cache.emplace(key, TuneVal{P->sel_fwd, P->sel_adj, P->fold_lines, P->fold_async, {0, 0, 0, 0}});
+    auto ins = g_tune_cache.emplace(key, TuneVal{P->sel_fwd, P->sel_adj, P->fold_lines, P->fold_async,
+                                                 P->fold_lines_st, P->fold_async_st, {0, 0, 0, 0}});
     if (ins.second) {
         for (int i = 0; i < 4; ++i) ins.first->second.ms[i] = P->tune_ms[i];
     } else {  // another thread tuned the same problem first: follow its choice
@@ -214,6 +242,8 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
         P->sel_adj = ins.first->second.adj;
         P->fold_lines = ins.first->second.lines;
         P->fold_async = ins.first->second.async;
+        P->fold_lines_st = ins.first->second.lines_st;
+        P->fold_async_st = ins.first->second.async_st;
     }
     return DR_OK;
 }
@@ -269,6 +299,20 @@ dr_status dr_plan_autotune(dr_plan *P, double *times_ms) {
     }
     if (times_ms)
         for (int i = 0; i < 4; ++i) times_ms[i] = P->tune_ms[i];
+    return DR_OK;
+}
+
+dr_status dr_plan_set_fold_strip(dr_plan *P, int lines, int async) {
+    clear_error();
+    if (!P) return fail(DR_EINVAL, "dr_plan_set_fold_strip: NULL plan");
+    if (!(P->fold_U > 0 && P->fold_fwd_ok)) return fail(DR_EINVAL, "dr_plan_set_fold_strip: no folded forward");
+    const int async_ok = P->m == P->M && ((P->prec == DR_F32 && P->M % 4 == 0) ||
+                                          (P->prec == DR_BF16_F32ACC && P->M % 8 == 0));
+    if (lines < 1 || (async != 0 && async != 1) || (async && !async_ok) || (async ? 2 : 1) * lines > P->fold_R)
+        return fail(DR_EINVAL, "dr_plan_set_fold_strip: lines must be in [1, " + std::to_string(P->fold_R) +
+                                   "] (half that with async), async only for whole 16-byte vectors");
+    P->fold_lines = P->fold_lines_st = lines;
+    P->fold_async = P->fold_async_st = async;
     return DR_OK;
 }
 

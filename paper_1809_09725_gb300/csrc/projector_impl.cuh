@@ -218,9 +218,9 @@ inline dr_status fwd_launch_t(dr_plan *P, const void *u, void *out, const void *
                         fwd_align16((size_t)Pp * sizeof(long long));
     const size_t smem = head + sizeof(T) * (size_t)Pp * R * wpad;
     auto kern = fwd_kernel<S, T, M>;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return cuda_fail(e, "fwd: smem attribute");
+    {
+        dr_status s = allow_dynamic_smem((const void *)kern, smem);
+        if (s != DR_OK) return s;
     }
     dim3 grid(P->n_fwd_blocks, P->nz);
     kern<<<grid, kFwdThreads, smem, st>>>((const S *)u, (S *)out, (const S *)gm, P->d_fwd, (const T *)P->d_PhiP,
@@ -519,9 +519,9 @@ inline dr_status adj_launch_t(dr_plan *P, const void *g, void *u, double alpha, 
         use_tma = (ok1 && ok2) ? 1 : 0;
     }
     auto kern = adj_kernel<S, T, M>;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return cuda_fail(e, "adj: smem attribute");
+    {
+        dr_status s = allow_dynamic_smem((const void *)kern, smem);
+        if (s != DR_OK) return s;
     }
     const int ntx = (P->nx + TX - 1) / TX, nty = (P->ny + kAdjTY - 1) / kAdjTY;
     dim3 grid(ntx * nty, P->nz);

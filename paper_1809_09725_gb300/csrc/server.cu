@@ -81,7 +81,7 @@ static size_t plan_table_bytes(const dr_job_desc &d) {
 }
 
 // Device bytes of the job streamed in slabs of S slices (cp_solve_slabs):
-// two stages of slab buffers with halos, the compute temporaries, folded-data
+// three stages of slab buffers with halos, the compute temporaries, folded-data
 // scratch for S slices (at most one distinct angle per projection) and the
 // power-iteration buffers when no operator norm is given.
 static size_t job_slab_bytes(const dr_job_desc &d, int S) {
@@ -91,16 +91,17 @@ static size_t job_slab_bytes(const dr_job_desc &d, int S) {
     const size_t um = (size_t)d.nx * d.ny * d.m, gk = (size_t)d.K * d.ns, f4 = (size_t)d.nx * d.ny * d.nt * 4;
     const size_t s = (size_t)S;
     size_t b = plan_table_bytes(d);
-    b += 2 * ((s + 1) * um * cs * 2 + s * gk * cs * 2 + (s + 1) * f4 * cs);
-    if (d.prec == DR_BF16_F32ACC) b += 2 * s * gk * 2;
+    b += 3 * ((s + 1) * um * cs * 2 + s * gk * cs * 2 + (s + 1) * f4 * cs);
+    if (d.prec == DR_BF16_F32ACC) b += 3 * s * gk * 2;
     b += s * um * cs + s * gk * cs + f4 * cs + um * cs;
+    const size_t nslab = ((size_t)d.nz + s - 1) / s;
+    if (nslab > 1 && nslab - 1 <= s) b += (nslab - 1) * um * cs;  // device halo copies of u~ (few slabs)
     if (d.prec != DR_F64) {
         const int MS = M <= 4 ? 4 : ((M % 8 == 0) ? M + 4 : M);
         b += sizeof(float) * s * gk * MS;
     }
     const bool power = !(d.params.op_norm > 0.0);
-    if (power) b += 2 * ((s + 2) * um * cs + s * um * cs);
-    const size_t nslab = ((size_t)d.nz + s - 1) / s;
+    if (power) b += 3 * ((s + 2) * um * cs + s * um * cs);
     const size_t pit = d.params.power_iters > 0 ? d.params.power_iters : 100;
     const size_t rows = std::max((size_t)std::max(d.params.iters, 0) * nslab, power ? (pit + 1) * nslab : 0);
     b += sizeof(double) * 3 * (rows + 1);

@@ -6,7 +6,11 @@
 // host-to-device copies, the computation and the device-to-host copies on
 // three streams.  Here every iteration walks the slabs z0 = 0, S, 2S, ... in
 // order; slab [z0, z1) needs
-//   * u~ on [z0, z1] (the slice above feeds the forward z difference of D),
+//   * u~ on [z0, z1] (the slice above feeds the forward z difference of D;
+//     when the volume has at most S+1 slabs, after the first iteration it
+//     comes from a device copy that the slab above left behind, so a slab's
+//     copy-in waits only for its own copy-out; with more slabs the halo
+//     copies would outgrow a slab and the halo is re-read from the host),
 //   * the NEW dual h2 on slice z0-1 (the backward difference of D^T): the
 //     previous slab computed it, and it is carried over on the device instead
 //     of being re-read from the host (where the old value is already gone),
@@ -15,10 +19,11 @@
 // order as the whole-volume solver, so with the same operator norm the
 // result is the in-core Chambolle-Pock result bit for bit.
 //
-// Two device stages alternate: while slab q computes, slab q+1 is copied in
-// and slab q-1 is copied out.  A slab's copy-in waits for the copy-out of the
-// slab that last used its stage and, from the previous iteration, of the
-// slab above it (which wrote the halo slice it reads).
+// Three device stages rotate: while slab q computes, slab q+1 is copied in
+// and slab q-1 is copied out, and the copy-in of q+1 need not wait for the
+// copy-out of q-1.  A slab's copy-in waits for the copy-out of the slab that
+// last used its stage and, from the previous iteration, of the slab above it
+// (which wrote the halo slice it reads).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -45,6 +50,8 @@ dr_status launch_convert_bf16(dr_plan *P, const void *in, void *out, size_t n, b
     } while (0)
 
 namespace {
+
+constexpr int kStages = 3;
 
 // Sizes of one slab problem (elements per slice of each array).
 struct SlabDims {
@@ -88,9 +95,10 @@ struct Stage {
 };
 
 struct Buffers {
-    Stage st[2];
+    Stage st[kStages];
     void *Abuf = nullptr, *GD = nullptr;          // R* h1 [S], R u - g [S]
     void *carry_h2 = nullptr, *carry_u = nullptr;  // one slice each
+    void *halo_ut = nullptr;                       // [nslab-1] u~ on the first slice of slabs 1..
     void *gt = nullptr;                            // folded-data scratch for S slices
     double *obj = nullptr;
     std::vector<void *> all;
@@ -113,14 +121,18 @@ struct Buffers {
     }
 };
 
+// Device copies of the u~ halo slices: worth it (and cheap) with few slabs.
+bool device_halo(const SlabDims &d) { return d.nslab > 1 && d.nslab - 1 <= d.S; }
+
 size_t device_bytes(const dr_plan *P, const SlabDims &d, bool bf, bool power, int rows) {
     const size_t S = d.S, cs = d.cs;
     size_t b = 0;
-    b += 2 * ((S + 1) * d.um * cs * 2 + S * d.gk * cs * 2 + (S + 1) * d.f4 * cs);
-    if (bf) b += 2 * S * d.gk * 2;
+    b += kStages * ((S + 1) * d.um * cs * 2 + S * d.gk * cs * 2 + (S + 1) * d.f4 * cs);
+    if (bf) b += kStages * S * d.gk * 2;
     b += S * d.um * cs + S * d.gk * cs + d.f4 * cs + d.um * cs;
+    if (device_halo(d)) b += (size_t)(d.nslab - 1) * d.um * cs;
     if (!P->d_gt) b += fold_scratch_bytes(P, d.S);
-    if (power) b += 2 * ((S + 2) * d.um * cs + S * d.um * cs);
+    if (power) b += kStages * ((S + 2) * d.um * cs + S * d.um * cs);
     b += sizeof(double) * 3 * (size_t)(rows + 1);
     return b;
 }
@@ -128,7 +140,7 @@ size_t device_bytes(const dr_plan *P, const SlabDims &d, bool bf, bool power, in
 // Three streams, per-stage and per-slab events.
 struct Pipe {
     cudaStream_t hs = nullptr, cs = nullptr, ds = nullptr;
-    cudaEvent_t ev_h2d[2] = {}, ev_comp[2] = {}, ev_d2h[2] = {};
+    cudaEvent_t ev_h2d[kStages] = {}, ev_comp[kStages] = {}, ev_d2h[kStages] = {};
     std::vector<cudaEvent_t> ev_slab;
     long long q = 0;     // slabs issued so far (selects the stage)
     bool first = true;   // no previous pass to wait for
@@ -137,7 +149,7 @@ struct Pipe {
         DR_CUDA_TRY(cudaStreamCreateWithFlags(&hs, cudaStreamNonBlocking));
         DR_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
         DR_CUDA_TRY(cudaStreamCreateWithFlags(&ds, cudaStreamNonBlocking));
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < kStages; ++i) {
             DR_CUDA_TRY(cudaEventCreateWithFlags(&ev_h2d[i], cudaEventDisableTiming));
             DR_CUDA_TRY(cudaEventCreateWithFlags(&ev_comp[i], cudaEventDisableTiming));
             DR_CUDA_TRY(cudaEventCreateWithFlags(&ev_d2h[i], cudaEventDisableTiming));
@@ -149,7 +161,7 @@ struct Pipe {
     ~Pipe() {
         for (cudaStream_t s : {hs, cs, ds})
             if (s) cudaStreamSynchronize(s);
-        for (int i = 0; i < 2; ++i)
+        for (int i = 0; i < kStages; ++i)
             for (cudaEvent_t e : {ev_h2d[i], ev_comp[i], ev_d2h[i]})
                 if (e) cudaEventDestroy(e);
         for (auto e : ev_slab)
@@ -164,13 +176,16 @@ struct Pipe {
         return DR_OK;
     }
     // One pass over all slabs: copy in, compute, copy out, overlapped.
-    dr_status pass(int nslab, const std::function<dr_status(int, int, cudaStream_t)> &h2d,
+    // halo_from_host: a slab's copy-in also reads the slice above it from the
+    // host, so it waits for the previous pass's copy-out of the next slab too.
+    dr_status pass(int nslab, bool halo_from_host, const std::function<dr_status(int, int, cudaStream_t)> &h2d,
                    const std::function<dr_status(int, int, cudaStream_t)> &comp,
                    const std::function<dr_status(int, int, cudaStream_t)> &d2h) {
         for (int s = 0; s < nslab; ++s, ++q) {
-            const int b = (int)(q & 1);
-            if (q >= 2) DR_CUDA_TRY(cudaStreamWaitEvent(hs, ev_d2h[b], 0));
-            if (!first) DR_CUDA_TRY(cudaStreamWaitEvent(hs, ev_slab[std::min(s + 1, nslab - 1)], 0));
+            const int b = (int)(q % kStages);
+            if (q >= kStages) DR_CUDA_TRY(cudaStreamWaitEvent(hs, ev_d2h[b], 0));
+            if (!first)
+                DR_CUDA_TRY(cudaStreamWaitEvent(hs, ev_slab[halo_from_host ? std::min(s + 1, nslab - 1) : s], 0));
             STRY(h2d(s, b, hs));
             DR_CUDA_TRY(cudaEventRecord(ev_h2d[b], hs));
             DR_CUDA_TRY(cudaStreamWaitEvent(cs, ev_h2d[b], 0));
@@ -268,7 +283,7 @@ static dr_status slab_solve(dr_plan *P, const void *g_user, void *u_user, const 
     PlanScope scope(P);
     Buffers B;
     const size_t cs = d.cs;
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < kStages; ++i) {
         Stage &t = B.st[i];
         t.U = B.get((S + 1) * d.um * cs);
         t.UT = B.get((S + 1) * d.um * cs);
@@ -281,6 +296,8 @@ static dr_status slab_solve(dr_plan *P, const void *g_user, void *u_user, const 
     B.GD = B.get(S * d.gk * cs);
     B.carry_h2 = B.get(d.f4 * cs);
     B.carry_u = B.get(d.um * cs);
+    const bool dev_halo = device_halo(d);
+    if (dev_halo) B.halo_ut = B.get((size_t)(d.nslab - 1) * d.um * cs);
     if (!P->d_gt && P->fold_U > 0) B.gt = B.get(fold_scratch_bytes(P, S));
     B.obj = (double *)B.get(sizeof(double) * 3 * (size_t)(rows + 1));
     if (!B.ok) return fail(DR_ENOMEM, "cp_solve_slabs: device allocation failed (use a thinner slab)");
@@ -320,8 +337,11 @@ static dr_status slab_solve(dr_plan *P, const void *g_user, void *u_user, const 
     double L = prm.op_norm;
     if (power) {
         const int iters = prm.power_iters > 0 ? prm.power_iters : 100;
-        void *X[2] = {B.get((S + 2) * d.um * cs), B.get((S + 2) * d.um * cs)};
-        void *Y[2] = {B.get(S * d.um * cs), B.get(S * d.um * cs)};
+        void *X[kStages], *Y[kStages];
+        for (int i = 0; i < kStages; ++i) {
+            X[i] = B.get((S + 2) * d.um * cs);
+            Y[i] = B.get(S * d.um * cs);
+        }
         if (!B.ok) return fail(DR_ENOMEM, "cp_solve_slabs: device allocation failed (use a thinner slab)");
         STRY(yh.alloc(nu * cs));
         HostBuf *yin = &uth, *yout = &yh;  // uth is free until the iterations start
@@ -344,7 +364,7 @@ static dr_status slab_solve(dr_plan *P, const void *g_user, void *u_user, const 
             auto lo_h = [&](int s) { return s > 0 ? 1 : 0; };
             auto hi_h = [&](int s) { return z0_of(s) + n_of(s) < nz ? 1 : 0; };
             STRY(pipe.pass(
-                d.nslab,
+                d.nslab, true,
                 [&](int s, int b, cudaStream_t st) -> dr_status {
                     if (it == 0) return DR_OK;  // the start vector is generated on the device
                     const size_t first = (size_t)(z0_of(s) - lo_h(s)) * d.um;
@@ -396,11 +416,11 @@ static dr_status slab_solve(dr_plan *P, const void *g_user, void *u_user, const 
     pipe.first = true;
     for (int it = 0; it < prm.iters; ++it) {
         STRY(pipe.pass(
-            d.nslab,
+            d.nslab, it == 0 || !dev_halo,
             [&](int s, int b, cudaStream_t st) -> dr_status {
                 const Stage &t = B.st[b];
                 const size_t z0 = z0_of(s), n = n_of(s);
-                const size_t hi = z0 + n < (size_t)nz ? 1 : 0;
+                const size_t hi = ((it == 0 || !dev_halo) && z0 + n < (size_t)nz) ? 1 : 0;
                 DR_CUDA_TRY(cudaMemcpyAsync((unsigned char *)t.U + d.um * cs, uh.at(z0 * d.um * cs), n * d.um * cs,
                                             cudaMemcpyHostToDevice, st));
                 DR_CUDA_TRY(cudaMemcpyAsync(t.UT, uth.at(z0 * d.um * cs), (n + hi) * d.um * cs, cudaMemcpyHostToDevice,
@@ -424,6 +444,11 @@ static dr_status slab_solve(dr_plan *P, const void *g_user, void *u_user, const 
                     DR_CUDA_TRY(cudaMemcpyAsync(t.H2, B.carry_h2, d.f4 * cs, cudaMemcpyDeviceToDevice, st));
                     if (want_obj) DR_CUDA_TRY(cudaMemcpyAsync(t.U, B.carry_u, d.um * cs, cudaMemcpyDeviceToDevice, st));
                 }
+                // the halo u~ (slice z1, as of the previous iteration) from the device copy
+                if (dev_halo && it > 0 && !last)
+                    DR_CUDA_TRY(cudaMemcpyAsync((unsigned char *)t.UT + (size_t)n * d.um * cs,
+                                                (unsigned char *)B.halo_ut + (size_t)s * d.um * cs, d.um * cs,
+                                                cudaMemcpyDeviceToDevice, st));
                 P->nz = n;
                 // Fig. 2 steps 3-6 on the slab
                 STRY(launch_fwd_calc(P, t.UT, t.H1, t.G, 2, sigma, st));
@@ -441,6 +466,10 @@ static dr_status slab_solve(dr_plan *P, const void *g_user, void *u_user, const 
                     DR_CUDA_TRY(cudaMemcpyAsync(B.carry_h2, (unsigned char *)H2b + (size_t)(n - 1) * d.f4 * cs,
                                                 d.f4 * cs, cudaMemcpyDeviceToDevice, st));
                 }
+                // the new u~ on this slab's first slice is the next iteration's halo of the slab below
+                if (dev_halo && s > 0)
+                    DR_CUDA_TRY(cudaMemcpyAsync((unsigned char *)B.halo_ut + (size_t)(s - 1) * d.um * cs, t.UT,
+                                                d.um * cs, cudaMemcpyDeviceToDevice, st));
                 if (want_obj) {
                     if (!last)
                         DR_CUDA_TRY(cudaMemcpyAsync(B.carry_u, (unsigned char *)Ub + (size_t)(n - 1) * d.um * cs,

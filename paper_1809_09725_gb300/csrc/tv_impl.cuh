@@ -477,11 +477,7 @@ inline size_t tab_smem(const dr_plan *P, bool gl) {
 
 template <typename K>
 inline dr_status prep_smem(K kern, size_t smem) {
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return cuda_fail(e, "tv: smem attribute");
-    }
-    return DR_OK;
+    return allow_dynamic_smem((const void *)kern, smem);
 }
 
 inline dr_status tv_launched(const char *what) {

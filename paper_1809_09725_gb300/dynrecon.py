@@ -30,7 +30,8 @@ _STATUS = {DR_EINVAL: "EINVAL", DR_ENOMEM: "ENOMEM", DR_ECUDA: "ECUDA", DR_ETIME
 
 # Every symbol include/dynrecon.h declares.
 EXPORTS = ("dr_plan_create", "dr_plan_destroy", "dr_plan_set_stream", "dr_plan_device_bytes",
-           "dr_plan_workspace_bytes", "dr_plan_sync", "dr_plan_set_variant", "dr_plan_autotune", "dr_plan_info",
+           "dr_plan_workspace_bytes", "dr_plan_sync", "dr_plan_set_variant", "dr_plan_autotune",
+           "dr_plan_set_fold_strip", "dr_plan_info",
            "dyn_radon_fwd", "dyn_radon_adj", "dyn_radon_adj_noalloc", "dr_fbp_init", "tv4d_grad", "tv4d_grad_adj", "tv4d_prox",
            "dr_solve_params_default", "admm_solve", "admm_solve_batch", "cp_solve_slabs",
            "cp_solve_slabs_device_bytes", "dr_job_device_bytes", "dr_job_slab_device_bytes", "dr_server_create",
@@ -105,6 +106,7 @@ def load(path: str = LIB_PATH):
         "dr_plan_sync": (i, [vp]),
         "dr_plan_set_variant": (i, [vp, i, i]),
         "dr_plan_autotune": (i, [vp, pd]),
+        "dr_plan_set_fold_strip": (i, [vp, i, i]),
         "dr_plan_info": (i, [vp, ctypes.POINTER(PlanInfo)]),
         "dyn_radon_fwd": (i, [vp, vp, vp]),
         "dyn_radon_adj": (i, [vp, vp, vp, d]),
@@ -248,6 +250,10 @@ class Plan:
         t = (ctypes.c_double * 4)()
         _check(load().dr_plan_autotune(self._h, t))
         return list(t)
+
+    def set_fold_strip(self, lines: int, async_copy: bool = False):
+        """Fix the folded forward's strip height and staging (results do not change)."""
+        _check(load().dr_plan_set_fold_strip(self._h, int(lines), int(bool(async_copy))))
 
     def info(self) -> dict:
         inf = PlanInfo()

@@ -143,3 +143,45 @@ def test_server_cancel_and_nonfinite_data():
     r = srv.wait(bad, timeout_s=300.0)
     assert r["state"] == dr.JOB_FAILED and r["rc"] == dr.DR_ENOTCONV
     srv.close()
+
+
+def test_concurrent_plans_with_different_shared_memory_sizes():
+    """Plans on several threads launch the same kernels with different dynamic
+    shared-memory sizes at once (strip heights, grid sizes); every launch must
+    succeed and give the single-threaded result."""
+    import threading
+
+    cases = [(48, 2), (160, 5), (96, 1), (224, 3)]
+    ref = {}
+    for N, lines in cases:
+        theta, t = synth.scan(90, 3.0)
+        plan = dr.Plan(N, N, 2, N, theta, t, dr.FOURIER, 8, 3, dr.F32)
+        plan.set_variant(dr.FOLD, dr.FOLD)
+        u = torch.from_numpy(synth.rng_for(N).standard_normal((2, N, N, 8))).float().cuda()
+        g = torch.zeros(plan.g_shape(), dtype=torch.float32, device="cuda")
+        dr.dyn_radon_fwd(plan, u, g)
+        plan.sync()
+        ref[N] = (plan, u, host_values(g), lines)
+    errors = []
+
+    def worker(N):
+        try:
+            plan, u, g_ref, lines = ref[N]
+            stream = torch.cuda.Stream()
+            with torch.cuda.stream(stream):
+                for rep in range(12):
+                    plan.set_fold_strip(1 + (rep + lines) % 3, False)
+                    g = torch.zeros(plan.g_shape(), dtype=torch.float32, device="cuda")
+                    dr.dyn_radon_fwd(plan, u, g)
+                    plan.sync()
+                    if not np.array_equal(host_values(g), g_ref):
+                        errors.append((N, rep, "mismatch"))
+        except Exception as exc:  # noqa: BLE001 -- collected and asserted below
+            errors.append((N, repr(exc)))
+
+    threads = [threading.Thread(target=worker, args=(N,)) for N, _ in cases]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
+    assert not errors, errors

@@ -143,9 +143,10 @@ def test_server_streams_cp_job_over_budget():
     prm = dr.solve_params(dr.CHAMBOLLE_POCK, iters=4, lambda1=LAM1, lambda2=LAM2, op_norm=60.0)
     u = np.zeros((NZ, N, N, M), dtype=np.float32)
     desc = dr.job_desc(N, N, NZ, N, theta, t, dr.FOURIER, M, NT, dr.F32, prm, g32, u)
-    budget = dr.job_slab_device_bytes(desc, 3) + 1
-    assert budget < dr.job_device_bytes(desc)
-    assert dr.job_slab_device_bytes(desc, 4) > budget
+    full = dr.job_device_bytes(desc)
+    slab = max(s for s in range(1, NZ) if dr.job_slab_device_bytes(desc, s) < full)
+    budget = dr.job_slab_device_bytes(desc, slab) + 1
+    assert dr.job_slab_device_bytes(desc, slab + 1) > budget
     srv = dr.Server(device=0, budget_bytes=budget, slots=2)
     jid = srv.submit(desc)
     r = srv.wait(jid, timeout_s=300.0)
@@ -155,6 +156,6 @@ def test_server_streams_cp_job_over_budget():
     assert err.value.status == dr.DR_ENOMEM
     srv.close()
     assert r["rc"] == dr.DR_OK and r["state"] == dr.JOB_DONE, r
-    assert r["slab_nz"] == 3 and r["device_bytes"] <= budget
-    u_ref, _ = _slabs(theta, t, g32.astype(np.float64), dr.F32, 4, None, 3, op_norm=60.0)
+    assert r["slab_nz"] == slab and r["device_bytes"] <= budget
+    u_ref, _ = _slabs(theta, t, g32.astype(np.float64), dr.F32, 4, None, slab, op_norm=60.0)
     np.testing.assert_array_equal(u.astype(np.float64), u_ref)
