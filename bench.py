@@ -39,6 +39,11 @@ PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 SMS, FP32_LANES, SM_MAX_GHZ = 152, 128, 2.07
 
 
+def smem_peak_tbs():
+    """Shared-memory bandwidth: 128 bytes per clock per SM (one wavefront)."""
+    return SMS * 128 * SM_MAX_GHZ * 1e9 / 1e12
+
+
 def fp32_peak_tflops(sm_mhz=None):
     ghz = (sm_mhz / 1000.0) if sm_mhz else SM_MAX_GHZ
     return SMS * FP32_LANES * 2 * ghz * 1e9 / 1e12
@@ -56,6 +61,10 @@ def parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-jobs", type=int, default=24)
     ap.add_argument("--no-slabs", action="store_true", help="skip the slab-streaming measurement")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the BF16-operator, FBP and slab-streaming measurements")
+    ap.add_argument("--fold-strip", type=int, default=0,
+                    help="with --variant: fix the folded forward's strip height (lines) instead of the default")
     ap.add_argument("--variant", default=None,
                     help="force projector variants 'fwd,adj' (0 direct, 1 fold); default: autotuned")
     ap.add_argument("--profile-small", action="store_true",
@@ -139,6 +148,41 @@ def replica_units(units_per_rank: float, world: int) -> float:
     return units_per_rank * world
 
 
+def joseph_samples(theta, nx, ny, ns, distinct=True):
+    """Number of Joseph interpolation samples of one static transform per
+    slice: for every angle (distinct angles mod pi when `distinct`), bin and
+    step line, the samples whose interpolation pair touches the grid (the
+    sample at xi contributes when -1 <= xi < n along the interpolated axis)."""
+    th = np.mod(np.asarray(theta, dtype=np.float64), np.pi) if distinct else np.asarray(theta, dtype=np.float64)
+    if distinct:
+        th = np.unique(np.round(th, 11))
+    sb = np.arange(ns) - 0.5 * (ns - 1)
+    total = 0
+    for a in th:
+        c, s = np.cos(a), np.sin(a)
+        if abs(c) >= abs(s):  # step over rows, interpolate in x
+            y = np.arange(ny) - 0.5 * (ny - 1)
+            xi = (sb[None, :] - y[:, None] * s) / c + 0.5 * (nx - 1)
+            n = nx
+        else:  # step over columns, interpolate in y
+            x = np.arange(nx) - 0.5 * (nx - 1)
+            xi = (sb[None, :] - x[:, None] * c) / s + 0.5 * (ny - 1)
+            n = ny
+        total += int(np.count_nonzero((xi >= -1.0) & (xi < n)))
+    return total
+
+
+def algorithmic_smem_bytes(w, theta, variant, U):
+    """Shared-memory bytes one projector application needs to read: every
+    Joseph sample of the folded forward reads two neighbouring pixel vectors
+    of m FP32 coefficients from the staged strip; the folded adjoint reads,
+    per voxel and distinct angle, two bins of the m folded sinograms from its
+    staged window.  (The direct variants stage data per projection.)"""
+    if variant == 1:
+        return 2 * w.m * 4 * joseph_samples(theta, w.N, w.N, w.ns) * w.nz
+    return 2 * w.m * 4 * w.K * w.voxels()
+
+
 def algorithmic_flops(w, variant, U):
     """FP32 flops of one projector application (FMA = 2 flops).
 
@@ -173,6 +217,8 @@ def run_ours(a):
     if a.variant:
         fv, av = (int(x) for x in a.variant.split(","))
         plan.set_variant(fv, av)
+        if a.fold_strip > 0:
+            plan.set_fold_strip(a.fold_strip, False)
 
     if a.profile_small:
         # one forward and one adjoint of each variant (direct, half-turn fold)
@@ -181,8 +227,16 @@ def run_ours(a):
         gout = torch.empty_like(g)
         for var in (dr.DIRECT, dr.FOLD):
             plan.set_variant(var, var)
+            if var == dr.FOLD and a.fold_strip > 0:
+                plan.set_fold_strip(a.fold_strip, False)
             dr.dyn_radon_fwd(plan, uin, gout)
             dr.dyn_radon_adj(plan, g, u)
+        # the folded forward on BF16 storage (bf16 strip)
+        pb = dr.Plan(w.N, w.N, w.nz, w.ns, theta, t, w.basis, w.m, w.nt, dr.BF16)
+        pb.set_variant(dr.FOLD, dr.FOLD)
+        pb.set_fold_strip(6, False)
+        gb = torch.empty(pb.g_shape(), dtype=torch.bfloat16, device=dev)
+        dr.dyn_radon_fwd(pb, uin.to(torch.bfloat16), gb)
         torch.cuda.synchronize()
         print(json.dumps({"profile_small": True}))
         return
@@ -249,10 +303,16 @@ def run_ours(a):
     clocks = clk.summary()
     peak = fp32_peak_tflops()
     traffic = load_traffic(kname)
+    if fwd_ms >= adj_ms:
+        smem_bytes = algorithmic_smem_bytes(w, theta, variant, U)
+    else:
+        smem_bytes = 2 * w.m * 4 * (U if variant == 1 else w.K) * w.voxels()
+    smem_achieved = smem_bytes / (launch_ms * 1e-3) / 1e12
+    smem_peak = smem_peak_tbs()
 
     # the projector pair on BF16 storage (FP32 accumulation) next to FP32
     bf16_ops = None
-    if rank == 0:
+    if rank == 0 and not a.no_extras:
         pb = dr.Plan(w.N, w.N, w.nz, w.ns, theta, t, w.basis, w.m, w.nt, dr.BF16)
         pb.autotune()
         ub = p_in.to(torch.bfloat16)
@@ -277,21 +337,9 @@ def run_ours(a):
         del pb, ub, gb, uab
 
     # FBP initial guess (Sec. 5), one window per half-turn: filter + one back-projection
-    ufbp = torch.empty(plan.u_shape(), dtype=torch.float32, device=dev)
-    n_win = int(round(w.n_halfturns))
-    for _ in range(3):
-        dr.fbp_init(plan, g, ufbp, n_win)
-    torch.cuda.synchronize()
-    fe0, fe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    fe0.record(stream)
-    for _ in range(5):
-        dr.fbp_init(plan, g, ufbp, n_win)
-    fe1.record(stream)
-    torch.cuda.synchronize()
-    fbp = {"ms": fe0.elapsed_time(fe1) / 5, "windows": n_win,
-           "note": "Shepp-Logan filter of nz*K rows + one folded back-projection; includes the "
-                   "blocking table upload of each call"}
-    del ufbp
+    fbp = None
+    if not a.no_extras:
+        fbp = run_fbp(plan, g, w, dev, stream)
 
     # end to end through the public call with host buffers (one full job per call)
     e2e = None
@@ -323,7 +371,7 @@ def run_ours(a):
         serving = {name: run_serving(a, local, prec) for name, prec in (("fp32", dr.F32), ("bf16", dr.BF16))}
 
     slabs = None
-    if rank == 0 and not a.no_slabs:
+    if rank == 0 and not (a.no_slabs or a.no_extras):
         slabs = run_slabs(w, theta, t, g_np, dev)
 
     cpu = None
@@ -347,14 +395,17 @@ def run_ours(a):
             "clocks": clocks,
             "e2e": e2e,
             "gpu_launches": launches_per_iter * a.steps + 2,
-            "roofline": {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak,
-                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+            "roofline": {"bound": "smem", "kernel": kname, "achieved": smem_achieved, "peak": smem_peak,
+                         "unit": "TB/s", "frac": smem_achieved / smem_peak, "traffic": traffic,
+                         "algorithmic_smem_bytes_per_launch": smem_bytes,
+                         "peak_source": "derived: 152 SMs x 128 B/clk shared-memory bandwidth x 2.07 GHz max SM clock",
+                         "alu": {"achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                                 "algorithmic_flops_per_launch": flops,
+                                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"},
                          "launch_ms": launch_ms, "fwd_ms": fwd_ms, "adj_ms": adj_ms,
-                         "algorithmic_flops_per_launch": flops,
                          "variants": {"unique_angles": U, "fwd": info["fwd_variant"], "adj": info["adj_variant"],
                                       "fold_lines": info["fold_lines"], "fold_async": info["fold_async"],
-                                      "autotune_ms_fwd_direct_fold_adj_direct_fold": tune},
-                         "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz max SM clock"},
+                                      "autotune_ms_fwd_direct_fold_adj_direct_fold": tune}},
             "cpu_baseline": cpu,
             "serving": serving,
             "fbp_init": fbp,
@@ -427,6 +478,29 @@ def run_serving(a, device, prec):
                       "half-turns, m in {4,8,16}, 30 ADMM-CG iterations" % len(jobs),
             "max_queue_s": max(r["queue_s"] for r in res),
             "errors": [{"job": i, "rc": r["rc"], "error": r["error"]} for i, r in enumerate(res) if r["rc"] != 0]}
+
+
+def run_fbp(plan, g, w, dev, stream):
+    """FBP initial guess with one window per half-turn, timed on the device."""
+    import torch
+
+    from paper_1809_09725_gb300 import dynrecon as dr
+
+    ufbp = torch.empty(plan.u_shape(), dtype=torch.float32, device=dev)
+    n_win = int(round(w.n_halfturns))
+    for _ in range(3):
+        dr.fbp_init(plan, g, ufbp, n_win)
+    torch.cuda.synchronize()
+    fe0, fe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    fe0.record(stream)
+    for _ in range(5):
+        dr.fbp_init(plan, g, ufbp, n_win)
+    fe1.record(stream)
+    torch.cuda.synchronize()
+    fbp = {"ms": fe0.elapsed_time(fe1) / 5, "windows": n_win,
+           "note": "Shepp-Logan filter of nz*K rows + one folded back-projection; includes the "
+                   "blocking table upload of each call"}
+    return fbp
 
 
 def run_slabs(w, theta, t, g_np, dev, slab=4, iters=10):
