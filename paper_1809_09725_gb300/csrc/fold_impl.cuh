@@ -90,6 +90,48 @@ __device__ __forceinline__ void load_vec(const T *p, T (&v)[M]) {
     }
 }
 
+// Copy one pixel's coefficient vector into the forward strip: bf16 strips
+// keep the stored values, float strips hold the compute type; slots j >= m
+// are zero.  async_stage (only when m == M) issues 16-byte cp.async copies.
+template <typename S, typename T, int M, typename ST>
+__device__ __forceinline__ void stage_pixel(ST *dst, const S *__restrict__ src, int m, int async_stage) {
+    if constexpr (sizeof(S) == 2) {
+        if constexpr ((M % 8) == 0) {
+            if (m == M) {
+                if (async_stage) {
+#pragma unroll
+                    for (int j = 0; j < M / 8; ++j) cp_async_16(dst + 8 * j, src + 8 * j);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < M / 8; ++j)
+                        reinterpret_cast<uint4 *>(dst)[j] = __ldg(reinterpret_cast<const uint4 *>(src) + j);
+                }
+                return;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < M; ++j) dst[j] = j < m ? src[j] : S(0.0f);
+    } else {
+        if constexpr (sizeof(S) == 4 && (M % 4) == 0) {
+            if (async_stage) {
+#pragma unroll
+                for (int j = 0; j < M / 4; ++j) cp_async_16(dst + 4 * j, src + 4 * j);
+                return;
+            }
+        }
+        T v[M];
+        load_coeffs<T, S, M>(src, m, v);
+        if constexpr (sizeof(T) == 4 && (M % 4) == 0) {
+#pragma unroll
+            for (int j = 0; j < M / 4; ++j)
+                reinterpret_cast<float4 *>(dst)[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < M; ++j) dst[j] = v[j];
+        }
+    }
+}
+
 // ===========================================================================
 // Forward
 // ===========================================================================
@@ -184,44 +226,7 @@ __global__ void __launch_bounds__(kFoldThreads, fold_fwd_min_blocks(M))
                 rl = qq - i * nl;
                 pix = zoff + (size_t)i * nx + (r0 + rl);
             }
-            ST *dst = buf + ((size_t)rl * wpad + kFwdGuard + i) * MS;
-            if constexpr (sizeof(S) == 2) {
-                // bf16 strip: the stored values as they are
-                if constexpr ((M % 8) == 0) {
-                    if (m == M) {
-                        if (async_stage) {
-#pragma unroll
-                            for (int j = 0; j < M / 8; ++j) cp_async_16(dst + 8 * j, u + pix * m + 8 * j);
-                        } else {
-#pragma unroll
-                            for (int j = 0; j < M / 8; ++j)
-                                reinterpret_cast<uint4 *>(dst)[j] = __ldg(reinterpret_cast<const uint4 *>(u + pix * m) + j);
-                        }
-                        continue;
-                    }
-                }
-#pragma unroll
-                for (int j = 0; j < M; ++j) dst[j] = j < m ? u[pix * m + j] : S(0.0f);
-                continue;
-            } else {
-            if constexpr (sizeof(S) == 4 && (M % 4) == 0) {
-                if (async_stage) {
-#pragma unroll
-                    for (int j = 0; j < M / 4; ++j) cp_async_16(dst + 4 * j, u + pix * m + 4 * j);
-                    continue;
-                }
-            }
-            T v[M];
-            load_coeffs<T, S, M>(u + pix * m, m, v);
-            if constexpr (sizeof(T) == 4 && (M % 4) == 0) {
-#pragma unroll
-                for (int j = 0; j < M / 4; ++j)
-                    reinterpret_cast<float4 *>(dst)[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
-            } else {
-#pragma unroll
-                for (int j = 0; j < M; ++j) dst[j] = v[j];
-            }
-            }
+            stage_pixel<S, T, M>(buf + ((size_t)rl * wpad + kFwdGuard + i) * MS, u + pix * m, m, async_stage);
         }
     };
     const size_t buf_elems = (size_t)R * wpad * MS;  // buffer b starts at strip + b * buf_elems

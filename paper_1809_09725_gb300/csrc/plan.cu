@@ -44,10 +44,18 @@ dr_status allow_dynamic_smem(const void *fn, size_t smem) {
     std::lock_guard<std::mutex> lk(mu);
     auto it = done.find({fn, dev});
     if (it == done.end()) {
+        // the dynamic allowance is the opt-in maximum less the kernel's static shared memory
         int optin = 0;
-        DR_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-        DR_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
-        it = done.emplace(std::make_pair(fn, dev), optin).first;
+        cudaFuncAttributes fa;
+        cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, fn);
+        const int limit = optin - (int)fa.sharedSizeBytes;
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, limit);
+        if (e != cudaSuccess) {
+            cudaGetLastError();  // not sticky: do not leave it for the next launch check
+            return cuda_fail(e, "raising the dynamic shared-memory allowance");
+        }
+        it = done.emplace(std::make_pair(fn, dev), limit).first;
     }
     if (smem > (size_t)it->second)
         return fail(DR_EINVAL, "a kernel needs " + std::to_string(smem) + " bytes of shared memory, more than the device allows");

@@ -40,6 +40,9 @@ CASES = {
     "orthonormal": (32, 32, 1, 32, 128, 4.0, True, dr.FOURIER | dr.ORTHONORMAL, 4, 4),
     "complex_m8": (36, 30, 2, 40, 160, 8.0, False, dr.COMPLEX_FOURIER, 16, 8),
     "complex_m4": (28, 28, 1, 28, 96, 4.0, True, dr.COMPLEX_FOURIER, 8, 4),
+    "thin": (3, 41, 2, 23, 40, 2.0, False, dr.FOURIER, 3, 2),
+    "flat": (57, 5, 1, 31, 44, 3.0, False, dr.LEGENDRE, 4, 3),
+    "tiny_det": (9, 8, 1, 3, 30, 2.0, False, dr.FOURIER, 2, 2),
 }
 
 
@@ -208,7 +211,10 @@ def test_fold_variant_matches_oracle(case):
     assert rel(host_values(uo), P.adj(g)) <= 1e-5
 
 
-@pytest.mark.parametrize("case", ["disks64", "narrow_det", "m16"])
+# the bf16 strip layouts: M = 4 (8-byte vectors), M = 8 with m = 8 (16-byte
+# copies) and m = 5 (element copies), M = 1, 12, 16, 24, 32 (odd slot counts)
+@pytest.mark.parametrize("case", ["disks64", "narrow_det", "ragged", "m1_static", "m12", "m16", "m24", "m32",
+                                  "thin", "tiny_det"])
 def test_fold_variant_bf16(case):
     args, u, g, P = _setup(case, seed=13)
     ub, gb = to_bf16_f64(u), to_bf16_f64(g)
@@ -317,3 +323,19 @@ def test_fold_strip_choices_are_bitwise_identical(prec):
         np.testing.assert_array_equal(o, outs[0])
     with pytest.raises(dr.DynreconError):
         plan.set_fold_strip(0, False)
+
+
+@pytest.mark.parametrize("prec,tol", [(dr.F64, 1e-13), (dr.F32, 1e-6)])
+def test_hand_worked_2x2_example_on_gpu(prec, tol):
+    """The Joseph sums of the 2 x 2 image worked by hand (tests/golden), computed
+    by the GPU forward with a static basis (m = 1)."""
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "joseph_2x2.json")))
+    theta = np.array([math.atan2(gold["sin"], gold["cos"])])
+    plan = dr.Plan(2, 2, 1, gold["ns"], theta, np.array([0.0]), dr.FOURIER, 1, 1, prec)
+    img = np.array(gold["image_rows_y_then_x"], dtype=np.float64)[None, :, :, None]
+    g = torch.zeros(plan.g_shape(), dtype=getattr(torch, plan.storage_dtype), device="cuda")
+    dr.dyn_radon_fwd(plan, dev_tensor(img, prec), g)
+    plan.sync()
+    np.testing.assert_allclose(host_values(g)[0, 0], gold["expected"], rtol=0, atol=tol * 10)
