@@ -7,6 +7,29 @@
 
 namespace dr {
 
+// Per-thread partial sum of a reduction whose total is accumulated in double
+// across threads and blocks.  For float terms the thread's own sum is
+// compensated (Kahan summation: the rounding error of every addition is
+// carried in c and fed back), so its error stays at a few float roundings of
+// the sum of magnitudes however many terms the thread adds, and the FP64 pipe
+// is touched once per thread instead of once per term.  Double terms are
+// added directly.
+template <typename T>
+struct PartialSum {
+    T s = T(0), c = T(0);
+    __device__ __forceinline__ void add(T x) {
+        if constexpr (sizeof(T) == 4) {
+            const T y = x - c;
+            const T t = s + y;
+            c = (t - s) - y;
+            s = t;
+        } else {
+            s += x;
+        }
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
 // Counter-based SplitMix64 (Steele, Lea, Flood, OOPSLA 2014): output i of the
 // stream with seed s is the finaliser applied to s + (i+1) * golden gamma.
 __device__ __forceinline__ double splitmix_uniform(unsigned long long seed, unsigned long long i) {

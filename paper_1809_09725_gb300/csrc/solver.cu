@@ -8,20 +8,73 @@
 // counter tells the reducing kernels which objective row to write.
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 
 #include "dr_device.cuh"
 
 namespace dr {
 
+// 16-byte vectors of the compute type: the vector kernels below move whole
+// vectors when every pointer they touch is 16-byte aligned (VEC), else single
+// elements.  Products are formed in the compute type, each thread sums its
+// own terms in a compensated PartialSum, and the thread totals are
+// accumulated in double across the block and the grid, in a fixed order
+// (deterministic for a given n and grid).  Double arithmetic per element
+// would dominate these kernels: FP64 runs at a small fraction of the FP32 rate
+// on this GPU.
 template <typename T>
+struct V16;
+template <>
+struct V16<float> {
+    using type = float4;
+    static constexpr int W = 4;
+    __device__ static float get(const float4 &v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w)); }
+    __device__ static void set(float4 &v, int k, float x) {
+        if (k == 0) v.x = x;
+        else if (k == 1) v.y = x;
+        else if (k == 2) v.z = x;
+        else v.w = x;
+    }
+};
+template <>
+struct V16<double> {
+    using type = double2;
+    static constexpr int W = 2;
+    __device__ static double get(const double2 &v, int k) { return k == 0 ? v.x : v.y; }
+    __device__ static void set(double2 &v, int k, double x) {
+        if (k == 0) v.x = x;
+        else v.y = x;
+    }
+};
+
+inline bool aligned16(const void *a, const void *b = nullptr, const void *c = nullptr, const void *d = nullptr) {
+    return (((uintptr_t)a | (uintptr_t)b | (uintptr_t)c | (uintptr_t)d) & 15u) == 0;
+}
+
+template <typename T, bool VEC>
 __global__ void __launch_bounds__(kRedThreads)
     dot_kernel(const T *__restrict__ a, const T *__restrict__ b, size_t n, double *partials, unsigned *counter,
                DevScalars *scal, double *obj, int row_off, int col, int to_lam) {
-    double acc = 0.0;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-        acc += (double)a[i] * (double)b[i];
-    double v[1] = {acc}, tot[1];
+    PartialSum<T> acc;
+    const size_t stride = (size_t)gridDim.x * blockDim.x, tid = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    size_t done = 0;
+    if constexpr (VEC) {
+        using V = V16<T>;
+        const size_t nv = n / V::W;
+        const typename V::type *av = reinterpret_cast<const typename V::type *>(a);
+        const typename V::type *bv = reinterpret_cast<const typename V::type *>(b);
+        for (size_t i = tid; i < nv; i += stride) {
+            const typename V::type x = __ldg(av + i), y = __ldg(bv + i);
+            T s = T(0);
+#pragma unroll
+            for (int k = 0; k < V::W; ++k) s = fma(V::get(x, k), V::get(y, k), s);
+            acc.add(s);
+        }
+        done = nv * V::W;
+    }
+    for (size_t i = done + tid; i < n; i += stride) acc.add(a[i] * b[i]);
+    double v[1] = {acc.value()}, tot[1];
     if (block_reduce_last<1>(v, partials, counter, tot)) {
         if (obj) obj[3 * (size_t)(scal->iter + row_off) + col] = tot[0];
         if (to_lam) scal->lam = tot[0];
@@ -30,19 +83,44 @@ __global__ void __launch_bounds__(kRedThreads)
 }
 
 // u += alpha p; r -= alpha q; rr_new = <r, r>; beta = rr_new / rr.
-template <typename T>
+template <typename T, bool VEC>
 __global__ void __launch_bounds__(kRedThreads)
     cg_update_kernel(T *__restrict__ u, T *__restrict__ r, const T *__restrict__ p, const T *__restrict__ q,
                      size_t n, double *partials, unsigned *counter, DevScalars *scal) {
     const T a = (T)scal->alpha;
-    double acc = 0.0;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    PartialSum<T> acc;
+    const size_t stride = (size_t)gridDim.x * blockDim.x, tid = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    size_t done = 0;
+    if constexpr (VEC) {
+        using V = V16<T>;
+        using VT = typename V::type;
+        const size_t nv = n / V::W;
+        VT *uv = reinterpret_cast<VT *>(u), *rv = reinterpret_cast<VT *>(r);
+        const VT *pv = reinterpret_cast<const VT *>(p), *qv = reinterpret_cast<const VT *>(q);
+        for (size_t i = tid; i < nv; i += stride) {
+            VT uu = uv[i], rr = rv[i];
+            const VT pp = __ldg(pv + i), qq = __ldg(qv + i);
+            T s = T(0);
+#pragma unroll
+            for (int k = 0; k < V::W; ++k) {
+                V::set(uu, k, V::get(uu, k) + a * V::get(pp, k));
+                const T rn = V::get(rr, k) - a * V::get(qq, k);
+                V::set(rr, k, rn);
+                s = fma(rn, rn, s);
+            }
+            acc.add(s);
+            uv[i] = uu;
+            rv[i] = rr;
+        }
+        done = nv * V::W;
+    }
+    for (size_t i = done + tid; i < n; i += stride) {
         u[i] += a * p[i];
         const T rn = r[i] - a * q[i];
         r[i] = rn;
-        acc += (double)rn * (double)rn;
+        acc.add(rn * rn);
     }
-    double v[1] = {acc}, tot[1];
+    double v[1] = {acc.value()}, tot[1];
     if (block_reduce_last<1>(v, partials, counter, tot)) {
         if (scal->active) {
             scal->beta = tot[0] / scal->rr;
@@ -53,11 +131,27 @@ __global__ void __launch_bounds__(kRedThreads)
     }
 }
 
-template <typename T>
+template <typename T, bool VEC>
 __global__ void cg_dir_kernel(T *__restrict__ p, const T *__restrict__ r, size_t n, const DevScalars *scal) {
     const T b = (T)scal->beta;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-        p[i] = r[i] + b * p[i];
+    const size_t stride = (size_t)gridDim.x * blockDim.x, tid = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    size_t done = 0;
+    if constexpr (VEC) {
+        using V = V16<T>;
+        using VT = typename V::type;
+        const size_t nv = n / V::W;
+        VT *pv = reinterpret_cast<VT *>(p);
+        const VT *rv = reinterpret_cast<const VT *>(r);
+        for (size_t i = tid; i < nv; i += stride) {
+            VT pp = pv[i];
+            const VT rr = __ldg(rv + i);
+#pragma unroll
+            for (int k = 0; k < V::W; ++k) V::set(pp, k, V::get(rr, k) + b * V::get(pp, k));
+            pv[i] = pp;
+        }
+        done = nv * V::W;
+    }
+    for (size_t i = done + tid; i < n; i += stride) p[i] = r[i] + b * p[i];
 }
 
 // Power-iteration start x_i = 0.5 + U_i (SplitMix64 stream, seed 1809) for
@@ -106,9 +200,16 @@ static int vec_grid(size_t n) { return red_grid(n); }
 template <typename T>
 static dr_status dot_t(dr_plan *P, const void *a, const void *b, size_t n, int slot, double *obj, int row_off,
                        int col, int to_lam, cudaStream_t st) {
-    dot_kernel<T><<<vec_grid(n), kRedThreads, 0, st>>>((const T *)a, (const T *)b, n,
-                                                        P->d_partials + slot * kRedSlotStride, P->d_counters + slot,
-                                                        P->d_scal, obj, row_off, col, to_lam);
+    if (aligned16(a, b))
+        dot_kernel<T, true><<<vec_grid(n), kRedThreads, 0, st>>>((const T *)a, (const T *)b, n,
+                                                                 P->d_partials + slot * kRedSlotStride,
+                                                                 P->d_counters + slot, P->d_scal, obj, row_off, col,
+                                                                 to_lam);
+    else
+        dot_kernel<T, false><<<vec_grid(n), kRedThreads, 0, st>>>((const T *)a, (const T *)b, n,
+                                                                  P->d_partials + slot * kRedSlotStride,
+                                                                  P->d_counters + slot, P->d_scal, obj, row_off, col,
+                                                                  to_lam);
     return launched("dot_kernel");
 }
 
@@ -183,12 +284,20 @@ template <typename T>
 static dr_status vec_launches(dr_plan *P, int which, void *a, void *b, void *c, void *d, size_t n, cudaStream_t st) {
     switch (which) {
         case 0:
-            cg_update_kernel<T><<<vec_grid(n), kRedThreads, 0, st>>>(
-                (T *)a, (T *)b, (const T *)c, (const T *)d, n, P->d_partials + kSlotUpd * kRedSlotStride,
-                P->d_counters + kSlotUpd, P->d_scal);
+            if (aligned16(a, b, c, d))
+                cg_update_kernel<T, true><<<vec_grid(n), kRedThreads, 0, st>>>(
+                    (T *)a, (T *)b, (const T *)c, (const T *)d, n, P->d_partials + kSlotUpd * kRedSlotStride,
+                    P->d_counters + kSlotUpd, P->d_scal);
+            else
+                cg_update_kernel<T, false><<<vec_grid(n), kRedThreads, 0, st>>>(
+                    (T *)a, (T *)b, (const T *)c, (const T *)d, n, P->d_partials + kSlotUpd * kRedSlotStride,
+                    P->d_counters + kSlotUpd, P->d_scal);
             return launched("cg_update_kernel");
         case 1:
-            cg_dir_kernel<T><<<vec_grid(n), kRedThreads, 0, st>>>((T *)a, (const T *)b, n, P->d_scal);
+            if (aligned16(a, b))
+                cg_dir_kernel<T, true><<<vec_grid(n), kRedThreads, 0, st>>>((T *)a, (const T *)b, n, P->d_scal);
+            else
+                cg_dir_kernel<T, false><<<vec_grid(n), kRedThreads, 0, st>>>((T *)a, (const T *)b, n, P->d_scal);
             return launched("cg_dir_kernel");
         case 2:
             pow_init_kernel<T><<<vec_grid(n), kRedThreads, 0, st>>>((T *)a, n, (size_t)0);

@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(kRedThreads)
     load_tables<T, M>(sm, PhiF, dPhiF, nullptr, nullptr, g.nt, false);
     const T *dph = sm + g.nt * M;
     const T kappa = lambda1 / rho, irho = T(1) / rho;
-    double acc_tv = 0.0, acc_pr = 0.0;
+    PartialSum<T> acc_tv, acc_pr;
     const size_t nv = (size_t)g.nx * g.ny * g.nz;
     for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < nv; v += (size_t)gridDim.x * blockDim.x) {
         int x, y, z;
@@ -268,17 +268,18 @@ __global__ void __launch_bounds__(kRedThreads)
             const T n = sqrt(n2);
             const T f = (n > T(0)) ? fmax(T(0), T(1) - kappa / n) : T(0);
             T mn[4], wn[4];
-            double pr = 0.0;
+            T pr = T(0);
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 const T psi = vv[c] * f;
                 const T r = d[c] - psi;
-                pr += (double)r * (double)r;
+                pr = fma(r, r, pr);
                 mn[c] = mv[c] + rho * r;
                 wn[c] = psi - mn[c] * irho;
             }
-            acc_tv += sqrt((double)dn2);
-            acc_pr += pr;
+            // per-frame terms in the compute type; FP64 only across threads
+            acc_tv.add(sqrt(dn2));
+            acc_pr.add(pr);
             typename V4<T>::type a, b;
             a.x = mn[0]; a.y = mn[1]; a.z = mn[2]; a.w = mn[3];
             b.x = wn[0]; b.y = wn[1]; b.z = wn[2]; b.w = wn[3];
@@ -286,7 +287,7 @@ __global__ void __launch_bounds__(kRedThreads)
             st4<T>(w + o, b);
         }
     }
-    double vals[2] = {acc_tv, acc_pr}, tot[2];
+    double vals[2] = {acc_tv.value(), acc_pr.value()}, tot[2];
     if (block_reduce_last<2>(vals, partials, counter, tot)) {
         double *row = use_iter ? obj + 3 * (size_t)scal->iter : obj;
         if (row) {
@@ -316,7 +317,7 @@ __global__ void __launch_bounds__(kRedThreads)
     load_tables<T, M>(sm, PhiF, dPhiF, G, Lt, g.nt, true);
     const T *Gs = sm + 2 * g.nt * M;
     const T *Ls = Gs + M * M;
-    double acc = 0.0;
+    PartialSum<T> acc;
     const size_t nv = (size_t)g.nx * g.ny * g.nz;
     const size_t sy = g.nx, sz = (size_t)g.nx * g.ny;
     for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < nv; v += (size_t)gridDim.x * blockDim.x) {
@@ -335,7 +336,7 @@ __global__ void __launch_bounds__(kRedThreads)
 #pragma unroll
             for (int j = 0; j < M; ++j) ls[j] += xc[j] - nb[j];
         }
-        double dotv = 0.0;
+        T dotv = T(0);  // this voxel's m products in the compute type (sums in a PartialSum)
 #pragma unroll(M <= 16 ? M : 1)
         for (int i = 0; i < M; ++i) {
             if (i >= g.m) break;
@@ -348,14 +349,14 @@ __global__ void __launch_bounds__(kRedThreads)
             out[idx] = r;
             if (mode == 2) {
                 pdir[idx] = r;
-                dotv += (double)r * (double)r;
+                dotv = fma(r, r, dotv);
             } else {
-                dotv += (double)xv[idx] * (double)r;
+                dotv = fma(xv[idx], r, dotv);
             }
         }
-        acc += dotv;
+        acc.add(dotv);
     }
-    double vals[1] = {acc}, tot[1];
+    double vals[1] = {acc.value()}, tot[1];
     if (block_reduce_last<1>(vals, partials, counter, tot)) {
         if (mode == 1) {
             const double pq = tot[0], rr = scal->rr;
@@ -447,7 +448,7 @@ __global__ void __launch_bounds__(kRedThreads)
     T *sm = reinterpret_cast<T *>(smem_raw);
     load_tables<T, M>(sm, PhiF, dPhiF, nullptr, nullptr, g.nt, false);
     const T *dph = sm + g.nt * M;
-    double acc = 0.0;
+    PartialSum<T> acc;
     const size_t nv = (size_t)g.nx * g.ny * g.nz;
     for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < nv; v += (size_t)gridDim.x * blockDim.x) {
         int x, y, z;
@@ -458,10 +459,10 @@ __global__ void __launch_bounds__(kRedThreads)
             T d[4];
             grad_frame<T, M>(sm, l, ex, ey, ez, d[0], d[1], d[2]);
             d[3] = dt_frame<T, M>(dph + l * M, lambda2, uc);
-            acc += sqrt((double)(d[0] * d[0] + d[1] * d[1] + d[2] * d[2] + d[3] * d[3]));
+            acc.add(sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2] + d[3] * d[3]));
         }
     }
-    double vals[1] = {acc}, tot[1];
+    double vals[1] = {acc.value()}, tot[1];
     if (block_reduce_last<1>(vals, partials, counter, tot)) obj[3 * (size_t)scal->iter + 1] = tot[0];
 }
 
