@@ -233,8 +233,12 @@ __global__ void __launch_bounds__(kRedThreads)
 // w = psi - mu/rho.  Reduces sum |Du| and ||Du - psi||^2.
 // obj: destination row (tv, primal^2); when use_iter the row is obj + 3*iter + 1.
 // ---------------------------------------------------------------------------
+// Resident CTAs per SM requested for the latency-bound per-voxel stencils
+// (more warps in flight to cover the strided dual reads).
+__host__ __device__ constexpr int tv_min_blocks(int M, int T_bytes) { return (T_bytes == 4 && M <= 8) ? 4 : 1; }
+
 template <typename T, typename S, int M>
-__global__ void __launch_bounds__(kRedThreads)
+__global__ void __launch_bounds__(kRedThreads, tv_min_blocks(M, sizeof(T)))
     prox_kernel(const S *__restrict__ u, T *__restrict__ mu, T *__restrict__ w, const T *PhiF, const T *dPhiF, Geo g,
                 T rho, T lambda1, T lambda2, double *partials, unsigned *counter, DevScalars *scal, double *obj,
                 int use_iter) {
@@ -308,7 +312,7 @@ __global__ void __launch_bounds__(kRedThreads)
 // reduce <out, out> into scal->rr, marking the CG active.
 // ---------------------------------------------------------------------------
 template <typename T, int M>
-__global__ void __launch_bounds__(kRedThreads)
+__global__ void __launch_bounds__(kRedThreads, tv_min_blocks(M, sizeof(T)))
     lap_kernel(const T *__restrict__ xv, T *__restrict__ out, T *__restrict__ pdir, const T *PhiF,
                const T *dPhiF, const T *G, const T *Lt, Geo g, T alpha, T beta, T lam2sq, double *partials,
                unsigned *counter, DevScalars *scal, int mode) {
