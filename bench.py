@@ -377,14 +377,23 @@ def run_ours(a):
     serving = None
     if not a.no_serving:
         serving = {name: run_serving(a, local, prec) for name, prec in (("fp32", dr.F32), ("bf16", dr.BF16))}
+        if rank == 0 and not a.no_extras:
+            serving["load_sweep_fp32"] = run_serving_sweep(a, local)
+
+    batched = None
+    if rank == 0 and not a.no_extras:
+        batched = run_batched(dev)
 
     slabs = None
     if rank == 0 and not (a.no_slabs or a.no_extras):
         slabs = run_slabs(w, theta, t, g_np, dev)
 
     cpu = None
+    accuracy = None
     if rank == 0 and not a.no_cpu_baseline:
         cpu = cpu_baseline(w, theta, t, g_np)
+        cpu["one_thread"] = cpu_baseline_1thread(w)
+        accuracy = accuracy_vs_oracle(w, theta, t, g_np, dev)
 
     if rank == 0:
         launches_per_iter = 6 + 5 * w.n_cg
@@ -416,6 +425,8 @@ def run_ours(a):
                                       "autotune_ms_fwd_direct_fold_adj_direct_fold": tune}},
             "cpu_baseline": cpu,
             "serving": serving,
+            "accuracy_vs_fp64_oracle": accuracy,
+            "batched_jobs": batched,
             "fbp_init": fbp,
             "bf16_operators": bf16_ops,
             "slab_streaming": slabs,
@@ -592,6 +603,152 @@ def cpu_baseline(w, theta, t, g_np, sample_slices=None):
     return {"value": units / el, "unit": "voxel*projection/s", "cores": os.cpu_count(), "kind": "oracle",
             "sample": "one forward + one back-projection, FP64 oracle, %d slices of the workload (%.1f s)"
                       % (nz, el)}
+
+
+def cpu_baseline_1thread(w):
+    """The oracle on one host thread (OMP_NUM_THREADS=1, a separate process):
+    one forward and one back-projection of one slice of the workload."""
+    code = (
+        "import sys, time, numpy as np; sys.path.insert(0, %r); import oracle\n"
+        "from paper_1809_09725_gb300 import synth\n"
+        "w = synth.WORKLOADS[%r]; theta, t = synth.scan(w.K, w.n_halfturns, w.mod_pi)\n"
+        "P = oracle.Problem(w.N, w.N, 1, w.ns, theta, t, w.basis, w.m, w.nt)\n"
+        "rng = np.random.default_rng(1); u = rng.standard_normal((1, w.N, w.N, w.m))\n"
+        "g = rng.standard_normal((1, w.K, w.ns))\n"
+        "t0 = time.perf_counter(); P.fwd(u); P.adj(g); print(time.perf_counter() - t0)\n"
+    ) % (os.path.dirname(os.path.abspath(__file__)), w.name)
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+        el = float(out.stdout.strip().splitlines()[-1])
+    except Exception as exc:  # noqa: BLE001 -- reported in the JSON line
+        return {"error": repr(exc)[:200]}
+    units = 2 * w.K * w.N * w.N
+    return {"value": units / el, "unit": "voxel*projection/s", "cores": 1, "kind": "oracle",
+            "sample": "one forward + one back-projection, FP64 oracle, 1 slice, one thread (%.1f s)" % el}
+
+
+def accuracy_vs_oracle(w, theta, t, g_np, dev, iters=3):
+    """Relative L2 error of the GPU solve against the FP64 oracle running the
+    same ADMM-CG iterations on a 1-slice cut of the workload."""
+    import torch
+
+    import oracle
+    from paper_1809_09725_gb300 import dynrecon as dr
+
+    g1 = g_np[:1]
+    P = oracle.Problem(w.N, w.N, 1, w.ns, theta, t, w.basis, w.m, w.nt)
+    t0 = time.perf_counter()
+    uo, oo, _ = P.admm_cg(g1, np.zeros((1, w.N, w.N, w.m)), iters, w.n_cg, w.lambda1, w.lambda2, w.rho)
+    t_or = time.perf_counter() - t0
+    out = {"cut": "slice 0 of the workload, %d ADMM-CG iterations from zero" % iters, "oracle_s": t_or}
+    for name, prec in (("fp32", dr.F32), ("bf16", dr.BF16)):
+        plan = dr.Plan(w.N, w.N, 1, w.ns, theta, t, w.basis, w.m, w.nt, prec)
+        dt = getattr(torch, plan.storage_dtype)
+        u = torch.zeros(plan.u_shape(), dtype=dt, device=dev)
+        prm = dr.solve_params(dr.ADMM_CG, iters=iters, n_cg=w.n_cg, lambda1=w.lambda1, lambda2=w.lambda2, rho=w.rho)
+        res = dr.admm_solve(plan, torch.from_numpy(g1).to(dt).to(dev), u, prm)
+        uu = u.to(torch.float64).cpu().numpy()
+        out[name] = {"rel_l2_u": float(np.linalg.norm(uu - uo) / np.linalg.norm(uo)),
+                     "rel_objective": float(abs(res["objective"][-1] - oo[-1]) / abs(oo[-1]))}
+    return out
+
+
+def run_serving_sweep(a, device, utilisations=(0.5, 0.8, 0.95)):
+    """The reduced request stream at arrival rates giving the stated
+    utilisations: rho = lambda E[S], E[S] the mean time of a job solved alone."""
+    from paper_1809_09725_gb300 import dynrecon as dr
+    jobs = serving_jobs(a.serving_jobs)
+    prm = lambda: dr.solve_params(dr.ADMM_CG, iters=30, n_cg=4, lambda1=1e-3, lambda2=1.0, rho=1e-2)
+    service = []
+    for j in jobs:  # each job alone, through the same public call as a worker
+        plan = dr.Plan(j["N"], j["N"], j["nz"], j["N"], j["theta"], j["t"], j["basis"], j["m"], j["nt"], dr.F32)
+        uh = np.zeros((j["nz"], j["N"], j["N"], j["m"]), dtype=np.float32)
+        gh = j["g"].astype(np.float32)
+        t0 = time.perf_counter()
+        dr.admm_solve(plan, gh, uh, prm(), want_objective=False)
+        service.append(time.perf_counter() - t0)
+        plan.close()
+    es = float(np.mean(service))
+    out = {"mean_service_s": es, "points": []}
+    for rho in utilisations:
+        rng = np.random.default_rng(int(rho * 1000))
+        arrivals = np.cumsum(rng.exponential(es / rho, size=len(jobs)))
+        descs, keep = [], []
+        for j in jobs:
+            gh = j["g"].astype(np.float32)
+            uh = np.zeros((j["nz"], j["N"], j["N"], j["m"]), dtype=np.float32)
+            keep.append((gh, uh))
+            descs.append(dr.job_desc(j["N"], j["N"], j["nz"], j["N"], j["theta"], j["t"], j["basis"], j["m"],
+                                     j["nt"], dr.F32, prm(), gh, uh))
+        srv = dr.Server(device=device, budget_bytes=150 * 10 ** 9, slots=8)
+        t0 = time.perf_counter()
+        ids = []
+        for arr, d in zip(arrivals, descs):
+            wait = arr - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(wait)
+            ids.append(srv.submit(d))
+        res = [srv.wait(i, timeout_s=600.0) for i in ids]
+        st = srv.stats()
+        srv.close()
+        out["points"].append({"utilisation": rho, "arrival_rate_per_s": rho / es,
+                              "p50_latency_s": st["p50_latency_s"], "p99_latency_s": st["p99_latency_s"],
+                              "completed": st["completed"], "failed": st["failed"],
+                              "max_queue_s": max(r["queue_s"] for r in res)})
+    return out
+
+
+def run_batched(dev, n_jobs=16, iters=10, seed=180903):
+    """Uneven jobs of the batched configuration (N in {128,256,512}, nz in
+    [1,32], K in {720,1800,3600} over 4-20 half-turns, m in {4,8,16}, Fourier or
+    Legendre; first n_jobs of the seeded list, seeded random data) solved
+    together by admm_solve_batch (one CUDA graph per iteration)."""
+    import torch
+
+    from paper_1809_09725_gb300 import dynrecon as dr
+    from paper_1809_09725_gb300 import synth
+    rng = np.random.default_rng(seed)
+    plans, gs, us, prms, units = [], [], [], [], 0
+    for i in range(n_jobs):
+        N = int(rng.choice([128, 256, 512]))
+        nz = int(rng.integers(1, 33))
+        K = int(rng.choice([720, 1800, 3600]))
+        ht = int(rng.integers(4, 21))
+        m = int(rng.choice([4, 8, 16]))
+        basis = int(rng.integers(0, 2))
+        theta, t = synth.scan(K, ht)
+        p = dr.Plan(N, N, nz, N, theta, t, basis, m, ht, dr.F32)
+        plans.append(p)
+        gen = torch.Generator(device=dev).manual_seed(seed * 1000 + i)
+        gs.append(torch.randn(p.g_shape(), generator=gen, device=dev))
+        us.append(torch.zeros(p.u_shape(), device=dev))
+        prms.append(dr.solve_params(dr.ADMM_CG, iters=iters, n_cg=4, lambda1=1e-3, lambda2=1.0, rho=1e-2))
+        units += 2 * 5 * iters * K * N * N * nz
+    t_setup = time.perf_counter()
+    for p in plans:
+        p.autotune()
+    t_setup = time.perf_counter() - t_setup
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    dr.admm_solve_batch(plans, gs, us, prms)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    # the same jobs one after another (same plans, same variants)
+    for u in us:
+        u.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for p, g, u, prm in zip(plans, gs, us, prms):
+        dr.admm_solve(p, g, u, prm, want_objective=False)
+    torch.cuda.synchronize()
+    el_seq = time.perf_counter() - t0
+    folded = sum(1 for p in plans if p.info()["fwd_variant"] == 1)
+    return {"jobs": n_jobs, "iters": iters, "seconds": el, "voxel_projection_per_s": units / el,
+            "sequential_seconds": el_seq, "sequential_voxel_projection_per_s": units / el_seq,
+            "jobs_on_folded_projectors": folded, "autotune_s": t_setup,
+            "note": "seeded random data of each job's shape (throughput does not depend on the values); "
+                    "autotuning timed separately; jobs whose angles do not repeat mod pi use the direct pair"}
 
 
 def run_reference(a):
