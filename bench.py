@@ -396,7 +396,12 @@ def run_ours(a):
         accuracy = accuracy_vs_oracle(w, theta, t, g_np, dev)
 
     if rank == 0:
-        launches_per_iter = 6 + 5 * w.n_cg
+        # per ADMM-CG iteration: n_cg + 1 forwards and adjoints (the folded
+        # adjoint is two launches: data fold + back-projection), n_cg + 1 D^T D
+        # (right-hand side + CG steps), prox, D^T w, n_cg updates, n_cg - 1
+        # direction updates, the fidelity dot, the iteration counter
+        adj_launches = 2 if info["adj_variant"] == 1 else 1
+        launches_per_iter = (w.n_cg + 1) * (2 + adj_launches) + 2 * w.n_cg + 3
         line = {
             "metric": "voxel*projection updates/s (dynamic projector + back-projector applications "
                       "inside ADMM-CG iterations)",
@@ -411,7 +416,7 @@ def run_ours(a):
             "objective_first_last": [float(obj[0]), float(obj[-1])],
             "clocks": clocks,
             "e2e": e2e,
-            "gpu_launches": launches_per_iter * a.steps + 2,
+            "gpu_launches": launches_per_iter * a.steps + 2,  # + the final fidelity (forward + dot)
             "roofline": {"bound": "smem", "kernel": kname, "achieved": smem_achieved, "peak": smem_peak,
                          "unit": "TB/s", "frac": smem_achieved / smem_peak, "traffic": traffic,
                          "algorithmic_smem_bytes_per_launch": smem_bytes,
