@@ -7,7 +7,9 @@ double precision, compiled with ``-ffp-contract=off``); this module only builds
 it with gcc and marshals numpy arrays through ctypes.
 
 Every function follows a passage of the paper:
-  * ``basis_table``            Sec. 4, Eq. (repr); Sec. 5 (Fourier basis)
+  * ``basis_table``            Sec. 4, Eq. (repr): real Fourier, shifted Legendre,
+                               Haar, Heaviside; Sec. 5 complex Fourier (real channels)
+  * ``ORTHONORMAL`` flag        Gram-Schmidt over the acquisition times (Sec. 4)
   * ``joseph_fwd_slice``       static Radon transform R of Eq. (radapr), Joseph rule
   * ``joseph_adj_slice``       its exact transpose (pixel-driven gather)
   * ``dyn_fwd`` / ``dyn_adj``  Eqs. (Rfwd)/(radapr) and (radadjapr)
@@ -19,6 +21,9 @@ Every function follows a passage of the paper:
   * ``chambolle_pock``         Sec. 3, Fig. 2
   * ``power_norm``             operator norm for tau, sigma (Fig. 2 footnote)
   * ``objective``              Eq. (lr12)
+  * ``shepp_logan_filter``     the Shepp-Logan filter of the FBP start (Sec. 5)
+  * ``fbp_windows`` / ``fbp_init``  windowed FBP images and their least-squares
+                               fit to the basis (the initial guess of Sec. 5)
 
 Parity unpinned: none of the functions above; each has a pin in
 ``tests/test_oracle_*.py``.
