@@ -66,7 +66,8 @@ def parse():
     ap.add_argument("--fold-strip", type=int, default=0,
                     help="with --variant: fix the folded forward's strip height (lines) instead of the default")
     ap.add_argument("--variant", default=None,
-                    help="force projector variants 'fwd,adj' (0 direct, 1 fold); default: autotuned")
+                    help="force projector variants 'fwd,adj' (0 direct, 1 fold, 2 fold in two kernels: forward "
+                         "only); default: autotuned")
     ap.add_argument("--profile-small", action="store_true",
                     help="run only a few operator launches of a 2-slice cut (for ncu captures)")
     return ap.parse_args()
@@ -185,8 +186,10 @@ def algorithmic_smem_bytes(w, theta, variant, U):
     Joseph sample of the folded forward reads two neighbouring pixel vectors
     of m FP32 coefficients from the staged strip; the folded adjoint reads,
     per voxel and distinct angle, two bins of the m folded sinograms from its
-    staged window.  (The direct variants stage data per projection.)"""
-    if variant == 1:
+    staged window.  (The direct variants stage data per projection.)  The
+    two-kernel folded forward (variant 2) reads the same samples in its
+    static-transform kernel."""
+    if variant in (1, 2):
         return 2 * w.m * 4 * joseph_samples(theta, w.N, w.N, w.ns) * w.nz
     return 2 * w.m * 4 * w.K * w.voxels()
 
@@ -200,8 +203,9 @@ def algorithmic_flops(w, variant, U):
     half-turn fold (Sec. 4): per voxel and distinct angle mod pi, 2 FMAs of
     the interpolation for each of the m coefficients, plus m FMAs per
     detector sample to distribute (fold) over the K projections:
-        2 (2 m U V + m K ns nz)."""
-    if variant == 1:
+        2 (2 m U V + m K ns nz).
+    The two-kernel folded forward does the same arithmetic in two launches."""
+    if variant in (1, 2):
         return 2.0 * (2 * w.m * U * w.voxels() + w.m * w.K * w.ns * w.nz)
     return 2.0 * (w.m + 2) * w.K * w.voxels()
 
@@ -300,7 +304,7 @@ def run_ours(a):
     U = info["unique_angles"]
     if fwd_ms >= adj_ms:
         variant = info["fwd_variant"]
-        kname = "fold_fwd_kernel" if variant == 1 else "fwd_kernel"
+        kname = {1: "fold_fwd_kernel", 2: "fold_fwd_kernel(static)+fold_dist_kernel"}.get(variant, "fwd_kernel")
         launch_ms = fwd_ms
     else:
         variant = info["adj_variant"]
@@ -400,8 +404,10 @@ def run_ours(a):
         # adjoint is two launches: data fold + back-projection), n_cg + 1 D^T D
         # (right-hand side + CG steps), prox, D^T w, n_cg updates, n_cg - 1
         # direction updates, the fidelity dot, the iteration counter
+        # (the two-kernel folded forward is two launches too: static transforms + distribution)
         adj_launches = 2 if info["adj_variant"] == 1 else 1
-        launches_per_iter = (w.n_cg + 1) * (2 + adj_launches) + 2 * w.n_cg + 3
+        fwd_launches = 2 if info["fwd_variant"] == 2 else 1
+        launches_per_iter = (w.n_cg + 1) * (1 + fwd_launches + adj_launches) + 2 * w.n_cg + 3
         line = {
             "metric": "voxel*projection updates/s (dynamic projector + back-projector applications "
                       "inside ADMM-CG iterations)",
@@ -413,7 +419,7 @@ def run_ours(a):
             "objective_first_last": [float(obj[0]), float(obj[-1])],
             "clocks": clocks,
             "e2e": e2e,
-            "gpu_launches": launches_per_iter * a.steps + 2,  # + the final fidelity (forward + dot)
+            "gpu_launches": launches_per_iter * a.steps + fwd_launches + 1,  # + the final fidelity (forward + dot)
             "roofline": {"bound": "smem", "kernel": kname, "achieved": smem_achieved, "peak": smem_peak,
                          "unit": "TB/s", "frac": smem_achieved / smem_peak, "traffic": traffic,
                          "algorithmic_smem_bytes_per_launch": smem_bytes,
@@ -424,7 +430,9 @@ def run_ours(a):
                          "launch_ms": launch_ms, "fwd_ms": fwd_ms, "adj_ms": adj_ms,
                          "variants": {"unique_angles": U, "fwd": info["fwd_variant"], "adj": info["adj_variant"],
                                       "fold_lines": info["fold_lines"], "fold_async": info["fold_async"],
-                                      "autotune_ms_fwd_direct_fold_adj_direct_fold": tune}},
+                                      "fold2_group_threads_lines": [info["fold2_group"], info["fold2_threads"],
+                                                                    info["fold2_lines"]],
+                                      "autotune_ms_fwd_direct_fold_adj_direct_fold_fwd_fold2": tune}},
             "cpu_baseline": cpu,
             "serving": serving,
             "accuracy_vs_fp64_oracle": accuracy,
@@ -745,7 +753,7 @@ def run_batched(dev, n_jobs=16, iters=10, seed=180903):
         dr.admm_solve(p, g, u, prm, want_objective=False)
     torch.cuda.synchronize()
     el_seq = time.perf_counter() - t0
-    folded = sum(1 for p in plans if p.info()["fwd_variant"] == 1)
+    folded = sum(1 for p in plans if p.info()["fwd_variant"] in (1, 2))
     return {"jobs": n_jobs, "iters": iters, "seconds": el, "voxel_projection_per_s": units / el,
             "sequential_seconds": el_seq, "sequential_voxel_projection_per_s": units / el_seq,
             "jobs_on_folded_projectors": folded, "autotune_s": t_setup,

@@ -127,20 +127,26 @@ size_t dr_plan_workspace_bytes(const dr_plan *plan, dr_algo algo);
  * weights phi_j(t_k); the adjoint first folds the data per theta0
  *     gt_j(theta0, s) = sum_{k: theta0_k = theta0} phi_j(t_k) g_k((-1)^n_k s)
  * and back-projects the m folded sinograms.  Same operator up to rounding;
- * the fold is offered for F32 and BF16 plans.  -1 = automatic (a cost model
- * until dr_plan_autotune or admm_solve has timed both).  Returns DR_EINVAL
- * if the fold is requested but unavailable.
+ * the fold is offered for F32 and BF16 plans.  2 (forward only, m >= 4) =
+ * the fold in two kernels: the static transforms of groups of 4 or 8
+ * coefficients are computed by separate CTAs (more rays per staged image,
+ * which pays off for wide images and large m) into the plan's folded-data
+ * scratch, then distributed to the K projections.  -1 = automatic (a cost
+ * model until dr_plan_autotune or admm_solve has timed them).  Returns
+ * DR_EINVAL if a fold variant is requested but unavailable.
  */
 dr_status dr_plan_set_variant(dr_plan *plan, int fwd_variant, int adj_variant);
 
 /*
- * Time both variants of both projectors on this plan's geometry (allocates
- * and frees scratch; synchronises) and keep the faster ones for automatic
- * selection; for the folded forward also choose the strip height and
- * staging mode (neither changes the result).  The decision is cached for the process, keyed by the sizes,
- * basis, precision, angles and times, so later plans of the same problem
- * reuse it (same kernels, bit-identical results) without timing again.  times_ms: HOST [4] nullable: forward direct, forward fold,
- * adjoint direct, adjoint fold (-1 where a variant is unavailable).
+ * Time the variants of both projectors on this plan's geometry (allocates
+ * and frees scratch; synchronises) and keep the fastest for automatic
+ * selection; for the folded forwards also choose the strip height, staging
+ * mode and coefficient group size (none changes the result).  The decision
+ * is cached for the process, keyed by the sizes, basis, precision, angles and
+ * times, so later plans of the same problem reuse it (same kernels,
+ * bit-identical results) without timing again.  times_ms: HOST [5] nullable:
+ * forward direct, forward fold, adjoint direct, adjoint fold, forward fold in
+ * two kernels (-1 where a variant is unavailable).
  */
 dr_status dr_plan_autotune(dr_plan *plan, double *times_ms);
 
@@ -155,15 +161,29 @@ dr_status dr_plan_autotune(dr_plan *plan, double *times_ms);
  */
 dr_status dr_plan_set_fold_strip(dr_plan *plan, int lines, int async);
 
+/*
+ * Fix the two-kernel folded forward's configuration: coefficients per CTA
+ * (group 4, or 8 when m > 4), CTA size (threads 256, 512 or 1024: 1024 to
+ * 4096 rays per CTA) and strip height (lines >= 1, within the strip budget).  Every
+ * coefficient's ray sums run the same march whatever the choice: results are
+ * identical.  DR_EINVAL if the variant is unavailable or the choice does not
+ * fit.
+ */
+dr_status dr_plan_set_fold_groups(dr_plan *plan, int group, int threads, int lines);
+
 typedef struct {
     int unique_angles;   /* distinct theta mod pi (0: the fold is unavailable) */
     int max_group;       /* most projections sharing one theta mod pi */
-    int fwd_variant;     /* variant the forward uses now (0 direct, 1 fold) */
+    int fwd_variant;     /* variant the forward uses now (0 direct, 1 fold, 2 fold in two kernels) */
     int adj_variant;     /* variant the adjoint uses now */
     int tuned;           /* 1 once the variants have been timed */
     size_t device_bytes; /* device memory held by the plan */
     int fold_lines;      /* folded forward: image lines staged per shared-memory strip */
     int fold_async;      /* folded forward: 1 if strips are double-buffered with cp.async */
+    int fold2_group;     /* two-kernel folded forward: coefficients per CTA (0: unavailable) */
+    int fold2_threads;   /* two-kernel folded forward: threads per CTA */
+    int fold2_lines;     /* two-kernel folded forward: strip lines */
+    int fwd_variant_storage; /* forward variant of storage-typed calls (differs on BF16 plans) */
 } dr_plan_info_t;
 
 /* Describe the plan (host struct filled in). */

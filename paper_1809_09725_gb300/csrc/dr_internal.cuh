@@ -162,12 +162,22 @@ struct dr_plan {
     int fold_lines = 0, fold_async = 0;  // folded forward: strip lines per buffer, cp.async double buffering
     int fold_lines_st = 0, fold_async_st = 0;  // the same for the bf16-strip kernel of BF16 plans
     bool fold_fwd_ok = false;         // the forward strip fits in shared memory
+    // folded forward in two kernels (variant 2): static transforms of groups of
+    // 4 or 8 coefficients of the distinct angles into d_gt, then distribution
+    int *d_fold_of_k = nullptr;       // [K] 2 * (distinct angle) + (1 if the bins are reversed)
+    // configurations gi = 0..5: 4 / 8 coefficients (odd gi: 8) x 256 / 512 / 1024 threads (gi / 2)
+    int fold2_P[6] = {}, fold2_nchunk[6] = {}, fold2_nblocks[6] = {}, fold2_R[6] = {};
+    int *d_fold2_blocks[6] = {};
+    bool fold2_ok = false;
+    int fold2_gi = 0;                 // configuration in use
+    int sel_fwd_st = 0;               // forward variant of storage-typed calls on BF16 plans (bf16 strips)
+    int fold2_lines = 1, fold2_lines_st = 1;  // strip lines (compute-typed / bf16 kernels)
     void *d_gt = nullptr;             // folded data [nz][U][ns][MS] float (allocated on first use)
     size_t gt_bytes = 0;
-    int var_fwd = -1, var_adj = -1;   // -1 automatic, 0 direct, 1 fold (explicit choice)
+    int var_fwd = -1, var_adj = -1;   // -1 automatic, 0 direct, 1 fold, 2 fold in two kernels (forward)
     int sel_fwd = 0, sel_adj = 0;     // variant in use
     bool tuned = false;
-    double tune_ms[4] = {0, 0, 0, 0}; // fwd direct, fwd fold, adj direct, adj fold
+    double tune_ms[5] = {0, 0, 0, 0, 0}; // fwd direct, fwd fold, adj direct, adj fold, fwd fold (two kernels)
     double *d_partials = nullptr;
     unsigned *d_counters = nullptr;
     dr::DevScalars *d_scal = nullptr;

@@ -37,6 +37,21 @@ constexpr int kFoldAdjStages = 2;
 __host__ __device__ constexpr int fold_ms(int M) { return M <= 4 ? 4 : ((M % 8 == 0) ? M + 4 : M); }
 __host__ __device__ constexpr int fold_rpt(int M) { return M <= 4 ? 8 : 32 / M; }
 
+// Static-transform CTAs of the two-kernel forward: configuration gi = 0..5
+// handles MC = 4 or 8 coefficients (odd gi: 8) with 256, 512 or 1024 threads
+// (gi / 2) and fold_static_rpt rays per thread: 1024 to 4096 rays per CTA.
+// The more rays a CTA carries, the more samples share each staged line.
+constexpr int kFoldStaticConfigs = 6;
+__host__ __device__ constexpr int fold_static_mc(int gi) { return (gi & 1) ? 8 : 4; }
+__host__ __device__ constexpr int fold_static_threads(int gi) { return 256 << (gi / 2); }
+__host__ __device__ constexpr int fold_static_rpt_gi(int gi) {
+    return gi < 4 ? 32 / fold_static_mc(gi) : 16 / fold_static_mc(gi);
+}
+// Strip element stride of a static group: 4 or 12 floats (bf16: 4 or 8).
+__host__ __device__ constexpr int fold_static_ps(int MC, bool bf16) {
+    return bf16 ? (MC == 4 ? 4 : 8) : (MC == 4 ? 4 : 12);
+}
+
 // Element stride of one pixel's coefficient vector in the forward strip.
 // Float strips use fold_ms.  BF16 plans stage the stored bf16 values as they
 // are (exact; the march widens them to float in registers), which halves the
@@ -90,14 +105,17 @@ __device__ __forceinline__ void load_vec(const T *p, T (&v)[M]) {
     }
 }
 
-// Copy one pixel's coefficient vector into the forward strip: bf16 strips
-// keep the stored values, float strips hold the compute type; slots j >= m
-// are zero.  async_stage (only when m == M) issues 16-byte cp.async copies.
+// Copy the coefficients j0 .. j0+count-1 of one pixel (src points at j0) into
+// the forward strip: bf16 strips keep the stored values, float strips hold
+// the compute type; slots >= count are zero.  vec: src is 16-byte aligned
+// and count == M, so whole 16-byte vectors may be moved (async_stage: with
+// cp.async).
 template <typename S, typename T, int M, typename ST>
-__device__ __forceinline__ void stage_pixel(ST *dst, const S *__restrict__ src, int m, int async_stage) {
-    if constexpr (sizeof(S) == 2) {
+__device__ __forceinline__ void stage_pixel(ST *dst, const S *__restrict__ src, int count, bool vec,
+                                            int async_stage) {
+    if constexpr (sizeof(S) == 2 && sizeof(ST) == 2) {
         if constexpr ((M % 8) == 0) {
-            if (m == M) {
+            if (vec) {
                 if (async_stage) {
 #pragma unroll
                     for (int j = 0; j < M / 8; ++j) cp_async_16(dst + 8 * j, src + 8 * j);
@@ -110,17 +128,32 @@ __device__ __forceinline__ void stage_pixel(ST *dst, const S *__restrict__ src, 
             }
         }
 #pragma unroll
-        for (int j = 0; j < M; ++j) dst[j] = j < m ? src[j] : S(0.0f);
+        for (int j = 0; j < M; ++j) dst[j] = j < count ? src[j] : S(0.0f);
     } else {
-        if constexpr (sizeof(S) == 4 && (M % 4) == 0) {
-            if (async_stage) {
-#pragma unroll
-                for (int j = 0; j < M / 4; ++j) cp_async_16(dst + 4 * j, src + 4 * j);
-                return;
-            }
-        }
         T v[M];
-        load_coeffs<T, S, M>(src, m, v);
+        if constexpr (sizeof(S) == 4 && (M % 4) == 0) {
+            if (vec) {
+                if (async_stage) {
+#pragma unroll
+                    for (int j = 0; j < M / 4; ++j) cp_async_16(dst + 4 * j, src + 4 * j);
+                    return;
+                }
+#pragma unroll
+                for (int j = 0; j < M / 4; ++j) {
+                    const float4 a = __ldg(reinterpret_cast<const float4 *>(src) + j);
+                    v[4 * j] = a.x;
+                    v[4 * j + 1] = a.y;
+                    v[4 * j + 2] = a.z;
+                    v[4 * j + 3] = a.w;
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < M; ++j) v[j] = j < count ? ldc<T>(src + j) : T(0);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < M; ++j) v[j] = j < count ? ldc<T>(src + j) : T(0);
+        }
         if constexpr (sizeof(T) == 4 && (M % 4) == 0) {
 #pragma unroll
             for (int j = 0; j < M / 4; ++j)
@@ -139,22 +172,34 @@ __device__ __forceinline__ void stage_pixel(ST *dst, const S *__restrict__ src, 
 // latency bound, and at M = 8 three CTAs (<= 85 registers) beat two.
 __host__ __device__ constexpr int fold_fwd_min_blocks(int M) { return M == 8 ? 3 : 1; }
 
-template <typename S, typename T, int M>
-__global__ void __launch_bounds__(kFoldThreads, fold_fwd_min_blocks(M))
+// STATIC = false: M covers all coefficients and the epilogue distributes each
+// ray to the projections of its angle.  STATIC = true: the CTA handles the
+// coefficient group j0 = (blockIdx.y % ngroups) * M .. j0 + M - 1 and writes
+// the scaled static transforms (R u_j)(theta0_a, s_b) to
+// ru[((z U + a) ns + b) ms_ru + j]; fold_dist_kernel distributes them.
+template <typename S, typename T, int M, bool STATIC, int THREADS = kFoldThreads, int RPTS = 0>
+__global__ void __launch_bounds__(THREADS, THREADS == kFoldThreads ? fold_fwd_min_blocks(M) : 1)
     fold_fwd_kernel(const S *__restrict__ u, S *__restrict__ out, const S *__restrict__ gm,
                     const FwdProj *__restrict__ uproj, const int *__restrict__ start, const int *__restrict__ member,
                     const T *__restrict__ phip, const int *__restrict__ blocks, int nx, int ny, int ns, int K,
-                    int m, int MP, int P, int R, int nchunk, int mode, T sigma, int async_stage) {
-    using ST = std::conditional_t<sizeof(S) == 2, S, T>;  // strip element: stored bf16, else the compute type
-    constexpr int MS = fold_strip_ps<S, T, M>();
-    constexpr int RPT = fold_rpt(M);
+                    int m, int MP, int P, int R, int nchunk, int mode, T sigma, int async_stage, int ngroups,
+                    T *__restrict__ ru, int U, int ms_ru) {
+    // strip element: stored bf16 for bf16 storage, else the compute type
+    constexpr bool BF16_STRIP = sizeof(S) == 2;
+    using ST = std::conditional_t<BF16_STRIP, S, T>;
+    constexpr int MS = STATIC ? fold_static_ps(M, BF16_STRIP) : fold_strip_ps<S, T, M>();
+    constexpr int RPT = STATIC ? RPTS : fold_rpt(M);
+    constexpr int VW = 16 / (int)sizeof(S);  // elements per 16-byte vector
     extern __shared__ __align__(16) unsigned char fold_smem[];
     T *scale_s = reinterpret_cast<T *>(fold_smem);                       // [64]
     long long *bfx_s = reinterpret_cast<long long *>(fold_smem + 256);   // [64]
     ST *strip = reinterpret_cast<ST *>(fold_smem + 768);                 // [R][wpad][MS]
 
     const int tid = threadIdx.x;
-    const int z = blockIdx.y;
+    const int z = blockIdx.y / ngroups;
+    const int j0 = (blockIdx.y - z * ngroups) * M;
+    const int count = min(M, m - j0);
+    const bool vec = count == M && (m % VW) == 0 && (j0 % VW) == 0;
     const int blk_id = blockIdx.x / nchunk, chunk = blockIdx.x - blk_id * nchunk;
     const int *blk = blocks + (size_t)blk_id * P;
     const int branch = uproj[blk[0]].branch;
@@ -162,15 +207,15 @@ __global__ void __launch_bounds__(kFoldThreads, fold_fwd_min_blocks(M))
     const int H = branch ? nx : ny;
     const int wpad = W + 2 * kFwdGuard;
 
-    for (int p = tid; p < P; p += kFoldThreads) {
+    for (int p = tid; p < P; p += THREADS) {
         const int a = blk[p];
         const FwdProj f = uproj[a >= 0 ? a : blk[0]];
         scale_s[p] = (T)f.scale;
         bfx_s[p] = f.B_fx;
     }
-    for (int i = tid; i < (async_stage ? 2 : 1) * R * wpad * MS; i += kFoldThreads) strip[i] = ST(0.0f);
+    for (int i = tid; i < (async_stage ? 2 : 1) * R * wpad * MS; i += THREADS) strip[i] = ST(0.0f);
 
-    const int rays_per_cta = kFoldThreads * RPT;
+    const int rays_per_cta = THREADS * RPT;
     const int b_base = chunk * rays_per_cta;
     long long x0fx[RPT];
     int lo[RPT], hi[RPT];
@@ -182,7 +227,7 @@ __global__ void __launch_bounds__(kFoldThreads, fold_fwd_min_blocks(M))
         x0fx[q] = 0;
 #pragma unroll
         for (int j = 0; j < M; ++j) acc[q][j] = T(0);
-        const int rid = b_base + tid + q * kFoldThreads;
+        const int rid = b_base + tid + q * THREADS;
         const int p = (nchunk > 1) ? 0 : rid / ns;
         const int b = (nchunk > 1) ? rid : rid - p * ns;
         if (p < P && b < ns) {
@@ -214,7 +259,7 @@ __global__ void __launch_bounds__(kFoldThreads, fold_fwd_min_blocks(M))
     // 16-byte float vectors, else through registers.
     auto stage = [&](ST *buf, int r0, int nl) {
         const int npx = nl * W;
-        for (int qq = tid; qq < npx; qq += kFoldThreads) {
+        for (int qq = tid; qq < npx; qq += THREADS) {
             int rl, i;
             size_t pix;
             if (branch == 0) {
@@ -226,7 +271,8 @@ __global__ void __launch_bounds__(kFoldThreads, fold_fwd_min_blocks(M))
                 rl = qq - i * nl;
                 pix = zoff + (size_t)i * nx + (r0 + rl);
             }
-            stage_pixel<S, T, M>(buf + ((size_t)rl * wpad + kFwdGuard + i) * MS, u + pix * m, m, async_stage);
+            stage_pixel<S, T, M>(buf + ((size_t)rl * wpad + kFwdGuard + i) * MS, u + pix * m + j0, count, vec,
+                                 async_stage);
         }
     };
     const size_t buf_elems = (size_t)R * wpad * MS;  // buffer b starts at strip + b * buf_elems
@@ -259,7 +305,7 @@ __global__ void __launch_bounds__(kFoldThreads, fold_fwd_min_blocks(M))
         for (int q = 0; q < RPT; ++q) {
             const int rs = max(lo[q], r0), re = min(hi[q], r0 + nl - 1);
             if (rs > re) continue;
-            const int rid = b_base + tid + q * kFoldThreads;
+            const int rid = b_base + tid + q * THREADS;
             const int p = (nchunk > 1) ? 0 : rid / ns;
             const long long bfx = bfx_s[p];
             long long x = x0fx[q] + (long long)rs * bfx;
@@ -271,7 +317,7 @@ __global__ void __launch_bounds__(kFoldThreads, fold_fwd_min_blocks(M))
                 const float w = __uint_as_float(0x3F800000u | ((unsigned)x >> 9)) - 1.0f;
                 const float w1m = 1.0f - w;
                 T t0[M], t1[M];
-                if constexpr (sizeof(S) == 2) {
+                if constexpr (BF16_STRIP) {
                     load_vec_bf16<M, MS>(row + i0 * MS, t0);
                     load_vec_bf16<M, MS>(row + (i0 + 1) * MS, t1);
                 } else {
@@ -287,10 +333,28 @@ __global__ void __launch_bounds__(kFoldThreads, fold_fwd_min_blocks(M))
         __syncthreads();
     }
 
+    if constexpr (STATIC) {
+        // ---- epilogue: the scaled static transforms of this coefficient group ----
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) {
+            const int rid = b_base + tid + q * THREADS;
+            const int p = (nchunk > 1) ? 0 : rid / ns;
+            const int b = (nchunk > 1) ? rid : rid - p * ns;
+            if (p >= P || b >= ns) continue;
+            const int a = blk[p];
+            if (a < 0) continue;
+            const T sc = scale_s[p];
+            T *dst = ru + (((size_t)z * U + a) * ns + b) * ms_ru + j0;
+#pragma unroll
+            for (int j = 0; j < M; ++j)
+                if (j < count) dst[j] = sc * acc[q][j];
+        }
+        return;
+    }
     // ---- epilogue: distribute each ray to every projection of its angle ----
 #pragma unroll
     for (int q = 0; q < RPT; ++q) {
-        const int rid = b_base + tid + q * kFoldThreads;
+        const int rid = b_base + tid + q * THREADS;
         const int p = (nchunk > 1) ? 0 : rid / ns;
         const int b = (nchunk > 1) ? rid : rid - p * ns;
         if (p >= P || b >= ns) continue;
@@ -316,6 +380,41 @@ __global__ void __launch_bounds__(kFoldThreads, fold_fwd_min_blocks(M))
                 const T h = ldc<T>(out + o);
                 stc<T>(out + o, (h + sigma * val - sigma * ldc<T>(gm + o)) / (T(1) + sigma));
             }
+        }
+    }
+}
+
+// ===========================================================================
+// Forward, two-kernel form, step 2: distribute the static transforms
+//   g[z][k][b] = sum_j phi_j(t_k) ru[z][a(k)][flip_k(b)][j]
+// with the forward epilogue modes (store, minus gm, CP dual update).
+// ===========================================================================
+template <typename S, typename T, int M>
+__global__ void __launch_bounds__(kRedThreads)
+    fold_dist_kernel(const T *__restrict__ ru, S *__restrict__ out, const S *__restrict__ gm,
+                     const int *__restrict__ of_k, const T *__restrict__ phip, int nz, int K, int ns, int U, int ms_ru,
+                     int m, int MP, int mode, T sigma) {
+    const size_t n = (size_t)nz * K * ns;
+    for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
+        const int b = (int)(o % ns);
+        const size_t zk = o / ns;
+        const int k = (int)(zk % K), z = (int)(zk / K);
+        const int ak = __ldg(of_k + k);
+        const int a = ak >> 1;
+        const int bb = (ak & 1) ? ns - 1 - b : b;
+        const T *r = ru + (((size_t)z * U + a) * ns + bb) * ms_ru;
+        const T *ph = phip + (size_t)k * MP;
+        T val = T(0);
+#pragma unroll
+        for (int j = 0; j < M; ++j)
+            if (j < m) val = fma(__ldg(ph + j), r[j], val);
+        if (mode == 0) {
+            stc<T>(out + o, val);
+        } else if (mode == 1) {
+            stc<T>(out + o, val - ldc<T>(gm + o));
+        } else {
+            const T h = ldc<T>(out + o);
+            stc<T>(out + o, (h + sigma * val - sigma * ldc<T>(gm + o)) / (T(1) + sigma));
         }
     }
 }
@@ -539,7 +638,7 @@ dr_status fold_fwd_launch_t(dr_plan *P, const void *u, void *out, const void *gm
     const int async_stage = async_ok && (bf16_strip ? P->fold_async_st : P->fold_async);
     const int R = std::max(1, bf16_strip ? P->fold_lines_st : P->fold_lines);
     const size_t smem = 768 + sizeof(ST) * (size_t)(async_stage ? 2 : 1) * R * wpad * MS;
-    auto kern = fold_fwd_kernel<S, T, M>;
+    auto kern = fold_fwd_kernel<S, T, M, false>;
     {
         dr_status s = allow_dynamic_smem((const void *)kern, smem);
         if (s != DR_OK) return s;
@@ -548,9 +647,76 @@ dr_status fold_fwd_launch_t(dr_plan *P, const void *u, void *out, const void *gm
     kern<<<grid, kFoldThreads, smem, st>>>((const S *)u, (S *)out, (const S *)gm, P->d_fold_fwd, P->d_fold_start,
                                            P->d_fold_member, (const T *)P->d_PhiP, P->d_fold_blocks, P->nx, P->ny,
                                            P->ns, P->K, P->m, P->MP, P->fold_P, R, P->fold_nchunk, mode,
-                                           (T)sigma, async_stage);
+                                           (T)sigma, async_stage, 1, (T *)nullptr, 0, 0);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? DR_OK : cuda_fail(e, "fold_fwd_kernel launch");
+}
+
+// Two-kernel folded forward: static transforms of coefficient groups of MC
+// (4 or 8) into the folded-data scratch, then the distribution.
+template <typename S, typename T, int M, int GI>
+dr_status fold_fwd2_launch_mc(dr_plan *P, const void *u, void *out, const void *gm, int mode, double sigma,
+                              cudaStream_t st) {
+    constexpr int MC = fold_static_mc(GI), THREADS = fold_static_threads(GI), RPT = fold_static_rpt_gi(GI);
+    constexpr bool BF16_STRIP = sizeof(S) == 2;
+    using ST = std::conditional_t<BF16_STRIP, S, T>;
+    constexpr int MS = fold_static_ps(MC, BF16_STRIP);
+    constexpr int VW = 16 / (int)sizeof(S);
+    const int gi = GI;
+    const int ngroups = (P->m + MC - 1) / MC;
+    const int wpad = std::max(P->nx, P->ny) + 2 * kFwdGuard;
+    const bool bf16_kernel = sizeof(S) == 2;
+    const int R = std::max(1, std::min(bf16_kernel ? P->fold2_lines_st : P->fold2_lines, P->fold2_R[gi]));
+    if ((size_t)P->nz * ngroups > 65535) return fail(DR_EINVAL, "two-kernel folded forward: too many slice groups");
+    // whole 16-byte vectors in every group: cp.async staging would be possible, but the
+    // two-kernel form stages through registers (one buffer)
+    (void)VW;
+    const size_t smem = 768 + sizeof(ST) * (size_t)R * wpad * MS;
+    auto kern = fold_fwd_kernel<S, T, MC, true, THREADS, RPT>;
+    {
+        dr_status s = allow_dynamic_smem((const void *)kern, smem);
+        if (s != DR_OK) return s;
+    }
+    {
+        dr_status s = ensure_fold_scratch(P);
+        if (s != DR_OK) return s;
+    }
+    constexpr int MSR = fold_ms(M);  // row stride of the folded-data scratch
+    dim3 grid(P->fold2_nblocks[gi] * P->fold2_nchunk[gi], P->nz * ngroups);
+    kern<<<grid, THREADS, smem, st>>>((const S *)u, (S *)out, (const S *)gm, P->d_fold_fwd, P->d_fold_start,
+                                           P->d_fold_member, (const T *)P->d_PhiP, P->d_fold2_blocks[gi], P->nx,
+                                           P->ny, P->ns, P->K, P->m, P->MP, P->fold2_P[gi], R, P->fold2_nchunk[gi],
+                                           mode, (T)sigma, 0, ngroups, (T *)P->d_gt, P->fold_U, MSR);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "fold_fwd_kernel (static) launch");
+    fold_dist_kernel<S, T, M><<<red_grid((size_t)P->nz * P->K * P->ns), kRedThreads, 0, st>>>(
+        (const T *)P->d_gt, (S *)out, (const S *)gm, P->d_fold_of_k, (const T *)P->d_PhiP, P->nz, P->K, P->ns,
+        P->fold_U, MSR, P->m, P->MP, mode, (T)sigma);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? DR_OK : cuda_fail(e, "fold_dist_kernel launch");
+}
+
+template <typename S, typename T, int M>
+dr_status fold_fwd2_launch_t(dr_plan *P, const void *u, void *out, const void *gm, int mode, double sigma,
+                             cudaStream_t st) {
+    if (!P->fold2_ok) return fail(DR_EINVAL, "two-kernel folded forward unavailable for this plan");
+    if constexpr (M >= 4) {
+        switch (P->fold2_gi) {
+            case 0: return fold_fwd2_launch_mc<S, T, M, 0>(P, u, out, gm, mode, sigma, st);
+            case 2: return fold_fwd2_launch_mc<S, T, M, 2>(P, u, out, gm, mode, sigma, st);
+            case 4: return fold_fwd2_launch_mc<S, T, M, 4>(P, u, out, gm, mode, sigma, st);
+            case 1:
+                if constexpr (M >= 8) return fold_fwd2_launch_mc<S, T, M, 1>(P, u, out, gm, mode, sigma, st);
+                break;
+            case 3:
+                if constexpr (M >= 8) return fold_fwd2_launch_mc<S, T, M, 3>(P, u, out, gm, mode, sigma, st);
+                break;
+            case 5:
+                if constexpr (M >= 8) return fold_fwd2_launch_mc<S, T, M, 5>(P, u, out, gm, mode, sigma, st);
+                break;
+        }
+    }
+    return fail(DR_EINVAL, "two-kernel folded forward: unsupported coefficient group");
 }
 
 template <typename S, typename T, int M>
@@ -592,6 +758,8 @@ template <typename S, typename T>
 struct FoldOps {
     static dr_status fwd(dr_plan *P, const void *u, void *out, const void *gm, int mode, double sigma,
                          cudaStream_t st);
+    static dr_status fwd2(dr_plan *P, const void *u, void *out, const void *gm, int mode, double sigma,
+                          cudaStream_t st);
     static dr_status adj(dr_plan *P, const void *g, void *u, double alpha, double beta, bool u_calc,
                          cudaStream_t st);
 };
@@ -613,6 +781,12 @@ template <typename S, typename T>
 dr_status FoldOps<S, T>::fwd(dr_plan *P, const void *u, void *out, const void *gm, int mode, double sigma,
                              cudaStream_t st) {
     DR_FOLD_DISPATCH(fold_fwd_launch_t, S, T, P, u, out, gm, mode, sigma, st)
+}
+
+template <typename S, typename T>
+dr_status FoldOps<S, T>::fwd2(dr_plan *P, const void *u, void *out, const void *gm, int mode, double sigma,
+                              cudaStream_t st) {
+    DR_FOLD_DISPATCH(fold_fwd2_launch_t, S, T, P, u, out, gm, mode, sigma, st)
 }
 
 template <typename S, typename T>

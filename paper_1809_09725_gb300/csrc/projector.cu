@@ -31,6 +31,10 @@ dr_status launch_fwd_variant(dr_plan *P, int variant, bool calc, const void *u, 
         if (P->prec == DR_BF16_F32ACC && !calc) return FoldOps<bf16, float>::fwd(P, u, out, gm, mode, sigma, st);
         return FoldOps<float, float>::fwd(P, u, out, gm, mode, sigma, st);
     }
+    if (variant == 2 && P->fold_U > 0 && P->fold2_ok) {
+        if (P->prec == DR_BF16_F32ACC && !calc) return FoldOps<bf16, float>::fwd2(P, u, out, gm, mode, sigma, st);
+        return FoldOps<float, float>::fwd2(P, u, out, gm, mode, sigma, st);
+    }
     switch (P->prec) {
         case DR_F32: return ProjOps<float, float>::fwd(P, u, out, gm, mode, sigma, st);
         case DR_BF16_F32ACC:
@@ -61,11 +65,15 @@ dr_status launch_adj_variant(dr_plan *P, int variant, bool calc, const void *g, 
 }
 
 static int fwd_choice(const dr_plan *P) { return P->var_fwd >= 0 ? P->var_fwd : P->sel_fwd; }
+// storage-typed calls on BF16 plans run the bf16-strip kernels, timed separately
+static int fwd_choice_st(const dr_plan *P) {
+    return P->var_fwd >= 0 ? P->var_fwd : (P->prec == DR_BF16_F32ACC ? P->sel_fwd_st : P->sel_fwd);
+}
 static int adj_choice(const dr_plan *P) { return P->var_adj >= 0 ? P->var_adj : P->sel_adj; }
 
 dr_status launch_fwd(dr_plan *P, const void *u, void *out, const void *gm, int mode, double sigma,
                      cudaStream_t st) {
-    return launch_fwd_variant(P, fwd_choice(P), false, u, out, gm, mode, sigma, st);
+    return launch_fwd_variant(P, fwd_choice_st(P), false, u, out, gm, mode, sigma, st);
 }
 
 dr_status launch_adj(dr_plan *P, const void *g, void *u, double alpha, double beta, bool u_calc,
@@ -101,8 +109,8 @@ struct TuneKey {
     }
 };
 struct TuneVal {
-    int fwd, adj, lines, async, lines_st, async_st;
-    double ms[4];
+    int fwd, adj, lines, async, lines_st, async_st, f2_gi, f2_lines, f2_lines_st, fwd_st;
+    double ms[5];
 };
 static std::mutex g_tune_mutex;
 static std::map<TuneKey, TuneVal> g_tune_cache;
@@ -134,7 +142,11 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
             P->fold_async = it->second.async;
             P->fold_lines_st = it->second.lines_st;
             P->fold_async_st = it->second.async_st;
-            for (int i = 0; i < 4; ++i) P->tune_ms[i] = it->second.ms[i];
+            P->fold2_gi = it->second.f2_gi;
+            P->fold2_lines = it->second.f2_lines;
+            P->fold2_lines_st = it->second.f2_lines_st;
+            P->sel_fwd_st = it->second.fwd_st;
+            for (int i = 0; i < 5; ++i) P->tune_ms[i] = it->second.ms[i];
             P->tuned = true;
             return DR_OK;
         }
@@ -146,7 +158,8 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
     const size_t cs = calc_size(P->prec);
     DR_CUDA_TRY(cudaMemsetAsync(u_scratch, 0, nu_elems(P) * cs, st));
     DR_CUDA_TRY(cudaMemsetAsync(g_scratch, 0, ng_elems(P) * cs, st));
-    double ms[4] = {1e30, 1e30, 1e30, 1e30};
+    double ms[5] = {1e30, 1e30, 1e30, 1e30, 1e30};
+    double ms_st1 = 1e30, ms_st2 = 1e30;  // bf16-strip kernels of BF16 plans: fold, fold in two kernels
     auto time_fwd = [&](int v, double &best, bool calc = true) -> dr_status {
         for (int rep = 0; rep < 3; ++rep) {
             DR_CUDA_TRY(cudaEventRecord(e0, st));
@@ -212,7 +225,63 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
                 }
             P->fold_lines_st = bl;
             P->fold_async_st = ba;
+            ms_st1 = best_t;
         }
+    }
+    if (P->fold2_ok) {
+        // two-kernel folded forward: coefficient group size and strip height
+        // (the grouping changes only which CTA computes a coefficient's ray sums:
+        // results do not depend on the choice)
+        const int lines_c[] = {1, 2, 3, 4, 6, 8, 12, 16};
+        int bgi = P->fold2_gi, bl = P->fold2_lines;
+        for (int gi = 0; gi < 6; ++gi) {
+            const int MC = (gi & 1) ? 8 : 4;
+            if (P->fold2_R[gi] < 1 || (MC == 8 && P->m <= 4) || (size_t)P->nz * ((P->m + MC - 1) / MC) > 65535)
+                continue;
+            for (int c : lines_c) {
+                if (c > P->fold2_R[gi]) continue;
+                P->fold2_gi = gi;
+                P->fold2_lines = c;
+                double t = 1e30;
+                dr_status s = time_fwd(2, t);
+                if (s != DR_OK) return s;
+                if (t < ms[4]) {
+                    ms[4] = t;
+                    bgi = gi;
+                    bl = c;
+                }
+            }
+        }
+        P->fold2_gi = bgi;
+        P->fold2_lines = bl;
+        P->fold2_lines_st = bl;
+        if (P->prec == DR_BF16_F32ACC) {
+            double best_t = 1e30;
+            for (int c : lines_c) {
+                if (c > P->fold2_R[bgi]) continue;
+                P->fold2_lines_st = c;
+                double t = 1e30;
+                dr_status s = time_fwd(2, t, false);
+                if (s != DR_OK) return s;
+                if (t < best_t) {
+                    best_t = t;
+                    bl = c;
+                }
+            }
+            P->fold2_lines_st = bl;
+            ms_st2 = best_t;
+        }
+    }
+    if (P->prec == DR_BF16_F32ACC) {
+        // storage-typed calls of BF16 plans run the bf16-strip kernels: their own choice
+        double ms_st0 = 1e30;
+        dr_status s0 = time_fwd(0, ms_st0, false);
+        if (s0 != DR_OK) return s0;
+        int best = 0;
+        double bt = ms_st0;
+        if (ms_st1 < bt) { best = 1; bt = ms_st1; }
+        if (ms_st2 < bt) { best = 2; bt = ms_st2; }
+        P->sel_fwd_st = best;
     }
     for (int v = 0; v < 2; ++v) {
         for (int rep = 0; rep < 3; ++rep) {
@@ -228,15 +297,22 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    for (int i = 0; i < 4; ++i) P->tune_ms[i] = ms[i] < 1e29 ? ms[i] : -1.0;
-    P->sel_fwd = ms[1] < ms[0] ? 1 : 0;
+    for (int i = 0; i < 5; ++i) P->tune_ms[i] = ms[i] < 1e29 ? ms[i] : -1.0;
+    {
+        int best = 0;
+        if (ms[1] < ms[best]) best = 1;
+        if (ms[4] < (best == 1 ? ms[1] : ms[0])) best = 2;
+        P->sel_fwd = best;
+        if (P->prec != DR_BF16_F32ACC) P->sel_fwd_st = best;
+    }
     P->sel_adj = ms[3] < ms[2] ? 1 : 0;
     P->tuned = true;
     std::lock_guard<std::mutex> lk(g_tune_mutex);
     auto ins = g_tune_cache.emplace(key, TuneVal{P->sel_fwd, P->sel_adj, P->fold_lines, P->fold_async,
-                                                 P->fold_lines_st, P->fold_async_st, {0, 0, 0, 0}});
+                                                 P->fold_lines_st, P->fold_async_st, P->fold2_gi, P->fold2_lines,
+                                                 P->fold2_lines_st, P->sel_fwd_st, {0, 0, 0, 0, 0}});
     if (ins.second) {
-        for (int i = 0; i < 4; ++i) ins.first->second.ms[i] = P->tune_ms[i];
+        for (int i = 0; i < 5; ++i) ins.first->second.ms[i] = P->tune_ms[i];
     } else {  // another thread tuned the same problem first: follow its choice
         P->sel_fwd = ins.first->second.fwd;
         P->sel_adj = ins.first->second.adj;
@@ -244,6 +320,10 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
         P->fold_async = ins.first->second.async;
         P->fold_lines_st = ins.first->second.lines_st;
         P->fold_async_st = ins.first->second.async_st;
+        P->fold2_gi = ins.first->second.f2_gi;
+        P->fold2_lines = ins.first->second.f2_lines;
+        P->fold2_lines_st = ins.first->second.f2_lines_st;
+        P->sel_fwd_st = ins.first->second.fwd_st;
     }
     return DR_OK;
 }
@@ -270,9 +350,11 @@ dr_status dyn_radon_adj(dr_plan *P, const void *g, void *u, double beta) {
 dr_status dr_plan_set_variant(dr_plan *P, int fwd_variant, int adj_variant) {
     clear_error();
     if (!P) return fail(DR_EINVAL, "dr_plan_set_variant: NULL plan");
-    if (fwd_variant < -1 || fwd_variant > 1 || adj_variant < -1 || adj_variant > 1)
-        return fail(DR_EINVAL, "dr_plan_set_variant: variants are -1 (auto), 0 (direct) or 1 (fold)");
-    if ((fwd_variant == 1 && !(P->fold_U > 0 && P->fold_fwd_ok)) || (adj_variant == 1 && P->fold_U == 0))
+    if (fwd_variant < -1 || fwd_variant > 2 || adj_variant < -1 || adj_variant > 1)
+        return fail(DR_EINVAL, "dr_plan_set_variant: forward variants are -1 (auto), 0 (direct), 1 (fold) or 2 "
+                               "(fold in two kernels); adjoint variants -1, 0 or 1");
+    if ((fwd_variant == 1 && !(P->fold_U > 0 && P->fold_fwd_ok)) || (adj_variant == 1 && P->fold_U == 0) ||
+        (fwd_variant == 2 && !(P->fold_U > 0 && P->fold2_ok)))
         return fail(DR_EINVAL, "dr_plan_set_variant: the half-turn fold is unavailable for this plan");
     P->var_fwd = fwd_variant;
     P->var_adj = adj_variant;
@@ -298,7 +380,7 @@ dr_status dr_plan_autotune(dr_plan *P, double *times_ms) {
         if (s != DR_OK) return s;
     }
     if (times_ms)
-        for (int i = 0; i < 4; ++i) times_ms[i] = P->tune_ms[i];
+        for (int i = 0; i < 5; ++i) times_ms[i] = P->tune_ms[i];
     return DR_OK;
 }
 
@@ -316,6 +398,21 @@ dr_status dr_plan_set_fold_strip(dr_plan *P, int lines, int async) {
     return DR_OK;
 }
 
+dr_status dr_plan_set_fold_groups(dr_plan *P, int group, int threads, int lines) {
+    clear_error();
+    if (!P) return fail(DR_EINVAL, "dr_plan_set_fold_groups: NULL plan");
+    if (!(P->fold_U > 0 && P->fold2_ok)) return fail(DR_EINVAL, "dr_plan_set_fold_groups: variant unavailable");
+    const int base = group == 4 ? 0 : (group == 8 ? 1 : -1);
+    const int gi = base < 0 ? -1 : base + (threads == 1024 ? 4 : (threads == 512 ? 2 : (threads == 256 ? 0 : -100)));
+    if (gi < 0 || (group == 8 && P->m <= 4) || lines < 1 || lines > P->fold2_R[gi] ||
+        (size_t)P->nz * ((P->m + group - 1) / group) > 65535)
+        return fail(DR_EINVAL, "dr_plan_set_fold_groups: group must be 4 or 8 (8 only for m > 4), threads 256, "
+                               "512 or 1024, and lines within the strip budget");
+    P->fold2_gi = gi;
+    P->fold2_lines = P->fold2_lines_st = lines;
+    return DR_OK;
+}
+
 dr_status dr_plan_info(const dr_plan *P, dr_plan_info_t *info) {
     clear_error();
     if (!P || !info) return fail(DR_EINVAL, "dr_plan_info: NULL argument");
@@ -327,6 +424,10 @@ dr_status dr_plan_info(const dr_plan *P, dr_plan_info_t *info) {
     info->device_bytes = P->table_bytes + P->ws.bytes + (P->d_gt ? P->gt_bytes : 0) + P->fbp_bytes;
     info->fold_lines = P->fold_lines;
     info->fold_async = P->fold_async;
+    info->fold2_group = P->fold2_ok ? ((P->fold2_gi & 1) ? 8 : 4) : 0;
+    info->fold2_threads = P->fold2_ok ? (256 << (P->fold2_gi / 2)) : 0;
+    info->fold2_lines = P->fold2_ok ? P->fold2_lines : 0;
+    info->fwd_variant_storage = P->var_fwd >= 0 ? P->var_fwd : P->sel_fwd_st;
     return DR_OK;
 }
 

@@ -31,7 +31,7 @@ _STATUS = {DR_EINVAL: "EINVAL", DR_ENOMEM: "ENOMEM", DR_ECUDA: "ECUDA", DR_ETIME
 # Every symbol include/dynrecon.h declares.
 EXPORTS = ("dr_plan_create", "dr_plan_destroy", "dr_plan_set_stream", "dr_plan_device_bytes",
            "dr_plan_workspace_bytes", "dr_plan_sync", "dr_plan_set_variant", "dr_plan_autotune",
-           "dr_plan_set_fold_strip", "dr_plan_info",
+           "dr_plan_set_fold_strip", "dr_plan_set_fold_groups", "dr_plan_info",
            "dyn_radon_fwd", "dyn_radon_adj", "dyn_radon_adj_noalloc", "dr_fbp_init", "tv4d_grad", "tv4d_grad_adj", "tv4d_prox",
            "dr_solve_params_default", "admm_solve", "admm_solve_batch", "cp_solve_slabs",
            "cp_solve_slabs_device_bytes", "dr_job_device_bytes", "dr_job_slab_device_bytes", "dr_server_create",
@@ -40,7 +40,7 @@ EXPORTS = ("dr_plan_create", "dr_plan_destroy", "dr_plan_set_stream", "dr_plan_d
 
 JOB_QUEUED, JOB_RUNNING, JOB_DONE, JOB_FAILED, JOB_CANCELED = 0, 1, 2, 3, 4
 
-DIRECT, FOLD, AUTO = 0, 1, -1
+DIRECT, FOLD, FOLD2, AUTO = 0, 1, 2, -1  # FOLD2: forward only, the fold in two kernels
 
 
 class DynreconError(RuntimeError):
@@ -52,7 +52,9 @@ class DynreconError(RuntimeError):
 class PlanInfo(ctypes.Structure):
     _fields_ = [("unique_angles", ctypes.c_int), ("max_group", ctypes.c_int), ("fwd_variant", ctypes.c_int),
                 ("adj_variant", ctypes.c_int), ("tuned", ctypes.c_int), ("device_bytes", ctypes.c_size_t),
-                ("fold_lines", ctypes.c_int), ("fold_async", ctypes.c_int)]
+                ("fold_lines", ctypes.c_int), ("fold_async", ctypes.c_int), ("fold2_group", ctypes.c_int),
+                ("fold2_threads", ctypes.c_int), ("fold2_lines", ctypes.c_int),
+                ("fwd_variant_storage", ctypes.c_int)]
 
 
 class SolveParams(ctypes.Structure):
@@ -107,6 +109,7 @@ def load(path: str = LIB_PATH):
         "dr_plan_set_variant": (i, [vp, i, i]),
         "dr_plan_autotune": (i, [vp, pd]),
         "dr_plan_set_fold_strip": (i, [vp, i, i]),
+        "dr_plan_set_fold_groups": (i, [vp, i, i, i]),
         "dr_plan_info": (i, [vp, ctypes.POINTER(PlanInfo)]),
         "dyn_radon_fwd": (i, [vp, vp, vp]),
         "dyn_radon_adj": (i, [vp, vp, vp, d]),
@@ -241,19 +244,24 @@ class Plan:
         _check(load().dr_plan_sync(self._h))
 
     def set_variant(self, fwd: int = AUTO, adj: int = AUTO):
-        """0 direct, 1 half-turn fold (Sec. 4), -1 automatic."""
+        """0 direct, 1 half-turn fold (Sec. 4), 2 (forward) fold in two kernels, -1 automatic."""
         _check(load().dr_plan_set_variant(self._h, int(fwd), int(adj)))
 
     def autotune(self):
-        """Time both projector variants; returns [fwd direct, fwd fold, adj direct, adj fold] ms."""
+        """Time the projector variants; returns [fwd direct, fwd fold, adj direct, adj fold,
+        fwd fold in two kernels] ms."""
         self.use_current_stream()
-        t = (ctypes.c_double * 4)()
+        t = (ctypes.c_double * 5)()
         _check(load().dr_plan_autotune(self._h, t))
         return list(t)
 
     def set_fold_strip(self, lines: int, async_copy: bool = False):
         """Fix the folded forward's strip height and staging (results do not change)."""
         _check(load().dr_plan_set_fold_strip(self._h, int(lines), int(bool(async_copy))))
+
+    def set_fold_groups(self, group: int, lines: int, threads: int = 256):
+        """Fix the two-kernel folded forward's coefficient group (4, 8), CTA size and strip height."""
+        _check(load().dr_plan_set_fold_groups(self._h, int(group), int(threads), int(lines)))
 
     def info(self) -> dict:
         inf = PlanInfo()

@@ -339,3 +339,71 @@ def test_hand_worked_2x2_example_on_gpu(prec, tol):
     dr.dyn_radon_fwd(plan, dev_tensor(img, prec), g)
     plan.sync()
     np.testing.assert_allclose(host_values(g)[0, 0], gold["expected"], rtol=0, atol=tol * 10)
+
+
+@pytest.mark.parametrize("case", sorted(c for c in CASES if CASES[c][8] >= 4))
+def test_fold2_variant_matches_oracle(case):
+    """The fold in two kernels (static transforms of coefficient groups, then
+    distribution) is the same operator as the direct form."""
+    args, u, _, P = _setup(case, seed=17)
+    u = u.astype(np.float32).astype(np.float64)
+    plan = _plan(args, dr.F32)
+    plan.set_variant(dr.FOLD2, dr.FOLD)
+    go = torch.zeros(plan.g_shape(), dtype=torch.float32, device="cuda")
+    dr.dyn_radon_fwd(plan, dev_tensor(u, dr.F32), go)
+    plan.sync()
+    assert rel(host_values(go), P.fwd(u)) <= 1e-5
+
+
+@pytest.mark.parametrize("case", ["narrow_det", "m12", "m16", "m32", "ragged"])
+def test_fold2_variant_bf16(case):
+    args, u, _, P = _setup(case, seed=19)
+    ub = to_bf16_f64(u)
+    plan = _plan(args, dr.BF16)
+    plan.set_variant(dr.FOLD2, dr.FOLD)
+    go = torch.zeros(plan.g_shape(), dtype=torch.bfloat16, device="cuda")
+    dr.dyn_radon_fwd(plan, dev_tensor(ub, dr.BF16), go)
+    plan.sync()
+    assert rel(host_values(go), to_bf16_f64(P.fwd(ub))) <= 1e-3
+
+
+def test_fold2_modes_match_fold():
+    """The residual (R u - g) and Chambolle-Pock dual epilogues of the
+    distribution kernel, through a short solve of each algorithm: the two
+    fold forms agree to FP32 rounding."""
+    args, _, g, P = _setup("narrow_det", seed=23)
+    g = g.astype(np.float32)
+    out = {}
+    for v in (dr.FOLD, dr.FOLD2):
+        for algo in (dr.ADMM_CG, dr.CHAMBOLLE_POCK):
+            plan = _plan(args, dr.F32)
+            plan.set_variant(v, dr.FOLD)
+            u = torch.zeros(plan.u_shape(), dtype=torch.float32, device="cuda")
+            prm = dr.solve_params(algo, iters=3, n_cg=3, lambda1=0.05, lambda2=1.0, rho=0.5, op_norm=40.0)
+            dr.admm_solve(plan, torch.from_numpy(g).cuda(), u, prm)
+            out[(v, algo)] = host_values(u)
+    for algo in (dr.ADMM_CG, dr.CHAMBOLLE_POCK):
+        assert rel(out[(dr.FOLD2, algo)], out[(dr.FOLD, algo)]) <= 1e-4
+
+
+@pytest.mark.parametrize("prec", [dr.F32, dr.BF16])
+def test_fold2_group_sizes_agree(prec):
+    """Every coefficient group size of the two-kernel forward computes the same
+    static transforms (each coefficient's ray sums run the same march): the
+    projections agree bit for bit."""
+    N, K = 40, 120
+    theta, t = synth.scan(K, 4.0)
+    rng = synth.rng_for(97)
+    u = rng.standard_normal((2, N, N, 8))
+    plan = dr.Plan(N, N, 2, N, theta, t, dr.LEGENDRE, 8, 4, prec)
+    plan.set_variant(dr.FOLD2, dr.FOLD)
+    ud = dev_tensor(u, prec)
+    outs = []
+    for group, threads in ((4, 256), (8, 256), (4, 512), (8, 512), (4, 1024), (8, 1024)):
+        plan.set_fold_groups(group, 2, threads)
+        g = torch.zeros(plan.g_shape(), dtype=getattr(torch, plan.storage_dtype), device="cuda")
+        dr.dyn_radon_fwd(plan, ud, g)
+        plan.sync()
+        outs.append(host_values(g))
+    for o in outs[1:]:
+        np.testing.assert_array_equal(o, outs[0])
