@@ -68,8 +68,11 @@ def parse():
     ap.add_argument("--variant", default=None,
                     help="force projector variants 'fwd,adj' (0 direct, 1 fold, 2 fold in two kernels: forward "
                          "only); default: autotuned")
+    ap.add_argument("--fold2-config", default=None,
+                    help="with --variant 2,x or --profile-small: fix the two-kernel folded forward's "
+                         "'group,threads,lines[,split[,async]]' instead of the default")
     ap.add_argument("--profile-small", action="store_true",
-                    help="run only a few operator launches of a 2-slice cut (for ncu captures)")
+                    help="run only one launch of each projector kernel on the workload (for ncu captures)")
     return ap.parse_args()
 
 
@@ -157,6 +160,13 @@ def replica_units(units_per_rank: float, world: int) -> float:
     return units_per_rank * world
 
 
+def set_fold2_config(plan, text):
+    """Apply 'group,threads,lines[,split[,async]]' to the two-kernel folded forward."""
+    v = [int(x) for x in text.split(",")]
+    plan.set_fold_groups(v[0], v[2], v[1])
+    plan.set_fold_march(v[3] if len(v) > 3 else 1, v[4] if len(v) > 4 else 0)
+
+
 def joseph_samples(theta, nx, ny, ns, distinct=True):
     """Number of Joseph interpolation samples of one static transform per
     slice: for every angle (distinct angles mod pi when `distinct`), bin and
@@ -231,6 +241,8 @@ def run_ours(a):
         plan.set_variant(fv, av)
         if a.fold_strip > 0:
             plan.set_fold_strip(a.fold_strip, False)
+        if fv == dr.FOLD2 and a.fold2_config:
+            set_fold2_config(plan, a.fold2_config)
 
     if a.profile_small:
         # one forward and one adjoint of each variant (direct, half-turn fold)
@@ -243,6 +255,11 @@ def run_ours(a):
                 plan.set_fold_strip(a.fold_strip, False)
             dr.dyn_radon_fwd(plan, uin, gout)
             dr.dyn_radon_adj(plan, g, u)
+        # the two-kernel folded forward (static transforms + distribution)
+        plan.set_variant(dr.FOLD2, dr.FOLD)
+        if a.fold2_config:
+            set_fold2_config(plan, a.fold2_config)
+        dr.dyn_radon_fwd(plan, uin, gout)
         # the folded forward on BF16 storage (bf16 strip)
         pb = dr.Plan(w.N, w.N, w.nz, w.ns, theta, t, w.basis, w.m, w.nt, dr.BF16)
         pb.set_variant(dr.FOLD, dr.FOLD)
@@ -430,8 +447,9 @@ def run_ours(a):
                          "launch_ms": launch_ms, "fwd_ms": fwd_ms, "adj_ms": adj_ms,
                          "variants": {"unique_angles": U, "fwd": info["fwd_variant"], "adj": info["adj_variant"],
                                       "fold_lines": info["fold_lines"], "fold_async": info["fold_async"],
-                                      "fold2_group_threads_lines": [info["fold2_group"], info["fold2_threads"],
-                                                                    info["fold2_lines"]],
+                                      "fold2_group_threads_lines_split_async": [
+                                          info["fold2_group"], info["fold2_threads"], info["fold2_lines"],
+                                          info["fold2_split"], info["fold2_async"]],
                                       "autotune_ms_fwd_direct_fold_adj_direct_fold_fwd_fold2": tune}},
             "cpu_baseline": cpu,
             "serving": serving,

@@ -171,6 +171,20 @@ dr_status dr_plan_set_fold_strip(dr_plan *plan, int lines, int async);
  */
 dr_status dr_plan_set_fold_groups(dr_plan *plan, int group, int threads, int lines);
 
+/*
+ * Fix how the two-kernel folded forward marches its rays.  nsplit (1..8):
+ * chunks of image lines per ray, nsplit times as many CTAs, each summing its
+ * chunk; the distribution kernel adds the chunks' partial sums in chunk order
+ * before the basis weights (Sec. 4 fold, Eq. 5 combine), so results change
+ * only by the rounding of those additions.  nsplit > 1 costs nsplit * nz * U
+ * * ns * ceil(m / 4) * 4 floats of device memory, allocated on the next
+ * forward (call that outside graph capture); slab-streamed solves use one
+ * chunk.  async (0/1): double-buffered strips, the next copied with cp.async
+ * while the current is marched (same arithmetic, results identical).
+ * DR_EINVAL if the variant is unavailable or an argument is out of range.
+ */
+dr_status dr_plan_set_fold_march(dr_plan *plan, int nsplit, int async);
+
 typedef struct {
     int unique_angles;   /* distinct theta mod pi (0: the fold is unavailable) */
     int max_group;       /* most projections sharing one theta mod pi */
@@ -183,6 +197,8 @@ typedef struct {
     int fold2_group;     /* two-kernel folded forward: coefficients per CTA (0: unavailable) */
     int fold2_threads;   /* two-kernel folded forward: threads per CTA */
     int fold2_lines;     /* two-kernel folded forward: strip lines */
+    int fold2_split;     /* two-kernel folded forward: line chunks of the march */
+    int fold2_async;     /* two-kernel folded forward: 1 if strips are double-buffered with cp.async */
     int fwd_variant_storage; /* forward variant of storage-typed calls (differs on BF16 plans) */
 } dr_plan_info_t;
 

@@ -171,6 +171,11 @@ struct dr_plan {
     bool fold2_ok = false;
     int fold2_gi = 0;                 // configuration in use
     int sel_fwd_st = 0;               // forward variant of storage-typed calls on BF16 plans (bf16 strips)
+    int fold2_split = 1;              // line chunks of the static march (partial sums added by the distribution)
+    int fold2_async = 0, fold2_async_st = 0;  // double-buffered cp.async strips (compute-typed / bf16 kernels)
+    bool split_off = false;           // set while a slab-streamed solve borrows the plan (its memory is budgeted)
+    void *d_ru_split = nullptr;       // partial sums of a split march (allocated on first use)
+    size_t ru_split_bytes = 0;
     int fold2_lines = 1, fold2_lines_st = 1;  // strip lines (compute-typed / bf16 kernels)
     void *d_gt = nullptr;             // folded data [nz][U][ns][MS] float (allocated on first use)
     size_t gt_bytes = 0;
@@ -267,6 +272,9 @@ dr_status launch_fwd_variant(dr_plan *P, int variant, bool calc, const void *u, 
 dr_status launch_adj_variant(dr_plan *P, int variant, bool calc, const void *g, void *u, double alpha,
                              double beta, bool u_calc, cudaStream_t st);
 dr_status ensure_fold_scratch(dr_plan *P);
+dr_status ensure_split_scratch(dr_plan *P, size_t bytes);
+// largest split scratch the autotuner may choose (small grids only need it)
+constexpr size_t kSplitScratchMax = 256ull << 20;
 dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch);
 
 }  // namespace dr

@@ -176,14 +176,16 @@ __host__ __device__ constexpr int fold_fwd_min_blocks(int M) { return M == 8 ? 3
 // ray to the projections of its angle.  STATIC = true: the CTA handles the
 // coefficient group j0 = (blockIdx.y % ngroups) * M .. j0 + M - 1 and writes
 // the scaled static transforms (R u_j)(theta0_a, s_b) to
-// ru[((z U + a) ns + b) ms_ru + j]; fold_dist_kernel distributes them.
+// ru[((z U + a) ns + b) ms_ru + j]; fold_dist_kernel distributes them.  With
+// nsplit > 1 the march is split into nsplit chunks of image lines
+// (blockIdx.z); chunk c writes its partial sums at ru + c * split_stride.
 template <typename S, typename T, int M, bool STATIC, int THREADS = kFoldThreads, int RPTS = 0>
 __global__ void __launch_bounds__(THREADS, THREADS == kFoldThreads ? fold_fwd_min_blocks(M) : 1)
     fold_fwd_kernel(const S *__restrict__ u, S *__restrict__ out, const S *__restrict__ gm,
                     const FwdProj *__restrict__ uproj, const int *__restrict__ start, const int *__restrict__ member,
                     const T *__restrict__ phip, const int *__restrict__ blocks, int nx, int ny, int ns, int K,
                     int m, int MP, int P, int R, int nchunk, int mode, T sigma, int async_stage, int ngroups,
-                    T *__restrict__ ru, int U, int ms_ru) {
+                    T *__restrict__ ru, int U, int ms_ru, int nsplit, size_t split_stride) {
     // strip element: stored bf16 for bf16 storage, else the compute type
     constexpr bool BF16_STRIP = sizeof(S) == 2;
     using ST = std::conditional_t<BF16_STRIP, S, T>;
@@ -206,6 +208,9 @@ __global__ void __launch_bounds__(THREADS, THREADS == kFoldThreads ? fold_fwd_mi
     const int W = branch ? ny : nx;
     const int H = branch ? nx : ny;
     const int wpad = W + 2 * kFwdGuard;
+    // image lines of this CTA's march: all, or chunk blockIdx.z of nsplit
+    const int L0 = STATIC ? (int)(((long long)blockIdx.z * H) / nsplit) : 0;
+    const int L1 = STATIC ? (int)(((long long)(blockIdx.z + 1) * H) / nsplit) : H;
 
     for (int p = tid; p < P; p += THREADS) {
         const int a = blk[p];
@@ -248,6 +253,8 @@ __global__ void __launch_bounds__(THREADS, THREADS == kFoldThreads ? fold_fwd_mi
                     lo[q] = max(0, (int)floorf(rmin) - 1);
                     hi[q] = min(H - 1, (int)ceilf(rmax) + 1);
                 }
+                lo[q] = max(lo[q], L0);
+                hi[q] = min(hi[q], L1 - 1);
             }
         }
     }
@@ -276,18 +283,18 @@ __global__ void __launch_bounds__(THREADS, THREADS == kFoldThreads ? fold_fwd_mi
         }
     };
     const size_t buf_elems = (size_t)R * wpad * MS;  // buffer b starts at strip + b * buf_elems
-    if (async_stage) {
-        stage(strip, 0, min(R, H));
+    if (async_stage && L0 < L1) {
+        stage(strip, L0, min(R, L1 - L0));
         cp_async_commit();
     }
     int s_idx = 0;
-    for (int r0 = 0; r0 < H; r0 += R, ++s_idx) {
-        const int nl = min(R, H - r0);
+    for (int r0 = L0; r0 < L1; r0 += R, ++s_idx) {
+        const int nl = min(R, L1 - r0);
         ST *cur;
         if (async_stage) {
             // prefetch the next strip into the other buffer, then wait for this one
-            if (r0 + R < H) {
-                stage(strip + ((s_idx + 1) & 1) * buf_elems, r0 + R, min(R, H - r0 - R));
+            if (r0 + R < L1) {
+                stage(strip + ((s_idx + 1) & 1) * buf_elems, r0 + R, min(R, L1 - r0 - R));
                 cp_async_commit();
                 cp_async_wait<1>();
             } else {
@@ -344,7 +351,7 @@ __global__ void __launch_bounds__(THREADS, THREADS == kFoldThreads ? fold_fwd_mi
             const int a = blk[p];
             if (a < 0) continue;
             const T sc = scale_s[p];
-            T *dst = ru + (((size_t)z * U + a) * ns + b) * ms_ru + j0;
+            T *dst = ru + blockIdx.z * split_stride + (((size_t)z * U + a) * ns + b) * ms_ru + j0;
 #pragma unroll
             for (int j = 0; j < M; ++j)
                 if (j < count) dst[j] = sc * acc[q][j];
@@ -387,13 +394,14 @@ __global__ void __launch_bounds__(THREADS, THREADS == kFoldThreads ? fold_fwd_mi
 // ===========================================================================
 // Forward, two-kernel form, step 2: distribute the static transforms
 //   g[z][k][b] = sum_j phi_j(t_k) ru[z][a(k)][flip_k(b)][j]
-// with the forward epilogue modes (store, minus gm, CP dual update).
+// with the forward epilogue modes (store, minus gm, CP dual update).  Line
+// chunks of a split march are added first, in chunk order.
 // ===========================================================================
 template <typename S, typename T, int M>
 __global__ void __launch_bounds__(kRedThreads)
     fold_dist_kernel(const T *__restrict__ ru, S *__restrict__ out, const S *__restrict__ gm,
                      const int *__restrict__ of_k, const T *__restrict__ phip, int nz, int K, int ns, int U, int ms_ru,
-                     int m, int MP, int mode, T sigma) {
+                     int m, int MP, int mode, T sigma, int nsplit, size_t split_stride) {
     const size_t n = (size_t)nz * K * ns;
     for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
         const int b = (int)(o % ns);
@@ -407,7 +415,11 @@ __global__ void __launch_bounds__(kRedThreads)
         T val = T(0);
 #pragma unroll
         for (int j = 0; j < M; ++j)
-            if (j < m) val = fma(__ldg(ph + j), r[j], val);
+            if (j < m) {
+                T rj = r[j];
+                for (int c = 1; c < nsplit; ++c) rj += r[c * split_stride + j];
+                val = fma(__ldg(ph + j), rj, val);
+            }
         if (mode == 0) {
             stc<T>(out + o, val);
         } else if (mode == 1) {
@@ -647,7 +659,7 @@ dr_status fold_fwd_launch_t(dr_plan *P, const void *u, void *out, const void *gm
     kern<<<grid, kFoldThreads, smem, st>>>((const S *)u, (S *)out, (const S *)gm, P->d_fold_fwd, P->d_fold_start,
                                            P->d_fold_member, (const T *)P->d_PhiP, P->d_fold_blocks, P->nx, P->ny,
                                            P->ns, P->K, P->m, P->MP, P->fold_P, R, P->fold_nchunk, mode,
-                                           (T)sigma, async_stage, 1, (T *)nullptr, 0, 0);
+                                           (T)sigma, async_stage, 1, (T *)nullptr, 0, 0, 1, (size_t)0);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? DR_OK : cuda_fail(e, "fold_fwd_kernel launch");
 }
@@ -668,30 +680,47 @@ dr_status fold_fwd2_launch_mc(dr_plan *P, const void *u, void *out, const void *
     const bool bf16_kernel = sizeof(S) == 2;
     const int R = std::max(1, std::min(bf16_kernel ? P->fold2_lines_st : P->fold2_lines, P->fold2_R[gi]));
     if ((size_t)P->nz * ngroups > 65535) return fail(DR_EINVAL, "two-kernel folded forward: too many slice groups");
-    // whole 16-byte vectors in every group: cp.async staging would be possible, but the
-    // two-kernel form stages through registers (one buffer)
+    // async: two strip buffers, the next strip copied with cp.async while the
+    // current one is marched (groups of whole 16-byte vectors; other pixels
+    // are staged through registers)
     (void)VW;
-    const size_t smem = 768 + sizeof(ST) * (size_t)R * wpad * MS;
+    const int async = bf16_kernel ? P->fold2_async_st : P->fold2_async;
+    const size_t smem = 768 + sizeof(ST) * (size_t)(async ? 2 : 1) * R * wpad * MS;
     auto kern = fold_fwd_kernel<S, T, MC, true, THREADS, RPT>;
     {
         dr_status s = allow_dynamic_smem((const void *)kern, smem);
         if (s != DR_OK) return s;
     }
-    {
+    // one march: static transforms into the folded-data scratch (row stride
+    // fold_ms(M)); a march split into line chunks: partial sums into the
+    // split scratch (row stride m rounded up to 4), one chunk after another
+    const int nsplit = P->split_off ? 1 : std::max(1, P->fold2_split);
+    T *ru;
+    int ms_ru;
+    size_t split_stride = 0;
+    if (nsplit == 1) {
         dr_status s = ensure_fold_scratch(P);
         if (s != DR_OK) return s;
+        ru = (T *)P->d_gt;
+        ms_ru = fold_ms(M);
+    } else {
+        ms_ru = (P->m + 3) / 4 * 4;
+        split_stride = (size_t)P->nz * P->fold_U * P->ns * ms_ru;
+        dr_status s = ensure_split_scratch(P, sizeof(T) * split_stride * nsplit);
+        if (s != DR_OK) return s;
+        ru = (T *)P->d_ru_split;
     }
-    constexpr int MSR = fold_ms(M);  // row stride of the folded-data scratch
-    dim3 grid(P->fold2_nblocks[gi] * P->fold2_nchunk[gi], P->nz * ngroups);
+    dim3 grid(P->fold2_nblocks[gi] * P->fold2_nchunk[gi], P->nz * ngroups, nsplit);
     kern<<<grid, THREADS, smem, st>>>((const S *)u, (S *)out, (const S *)gm, P->d_fold_fwd, P->d_fold_start,
                                            P->d_fold_member, (const T *)P->d_PhiP, P->d_fold2_blocks[gi], P->nx,
                                            P->ny, P->ns, P->K, P->m, P->MP, P->fold2_P[gi], R, P->fold2_nchunk[gi],
-                                           mode, (T)sigma, 0, ngroups, (T *)P->d_gt, P->fold_U, MSR);
+                                           mode, (T)sigma, async, ngroups, ru, P->fold_U, ms_ru, nsplit,
+                                           split_stride);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "fold_fwd_kernel (static) launch");
     fold_dist_kernel<S, T, M><<<red_grid((size_t)P->nz * P->K * P->ns), kRedThreads, 0, st>>>(
-        (const T *)P->d_gt, (S *)out, (const S *)gm, P->d_fold_of_k, (const T *)P->d_PhiP, P->nz, P->K, P->ns,
-        P->fold_U, MSR, P->m, P->MP, mode, (T)sigma);
+        ru, (S *)out, (const S *)gm, P->d_fold_of_k, (const T *)P->d_PhiP, P->nz, P->K, P->ns, P->fold_U, ms_ru,
+        P->m, P->MP, mode, (T)sigma, nsplit, split_stride);
     e = cudaGetLastError();
     return e == cudaSuccess ? DR_OK : cuda_fail(e, "fold_dist_kernel launch");
 }

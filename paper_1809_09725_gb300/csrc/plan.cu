@@ -582,7 +582,7 @@ dr_status dr_plan_destroy(dr_plan *P) {
                     P->d_scal,       P->d_status,    P->d_fold_fwd,   P->d_fold_adj,    P->d_fold_start,
                     P->d_fold_member, P->d_fold_blocks, P->d_gt, P->d_fbp_taps, P->d_fbp_phi, P->d_fbp_q,
                     P->d_fbp_u, P->d_fold_of_k, P->d_fold2_blocks[0], P->d_fold2_blocks[1],
-                    P->d_fold2_blocks[2], P->d_fold2_blocks[3], P->d_fold2_blocks[4], P->d_fold2_blocks[5]};
+                    P->d_fold2_blocks[2], P->d_fold2_blocks[3], P->d_fold2_blocks[4], P->d_fold2_blocks[5], P->d_ru_split};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (P->graph_stream) cudaStreamDestroy(P->graph_stream);
@@ -599,7 +599,7 @@ dr_status dr_plan_set_stream(dr_plan *P, void *s) {
 }
 
 size_t dr_plan_device_bytes(const dr_plan *P) {
-    return P ? P->table_bytes + P->ws.bytes + (P->d_gt ? P->gt_bytes : 0) + P->fbp_bytes : 0;
+    return P ? P->table_bytes + P->ws.bytes + (P->d_gt ? P->gt_bytes : 0) + P->fbp_bytes + P->ru_split_bytes : 0;
 }
 
 dr_status dr_plan_sync(dr_plan *P) {

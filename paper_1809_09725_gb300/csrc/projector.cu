@@ -23,6 +23,23 @@ dr_status ensure_fold_scratch(dr_plan *P) {
     return DR_OK;
 }
 
+dr_status ensure_split_scratch(dr_plan *P, size_t bytes) {
+    if (P->d_ru_split && P->ru_split_bytes >= bytes) return DR_OK;
+    if (P->d_ru_split) {
+        cudaError_t e = cudaFree(P->d_ru_split);
+        P->d_ru_split = nullptr;
+        P->ru_split_bytes = 0;
+        if (e != cudaSuccess) return cuda_fail(e, "split scratch release");
+    }
+    cudaError_t e = cudaMalloc(&P->d_ru_split, bytes);
+    if (e != cudaSuccess) {
+        P->d_ru_split = nullptr;
+        return cuda_fail(e, "split scratch allocation");
+    }
+    P->ru_split_bytes = bytes;
+    return DR_OK;
+}
+
 // variant 0: direct (every projection at its own angle); 1: half-turn fold.
 // calc: buffers are compute typed (float for F32/BF16 plans, double for F64).
 dr_status launch_fwd_variant(dr_plan *P, int variant, bool calc, const void *u, void *out, const void *gm,
@@ -109,7 +126,8 @@ struct TuneKey {
     }
 };
 struct TuneVal {
-    int fwd, adj, lines, async, lines_st, async_st, f2_gi, f2_lines, f2_lines_st, fwd_st;
+    int fwd, adj, lines, async, lines_st, async_st, f2_gi, f2_lines, f2_lines_st, fwd_st, f2_split, f2_async,
+        f2_async_st;
     double ms[5];
 };
 static std::mutex g_tune_mutex;
@@ -146,6 +164,9 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
             P->fold2_lines = it->second.f2_lines;
             P->fold2_lines_st = it->second.f2_lines_st;
             P->sel_fwd_st = it->second.fwd_st;
+            P->fold2_split = P->split_off ? 1 : it->second.f2_split;
+            P->fold2_async = it->second.f2_async;
+            P->fold2_async_st = it->second.f2_async_st;
             for (int i = 0; i < 5; ++i) P->tune_ms[i] = it->second.ms[i];
             P->tuned = true;
             return DR_OK;
@@ -229,46 +250,88 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
         }
     }
     if (P->fold2_ok) {
-        // two-kernel folded forward: coefficient group size and strip height
-        // (the grouping changes only which CTA computes a coefficient's ray sums:
-        // results do not depend on the choice)
+        // two-kernel folded forward: coefficient group and CTA size, strip
+        // height, staging mode, line chunks.  Group, CTA size, strip height and
+        // staging change only which CTA computes a ray sum and when its lines
+        // are copied: results do not depend on them.
         const int lines_c[] = {1, 2, 3, 4, 6, 8, 12, 16};
         int bgi = P->fold2_gi, bl = P->fold2_lines;
+        // strip heights of the current configuration; true if one beat `best`
+        auto sweep_lines = [&](int gi, bool calc, double &best, int &best_lines, bool &better) -> dr_status {
+            better = false;
+            for (int c : lines_c) {
+                if (c > P->fold2_R[gi]) continue;
+                if (calc) P->fold2_lines = c;
+                else P->fold2_lines_st = c;
+                double t = 1e30;
+                dr_status s = time_fwd(2, t, calc);
+                if (s != DR_OK) return s;
+                if (t < best) {
+                    best = t;
+                    best_lines = c;
+                    better = true;
+                }
+            }
+            return DR_OK;
+        };
+        bool better = false;
+        P->fold2_split = 1;
+        P->fold2_async = 0;
         for (int gi = 0; gi < 6; ++gi) {
             const int MC = (gi & 1) ? 8 : 4;
             if (P->fold2_R[gi] < 1 || (MC == 8 && P->m <= 4) || (size_t)P->nz * ((P->m + MC - 1) / MC) > 65535)
                 continue;
-            for (int c : lines_c) {
-                if (c > P->fold2_R[gi]) continue;
-                P->fold2_gi = gi;
-                P->fold2_lines = c;
-                double t = 1e30;
-                dr_status s = time_fwd(2, t);
-                if (s != DR_OK) return s;
-                if (t < ms[4]) {
-                    ms[4] = t;
-                    bgi = gi;
-                    bl = c;
-                }
-            }
+            P->fold2_gi = gi;
+            dr_status s = sweep_lines(gi, true, ms[4], bl, better);
+            if (s != DR_OK) return s;
+            if (better) bgi = gi;
         }
         P->fold2_gi = bgi;
-        P->fold2_lines = bl;
-        P->fold2_lines_st = bl;
-        if (P->prec == DR_BF16_F32ACC) {
-            double best_t = 1e30;
-            for (int c : lines_c) {
-                if (c > P->fold2_R[bgi]) continue;
-                P->fold2_lines_st = c;
-                double t = 1e30;
-                dr_status s = time_fwd(2, t, false);
+        // double-buffered cp.async strips
+        {
+            P->fold2_async = 1;
+            int l2 = bl;
+            dr_status s = sweep_lines(bgi, true, ms[4], l2, better);
+            if (s != DR_OK) return s;
+            if (better) bl = l2;
+            else P->fold2_async = 0;
+        }
+        // small grids leave SMs idle in the last wave: try splitting the march
+        // into line chunks (more CTAs; the distribution adds the partial sums)
+        if (!P->split_off) {
+            const size_t chunk = sizeof(float) * (size_t)P->nz * P->fold_U * P->ns * ((P->m + 3) / 4 * 4);
+            int bs = 1;
+            for (int ns2 = 2; ns2 <= 4 && chunk * ns2 <= kSplitScratchMax; ++ns2) {
+                P->fold2_split = ns2;
+                int l2 = bl;
+                dr_status s = sweep_lines(bgi, true, ms[4], l2, better);
                 if (s != DR_OK) return s;
-                if (t < best_t) {
-                    best_t = t;
-                    bl = c;
+                if (better) {
+                    bs = ns2;
+                    bl = l2;
                 }
             }
-            P->fold2_lines_st = bl;
+            P->fold2_split = bs;
+            if (bs == 1 && P->d_ru_split) {
+                cudaFree(P->d_ru_split);
+                P->d_ru_split = nullptr;
+                P->ru_split_bytes = 0;
+            }
+        }
+        P->fold2_lines = bl;
+        P->fold2_lines_st = bl;
+        P->fold2_async_st = P->fold2_async;
+        if (P->prec == DR_BF16_F32ACC) {
+            double best_t = 1e30;
+            int bls = bl, bas = 0;
+            for (int as = 0; as < 2; ++as) {
+                P->fold2_async_st = as;
+                dr_status s = sweep_lines(bgi, false, best_t, bls, better);
+                if (s != DR_OK) return s;
+                if (better) bas = as;
+            }
+            P->fold2_lines_st = bls;
+            P->fold2_async_st = bas;
             ms_st2 = best_t;
         }
     }
@@ -310,7 +373,8 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
     std::lock_guard<std::mutex> lk(g_tune_mutex);
     auto ins = g_tune_cache.emplace(key, TuneVal{P->sel_fwd, P->sel_adj, P->fold_lines, P->fold_async,
                                                  P->fold_lines_st, P->fold_async_st, P->fold2_gi, P->fold2_lines,
-                                                 P->fold2_lines_st, P->sel_fwd_st, {0, 0, 0, 0, 0}});
+                                                 P->fold2_lines_st, P->sel_fwd_st, P->fold2_split,
+                                                 P->fold2_async, P->fold2_async_st, {0, 0, 0, 0, 0}});
     if (ins.second) {
         for (int i = 0; i < 5; ++i) ins.first->second.ms[i] = P->tune_ms[i];
     } else {  // another thread tuned the same problem first: follow its choice
@@ -324,6 +388,9 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
         P->fold2_lines = ins.first->second.f2_lines;
         P->fold2_lines_st = ins.first->second.f2_lines_st;
         P->sel_fwd_st = ins.first->second.fwd_st;
+        P->fold2_split = P->split_off ? 1 : ins.first->second.f2_split;
+        P->fold2_async = ins.first->second.f2_async;
+        P->fold2_async_st = ins.first->second.f2_async_st;
     }
     return DR_OK;
 }
@@ -413,6 +480,17 @@ dr_status dr_plan_set_fold_groups(dr_plan *P, int group, int threads, int lines)
     return DR_OK;
 }
 
+dr_status dr_plan_set_fold_march(dr_plan *P, int nsplit, int async) {
+    clear_error();
+    if (!P) return fail(DR_EINVAL, "dr_plan_set_fold_march: NULL plan");
+    if (!(P->fold_U > 0 && P->fold2_ok)) return fail(DR_EINVAL, "dr_plan_set_fold_march: variant unavailable");
+    if (nsplit < 1 || nsplit > 8 || async < 0 || async > 1)
+        return fail(DR_EINVAL, "dr_plan_set_fold_march: nsplit must be 1..8 and async 0 or 1");
+    P->fold2_split = nsplit;
+    P->fold2_async = P->fold2_async_st = async;
+    return DR_OK;
+}
+
 dr_status dr_plan_info(const dr_plan *P, dr_plan_info_t *info) {
     clear_error();
     if (!P || !info) return fail(DR_EINVAL, "dr_plan_info: NULL argument");
@@ -421,12 +499,15 @@ dr_status dr_plan_info(const dr_plan *P, dr_plan_info_t *info) {
     info->fwd_variant = P->var_fwd >= 0 ? P->var_fwd : P->sel_fwd;
     info->adj_variant = P->var_adj >= 0 ? P->var_adj : P->sel_adj;
     info->tuned = P->tuned ? 1 : 0;
-    info->device_bytes = P->table_bytes + P->ws.bytes + (P->d_gt ? P->gt_bytes : 0) + P->fbp_bytes;
+    info->device_bytes = P->table_bytes + P->ws.bytes + (P->d_gt ? P->gt_bytes : 0) + P->fbp_bytes +
+                         P->ru_split_bytes;
     info->fold_lines = P->fold_lines;
     info->fold_async = P->fold_async;
     info->fold2_group = P->fold2_ok ? ((P->fold2_gi & 1) ? 8 : 4) : 0;
     info->fold2_threads = P->fold2_ok ? (256 << (P->fold2_gi / 2)) : 0;
     info->fold2_lines = P->fold2_ok ? P->fold2_lines : 0;
+    info->fold2_split = P->fold2_ok ? P->fold2_split : 0;
+    info->fold2_async = P->fold2_ok ? P->fold2_async : 0;
     info->fwd_variant_storage = P->var_fwd >= 0 ? P->var_fwd : P->sel_fwd_st;
     return DR_OK;
 }

@@ -118,6 +118,8 @@ static size_t job_bytes(const dr_job_desc &d) {
     if (d.prec != DR_F64) {
         const int MS = M <= 4 ? 4 : ((M % 8 == 0) ? M + 4 : M);
         b += sizeof(float) * ng * MS;  // folded data (at most one distinct angle per projection)
+        // partial sums of a split two-kernel forward (the autotuner keeps them under a cap)
+        b += std::min<size_t>(kSplitScratchMax, 4 * sizeof(float) * ng * ((d.m + 3) / 4 * 4));
     }
     const dr_algo algo = d.params.algo;
     if (algo == DR_ADMM_CG) b += 3 * nu * cs + ng * cs + 2 * nf * cs;

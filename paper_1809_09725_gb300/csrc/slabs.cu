@@ -221,8 +221,9 @@ struct PlanScope {
     dr_plan *P;
     int nz;
     void *gt;
-    explicit PlanScope(dr_plan *p) : P(p), nz(p->nz), gt(p->d_gt) {}
+    explicit PlanScope(dr_plan *p) : P(p), nz(p->nz), gt(p->d_gt) { P->split_off = true; }
     ~PlanScope() {
+        P->split_off = false;
         P->nz = nz;
         P->z_open_lo = P->z_open_hi = 0;
         P->d_gt = gt;
