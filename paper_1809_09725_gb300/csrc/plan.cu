@@ -575,7 +575,10 @@ dr_status dr_plan_create(dr_plan **out, int nx, int ny, int nz, int ns, int K, c
 
 dr_status dr_plan_destroy(dr_plan *P) {
     if (!P) return DR_OK;
-    if (P->stream || P->graph_stream) cudaDeviceSynchronize();
+    // the plan's own streams only: a device-wide synchronisation would also
+    // touch (and could invalidate) graph captures of other threads' plans
+    cudaStreamSynchronize(P->stream);  // the caller's stream (0: the legacy stream)
+    if (P->graph_stream) cudaStreamSynchronize(P->graph_stream);
     free_workspace(P);
     void *ptrs[] = {P->d_fwd,        P->d_adj,       P->d_PhiP,       P->d_fwd_blocks,  P->d_PhiF,
                     P->d_dPhiF,      P->d_G,         P->d_Lt,         P->d_partials,    P->d_counters,

@@ -562,21 +562,30 @@ static dr_status solve_end(dr_plan *P, SolveCtx &c) {
 }
 
 // Capture `body` (launches on per-job streams) as one graph on stream `root`.
+// A device-wide call from another thread (a plan or buffer freed by another
+// job) can invalidate a capture in progress; the capture is then repeated, a
+// bounded number of times (the iteration bodies keep all state in device
+// memory, so a discarded capture leaves nothing behind).
 template <typename F>
 static dr_status capture_graph(cudaStream_t root, F body, cudaGraphExec_t *exec) {
-    cudaGraph_t graph = nullptr;
-    DR_CUDA_TRY(cudaStreamBeginCapture(root, cudaStreamCaptureModeThreadLocal));
-    dr_status st = body();
-    cudaError_t ce = cudaStreamEndCapture(root, &graph);
-    if (st != DR_OK) {
+    dr_status last = DR_OK;
+    for (int attempt = 0; attempt < 4; ++attempt) {
+        cudaGraph_t graph = nullptr;
+        DR_CUDA_TRY(cudaStreamBeginCapture(root, cudaStreamCaptureModeThreadLocal));
+        const dr_status st = body();
+        cudaError_t ce = cudaStreamEndCapture(root, &graph);
+        if (st == DR_OK && ce == cudaSuccess) {
+            ce = cudaGraphInstantiate(exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ce != cudaSuccess) return cuda_fail(ce, "graph instantiate");
+            return DR_OK;
+        }
         if (graph) cudaGraphDestroy(graph);
-        return st;
+        cudaGetLastError();  // capture errors are not sticky
+        last = st != DR_OK ? st : cuda_fail(ce, "graph capture");
+        if (ce != cudaErrorStreamCaptureInvalidated) break;
     }
-    if (ce != cudaSuccess) return cuda_fail(ce, "graph capture");
-    ce = cudaGraphInstantiate(exec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (ce != cudaSuccess) return cuda_fail(ce, "graph instantiate");
-    return DR_OK;
+    return last;
 }
 
 static dr_status solve(dr_plan *P, const void *g_in, void *u_io, const dr_solve_params &prm) {
@@ -588,11 +597,16 @@ static dr_status solve(dr_plan *P, const void *g_in, void *u_io, const dr_solve_
         TRY(solve_iter(P, c, st));
         if (prm.iters > 1) {
             cudaGraphExec_t exec = nullptr;
-            TRY(capture_graph(st, [&]() { return solve_iter(P, c, st); }, &exec));
-            cudaError_t ce = cudaSuccess;
-            for (int it = 1; it < prm.iters && ce == cudaSuccess; ++it) ce = cudaGraphLaunch(exec, st);
-            cudaGraphExecDestroy(exec);
-            if (ce != cudaSuccess) return cuda_fail(ce, "admm_solve: graph launch");
+            if (capture_graph(st, [&]() { return solve_iter(P, c, st); }, &exec) == DR_OK) {
+                cudaError_t ce = cudaSuccess;
+                for (int it = 1; it < prm.iters && ce == cudaSuccess; ++it) ce = cudaGraphLaunch(exec, st);
+                cudaGraphExecDestroy(exec);
+                if (ce != cudaSuccess) return cuda_fail(ce, "admm_solve: graph launch");
+            } else {
+                // no graph: the same launches, issued one iteration at a time
+                clear_error();
+                for (int it = 1; it < prm.iters; ++it) TRY(solve_iter(P, c, st));
+            }
         }
     }
     return solve_end(P, c);
@@ -646,7 +660,20 @@ static dr_status solve_batch(int n, dr_plan *const *plans, const void *const *g,
                 return DR_OK;
             },
             &exec);
-        if (result != DR_OK) break;
+        if (result != DR_OK) {
+            // no graph: the same launches, one iteration at a time on each job's stream
+            // (the root stream joins them afterwards)
+            clear_error();
+            result = DR_OK;
+            for (int r = 0; r < reps && result == DR_OK; ++r)
+                for (int j : act) {
+                    result = solve_iter(plans[j], c[j], plans[j]->graph_stream);
+                    if (result != DR_OK) break;
+                }
+            if (result != DR_OK) break;
+            for (int j : act) c[j].done += reps;
+            continue;
+        }
         cudaError_t ce = cudaSuccess;
         for (int r = 0; r < reps && ce == cudaSuccess; ++r) ce = cudaGraphLaunch(exec, root);
         cudaGraphExecDestroy(exec);
