@@ -185,6 +185,16 @@ dr_status dr_plan_set_fold_groups(dr_plan *plan, int group, int threads, int lin
  */
 dr_status dr_plan_set_fold_march(dr_plan *plan, int nsplit, int async);
 
+/*
+ * Fix the folded adjoint's distinct angles per pipeline stage (1..32; the
+ * autotuner picks among 8, 7 and 6).  Each stage's folded-data windows share
+ * a CTA's shared memory, so fewer angles per stage fit more CTAs on an SM.
+ * The angles are summed in the same order whatever the choice: results are
+ * identical.  DR_EINVAL if the plan has no folded adjoint or angles is out of
+ * range.
+ */
+dr_status dr_plan_set_fold_adj_stage(dr_plan *plan, int angles);
+
 typedef struct {
     int unique_angles;   /* distinct theta mod pi (0: the fold is unavailable) */
     int max_group;       /* most projections sharing one theta mod pi */
@@ -199,6 +209,7 @@ typedef struct {
     int fold2_lines;     /* two-kernel folded forward: strip lines */
     int fold2_split;     /* two-kernel folded forward: line chunks of the march */
     int fold2_async;     /* two-kernel folded forward: 1 if strips are double-buffered with cp.async */
+    int fold_adj_angles; /* folded adjoint: distinct angles per pipeline stage */
     int fwd_variant_storage; /* forward variant of storage-typed calls (differs on BF16 plans) */
 } dr_plan_info_t;
 

@@ -173,6 +173,7 @@ struct dr_plan {
     int sel_fwd_st = 0;               // forward variant of storage-typed calls on BF16 plans (bf16 strips)
     int fold2_split = 1;              // line chunks of the static march (partial sums added by the distribution)
     int fold2_async = 0, fold2_async_st = 0;  // double-buffered cp.async strips (compute-typed / bf16 kernels)
+    int fold_adj_pp = 8;              // folded adjoint: distinct angles per pipeline stage
     bool split_off = false;           // set while a slab-streamed solve borrows the plan (its memory is budgeted)
     void *d_ru_split = nullptr;       // partial sums of a split march (allocated on first use)
     size_t ru_split_bytes = 0;

@@ -27,7 +27,7 @@
 namespace dr {
 
 constexpr int kFoldThreads = 256;
-constexpr int kFoldAdjP = 8;       // unique angles per adjoint pipeline stage
+constexpr int kFoldAdjP = 8;       // unique angles per adjoint pipeline stage (default; at most 32)
 constexpr int kFoldAdjStages = 2;
 
 // Padded coefficient stride in shared memory and in the folded data:
@@ -493,11 +493,10 @@ template <typename S, typename T, int M>
 __global__ void __launch_bounds__(kAdjThreads)
     fold_adj_kernel(const __grid_constant__ CUtensorMap tm_gt, const AdjProj *__restrict__ uproj,
                     S *__restrict__ u_s, T *__restrict__ u_c, int nx, int ny, int U, int m, int Wb, T alpha, T beta,
-                    int *status) {
+                    int *status, int PP) {
     constexpr int VPT = FoldAdjShape<M>::VPT;
     constexpr int TX = FoldAdjShape<M>::TX;
     constexpr int TY = kAdjTY;
-    constexpr int PP = kFoldAdjP;
     constexpr int NST = kFoldAdjStages;
     constexpr int MS = fold_ms(M);
     constexpr float kMag = 12582912.0f;
@@ -766,8 +765,11 @@ dr_status fold_adj_launch_t(dr_plan *P, const void *g, void *u, double alpha, do
     const uint32_t box[3] = {(uint32_t)MS, (uint32_t)Wb, 1};
     if (!encode_tensor_map(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, P->d_gt, dims, strides, box))
         return fail(DR_ECUDA, "fold adj: tensor map encode failed");
+    // angles per pipeline stage: fewer shrink the windows' shared memory so that
+    // more CTAs fit on an SM (the angles are summed in the same order)
+    const int pp = std::max(1, std::min(32, P->fold_adj_pp));
     const size_t row_bytes = ((size_t)Wb * MS * sizeof(T) + 127) & ~(size_t)127;
-    const size_t stage = kFoldAdjP * row_bytes + 128 * ((kFoldAdjP * sizeof(FoldPrm) + 127) / 128);
+    const size_t stage = pp * row_bytes + 128 * ((pp * sizeof(FoldPrm) + 127) / 128);
     const size_t smem = stage * kFoldAdjStages + 128;
     auto kern = fold_adj_kernel<S, T, M>;
     {
@@ -778,7 +780,7 @@ dr_status fold_adj_launch_t(dr_plan *P, const void *g, void *u, double alpha, do
     const int ntx = (P->nx + TX - 1) / TX, nty = (P->ny + kAdjTY - 1) / kAdjTY;
     dim3 grid(ntx * nty, P->nz);
     kern<<<grid, kAdjThreads, smem, st>>>(tm, P->d_fold_adj, u_calc ? nullptr : (S *)u, u_calc ? (T *)u : nullptr,
-                                          P->nx, P->ny, P->fold_U, P->m, Wb, (T)alpha, (T)beta, P->d_status);
+                                          P->nx, P->ny, P->fold_U, P->m, Wb, (T)alpha, (T)beta, P->d_status, pp);
     e = cudaGetLastError();
     return e == cudaSuccess ? DR_OK : cuda_fail(e, "fold_adj_kernel launch");
 }

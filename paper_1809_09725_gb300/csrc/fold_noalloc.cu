@@ -66,8 +66,9 @@ static dr_status noalloc_adj_t(dr_plan *P, const void *g, void *u, double beta, 
     const uint32_t box[3] = {(uint32_t)MS, (uint32_t)Wb, 1};
     if (!encode_tensor_map(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, scratch, dims, strides, box))
         return fail(DR_ECUDA, "dyn_radon_adj_noalloc: tensor map encode failed");
+    const int pp = std::max(1, std::min(32, P->fold_adj_pp));
     const size_t row_bytes = ((size_t)Wb * MS * sizeof(T) + 127) & ~(size_t)127;
-    const size_t stage = kFoldAdjP * row_bytes + 128 * ((kFoldAdjP * sizeof(FoldPrm) + 127) / 128);
+    const size_t stage = pp * row_bytes + 128 * ((pp * sizeof(FoldPrm) + 127) / 128);
     const size_t smem = stage * kFoldAdjStages + 128;
     auto kern = fold_adj_kernel<S, T, M>;
     {
@@ -78,7 +79,7 @@ static dr_status noalloc_adj_t(dr_plan *P, const void *g, void *u, double beta, 
     const int ntx = (P->nx + TX - 1) / TX, nty = (P->ny + kAdjTY - 1) / kAdjTY;
     dim3 grid(ntx * nty, P->nz);
     kern<<<grid, kAdjThreads, smem, st>>>(tm, P->d_fold_adj, (S *)u, nullptr, P->nx, P->ny, P->fold_U, P->m, Wb,
-                                          1.0f, (float)beta, P->d_status);
+                                          1.0f, (float)beta, P->d_status, pp);
     e = cudaGetLastError();
     return e == cudaSuccess ? DR_OK : cuda_fail(e, "dyn_radon_adj_noalloc: fold_adj_kernel launch");
 }

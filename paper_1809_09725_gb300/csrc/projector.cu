@@ -127,7 +127,7 @@ struct TuneKey {
 };
 struct TuneVal {
     int fwd, adj, lines, async, lines_st, async_st, f2_gi, f2_lines, f2_lines_st, fwd_st, f2_split, f2_async,
-        f2_async_st;
+        f2_async_st, adj_pp;
     double ms[5];
 };
 static std::mutex g_tune_mutex;
@@ -167,6 +167,7 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
             P->fold2_split = P->split_off ? 1 : it->second.f2_split;
             P->fold2_async = it->second.f2_async;
             P->fold2_async_st = it->second.f2_async_st;
+            P->fold_adj_pp = it->second.adj_pp;
             for (int i = 0; i < 5; ++i) P->tune_ms[i] = it->second.ms[i];
             P->tuned = true;
             return DR_OK;
@@ -194,6 +195,49 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
         }
         return DR_OK;
     };
+    // Strip-height search: the heights 2, 4, 8, 16 (those within rmax, and the
+    // largest that fits), then the neighbours of the best one among
+    // 1, 2, 3, 4, 6, 8, 12, 16.  run(lines, t) times one configuration; best_t
+    // may come in holding another configuration's time, and `improved` says
+    // whether one of these heights beat it.
+    auto search_lines = [&](int rmax, auto run, int &best_lines, double &best_t, bool &improved) -> dr_status {
+        const int all[] = {1, 2, 3, 4, 6, 8, 12, 16};
+        bool tried[8] = {};
+        improved = false;
+        int best_i = -1;
+        auto try_one = [&](int i) -> dr_status {
+            if (i < 0 || i > 7 || tried[i] || all[i] > rmax) return DR_OK;
+            tried[i] = true;
+            double t = 1e30;
+            dr_status s = run(all[i], t);
+            if (s != DR_OK) return s;
+            if (t < best_t) {
+                best_t = t;
+                best_lines = all[i];
+                best_i = i;
+                improved = true;
+            }
+            return DR_OK;
+        };
+        int imax = 0;
+        while (imax < 7 && all[imax + 1] <= rmax) ++imax;
+        for (int i : {1, 3, 5, 7, imax}) {
+            dr_status s = try_one(i);
+            if (s != DR_OK) return s;
+        }
+        if (!tried[1]) {  // rmax < 2
+            dr_status s = try_one(0);
+            if (s != DR_OK) return s;
+        }
+        if (best_i >= 0) {
+            const int bi = best_i;
+            for (int i : {bi - 1, bi + 1}) {
+                dr_status s = try_one(i);
+                if (s != DR_OK) return s;
+            }
+        }
+        return DR_OK;
+    };
     {
         dr_status s = time_fwd(0, ms[0]);
         if (s != DR_OK) return s;
@@ -205,23 +249,20 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
         int best_lines = P->fold_R, best_async = 0;
         const int async_ok = P->m == P->M && ((P->prec == DR_F32 && P->M % 4 == 0) ||
                                               (P->prec == DR_BF16_F32ACC && P->M % 8 == 0));
-        const int cand[] = {1, 2, 3, 4, 6, 8, 12, 16};
-        for (int as = 0; as <= async_ok; ++as)
-            for (int c : cand) {
-                const int lines = c;
-                // both buffers of the double-buffered mode share the strip budget
-                if ((as ? 2 : 1) * lines > P->fold_R) continue;
-                P->fold_lines = lines;
-                P->fold_async = as;
-                double t = 1e30;
-                dr_status s = time_fwd(1, t);
-                if (s != DR_OK) return s;
-                if (t < ms[1]) {
-                    ms[1] = t;
-                    best_lines = lines;
-                    best_async = as;
-                }
-            }
+        for (int as = 0; as <= async_ok; ++as) {
+            // both buffers of the double-buffered mode share the strip budget
+            P->fold_async = as;
+            bool better = false;
+            dr_status s = search_lines(
+                as ? P->fold_R / 2 : P->fold_R,
+                [&](int lines, double &t) {
+                    P->fold_lines = lines;
+                    return time_fwd(1, t);
+                },
+                best_lines, ms[1], better);
+            if (s != DR_OK) return s;
+            if (better) best_async = as;
+        }
         P->fold_lines = best_lines;
         P->fold_async = best_async;
         if (P->prec == DR_BF16_F32ACC) {
@@ -230,20 +271,19 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
             const int async_st_ok = P->m == P->M && P->M % 8 == 0;
             double best_t = 1e30;
             int bl = P->fold_R, ba = 0;
-            for (int as = 0; as <= async_st_ok; ++as)
-                for (int c : cand) {
-                    if ((as ? 2 : 1) * c > P->fold_R) continue;
-                    P->fold_lines_st = c;
-                    P->fold_async_st = as;
-                    double t = 1e30;
-                    dr_status s = time_fwd(1, t, false);
-                    if (s != DR_OK) return s;
-                    if (t < best_t) {
-                        best_t = t;
-                        bl = c;
-                        ba = as;
-                    }
-                }
+            for (int as = 0; as <= async_st_ok; ++as) {
+                P->fold_async_st = as;
+                bool better = false;
+                dr_status s = search_lines(
+                    as ? P->fold_R / 2 : P->fold_R,
+                    [&](int lines, double &t) {
+                        P->fold_lines_st = lines;
+                        return time_fwd(1, t, false);
+                    },
+                    bl, best_t, better);
+                if (s != DR_OK) return s;
+                if (better) ba = as;
+            }
             P->fold_lines_st = bl;
             P->fold_async_st = ba;
             ms_st1 = best_t;
@@ -254,61 +294,70 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
         // height, staging mode, line chunks.  Group, CTA size, strip height and
         // staging change only which CTA computes a ray sum and when its lines
         // are copied: results do not depend on them.
-        const int lines_c[] = {1, 2, 3, 4, 6, 8, 12, 16};
-        int bgi = P->fold2_gi, bl = P->fold2_lines;
-        // strip heights of the current configuration; true if one beat `best`
-        auto sweep_lines = [&](int gi, bool calc, double &best, int &best_lines, bool &better) -> dr_status {
-            better = false;
-            for (int c : lines_c) {
-                if (c > P->fold2_R[gi]) continue;
-                if (calc) P->fold2_lines = c;
-                else P->fold2_lines_st = c;
-                double t = 1e30;
-                dr_status s = time_fwd(2, t, calc);
-                if (s != DR_OK) return s;
-                if (t < best) {
-                    best = t;
-                    best_lines = c;
-                    better = true;
-                }
-            }
-            return DR_OK;
+        auto run2 = [&](bool calc) {
+            return [&, calc](int lines, double &t) {
+                if (calc) P->fold2_lines = lines;
+                else P->fold2_lines_st = lines;
+                return time_fwd(2, t, calc);
+            };
         };
         bool better = false;
+        int bgi = P->fold2_gi, bl = P->fold2_lines;
         P->fold2_split = 1;
         P->fold2_async = 0;
-        for (int gi = 0; gi < 6; ++gi) {
+        // screen the group / CTA configurations at two strip heights, refine the best
+        auto gi_ok = [&](int gi) {
             const int MC = (gi & 1) ? 8 : 4;
-            if (P->fold2_R[gi] < 1 || (MC == 8 && P->m <= 4) || (size_t)P->nz * ((P->m + MC - 1) / MC) > 65535)
-                continue;
+            return P->fold2_R[gi] >= 1 && !(MC == 8 && P->m <= 4) &&
+                   (size_t)P->nz * ((P->m + MC - 1) / MC) <= 65535;
+        };
+        for (int gi = 0; gi < 6; ++gi) {
+            if (!gi_ok(gi)) continue;
             P->fold2_gi = gi;
-            dr_status s = sweep_lines(gi, true, ms[4], bl, better);
-            if (s != DR_OK) return s;
-            if (better) bgi = gi;
+            for (int c : {4, std::min(16, P->fold2_R[gi])}) {
+                if (c > P->fold2_R[gi]) continue;
+                double t = 1e30;
+                dr_status s = run2(true)(c, t);
+                if (s != DR_OK) return s;
+                if (t < ms[4]) {
+                    ms[4] = t;
+                    bgi = gi;
+                    bl = c;
+                }
+            }
         }
         P->fold2_gi = bgi;
+        {
+            dr_status s = search_lines(P->fold2_R[bgi], run2(true), bl, ms[4], better);
+            if (s != DR_OK) return s;
+        }
         // double-buffered cp.async strips
         {
             P->fold2_async = 1;
-            int l2 = bl;
-            dr_status s = sweep_lines(bgi, true, ms[4], l2, better);
+            dr_status s = search_lines(P->fold2_R[bgi], run2(true), bl, ms[4], better);
             if (s != DR_OK) return s;
-            if (better) bl = l2;
-            else P->fold2_async = 0;
+            if (!better) P->fold2_async = 0;
         }
-        // small grids leave SMs idle in the last wave: try splitting the march
-        // into line chunks (more CTAs; the distribution adds the partial sums)
-        if (!P->split_off) {
+        // grids of a few waves leave SMs idle in the last one: try splitting the
+        // march into line chunks (more CTAs; the distribution adds the partial sums)
+        const long long ctas = (long long)P->fold2_nblocks[bgi] * P->fold2_nchunk[bgi] * P->nz *
+                               ((P->m + fold_static_mc(bgi) - 1) / fold_static_mc(bgi));
+        if (!P->split_off && ctas < 4LL * P->num_sms) {
             const size_t chunk = sizeof(float) * (size_t)P->nz * P->fold_U * P->ns * ((P->m + 3) / 4 * 4);
             int bs = 1;
+            const int l0 = bl;
             for (int ns2 = 2; ns2 <= 4 && chunk * ns2 <= kSplitScratchMax; ++ns2) {
                 P->fold2_split = ns2;
-                int l2 = bl;
-                dr_status s = sweep_lines(bgi, true, ms[4], l2, better);
-                if (s != DR_OK) return s;
-                if (better) {
-                    bs = ns2;
-                    bl = l2;
+                for (int c : {l0, std::max(1, l0 / 2)}) {
+                    double t = 1e30;
+                    dr_status s = run2(true)(c, t);
+                    if (s != DR_OK) return s;
+                    if (t < ms[4]) {
+                        ms[4] = t;
+                        bs = ns2;
+                        bl = c;
+                    }
+                    if (l0 == 1) break;
                 }
             }
             P->fold2_split = bs;
@@ -326,7 +375,7 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
             int bls = bl, bas = 0;
             for (int as = 0; as < 2; ++as) {
                 P->fold2_async_st = as;
-                dr_status s = sweep_lines(bgi, false, best_t, bls, better);
+                dr_status s = search_lines(P->fold2_R[bgi], run2(false), bls, best_t, better);
                 if (s != DR_OK) return s;
                 if (better) bas = as;
             }
@@ -346,7 +395,7 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
         if (ms_st2 < bt) { best = 2; bt = ms_st2; }
         P->sel_fwd_st = best;
     }
-    for (int v = 0; v < 2; ++v) {
+    auto time_adj = [&](int v, double &best) -> dr_status {
         for (int rep = 0; rep < 3; ++rep) {
             DR_CUDA_TRY(cudaEventRecord(e0, st));
             dr_status s = launch_adj_variant(P, v, true, g_scratch, u_scratch, 1.0, 0.0, true, st);
@@ -355,8 +404,29 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
             DR_CUDA_TRY(cudaEventSynchronize(e1));
             float t = 0.f;
             DR_CUDA_TRY(cudaEventElapsedTime(&t, e0, e1));
-            if (rep > 0) ms[2 + v] = std::min(ms[2 + v], (double)t);
+            if (rep > 0) best = std::min(best, (double)t);
         }
+        return DR_OK;
+    };
+    {
+        dr_status s = time_adj(0, ms[2]);
+        if (s != DR_OK) return s;
+    }
+    if (P->fold_U > 0) {
+        // folded adjoint: distinct angles per pipeline stage (8, 7, 6: smaller
+        // windows let more CTAs share an SM; the summation order is the same)
+        int best_pp = 8;
+        for (int pp : {8, 7, 6}) {
+            P->fold_adj_pp = pp;
+            double t = 1e30;
+            dr_status s = time_adj(1, t);
+            if (s != DR_OK) return s;
+            if (t < ms[3]) {
+                ms[3] = t;
+                best_pp = pp;
+            }
+        }
+        P->fold_adj_pp = best_pp;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -374,7 +444,8 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
     auto ins = g_tune_cache.emplace(key, TuneVal{P->sel_fwd, P->sel_adj, P->fold_lines, P->fold_async,
                                                  P->fold_lines_st, P->fold_async_st, P->fold2_gi, P->fold2_lines,
                                                  P->fold2_lines_st, P->sel_fwd_st, P->fold2_split,
-                                                 P->fold2_async, P->fold2_async_st, {0, 0, 0, 0, 0}});
+                                                 P->fold2_async, P->fold2_async_st, P->fold_adj_pp,
+                                                 {0, 0, 0, 0, 0}});
     if (ins.second) {
         for (int i = 0; i < 5; ++i) ins.first->second.ms[i] = P->tune_ms[i];
     } else {  // another thread tuned the same problem first: follow its choice
@@ -391,6 +462,7 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
         P->fold2_split = P->split_off ? 1 : ins.first->second.f2_split;
         P->fold2_async = ins.first->second.f2_async;
         P->fold2_async_st = ins.first->second.f2_async_st;
+        P->fold_adj_pp = ins.first->second.adj_pp;
     }
     return DR_OK;
 }
@@ -491,6 +563,15 @@ dr_status dr_plan_set_fold_march(dr_plan *P, int nsplit, int async) {
     return DR_OK;
 }
 
+dr_status dr_plan_set_fold_adj_stage(dr_plan *P, int angles) {
+    clear_error();
+    if (!P) return fail(DR_EINVAL, "dr_plan_set_fold_adj_stage: NULL plan");
+    if (P->fold_U == 0) return fail(DR_EINVAL, "dr_plan_set_fold_adj_stage: no folded adjoint");
+    if (angles < 1 || angles > 32) return fail(DR_EINVAL, "dr_plan_set_fold_adj_stage: angles must be 1..32");
+    P->fold_adj_pp = angles;
+    return DR_OK;
+}
+
 dr_status dr_plan_info(const dr_plan *P, dr_plan_info_t *info) {
     clear_error();
     if (!P || !info) return fail(DR_EINVAL, "dr_plan_info: NULL argument");
@@ -508,6 +589,7 @@ dr_status dr_plan_info(const dr_plan *P, dr_plan_info_t *info) {
     info->fold2_lines = P->fold2_ok ? P->fold2_lines : 0;
     info->fold2_split = P->fold2_ok ? P->fold2_split : 0;
     info->fold2_async = P->fold2_ok ? P->fold2_async : 0;
+    info->fold_adj_angles = P->fold_U > 0 ? P->fold_adj_pp : 0;
     info->fwd_variant_storage = P->var_fwd >= 0 ? P->var_fwd : P->sel_fwd_st;
     return DR_OK;
 }
