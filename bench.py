@@ -71,6 +71,9 @@ def parse():
     ap.add_argument("--fold2-config", default=None,
                     help="with --variant 2,x or --profile-small: fix the two-kernel folded forward's "
                          "'group,threads,lines[,split[,async]]' instead of the default")
+    ap.add_argument("--fold-adj-angles", type=int, default=0,
+                    help="with --variant x,1 or --profile-small: fix the folded adjoint's distinct angles per "
+                         "pipeline stage instead of the default")
     ap.add_argument("--profile-small", action="store_true",
                     help="run only one launch of each projector kernel on the workload (for ncu captures)")
     return ap.parse_args()
@@ -243,6 +246,8 @@ def run_ours(a):
             plan.set_fold_strip(a.fold_strip, False)
         if fv == dr.FOLD2 and a.fold2_config:
             set_fold2_config(plan, a.fold2_config)
+        if av == dr.FOLD and a.fold_adj_angles > 0:
+            plan.set_fold_adj_stage(a.fold_adj_angles)
 
     if a.profile_small:
         # one forward and one adjoint of each variant (direct, half-turn fold)
@@ -253,6 +258,8 @@ def run_ours(a):
             plan.set_variant(var, var)
             if var == dr.FOLD and a.fold_strip > 0:
                 plan.set_fold_strip(a.fold_strip, False)
+            if var == dr.FOLD and a.fold_adj_angles > 0:
+                plan.set_fold_adj_stage(a.fold_adj_angles)
             dr.dyn_radon_fwd(plan, uin, gout)
             dr.dyn_radon_adj(plan, g, u)
         # the two-kernel folded forward (static transforms + distribution)
@@ -447,6 +454,7 @@ def run_ours(a):
                          "launch_ms": launch_ms, "fwd_ms": fwd_ms, "adj_ms": adj_ms,
                          "variants": {"unique_angles": U, "fwd": info["fwd_variant"], "adj": info["adj_variant"],
                                       "fold_lines": info["fold_lines"], "fold_async": info["fold_async"],
+                                      "fold_adj_angles_per_stage": info["fold_adj_angles"],
                                       "fold2_group_threads_lines_split_async": [
                                           info["fold2_group"], info["fold2_threads"], info["fold2_lines"],
                                           info["fold2_split"], info["fold2_async"]],

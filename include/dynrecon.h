@@ -195,6 +195,17 @@ dr_status dr_plan_set_fold_march(dr_plan *plan, int nsplit, int async);
  */
 dr_status dr_plan_set_fold_adj_stage(dr_plan *plan, int angles);
 
+/*
+ * Fix the two-kernel folded forward's angle blocks: extra (0..3) more blocks
+ * per stepping axis than the fewest whose rays fill a CTA, with the angles
+ * spread evenly over them (smaller blocks, more CTAs: a fuller last wave).
+ * Each ray's march is unchanged: results are identical.
+ * dr_plan_set_fold_groups resets it to 0: set it afterwards.
+ * DR_EINVAL if the variant is unavailable or does not exist for this plan
+ * (variants that would repeat the block size of the one below are not built).
+ */
+dr_status dr_plan_set_fold_blocks(dr_plan *plan, int extra);
+
 typedef struct {
     int unique_angles;   /* distinct theta mod pi (0: the fold is unavailable) */
     int max_group;       /* most projections sharing one theta mod pi */
@@ -210,6 +221,7 @@ typedef struct {
     int fold2_split;     /* two-kernel folded forward: line chunks of the march */
     int fold2_async;     /* two-kernel folded forward: 1 if strips are double-buffered with cp.async */
     int fold_adj_angles; /* folded adjoint: distinct angles per pipeline stage */
+    int fold2_angles;    /* two-kernel folded forward: distinct angles per CTA block */
     int fwd_variant_storage; /* forward variant of storage-typed calls (differs on BF16 plans) */
 } dr_plan_info_t;
 

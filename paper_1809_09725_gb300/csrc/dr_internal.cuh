@@ -72,6 +72,7 @@ constexpr int kFwdGuard = 4; // zero cells on each side of a staged line
 // Shared-memory budget of the folded forward's strip (float lines; both
 // buffers when double-buffered): two CTAs of 256 threads still fit an SM.
 constexpr int kFoldStripBudget = 110 * 1024;
+constexpr int kFold2BlockVariants = 4;
 
 constexpr int kRedThreads = 256;
 constexpr int kRedBlocksMax = 1024;
@@ -164,10 +165,13 @@ struct dr_plan {
     bool fold_fwd_ok = false;         // the forward strip fits in shared memory
     // folded forward in two kernels (variant 2): static transforms of groups of
     // 4 or 8 coefficients of the distinct angles into d_gt, then distribution
-    int *d_fold_of_k = nullptr;       // [K] 2 * (distinct angle) + (1 if the bins are reversed)
     // configurations gi = 0..5: 4 / 8 coefficients (odd gi: 8) x 256 / 512 / 1024 threads (gi / 2)
-    int fold2_P[6] = {}, fold2_nchunk[6] = {}, fold2_nblocks[6] = {}, fold2_R[6] = {};
-    int *d_fold2_blocks[6] = {};
+    // angle blocks: variant v spreads each stepping axis's angles evenly over v more
+    // blocks than the fewest that fit a CTA (smaller blocks, more CTAs: fuller last wave)
+    int fold2_nchunk[6] = {}, fold2_R[6] = {};
+    int fold2_P[6][dr::kFold2BlockVariants] = {}, fold2_nblocks[6][dr::kFold2BlockVariants] = {};
+    int *d_fold2_blocks[6][dr::kFold2BlockVariants] = {};
+    int fold2_bv = 0;                 // angle-block variant in use
     bool fold2_ok = false;
     int fold2_gi = 0;                 // configuration in use
     int sel_fwd_st = 0;               // forward variant of storage-typed calls on BF16 plans (bf16 strips)

@@ -395,38 +395,88 @@ __global__ void __launch_bounds__(THREADS, THREADS == kFoldThreads ? fold_fwd_mi
 // Forward, two-kernel form, step 2: distribute the static transforms
 //   g[z][k][b] = sum_j phi_j(t_k) ru[z][a(k)][flip_k(b)][j]
 // with the forward epilogue modes (store, minus gm, CP dual update).  Line
-// chunks of a split march are added first, in chunk order.
+// chunks of a split march are added first, in chunk order.  A thread takes
+// one row (z, a, b) of the static transforms, reads it once, and writes the
+// bins of every projection k of angle a (at b, or ns-1-b for odd half-turns):
+// consecutive threads write consecutive bins of the same projection.
 // ===========================================================================
 template <typename S, typename T, int M>
 __global__ void __launch_bounds__(kRedThreads)
     fold_dist_kernel(const T *__restrict__ ru, S *__restrict__ out, const S *__restrict__ gm,
-                     const int *__restrict__ of_k, const T *__restrict__ phip, int nz, int K, int ns, int U, int ms_ru,
-                     int m, int MP, int mode, T sigma, int nsplit, size_t split_stride) {
-    const size_t n = (size_t)nz * K * ns;
-    for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
-        const int b = (int)(o % ns);
-        const size_t zk = o / ns;
-        const int k = (int)(zk % K), z = (int)(zk / K);
-        const int ak = __ldg(of_k + k);
-        const int a = ak >> 1;
-        const int bb = (ak & 1) ? ns - 1 - b : b;
-        const T *r = ru + (((size_t)z * U + a) * ns + bb) * ms_ru;
-        const T *ph = phip + (size_t)k * MP;
-        T val = T(0);
+                     const int *__restrict__ start, const int *__restrict__ member, const T *__restrict__ phip,
+                     int nz, int K, int ns, int U, int ms_ru, int m, int MP, int mode, T sigma, int nsplit,
+                     size_t split_stride) {
+    // rows and table rows are multiples of 4 floats from 16-byte aligned bases
+    constexpr bool V4 = sizeof(T) == 4;
+    const size_t n = (size_t)nz * U * ns;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int b = (int)(i % ns);
+        const size_t za = i / ns;
+        const int a = (int)(za % U), z = (int)(za / U);
+        const T *r = ru + i * ms_ru;
+        T rv[M];
+        if constexpr (V4 && M % 4 == 0) {
 #pragma unroll
-        for (int j = 0; j < M; ++j)
-            if (j < m) {
-                T rj = r[j];
-                for (int c = 1; c < nsplit; ++c) rj += r[c * split_stride + j];
-                val = fma(__ldg(ph + j), rj, val);
+            for (int q = 0; q < M / 4; ++q) {
+                if (4 * q < m) {
+                    float4 v = *reinterpret_cast<const float4 *>(r + 4 * q);
+                    for (int c = 1; c < nsplit; ++c) {
+                        const float4 w = *reinterpret_cast<const float4 *>(r + c * split_stride + 4 * q);
+                        v.x += w.x;
+                        v.y += w.y;
+                        v.z += w.z;
+                        v.w += w.w;
+                    }
+                    rv[4 * q] = v.x;
+                    rv[4 * q + 1] = v.y;
+                    rv[4 * q + 2] = v.z;
+                    rv[4 * q + 3] = v.w;
+                } else {
+                    rv[4 * q] = rv[4 * q + 1] = rv[4 * q + 2] = rv[4 * q + 3] = T(0);
+                }
             }
-        if (mode == 0) {
-            stc<T>(out + o, val);
-        } else if (mode == 1) {
-            stc<T>(out + o, val - ldc<T>(gm + o));
         } else {
-            const T h = ldc<T>(out + o);
-            stc<T>(out + o, (h + sigma * val - sigma * ldc<T>(gm + o)) / (T(1) + sigma));
+#pragma unroll
+            for (int j = 0; j < M; ++j) {
+                T rj = T(0);
+                if (j < m) {
+                    rj = r[j];
+                    for (int c = 1; c < nsplit; ++c) rj += r[c * split_stride + j];
+                }
+                rv[j] = rj;
+            }
+        }
+        const int e = __ldg(start + a + 1);
+        for (int idx = __ldg(start + a); idx < e; ++idx) {
+            const int mem = __ldg(member + idx);
+            const int k = mem >> 1;
+            const int bb = (mem & 1) ? ns - 1 - b : b;
+            const T *ph = phip + (size_t)k * MP;
+            T val = T(0);
+            if constexpr (V4 && M % 4 == 0) {
+#pragma unroll
+                for (int q = 0; q < M / 4; ++q) {
+                    if (4 * q >= m) break;
+                    const float4 f = __ldg(reinterpret_cast<const float4 *>(ph) + q);
+                    const float fv[4] = {f.x, f.y, f.z, f.w};
+#pragma unroll
+                    for (int t = 0; t < 4; ++t)
+                        if (4 * q + t < m) val = fma(fv[t], rv[4 * q + t], val);
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < M; ++j)
+                    if (j < m) val = fma(__ldg(ph + j), rv[j], val);
+            }
+            const size_t o = ((size_t)z * K + k) * ns + bb;
+            if (mode == 0) {
+                stc<T>(out + o, val);
+            } else if (mode == 1) {
+                stc<T>(out + o, val - ldc<T>(gm + o));
+            } else {
+                const T h = ldc<T>(out + o);
+                stc<T>(out + o, (h + sigma * val - sigma * ldc<T>(gm + o)) / (T(1) + sigma));
+            }
         }
     }
 }
@@ -709,17 +759,19 @@ dr_status fold_fwd2_launch_mc(dr_plan *P, const void *u, void *out, const void *
         if (s != DR_OK) return s;
         ru = (T *)P->d_ru_split;
     }
-    dim3 grid(P->fold2_nblocks[gi] * P->fold2_nchunk[gi], P->nz * ngroups, nsplit);
+    const int bv = P->d_fold2_blocks[gi][P->fold2_bv] ? P->fold2_bv : 0;
+    dim3 grid(P->fold2_nblocks[gi][bv] * P->fold2_nchunk[gi], P->nz * ngroups, nsplit);
     kern<<<grid, THREADS, smem, st>>>((const S *)u, (S *)out, (const S *)gm, P->d_fold_fwd, P->d_fold_start,
-                                           P->d_fold_member, (const T *)P->d_PhiP, P->d_fold2_blocks[gi], P->nx,
-                                           P->ny, P->ns, P->K, P->m, P->MP, P->fold2_P[gi], R, P->fold2_nchunk[gi],
+                                           P->d_fold_member, (const T *)P->d_PhiP, P->d_fold2_blocks[gi][bv],
+                                           P->nx, P->ny, P->ns, P->K, P->m, P->MP, P->fold2_P[gi][bv], R,
+                                           P->fold2_nchunk[gi],
                                            mode, (T)sigma, async, ngroups, ru, P->fold_U, ms_ru, nsplit,
                                            split_stride);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "fold_fwd_kernel (static) launch");
-    fold_dist_kernel<S, T, M><<<red_grid((size_t)P->nz * P->K * P->ns), kRedThreads, 0, st>>>(
-        ru, (S *)out, (const S *)gm, P->d_fold_of_k, (const T *)P->d_PhiP, P->nz, P->K, P->ns, P->fold_U, ms_ru,
-        P->m, P->MP, mode, (T)sigma, nsplit, split_stride);
+    fold_dist_kernel<S, T, M><<<red_grid((size_t)P->nz * P->fold_U * P->ns), kRedThreads, 0, st>>>(
+        ru, (S *)out, (const S *)gm, P->d_fold_start, P->d_fold_member, (const T *)P->d_PhiP, P->nz, P->K, P->ns,
+        P->fold_U, ms_ru, P->m, P->MP, mode, (T)sigma, nsplit, split_stride);
     e = cudaGetLastError();
     return e == cudaSuccess ? DR_OK : cuda_fail(e, "fold_dist_kernel launch");
 }

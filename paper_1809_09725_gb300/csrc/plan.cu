@@ -437,35 +437,36 @@ static dr_status build_tables(dr_plan *P) {
         if (!fb.empty())
             DR_CUDA_TRY(cudaMemcpy(P->d_fold_blocks, fb.data(), sizeof(int) * fb.size(), cudaMemcpyHostToDevice));
         P->gt_bytes = sizeof(float) * (size_t)P->nz * U * P->ns * MS;
-        // two-kernel folded forward: projection -> (angle, reversal); work lists and
-        // strip budgets for coefficient groups of 4 (8 rays per thread) and of 8 (4)
-        std::vector<int> of_k(K);
-        for (int a = 0; a < U; ++a)
-            for (int i = start[a]; i < start[a + 1]; ++i) of_k[member[i] >> 1] = 2 * a + (member[i] & 1);
-        DR_CUDA_TRY(cudaMalloc(&P->d_fold_of_k, sizeof(int) * K));
-        DR_CUDA_TRY(cudaMemcpy(P->d_fold_of_k, of_k.data(), sizeof(int) * K, cudaMemcpyHostToDevice));
-        bytes += sizeof(int) * K;
+        // two-kernel folded forward: work lists and strip budgets of the six
+        // coefficient-group / CTA-size configurations
         for (int gi = 0; gi < 6; ++gi) {  // 4 or 8 coefficients; 256, 512 or 1024 threads
             const int MC = (gi & 1) ? 8 : 4;
             const int rays2 = (256 << (gi / 2)) * (gi < 4 ? 32 / MC : 16 / MC);
-            int P2, nch2;
-            if (P->ns <= rays2) { P2 = std::min(64, rays2 / P->ns); nch2 = 1; }
-            else { P2 = 1; nch2 = (P->ns + rays2 - 1) / rays2; }
-            std::vector<int> fb2;
-            for (const std::vector<int> *grp : {&ub0, &ub1})
-                for (size_t i = 0; i < grp->size(); i += P2)
-                    for (int q = 0; q < P2; ++q) fb2.push_back(i + q < grp->size() ? (*grp)[i + q] : -1);
+            int Pmax, nch2;
+            if (P->ns <= rays2) { Pmax = std::min(64, rays2 / P->ns); nch2 = 1; }
+            else { Pmax = 1; nch2 = (P->ns + rays2 - 1) / rays2; }
             const int ps2 = MC == 4 ? 4 : 12;  // float strip stride of the group
             const size_t line2 = sizeof(float) * (size_t)(std::max(P->nx, P->ny) + 2 * kFwdGuard) * ps2;
             P->fold2_R[gi] = std::min(16, (int)(kFoldStripBudget / line2));
-            P->fold2_P[gi] = P2;
             P->fold2_nchunk[gi] = nch2;
-            P->fold2_nblocks[gi] = (int)(fb2.size() / P2);
-            DR_CUDA_TRY(cudaMalloc(&P->d_fold2_blocks[gi], sizeof(int) * std::max<size_t>(fb2.size(), 1)));
-            if (!fb2.empty())
-                DR_CUDA_TRY(cudaMemcpy(P->d_fold2_blocks[gi], fb2.data(), sizeof(int) * fb2.size(),
-                                       cudaMemcpyHostToDevice));
-            bytes += sizeof(int) * fb2.size();
+            const int nmax = (int)std::max(ub0.size(), ub1.size());
+            for (int v = 0; v < kFold2BlockVariants; ++v) {
+                // v more blocks per stepping axis than the fewest, angles spread evenly
+                const int nb = (nmax + Pmax - 1) / Pmax + v;
+                const int P2 = v == 0 ? Pmax : std::max(1, (nmax + nb - 1) / nb);
+                if (v > 0 && (nch2 > 1 || P2 == P->fold2_P[gi][v - 1])) break;  // nothing new
+                std::vector<int> fb2;
+                for (const std::vector<int> *grp : {&ub0, &ub1})
+                    for (size_t i = 0; i < grp->size(); i += P2)
+                        for (int q = 0; q < P2; ++q) fb2.push_back(i + q < grp->size() ? (*grp)[i + q] : -1);
+                P->fold2_P[gi][v] = P2;
+                P->fold2_nblocks[gi][v] = (int)(fb2.size() / P2);
+                DR_CUDA_TRY(cudaMalloc(&P->d_fold2_blocks[gi][v], sizeof(int) * std::max<size_t>(fb2.size(), 1)));
+                if (!fb2.empty())
+                    DR_CUDA_TRY(cudaMemcpy(P->d_fold2_blocks[gi][v], fb2.data(), sizeof(int) * fb2.size(),
+                                           cudaMemcpyHostToDevice));
+                bytes += sizeof(int) * fb2.size();
+            }
         }
         P->fold2_ok = P->m >= 4 && P->fold2_R[0] >= 1;
         // default: groups of 4 coefficients, 256 threads (the autotuner times all)
@@ -584,10 +585,12 @@ dr_status dr_plan_destroy(dr_plan *P) {
                     P->d_dPhiF,      P->d_G,         P->d_Lt,         P->d_partials,    P->d_counters,
                     P->d_scal,       P->d_status,    P->d_fold_fwd,   P->d_fold_adj,    P->d_fold_start,
                     P->d_fold_member, P->d_fold_blocks, P->d_gt, P->d_fbp_taps, P->d_fbp_phi, P->d_fbp_q,
-                    P->d_fbp_u, P->d_fold_of_k, P->d_fold2_blocks[0], P->d_fold2_blocks[1],
-                    P->d_fold2_blocks[2], P->d_fold2_blocks[3], P->d_fold2_blocks[4], P->d_fold2_blocks[5], P->d_ru_split};
+                    P->d_fbp_u, P->d_ru_split};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    for (auto &row : P->d_fold2_blocks)
+        for (int *p : row)
+            if (p) cudaFree(p);
     if (P->graph_stream) cudaStreamDestroy(P->graph_stream);
     if (P->ev_a) cudaEventDestroy(P->ev_a);
     if (P->ev_b) cudaEventDestroy(P->ev_b);

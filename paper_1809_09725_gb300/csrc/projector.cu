@@ -127,7 +127,7 @@ struct TuneKey {
 };
 struct TuneVal {
     int fwd, adj, lines, async, lines_st, async_st, f2_gi, f2_lines, f2_lines_st, fwd_st, f2_split, f2_async,
-        f2_async_st, adj_pp;
+        f2_async_st, adj_pp, f2_bv;
     double ms[5];
 };
 static std::mutex g_tune_mutex;
@@ -168,6 +168,7 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
             P->fold2_async = it->second.f2_async;
             P->fold2_async_st = it->second.f2_async_st;
             P->fold_adj_pp = it->second.adj_pp;
+            P->fold2_bv = it->second.f2_bv;
             for (int i = 0; i < 5; ++i) P->tune_ms[i] = it->second.ms[i];
             P->tuned = true;
             return DR_OK;
@@ -305,6 +306,7 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
         int bgi = P->fold2_gi, bl = P->fold2_lines;
         P->fold2_split = 1;
         P->fold2_async = 0;
+        P->fold2_bv = 0;
         // screen the group / CTA configurations at two strip heights, refine the best
         auto gi_ok = [&](int gi) {
             const int MC = (gi & 1) ? 8 : 4;
@@ -338,33 +340,61 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
             if (s != DR_OK) return s;
             if (!better) P->fold2_async = 0;
         }
+        // smaller angle blocks (more CTAs, each with less work): a fuller last wave
+        {
+            int bbv = 0;
+            for (int v = 1; v < kFold2BlockVariants && P->d_fold2_blocks[bgi][v]; ++v) {
+                P->fold2_bv = v;
+                double t = 1e30;
+                dr_status s = run2(true)(bl, t);
+                if (s != DR_OK) return s;
+                if (t < ms[4]) {
+                    ms[4] = t;
+                    bbv = v;
+                }
+            }
+            P->fold2_bv = bbv;
+        }
         // grids of a few waves leave SMs idle in the last one: try splitting the
         // march into line chunks (more CTAs; the distribution adds the partial sums)
-        const long long ctas = (long long)P->fold2_nblocks[bgi] * P->fold2_nchunk[bgi] * P->nz *
+        const long long ctas = (long long)P->fold2_nblocks[bgi][P->fold2_bv] * P->fold2_nchunk[bgi] * P->nz *
                                ((P->m + fold_static_mc(bgi) - 1) / fold_static_mc(bgi));
         if (!P->split_off && ctas < 4LL * P->num_sms) {
             const size_t chunk = sizeof(float) * (size_t)P->nz * P->fold_U * P->ns * ((P->m + 3) / 4 * 4);
-            int bs = 1;
-            const int l0 = bl;
+            int bs = 1, bbv = P->fold2_bv;
+            const int l0 = bl, bv0 = P->fold2_bv;
             for (int ns2 = 2; ns2 <= 4 && chunk * ns2 <= kSplitScratchMax; ++ns2) {
                 P->fold2_split = ns2;
-                for (int c : {l0, std::max(1, l0 / 2)}) {
-                    double t = 1e30;
-                    dr_status s = run2(true)(c, t);
-                    if (s != DR_OK) return s;
-                    if (t < ms[4]) {
-                        ms[4] = t;
-                        bs = ns2;
-                        bl = c;
+                // chunks change the wave count: block sizes are searched with them
+                for (int v = 0; v < kFold2BlockVariants && P->d_fold2_blocks[bgi][v]; ++v) {
+                    if (v != 0 && v != bv0 && v != 1) continue;
+                    P->fold2_bv = v;
+                    for (int c : {l0, std::max(1, l0 / 2)}) {
+                        double t = 1e30;
+                        dr_status s = run2(true)(c, t);
+                        if (s != DR_OK) return s;
+                        if (t < ms[4]) {
+                            ms[4] = t;
+                            bs = ns2;
+                            bl = c;
+                            bbv = v;
+                        }
+                        if (l0 == 1) break;
                     }
-                    if (l0 == 1) break;
                 }
             }
             P->fold2_split = bs;
-            if (bs == 1 && P->d_ru_split) {
+            P->fold2_bv = bbv;
+            // keep exactly the chosen chunks' scratch (the trials grew it to the largest)
+            const size_t keep = bs > 1 ? chunk * bs : 0;
+            if (P->d_ru_split && P->ru_split_bytes != keep) {
                 cudaFree(P->d_ru_split);
                 P->d_ru_split = nullptr;
                 P->ru_split_bytes = 0;
+                if (keep) {
+                    dr_status s = ensure_split_scratch(P, keep);
+                    if (s != DR_OK) return s;
+                }
             }
         }
         P->fold2_lines = bl;
@@ -444,7 +474,7 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
     auto ins = g_tune_cache.emplace(key, TuneVal{P->sel_fwd, P->sel_adj, P->fold_lines, P->fold_async,
                                                  P->fold_lines_st, P->fold_async_st, P->fold2_gi, P->fold2_lines,
                                                  P->fold2_lines_st, P->sel_fwd_st, P->fold2_split,
-                                                 P->fold2_async, P->fold2_async_st, P->fold_adj_pp,
+                                                 P->fold2_async, P->fold2_async_st, P->fold_adj_pp, P->fold2_bv,
                                                  {0, 0, 0, 0, 0}});
     if (ins.second) {
         for (int i = 0; i < 5; ++i) ins.first->second.ms[i] = P->tune_ms[i];
@@ -463,6 +493,7 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
         P->fold2_async = ins.first->second.f2_async;
         P->fold2_async_st = ins.first->second.f2_async_st;
         P->fold_adj_pp = ins.first->second.adj_pp;
+        P->fold2_bv = ins.first->second.f2_bv;
     }
     return DR_OK;
 }
@@ -549,6 +580,7 @@ dr_status dr_plan_set_fold_groups(dr_plan *P, int group, int threads, int lines)
                                "512 or 1024, and lines within the strip budget");
     P->fold2_gi = gi;
     P->fold2_lines = P->fold2_lines_st = lines;
+    P->fold2_bv = 0;
     return DR_OK;
 }
 
@@ -560,6 +592,16 @@ dr_status dr_plan_set_fold_march(dr_plan *P, int nsplit, int async) {
         return fail(DR_EINVAL, "dr_plan_set_fold_march: nsplit must be 1..8 and async 0 or 1");
     P->fold2_split = nsplit;
     P->fold2_async = P->fold2_async_st = async;
+    return DR_OK;
+}
+
+dr_status dr_plan_set_fold_blocks(dr_plan *P, int extra) {
+    clear_error();
+    if (!P) return fail(DR_EINVAL, "dr_plan_set_fold_blocks: NULL plan");
+    if (!(P->fold_U > 0 && P->fold2_ok)) return fail(DR_EINVAL, "dr_plan_set_fold_blocks: variant unavailable");
+    if (extra < 0 || extra >= kFold2BlockVariants || !P->d_fold2_blocks[P->fold2_gi][extra])
+        return fail(DR_EINVAL, "dr_plan_set_fold_blocks: no such block variant for this plan and group");
+    P->fold2_bv = extra;
     return DR_OK;
 }
 
@@ -590,6 +632,8 @@ dr_status dr_plan_info(const dr_plan *P, dr_plan_info_t *info) {
     info->fold2_split = P->fold2_ok ? P->fold2_split : 0;
     info->fold2_async = P->fold2_ok ? P->fold2_async : 0;
     info->fold_adj_angles = P->fold_U > 0 ? P->fold_adj_pp : 0;
+    info->fold2_angles =
+        P->fold2_ok ? P->fold2_P[P->fold2_gi][P->d_fold2_blocks[P->fold2_gi][P->fold2_bv] ? P->fold2_bv : 0] : 0;
     info->fwd_variant_storage = P->var_fwd >= 0 ? P->var_fwd : P->sel_fwd_st;
     return DR_OK;
 }

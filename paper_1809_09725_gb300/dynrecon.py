@@ -31,7 +31,7 @@ _STATUS = {DR_EINVAL: "EINVAL", DR_ENOMEM: "ENOMEM", DR_ECUDA: "ECUDA", DR_ETIME
 # Every symbol include/dynrecon.h declares.
 EXPORTS = ("dr_plan_create", "dr_plan_destroy", "dr_plan_set_stream", "dr_plan_device_bytes",
            "dr_plan_workspace_bytes", "dr_plan_sync", "dr_plan_set_variant", "dr_plan_autotune",
-           "dr_plan_set_fold_strip", "dr_plan_set_fold_groups", "dr_plan_set_fold_march", "dr_plan_set_fold_adj_stage", "dr_plan_info",
+           "dr_plan_set_fold_strip", "dr_plan_set_fold_groups", "dr_plan_set_fold_march", "dr_plan_set_fold_adj_stage", "dr_plan_set_fold_blocks", "dr_plan_info",
            "dyn_radon_fwd", "dyn_radon_adj", "dyn_radon_adj_noalloc", "dr_fbp_init", "tv4d_grad", "tv4d_grad_adj", "tv4d_prox",
            "dr_solve_params_default", "admm_solve", "admm_solve_batch", "cp_solve_slabs",
            "cp_solve_slabs_device_bytes", "dr_job_device_bytes", "dr_job_slab_device_bytes", "dr_server_create",
@@ -55,6 +55,7 @@ class PlanInfo(ctypes.Structure):
                 ("fold_lines", ctypes.c_int), ("fold_async", ctypes.c_int), ("fold2_group", ctypes.c_int),
                 ("fold2_threads", ctypes.c_int), ("fold2_lines", ctypes.c_int), ("fold2_split", ctypes.c_int),
                 ("fold2_async", ctypes.c_int), ("fold_adj_angles", ctypes.c_int),
+                ("fold2_angles", ctypes.c_int),
                 ("fwd_variant_storage", ctypes.c_int)]
 
 
@@ -113,6 +114,7 @@ def load(path: str = LIB_PATH):
         "dr_plan_set_fold_groups": (i, [vp, i, i, i]),
         "dr_plan_set_fold_march": (i, [vp, i, i]),
         "dr_plan_set_fold_adj_stage": (i, [vp, i]),
+        "dr_plan_set_fold_blocks": (i, [vp, i]),
         "dr_plan_info": (i, [vp, ctypes.POINTER(PlanInfo)]),
         "dyn_radon_fwd": (i, [vp, vp, vp]),
         "dyn_radon_adj": (i, [vp, vp, vp, d]),
@@ -274,6 +276,10 @@ class Plan:
     def set_fold_adj_stage(self, angles: int):
         """Folded adjoint: distinct angles per pipeline stage."""
         _check(load().dr_plan_set_fold_adj_stage(self._h, int(angles)))
+
+    def set_fold_blocks(self, extra: int):
+        """Two-kernel folded forward: extra angle blocks per stepping axis (0..3)."""
+        _check(load().dr_plan_set_fold_blocks(self._h, int(extra)))
 
     def info(self) -> dict:
         inf = PlanInfo()

@@ -502,3 +502,30 @@ def test_fold_adjoint_stage_sizes_bitwise(case):
     for o in outs[1:]:
         np.testing.assert_array_equal(o, outs[0])
     assert rel(outs[0], P.adj(g)) <= 1e-5
+
+
+@pytest.mark.parametrize("case", ["narrow_det", "m16", "ragged", "complex_m8"])
+def test_fold2_angle_blocks_bitwise(case):
+    """Spreading the distinct angles over more, smaller CTA blocks changes
+    which CTA marches a ray, not the march: projections identical bit for
+    bit, and equal to the oracle."""
+    args, u, _, P = _setup(case, seed=47)
+    u = u.astype(np.float32).astype(np.float64)
+    plan = _plan(args, dr.F32)
+    plan.set_variant(dr.FOLD2, dr.FOLD)
+    ud = dev_tensor(u, dr.F32)
+    outs, sizes = [], []
+    for extra in range(4):
+        try:
+            plan.set_fold_blocks(extra)
+        except dr.DynreconError:
+            break  # this plan has no smaller blocks
+        g = torch.zeros(plan.g_shape(), dtype=torch.float32, device="cuda")
+        dr.dyn_radon_fwd(plan, ud, g)
+        plan.sync()
+        outs.append(host_values(g))
+        sizes.append(plan.info()["fold2_angles"])
+    assert sizes == sorted(sizes, reverse=True) and len(set(sizes)) == len(sizes)
+    for o in outs[1:]:
+        np.testing.assert_array_equal(o, outs[0])
+    assert rel(outs[0], P.fwd(u)) <= 1e-5
