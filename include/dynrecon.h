@@ -206,6 +206,7 @@ dr_status dr_plan_set_fold_adj_stage(dr_plan *plan, int angles);
  */
 dr_status dr_plan_set_fold_blocks(dr_plan *plan, int extra);
 
+
 typedef struct {
     int unique_angles;   /* distinct theta mod pi (0: the fold is unavailable) */
     int max_group;       /* most projections sharing one theta mod pi */

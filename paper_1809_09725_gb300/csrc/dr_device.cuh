@@ -98,6 +98,43 @@ __device__ __forceinline__ void load_coeffs(const S *__restrict__ p, int m, T (&
     for (int j = 0; j < M; ++j) out[j] = (j < m) ? ldc<T>(p + j) : T(0);
 }
 
+// Compute-typed rows of m (<= M) values that the calling kernel also writes:
+// plain (coherent) loads, and stores of the first m values; 16-byte vectors
+// when the row is a whole number of them.
+template <typename T, int M>
+__device__ __forceinline__ void load_row(const T *p, int m, T (&out)[M]) {
+    if constexpr (sizeof(T) == 4 && (M % 4) == 0) {
+        if (m == M) {
+#pragma unroll
+            for (int j = 0; j < M / 4; ++j) {
+                const float4 v = reinterpret_cast<const float4 *>(p)[j];
+                out[4 * j] = v.x;
+                out[4 * j + 1] = v.y;
+                out[4 * j + 2] = v.z;
+                out[4 * j + 3] = v.w;
+            }
+            return;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < M; ++j) out[j] = (j < m) ? p[j] : T(0);
+}
+
+template <typename T, int M>
+__device__ __forceinline__ void store_row(T *p, int m, const T (&v)[M]) {
+    if constexpr (sizeof(T) == 4 && (M % 4) == 0) {
+        if (m == M) {
+#pragma unroll
+            for (int j = 0; j < M / 4; ++j)
+                reinterpret_cast<float4 *>(p)[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+            return;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < M; ++j)
+        if (j < m) p[j] = v[j];
+}
+
 // ---------------------------------------------------------------------------
 // Reductions.  Each block reduces NV doubles, writes them to its partial
 // slot, and the last block to finish sums all partials in a fixed order, so

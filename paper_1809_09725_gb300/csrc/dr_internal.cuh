@@ -73,6 +73,17 @@ constexpr int kFwdGuard = 4; // zero cells on each side of a staged line
 // buffers when double-buffered): two CTAs of 256 threads still fit an SM.
 constexpr int kFoldStripBudget = 110 * 1024;
 constexpr int kFold2BlockVariants = 4;
+// Static-transform CTA configurations of the two-kernel folded forward:
+// gi = 0..5 with MC = 4 or 8 coefficients (odd gi: 8) and 256, 512 or 1024
+// threads (gi / 2).
+constexpr int kFold2Configs = 6;
+__host__ __device__ constexpr int fold_static_mc(int gi) { return (gi & 1) ? 8 : 4; }
+__host__ __device__ constexpr int fold_static_threads(int gi) { return 256 << (gi / 2); }
+// rays per thread
+__host__ __device__ constexpr int fold_static_rpt_gi(int gi) {
+    return gi < 4 ? 32 / fold_static_mc(gi) : 16 / fold_static_mc(gi);
+}
+__host__ __device__ constexpr int fold_static_rays(int gi) { return fold_static_threads(gi) * fold_static_rpt_gi(gi); }
 
 constexpr int kRedThreads = 256;
 constexpr int kRedBlocksMax = 1024;
@@ -168,9 +179,10 @@ struct dr_plan {
     // configurations gi = 0..5: 4 / 8 coefficients (odd gi: 8) x 256 / 512 / 1024 threads (gi / 2)
     // angle blocks: variant v spreads each stepping axis's angles evenly over v more
     // blocks than the fewest that fit a CTA (smaller blocks, more CTAs: fuller last wave)
-    int fold2_nchunk[6] = {}, fold2_R[6] = {};
-    int fold2_P[6][dr::kFold2BlockVariants] = {}, fold2_nblocks[6][dr::kFold2BlockVariants] = {};
-    int *d_fold2_blocks[6][dr::kFold2BlockVariants] = {};
+    int fold2_nchunk[dr::kFold2Configs] = {}, fold2_R[dr::kFold2Configs] = {};
+    int fold2_P[dr::kFold2Configs][dr::kFold2BlockVariants] = {};
+    int fold2_nblocks[dr::kFold2Configs][dr::kFold2BlockVariants] = {};
+    int *d_fold2_blocks[dr::kFold2Configs][dr::kFold2BlockVariants] = {};
     int fold2_bv = 0;                 // angle-block variant in use
     bool fold2_ok = false;
     int fold2_gi = 0;                 // configuration in use

@@ -37,16 +37,9 @@ constexpr int kFoldAdjStages = 2;
 __host__ __device__ constexpr int fold_ms(int M) { return M <= 4 ? 4 : ((M % 8 == 0) ? M + 4 : M); }
 __host__ __device__ constexpr int fold_rpt(int M) { return M <= 4 ? 8 : 32 / M; }
 
-// Static-transform CTAs of the two-kernel forward: configuration gi = 0..5
-// handles MC = 4 or 8 coefficients (odd gi: 8) with 256, 512 or 1024 threads
-// (gi / 2) and fold_static_rpt rays per thread: 1024 to 4096 rays per CTA.
-// The more rays a CTA carries, the more samples share each staged line.
-constexpr int kFoldStaticConfigs = 6;
-__host__ __device__ constexpr int fold_static_mc(int gi) { return (gi & 1) ? 8 : 4; }
-__host__ __device__ constexpr int fold_static_threads(int gi) { return 256 << (gi / 2); }
-__host__ __device__ constexpr int fold_static_rpt_gi(int gi) {
-    return gi < 4 ? 32 / fold_static_mc(gi) : 16 / fold_static_mc(gi);
-}
+// Static-transform CTAs of the two-kernel forward (configurations in
+// dr_internal.cuh): 1024 to 4096 rays per CTA.  The more rays a CTA carries,
+// the more samples share each staged line.
 // Strip element stride of a static group: 4 or 12 floats (bf16: 4 or 8).
 __host__ __device__ constexpr int fold_static_ps(int MC, bool bf16) {
     return bf16 ? (MC == 4 ? 4 : 8) : (MC == 4 ? 4 : 12);
@@ -499,15 +492,39 @@ __global__ void __launch_bounds__(kRedThreads)
         T acc[M];
 #pragma unroll
         for (int j = 0; j < M; ++j) acc[j] = T(0);
-        const int e = start[a + 1];
-        for (int idx = start[a]; idx < e; ++idx) {
-            const int mem = __ldg(member + idx);
-            const int k = mem >> 1;
-            const int bb = (mem & 1) ? (ns - 1 - b) : b;
-            const T gv = ldc<T>(g + ((size_t)z * K + k) * ns + bb);
-            const T *ph = phip + (size_t)k * MP;
+        const int e = __ldg(start + a + 1);
+        // members in groups of 4: their data loads are issued together (the
+        // accumulation keeps the member order)
+        constexpr int G = 4;
+        for (int idx0 = __ldg(start + a); idx0 < e; idx0 += G) {
+            int kq[G];
+            T gv[G];
 #pragma unroll
-            for (int j = 0; j < M; ++j) acc[j] = fmaf(__ldg(ph + j), gv, acc[j]);
+            for (int q = 0; q < G; ++q) {
+                const int idx = idx0 + q;
+                const int mem = idx < e ? __ldg(member + idx) : 0;
+                kq[q] = mem >> 1;
+                const int bb = (mem & 1) ? (ns - 1 - b) : b;
+                gv[q] = idx < e ? ldc<T>(g + ((size_t)z * K + kq[q]) * ns + bb) : T(0);
+            }
+#pragma unroll
+            for (int q = 0; q < G; ++q) {
+                if (idx0 + q >= e) break;
+                const T *ph = phip + (size_t)kq[q] * MP;
+                if constexpr (sizeof(T) == 4 && M % 4 == 0) {
+#pragma unroll
+                    for (int c = 0; c < M / 4; ++c) {
+                        const float4 f = __ldg(reinterpret_cast<const float4 *>(ph) + c);
+                        acc[4 * c] = fmaf(f.x, gv[q], acc[4 * c]);
+                        acc[4 * c + 1] = fmaf(f.y, gv[q], acc[4 * c + 1]);
+                        acc[4 * c + 2] = fmaf(f.z, gv[q], acc[4 * c + 2]);
+                        acc[4 * c + 3] = fmaf(f.w, gv[q], acc[4 * c + 3]);
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < M; ++j) acc[j] = fmaf(__ldg(ph + j), gv[q], acc[j]);
+                }
+            }
         }
         T *dst = gt + i * MS;
         if constexpr ((MS % 4) == 0 && sizeof(T) == 4) {

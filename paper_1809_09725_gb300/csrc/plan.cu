@@ -439,9 +439,9 @@ static dr_status build_tables(dr_plan *P) {
         P->gt_bytes = sizeof(float) * (size_t)P->nz * U * P->ns * MS;
         // two-kernel folded forward: work lists and strip budgets of the six
         // coefficient-group / CTA-size configurations
-        for (int gi = 0; gi < 6; ++gi) {  // 4 or 8 coefficients; 256, 512 or 1024 threads
-            const int MC = (gi & 1) ? 8 : 4;
-            const int rays2 = (256 << (gi / 2)) * (gi < 4 ? 32 / MC : 16 / MC);
+        for (int gi = 0; gi < kFold2Configs; ++gi) {
+            const int MC = fold_static_mc(gi);
+            const int rays2 = fold_static_rays(gi);
             int Pmax, nch2;
             if (P->ns <= rays2) { Pmax = std::min(64, rays2 / P->ns); nch2 = 1; }
             else { Pmax = 1; nch2 = (P->ns + rays2 - 1) / rays2; }

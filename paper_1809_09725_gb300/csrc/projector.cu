@@ -313,7 +313,7 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
             return P->fold2_R[gi] >= 1 && !(MC == 8 && P->m <= 4) &&
                    (size_t)P->nz * ((P->m + MC - 1) / MC) <= 65535;
         };
-        for (int gi = 0; gi < 6; ++gi) {
+        for (int gi = 0; gi < kFold2Configs; ++gi) {
             if (!gi_ok(gi)) continue;
             P->fold2_gi = gi;
             for (int c : {4, std::min(16, P->fold2_R[gi])}) {
@@ -626,8 +626,8 @@ dr_status dr_plan_info(const dr_plan *P, dr_plan_info_t *info) {
                          P->ru_split_bytes;
     info->fold_lines = P->fold_lines;
     info->fold_async = P->fold_async;
-    info->fold2_group = P->fold2_ok ? ((P->fold2_gi & 1) ? 8 : 4) : 0;
-    info->fold2_threads = P->fold2_ok ? (256 << (P->fold2_gi / 2)) : 0;
+    info->fold2_group = P->fold2_ok ? fold_static_mc(P->fold2_gi) : 0;
+    info->fold2_threads = P->fold2_ok ? fold_static_threads(P->fold2_gi) : 0;
     info->fold2_lines = P->fold2_ok ? P->fold2_lines : 0;
     info->fold2_split = P->fold2_ok ? P->fold2_split : 0;
     info->fold2_async = P->fold2_ok ? P->fold2_async : 0;

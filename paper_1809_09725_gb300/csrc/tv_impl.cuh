@@ -211,19 +211,26 @@ __global__ void __launch_bounds__(kRedThreads)
         vox_xyz(v, g, x, y, z);
         T o[M];
         gradT_voxel<T, M>(p, v, x, y, z, g, sm, lambda2, o);
+        if (u_c) {
+            // compute-typed row: vector loads and stores
+            T ov[M];
+#pragma unroll
+            for (int j = 0; j < M; ++j) o[j] = alpha * o[j];
+            if (beta != T(0)) {
+                load_row<T, M>(u_c + v * g.m, g.m, ov);
+#pragma unroll
+                for (int j = 0; j < M; ++j) o[j] += beta * ov[j];
+            }
+            store_row<T, M>(u_c + v * g.m, g.m, o);
+            continue;
+        }
 #pragma unroll
         for (int j = 0; j < M; ++j) {
             if (j >= g.m) break;
             const size_t i = v * g.m + j;
-            if (u_c) {
-                T r = alpha * o[j];
-                if (beta != T(0)) r += beta * u_c[i];
-                u_c[i] = r;
-            } else {
-                T r = alpha * o[j];
-                if (beta != T(0)) r += beta * ldc<T>(u_s + i);
-                stc<T>(u_s + i, r);
-            }
+            T r = alpha * o[j];
+            if (beta != T(0)) r += beta * ldc<T>(u_s + i);
+            stc<T>(u_s + i, r);
         }
     }
 }
@@ -341,21 +348,43 @@ __global__ void __launch_bounds__(kRedThreads, tv_min_blocks(M, sizeof(T)))
             for (int j = 0; j < M; ++j) ls[j] += xc[j] - nb[j];
         }
         T dotv = T(0);  // this voxel's m products in the compute type (sums in a PartialSum)
-#pragma unroll(M <= 16 ? M : 1)
-        for (int i = 0; i < M; ++i) {
-            if (i >= g.m) break;
-            T s = T(0);
+        if constexpr (M <= 16) {
+            // the row in registers: vector loads and stores of out (and pdir)
+            T rv[M], ov[M];
 #pragma unroll
-            for (int j = 0; j < M; ++j) s = fma(Gs[i * M + j], ls[j], fma(lam2sq * Ls[i * M + j], xc[j], s));
-            const size_t idx = v * g.m + i;
-            T r = alpha * s;
-            if (beta != T(0)) r += beta * out[idx];
-            out[idx] = r;
-            if (mode == 2) {
-                pdir[idx] = r;
-                dotv = fma(r, r, dotv);
-            } else {
-                dotv = fma(xv[idx], r, dotv);
+            for (int i = 0; i < M; ++i) {
+                T s = T(0);
+#pragma unroll
+                for (int j = 0; j < M; ++j) s = fma(Gs[i * M + j], ls[j], fma(lam2sq * Ls[i * M + j], xc[j], s));
+                rv[i] = alpha * s;
+            }
+            if (beta != T(0)) {
+                load_row<T, M>(out + v * g.m, g.m, ov);
+#pragma unroll
+                for (int i = 0; i < M; ++i) rv[i] += beta * ov[i];
+            }
+            store_row<T, M>(out + v * g.m, g.m, rv);
+            if (mode == 2) store_row<T, M>(pdir + v * g.m, g.m, rv);
+#pragma unroll
+            for (int i = 0; i < M; ++i)
+                if (i < g.m) dotv = mode == 2 ? fma(rv[i], rv[i], dotv) : fma(xc[i], rv[i], dotv);
+        } else {
+#pragma unroll 1
+            for (int i = 0; i < M; ++i) {
+                if (i >= g.m) break;
+                T s = T(0);
+#pragma unroll
+                for (int j = 0; j < M; ++j) s = fma(Gs[i * M + j], ls[j], fma(lam2sq * Ls[i * M + j], xc[j], s));
+                const size_t idx = v * g.m + i;
+                T r = alpha * s;
+                if (beta != T(0)) r += beta * out[idx];
+                out[idx] = r;
+                if (mode == 2) {
+                    pdir[idx] = r;
+                    dotv = fma(r, r, dotv);
+                } else {
+                    dotv = fma(xv[idx], r, dotv);
+                }
             }
         }
         acc.add(dotv);

@@ -53,7 +53,8 @@ class PlanInfo(ctypes.Structure):
     _fields_ = [("unique_angles", ctypes.c_int), ("max_group", ctypes.c_int), ("fwd_variant", ctypes.c_int),
                 ("adj_variant", ctypes.c_int), ("tuned", ctypes.c_int), ("device_bytes", ctypes.c_size_t),
                 ("fold_lines", ctypes.c_int), ("fold_async", ctypes.c_int), ("fold2_group", ctypes.c_int),
-                ("fold2_threads", ctypes.c_int), ("fold2_lines", ctypes.c_int), ("fold2_split", ctypes.c_int),
+                ("fold2_threads", ctypes.c_int), ("fold2_lines", ctypes.c_int),
+                ("fold2_split", ctypes.c_int),
                 ("fold2_async", ctypes.c_int), ("fold_adj_angles", ctypes.c_int),
                 ("fold2_angles", ctypes.c_int),
                 ("fwd_variant_storage", ctypes.c_int)]
