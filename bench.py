@@ -70,7 +70,7 @@ def parse():
                          "only); default: autotuned")
     ap.add_argument("--fold2-config", default=None,
                     help="with --variant 2,x or --profile-small: fix the two-kernel folded forward's "
-                         "'group,threads,lines[,split[,async]]' instead of the default")
+                         "'group,threads,lines[,split[,async[,rays_per_thread]]]' instead of the default")
     ap.add_argument("--fold-adj-angles", type=int, default=0,
                     help="with --variant x,1 or --profile-small: fix the folded adjoint's distinct angles per "
                          "pipeline stage instead of the default")
@@ -164,9 +164,9 @@ def replica_units(units_per_rank: float, world: int) -> float:
 
 
 def set_fold2_config(plan, text):
-    """Apply 'group,threads,lines[,split[,async]]' to the two-kernel folded forward."""
+    """Apply 'group,threads,lines[,split[,async[,rays_per_thread]]]' to the two-kernel folded forward."""
     v = [int(x) for x in text.split(",")]
-    plan.set_fold_groups(v[0], v[2], v[1])
+    plan.set_fold_groups(v[0], v[2], v[1], v[5] if len(v) > 5 else 0)
     plan.set_fold_march(v[3] if len(v) > 3 else 1, v[4] if len(v) > 4 else 0)
 
 
@@ -455,9 +455,9 @@ def run_ours(a):
                          "variants": {"unique_angles": U, "fwd": info["fwd_variant"], "adj": info["adj_variant"],
                                       "fold_lines": info["fold_lines"], "fold_async": info["fold_async"],
                                       "fold_adj_angles_per_stage": info["fold_adj_angles"],
-                                      "fold2_group_threads_lines_split_async": [
+                                      "fold2_group_threads_lines_split_async_rpt": [
                                           info["fold2_group"], info["fold2_threads"], info["fold2_lines"],
-                                          info["fold2_split"], info["fold2_async"]],
+                                          info["fold2_split"], info["fold2_async"], info["fold2_rays_per_thread"]],
                                       "autotune_ms_fwd_direct_fold_adj_direct_fold_fwd_fold2": tune}},
             "cpu_baseline": cpu,
             "serving": serving,

@@ -163,13 +163,16 @@ dr_status dr_plan_set_fold_strip(dr_plan *plan, int lines, int async);
 
 /*
  * Fix the two-kernel folded forward's configuration: coefficients per CTA
- * (group 4, or 8 when m > 4), CTA size (threads 256, 512 or 1024: 1024 to
- * 4096 rays per CTA) and strip height (lines >= 1, within the strip budget).  Every
+ * (group 4, or 8 when m > 4), CTA size and rays per thread, and strip height
+ * (lines >= 1, within the strip budget).  The configurations: threads 256 or
+ * 512 with 32 / group rays per thread, 1024 with 16 / group (one CTA per SM at
+ * 512 and 1024), and 512 with 16 / group (two CTAs per SM).  rays_per_thread
+ * 0 picks the most rays per thread for the group and CTA size.  Every
  * coefficient's ray sums run the same march whatever the choice: results are
  * identical.  DR_EINVAL if the variant is unavailable or the choice does not
- * fit.
+ * exist or fit.
  */
-dr_status dr_plan_set_fold_groups(dr_plan *plan, int group, int threads, int lines);
+dr_status dr_plan_set_fold_groups(dr_plan *plan, int group, int threads, int rays_per_thread, int lines);
 
 /*
  * Fix how the two-kernel folded forward marches its rays.  nsplit (1..8):
@@ -218,6 +221,7 @@ typedef struct {
     int fold_async;      /* folded forward: 1 if strips are double-buffered with cp.async */
     int fold2_group;     /* two-kernel folded forward: coefficients per CTA (0: unavailable) */
     int fold2_threads;   /* two-kernel folded forward: threads per CTA */
+    int fold2_rays_per_thread; /* two-kernel folded forward: rays each thread marches */
     int fold2_lines;     /* two-kernel folded forward: strip lines */
     int fold2_split;     /* two-kernel folded forward: line chunks of the march */
     int fold2_async;     /* two-kernel folded forward: 1 if strips are double-buffered with cp.async */

@@ -74,15 +74,18 @@ constexpr int kFwdGuard = 4; // zero cells on each side of a staged line
 constexpr int kFoldStripBudget = 110 * 1024;
 constexpr int kFold2BlockVariants = 4;
 // Static-transform CTA configurations of the two-kernel folded forward:
-// gi = 0..5 with MC = 4 or 8 coefficients (odd gi: 8) and 256, 512 or 1024
-// threads (gi / 2).
-constexpr int kFold2Configs = 6;
+// MC = 4 or 8 coefficients (odd gi: 8); gi = 0..5: 256, 512 or 1024 threads
+// (gi / 2), one CTA per SM at the larger sizes; gi = 6, 7: 512 threads with
+// half the rays, two CTAs per SM (<= 64 registers), so that one CTA's strip
+// barrier leaves the other running.
+constexpr int kFold2Configs = 8;
 __host__ __device__ constexpr int fold_static_mc(int gi) { return (gi & 1) ? 8 : 4; }
-__host__ __device__ constexpr int fold_static_threads(int gi) { return 256 << (gi / 2); }
+__host__ __device__ constexpr int fold_static_threads(int gi) { return gi < 6 ? 256 << (gi / 2) : 512; }
 // rays per thread
 __host__ __device__ constexpr int fold_static_rpt_gi(int gi) {
     return gi < 4 ? 32 / fold_static_mc(gi) : 16 / fold_static_mc(gi);
 }
+__host__ __device__ constexpr int fold_static_min_blocks(int gi) { return gi < 6 ? 1 : 2; }
 __host__ __device__ constexpr int fold_static_rays(int gi) { return fold_static_threads(gi) * fold_static_rpt_gi(gi); }
 
 constexpr int kRedThreads = 256;

@@ -172,8 +172,8 @@ __host__ __device__ constexpr int fold_fwd_min_blocks(int M) { return M == 8 ? 3
 // ru[((z U + a) ns + b) ms_ru + j]; fold_dist_kernel distributes them.  With
 // nsplit > 1 the march is split into nsplit chunks of image lines
 // (blockIdx.z); chunk c writes its partial sums at ru + c * split_stride.
-template <typename S, typename T, int M, bool STATIC, int THREADS = kFoldThreads, int RPTS = 0>
-__global__ void __launch_bounds__(THREADS, THREADS == kFoldThreads ? fold_fwd_min_blocks(M) : 1)
+template <typename S, typename T, int M, bool STATIC, int THREADS = kFoldThreads, int RPTS = 0, int MINB = 1>
+__global__ void __launch_bounds__(THREADS, THREADS == kFoldThreads ? fold_fwd_min_blocks(M) : MINB)
     fold_fwd_kernel(const S *__restrict__ u, S *__restrict__ out, const S *__restrict__ gm,
                     const FwdProj *__restrict__ uproj, const int *__restrict__ start, const int *__restrict__ member,
                     const T *__restrict__ phip, const int *__restrict__ blocks, int nx, int ny, int ns, int K,
@@ -735,7 +735,8 @@ dr_status fold_fwd_launch_t(dr_plan *P, const void *u, void *out, const void *gm
 template <typename S, typename T, int M, int GI>
 dr_status fold_fwd2_launch_mc(dr_plan *P, const void *u, void *out, const void *gm, int mode, double sigma,
                               cudaStream_t st) {
-    constexpr int MC = fold_static_mc(GI), THREADS = fold_static_threads(GI), RPT = fold_static_rpt_gi(GI);
+    constexpr int MC = fold_static_mc(GI), THREADS = fold_static_threads(GI), RPT = fold_static_rpt_gi(GI),
+                  MINB = fold_static_min_blocks(GI);
     constexpr bool BF16_STRIP = sizeof(S) == 2;
     using ST = std::conditional_t<BF16_STRIP, S, T>;
     constexpr int MS = fold_static_ps(MC, BF16_STRIP);
@@ -752,7 +753,7 @@ dr_status fold_fwd2_launch_mc(dr_plan *P, const void *u, void *out, const void *
     (void)VW;
     const int async = bf16_kernel ? P->fold2_async_st : P->fold2_async;
     const size_t smem = 768 + sizeof(ST) * (size_t)(async ? 2 : 1) * R * wpad * MS;
-    auto kern = fold_fwd_kernel<S, T, MC, true, THREADS, RPT>;
+    auto kern = fold_fwd_kernel<S, T, MC, true, THREADS, RPT, MINB>;
     {
         dr_status s = allow_dynamic_smem((const void *)kern, smem);
         if (s != DR_OK) return s;
@@ -802,6 +803,7 @@ dr_status fold_fwd2_launch_t(dr_plan *P, const void *u, void *out, const void *g
             case 0: return fold_fwd2_launch_mc<S, T, M, 0>(P, u, out, gm, mode, sigma, st);
             case 2: return fold_fwd2_launch_mc<S, T, M, 2>(P, u, out, gm, mode, sigma, st);
             case 4: return fold_fwd2_launch_mc<S, T, M, 4>(P, u, out, gm, mode, sigma, st);
+            case 6: return fold_fwd2_launch_mc<S, T, M, 6>(P, u, out, gm, mode, sigma, st);
             case 1:
                 if constexpr (M >= 8) return fold_fwd2_launch_mc<S, T, M, 1>(P, u, out, gm, mode, sigma, st);
                 break;
@@ -810,6 +812,9 @@ dr_status fold_fwd2_launch_t(dr_plan *P, const void *u, void *out, const void *g
                 break;
             case 5:
                 if constexpr (M >= 8) return fold_fwd2_launch_mc<S, T, M, 5>(P, u, out, gm, mode, sigma, st);
+                break;
+            case 7:
+                if constexpr (M >= 8) return fold_fwd2_launch_mc<S, T, M, 7>(P, u, out, gm, mode, sigma, st);
                 break;
         }
     }

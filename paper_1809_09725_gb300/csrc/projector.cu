@@ -1,12 +1,14 @@
 // projector.cu -- precision dispatch and C entry points of the dynamic
 // projector pair (Sec. 4, Eqs. radapr and radadjapr).  The kernels live in
 // projector_impl.cuh and are instantiated per precision in projector_*.cu.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <map>
 #include <mutex>
 #include <string>
 #include <tuple>
+#include <vector>
 
 #include "projector_impl.cuh"
 #include "fold_impl.cuh"
@@ -307,39 +309,57 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
         P->fold2_split = 1;
         P->fold2_async = 0;
         P->fold2_bv = 0;
-        // screen the group / CTA configurations at two strip heights, refine the best
+        // screen the group / CTA configurations, each with and without
+        // double-buffered cp.async strips (which doubles the strip memory and can
+        // halve the CTAs an SM holds) at two strip heights; refine the two best
         auto gi_ok = [&](int gi) {
-            const int MC = (gi & 1) ? 8 : 4;
+            const int MC = fold_static_mc(gi);
             return P->fold2_R[gi] >= 1 && !(MC == 8 && P->m <= 4) &&
                    (size_t)P->nz * ((P->m + MC - 1) / MC) <= 65535;
         };
+        struct Cand {
+            double t;
+            int gi, async, lines;
+        };
+        std::vector<Cand> cands;
         for (int gi = 0; gi < kFold2Configs; ++gi) {
             if (!gi_ok(gi)) continue;
             P->fold2_gi = gi;
-            for (int c : {4, std::min(16, P->fold2_R[gi])}) {
-                if (c > P->fold2_R[gi]) continue;
-                double t = 1e30;
-                dr_status s = run2(true)(c, t);
-                if (s != DR_OK) return s;
-                if (t < ms[4]) {
-                    ms[4] = t;
-                    bgi = gi;
-                    bl = c;
+            for (int as = 0; as < 2; ++as) {
+                P->fold2_async = as;
+                Cand best{1e30, gi, as, 1};
+                for (int c : {4, std::min(12, P->fold2_R[gi])}) {
+                    if (c > P->fold2_R[gi] || (c == best.lines && best.t < 1e30)) continue;
+                    double t = 1e30;
+                    dr_status s = run2(true)(c, t);
+                    if (s != DR_OK) return s;
+                    if (t < best.t) best = Cand{t, gi, as, c};
                 }
+                if (best.t < 1e30) cands.push_back(best);
+            }
+        }
+        std::sort(cands.begin(), cands.end(), [](const Cand &a, const Cand &b) { return a.t < b.t; });
+        int basync = 0;
+        for (size_t i = 0; i < cands.size() && i < 2; ++i) {
+            P->fold2_gi = cands[i].gi;
+            P->fold2_async = cands[i].async;
+            int l2 = cands[i].lines;
+            if (cands[i].t < ms[4]) {
+                ms[4] = cands[i].t;
+                bgi = cands[i].gi;
+                basync = cands[i].async;
+                bl = l2;
+            }
+            dr_status s = search_lines(P->fold2_R[cands[i].gi], run2(true), l2, ms[4], better);
+            if (s != DR_OK) return s;
+            if (better) {
+                bgi = cands[i].gi;
+                basync = cands[i].async;
+                bl = l2;
             }
         }
         P->fold2_gi = bgi;
-        {
-            dr_status s = search_lines(P->fold2_R[bgi], run2(true), bl, ms[4], better);
-            if (s != DR_OK) return s;
-        }
-        // double-buffered cp.async strips
-        {
-            P->fold2_async = 1;
-            dr_status s = search_lines(P->fold2_R[bgi], run2(true), bl, ms[4], better);
-            if (s != DR_OK) return s;
-            if (!better) P->fold2_async = 0;
-        }
+        P->fold2_async = basync;
         // smaller angle blocks (more CTAs, each with less work): a fuller last wave
         {
             int bbv = 0;
@@ -359,7 +379,7 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
         // march into line chunks (more CTAs; the distribution adds the partial sums)
         const long long ctas = (long long)P->fold2_nblocks[bgi][P->fold2_bv] * P->fold2_nchunk[bgi] * P->nz *
                                ((P->m + fold_static_mc(bgi) - 1) / fold_static_mc(bgi));
-        if (!P->split_off && ctas < 4LL * P->num_sms) {
+        if (!P->split_off && ctas < 4LL * P->num_sms * fold_static_min_blocks(bgi)) {
             const size_t chunk = sizeof(float) * (size_t)P->nz * P->fold_U * P->ns * ((P->m + 3) / 4 * 4);
             int bs = 1, bbv = P->fold2_bv;
             const int l0 = bl, bv0 = P->fold2_bv;
@@ -568,16 +588,23 @@ dr_status dr_plan_set_fold_strip(dr_plan *P, int lines, int async) {
     return DR_OK;
 }
 
-dr_status dr_plan_set_fold_groups(dr_plan *P, int group, int threads, int lines) {
+dr_status dr_plan_set_fold_groups(dr_plan *P, int group, int threads, int rays_per_thread, int lines) {
     clear_error();
     if (!P) return fail(DR_EINVAL, "dr_plan_set_fold_groups: NULL plan");
     if (!(P->fold_U > 0 && P->fold2_ok)) return fail(DR_EINVAL, "dr_plan_set_fold_groups: variant unavailable");
-    const int base = group == 4 ? 0 : (group == 8 ? 1 : -1);
-    const int gi = base < 0 ? -1 : base + (threads == 1024 ? 4 : (threads == 512 ? 2 : (threads == 256 ? 0 : -100)));
+    // the configuration with this group and CTA size, and these rays per thread
+    // (0: the most rays per thread that configuration family has)
+    int gi = -1;
+    for (int c = 0; c < kFold2Configs; ++c)
+        if (fold_static_mc(c) == group && fold_static_threads(c) == threads &&
+            (rays_per_thread == 0 ? (gi < 0 || fold_static_rpt_gi(c) > fold_static_rpt_gi(gi))
+                                  : fold_static_rpt_gi(c) == rays_per_thread))
+            gi = c;
     if (gi < 0 || (group == 8 && P->m <= 4) || lines < 1 || lines > P->fold2_R[gi] ||
         (size_t)P->nz * ((P->m + group - 1) / group) > 65535)
-        return fail(DR_EINVAL, "dr_plan_set_fold_groups: group must be 4 or 8 (8 only for m > 4), threads 256, "
-                               "512 or 1024, and lines within the strip budget");
+        return fail(DR_EINVAL, "dr_plan_set_fold_groups: no such configuration (group 4 or 8, 8 only for m > 4; "
+                               "threads 256, 512 or 1024 with their rays per thread) or lines outside the strip "
+                               "budget");
     P->fold2_gi = gi;
     P->fold2_lines = P->fold2_lines_st = lines;
     P->fold2_bv = 0;
@@ -628,6 +655,7 @@ dr_status dr_plan_info(const dr_plan *P, dr_plan_info_t *info) {
     info->fold_async = P->fold_async;
     info->fold2_group = P->fold2_ok ? fold_static_mc(P->fold2_gi) : 0;
     info->fold2_threads = P->fold2_ok ? fold_static_threads(P->fold2_gi) : 0;
+    info->fold2_rays_per_thread = P->fold2_ok ? fold_static_rpt_gi(P->fold2_gi) : 0;
     info->fold2_lines = P->fold2_ok ? P->fold2_lines : 0;
     info->fold2_split = P->fold2_ok ? P->fold2_split : 0;
     info->fold2_async = P->fold2_ok ? P->fold2_async : 0;

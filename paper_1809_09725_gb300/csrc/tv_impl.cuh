@@ -180,20 +180,41 @@ __device__ __forceinline__ void gradT_voxel(const T *__restrict__ p, size_t v, i
     for (int j = 0; j < M; ++j) outj[j] = T(0);
     const size_t sx = (size_t)g.nt * 4, sy = (size_t)g.nx * g.nt * 4, sz = (size_t)g.nx * g.ny * g.nt * 4;
     const T *pv = p + v * g.nt * 4;
-    for (int l = 0; l < g.nt; ++l) {
-        const typename V4<T>::type q = ld4<T>(pv + l * 4);
-        T s = T(0);
-        if (x + 1 < g.nx) s -= q.x;
-        if (x > 0) s += (pv - sx)[l * 4 + 0];
-        if (y + 1 < g.ny) s -= q.y;
-        if (y > 0) s += (pv - sy)[l * 4 + 1];
-        if (z + 1 < g.nz || g.zhi) s -= q.z;
-        if (z > 0 || g.zlo) s += (pv - sz)[l * 4 + 2];
-        const T qt = lambda2 * q.w;
-        const T *ph = sm + l * M;
-        const T *dp = dph + l * M;
+    const bool hx = x + 1 < g.nx, lx = x > 0, hy = y + 1 < g.ny, ly = y > 0;
+    const bool hz = z + 1 < g.nz || g.zhi, lz = z > 0 || g.zlo;
+    // frames in groups of FG: all their loads are issued before the sums
+    // (more bytes in flight per thread); the sums keep the frame order
+    constexpr int FG = 4;
+    for (int l0 = 0; l0 < g.nt; l0 += FG) {
+        typename V4<T>::type q[FG];
+        T nbx[FG], nby[FG], nbz[FG];
 #pragma unroll
-        for (int j = 0; j < M; ++j) outj[j] = fma(ph[j], s, fma(dp[j], qt, outj[j]));
+        for (int f = 0; f < FG; ++f) {
+            const int l = l0 + f;
+            if (l < g.nt) {
+                q[f] = ld4<T>(pv + l * 4);
+                nbx[f] = lx ? (pv - sx)[l * 4 + 0] : T(0);
+                nby[f] = ly ? (pv - sy)[l * 4 + 1] : T(0);
+                nbz[f] = lz ? (pv - sz)[l * 4 + 2] : T(0);
+            }
+        }
+#pragma unroll
+        for (int f = 0; f < FG; ++f) {
+            const int l = l0 + f;
+            if (l >= g.nt) break;
+            T s = T(0);
+            if (hx) s -= q[f].x;
+            if (lx) s += nbx[f];
+            if (hy) s -= q[f].y;
+            if (ly) s += nby[f];
+            if (hz) s -= q[f].z;
+            if (lz) s += nbz[f];
+            const T qt = lambda2 * q[f].w;
+            const T *ph = sm + l * M;
+            const T *dp = dph + l * M;
+#pragma unroll
+            for (int j = 0; j < M; ++j) outj[j] = fma(ph[j], s, fma(dp[j], qt, outj[j]));
+        }
     }
 }
 
@@ -244,8 +265,12 @@ __global__ void __launch_bounds__(kRedThreads)
 // (more warps in flight to cover the strided dual reads).
 __host__ __device__ constexpr int tv_min_blocks(int M, int T_bytes) { return (T_bytes == 4 && M <= 8) ? 4 : 1; }
 
+// prox keeps a group of frames' duals in registers besides the coefficient
+// differences: three CTAs per SM (85 registers) instead of four
+__host__ __device__ constexpr int prox_min_blocks(int M, int T_bytes) { return (T_bytes == 4 && M <= 8) ? 3 : 1; }
+
 template <typename T, typename S, int M>
-__global__ void __launch_bounds__(kRedThreads, tv_min_blocks(M, sizeof(T)))
+__global__ void __launch_bounds__(kRedThreads, prox_min_blocks(M, sizeof(T)))
     prox_kernel(const S *__restrict__ u, T *__restrict__ mu, T *__restrict__ w, const T *PhiF, const T *dPhiF, Geo g,
                 T rho, T lambda1, T lambda2, double *partials, unsigned *counter, DevScalars *scal, double *obj,
                 int use_iter) {
@@ -261,41 +286,52 @@ __global__ void __launch_bounds__(kRedThreads, tv_min_blocks(M, sizeof(T)))
         vox_xyz(v, g, x, y, z);
         T uc[M], ex[M], ey[M], ez[M];
         coeff_diffs<T, S, M>(u, v, x, y, z, g, uc, ex, ey, ez);
-        for (int l = 0; l < g.nt; ++l) {
-            T d[4];
-            grad_frame<T, M>(sm, l, ex, ey, ez, d[0], d[1], d[2]);
-            d[3] = dt_frame<T, M>(dph + l * M, lambda2, uc);
-            const size_t o = (v * g.nt + l) * 4;
-            const typename V4<T>::type mo = ld4<T>(mu + o);
-            const T mv[4] = {mo.x, mo.y, mo.z, mo.w};
-            T vv[4];
-            T n2 = T(0), dn2 = T(0);
+        // frames in groups of FG: the group's dual loads are issued first (more
+        // bytes in flight per thread); the frames are then processed in order
+        constexpr int FG = 2;
+        for (int l0 = 0; l0 < g.nt; l0 += FG) {
+            typename V4<T>::type mg[FG];
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                vv[c] = d[c] + mv[c] * irho;
-                n2 += vv[c] * vv[c];
-                dn2 += d[c] * d[c];
-            }
-            const T n = sqrt(n2);
-            const T f = (n > T(0)) ? fmax(T(0), T(1) - kappa / n) : T(0);
-            T mn[4], wn[4];
-            T pr = T(0);
+            for (int h = 0; h < FG; ++h)
+                if (l0 + h < g.nt) mg[h] = ld4<T>(mu + (v * g.nt + l0 + h) * 4);
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const T psi = vv[c] * f;
-                const T r = d[c] - psi;
-                pr = fma(r, r, pr);
-                mn[c] = mv[c] + rho * r;
-                wn[c] = psi - mn[c] * irho;
+            for (int h = 0; h < FG; ++h) {
+                const int l = l0 + h;
+                if (l >= g.nt) break;
+                T d[4];
+                grad_frame<T, M>(sm, l, ex, ey, ez, d[0], d[1], d[2]);
+                d[3] = dt_frame<T, M>(dph + l * M, lambda2, uc);
+                const size_t o = (v * g.nt + l) * 4;
+                const T mv[4] = {mg[h].x, mg[h].y, mg[h].z, mg[h].w};
+                T vv[4];
+                T n2 = T(0), dn2 = T(0);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    vv[c] = d[c] + mv[c] * irho;
+                    n2 += vv[c] * vv[c];
+                    dn2 += d[c] * d[c];
+                }
+                const T n = sqrt(n2);
+                const T f = (n > T(0)) ? fmax(T(0), T(1) - kappa / n) : T(0);
+                T mn[4], wn[4];
+                T pr = T(0);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const T psi = vv[c] * f;
+                    const T r = d[c] - psi;
+                    pr = fma(r, r, pr);
+                    mn[c] = mv[c] + rho * r;
+                    wn[c] = psi - mn[c] * irho;
+                }
+                // per-frame terms in the compute type; FP64 only across threads
+                acc_tv.add(sqrt(dn2));
+                acc_pr.add(pr);
+                typename V4<T>::type a, b;
+                a.x = mn[0]; a.y = mn[1]; a.z = mn[2]; a.w = mn[3];
+                b.x = wn[0]; b.y = wn[1]; b.z = wn[2]; b.w = wn[3];
+                st4<T>(mu + o, a);
+                st4<T>(w + o, b);
             }
-            // per-frame terms in the compute type; FP64 only across threads
-            acc_tv.add(sqrt(dn2));
-            acc_pr.add(pr);
-            typename V4<T>::type a, b;
-            a.x = mn[0]; a.y = mn[1]; a.z = mn[2]; a.w = mn[3];
-            b.x = wn[0]; b.y = wn[1]; b.z = wn[2]; b.w = wn[3];
-            st4<T>(mu + o, a);
-            st4<T>(w + o, b);
         }
     }
     double vals[2] = {acc_tv.value(), acc_pr.value()}, tot[2];

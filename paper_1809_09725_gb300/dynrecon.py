@@ -53,7 +53,8 @@ class PlanInfo(ctypes.Structure):
     _fields_ = [("unique_angles", ctypes.c_int), ("max_group", ctypes.c_int), ("fwd_variant", ctypes.c_int),
                 ("adj_variant", ctypes.c_int), ("tuned", ctypes.c_int), ("device_bytes", ctypes.c_size_t),
                 ("fold_lines", ctypes.c_int), ("fold_async", ctypes.c_int), ("fold2_group", ctypes.c_int),
-                ("fold2_threads", ctypes.c_int), ("fold2_lines", ctypes.c_int),
+                ("fold2_threads", ctypes.c_int),
+                ("fold2_rays_per_thread", ctypes.c_int), ("fold2_lines", ctypes.c_int),
                 ("fold2_split", ctypes.c_int),
                 ("fold2_async", ctypes.c_int), ("fold_adj_angles", ctypes.c_int),
                 ("fold2_angles", ctypes.c_int),
@@ -112,7 +113,7 @@ def load(path: str = LIB_PATH):
         "dr_plan_set_variant": (i, [vp, i, i]),
         "dr_plan_autotune": (i, [vp, pd]),
         "dr_plan_set_fold_strip": (i, [vp, i, i]),
-        "dr_plan_set_fold_groups": (i, [vp, i, i, i]),
+        "dr_plan_set_fold_groups": (i, [vp, i, i, i, i]),
         "dr_plan_set_fold_march": (i, [vp, i, i]),
         "dr_plan_set_fold_adj_stage": (i, [vp, i]),
         "dr_plan_set_fold_blocks": (i, [vp, i]),
@@ -265,9 +266,10 @@ class Plan:
         """Fix the folded forward's strip height and staging (results do not change)."""
         _check(load().dr_plan_set_fold_strip(self._h, int(lines), int(bool(async_copy))))
 
-    def set_fold_groups(self, group: int, lines: int, threads: int = 256):
-        """Fix the two-kernel folded forward's coefficient group (4, 8), CTA size and strip height."""
-        _check(load().dr_plan_set_fold_groups(self._h, int(group), int(threads), int(lines)))
+    def set_fold_groups(self, group: int, lines: int, threads: int = 256, rays_per_thread: int = 0):
+        """Fix the two-kernel folded forward's coefficient group (4, 8), CTA size,
+        rays per thread (0: the most for the group and CTA size) and strip height."""
+        _check(load().dr_plan_set_fold_groups(self._h, int(group), int(threads), int(rays_per_thread), int(lines)))
 
     def set_fold_march(self, nsplit: int = 1, async_stage: int = 0):
         """Two-kernel folded forward: line chunks of each ray's march, and

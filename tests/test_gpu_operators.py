@@ -399,8 +399,10 @@ def test_fold2_group_sizes_agree(prec):
     plan.set_variant(dr.FOLD2, dr.FOLD)
     ud = dev_tensor(u, prec)
     outs = []
-    for group, threads in ((4, 256), (8, 256), (4, 512), (8, 512), (4, 1024), (8, 1024)):
-        plan.set_fold_groups(group, 2, threads)
+    for group, threads, rpt in ((4, 256, 0), (8, 256, 0), (4, 512, 0), (8, 512, 0), (4, 1024, 0), (8, 1024, 0),
+                                (4, 512, 4), (8, 512, 2)):
+        plan.set_fold_groups(group, 2, threads, rpt)
+        assert plan.info()["fold2_rays_per_thread"] == (rpt or (32 if threads < 1024 else 16) // group)
         g = torch.zeros(plan.g_shape(), dtype=getattr(torch, plan.storage_dtype), device="cuda")
         dr.dyn_radon_fwd(plan, ud, g)
         plan.sync()
