@@ -428,10 +428,13 @@ def run_ours(a):
         # adjoint is two launches: data fold + back-projection), n_cg + 1 D^T D
         # (right-hand side + CG steps), prox, D^T w, n_cg updates, n_cg - 1
         # direction updates, the fidelity dot, the iteration counter
-        # (the two-kernel folded forward is two launches too: static transforms + distribution)
+        # (the two-kernel folded forward is two launches too: static transforms +
+        # distribution).  With both folded, the CG steps' R*R p is the folded
+        # normal operator: static transforms, Gram mix, back-projection.
         adj_launches = 2 if info["adj_variant"] == 1 else 1
         fwd_launches = 2 if info["fwd_variant"] == 2 else 1
-        launches_per_iter = (w.n_cg + 1) * (1 + fwd_launches + adj_launches) + 2 * w.n_cg + 3
+        normal_launches = 3 if (info["fwd_variant"], info["adj_variant"]) == (2, 1) else fwd_launches + adj_launches
+        launches_per_iter = ((1 + fwd_launches + adj_launches) + w.n_cg * (1 + normal_launches) + 2 * w.n_cg + 3)
         line = {
             "metric": "voxel*projection updates/s (dynamic projector + back-projector applications "
                       "inside ADMM-CG iterations)",

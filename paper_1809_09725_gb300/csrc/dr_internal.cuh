@@ -193,6 +193,7 @@ struct dr_plan {
     int fold2_split = 1;              // line chunks of the static march (partial sums added by the distribution)
     int fold2_async = 0, fold2_async_st = 0;  // double-buffered cp.async strips (compute-typed / bf16 kernels)
     int fold_adj_pp = 8;              // folded adjoint: distinct angles per pipeline stage
+    void *d_fold_gram = nullptr;      // [U][M][M] float: sum over an angle's projections of phi phi^T
     bool split_off = false;           // set while a slab-streamed solve borrows the plan (its memory is budgeted)
     void *d_ru_split = nullptr;       // partial sums of a split march (allocated on first use)
     size_t ru_split_bytes = 0;
@@ -293,6 +294,9 @@ dr_status launch_adj_variant(dr_plan *P, int variant, bool calc, const void *g, 
                              double beta, bool u_calc, cudaStream_t st);
 dr_status ensure_fold_scratch(dr_plan *P);
 dr_status ensure_split_scratch(dr_plan *P, size_t bytes);
+// y = R*R x on compute-typed buffers; gscratch: a projection-sized buffer used
+// when the folded normal operator does not apply
+dr_status launch_normal_calc(dr_plan *P, const void *x, void *y, void *gscratch, cudaStream_t st);
 // largest split scratch the autotuner may choose (small grids only need it)
 constexpr size_t kSplitScratchMax = 256ull << 20;
 dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch);

@@ -732,9 +732,16 @@ dr_status fold_fwd_launch_t(dr_plan *P, const void *u, void *out, const void *gm
 
 // Two-kernel folded forward: static transforms of coefficient groups of MC
 // (4 or 8) into the folded-data scratch, then the distribution.
+// Static transforms of the two-kernel forward (step 1), into the folded-data
+// scratch (one march) or the split scratch (line chunks); `rs` says where.
+struct StaticOut {
+    void *ru;
+    int ms_ru, nsplit;
+    size_t split_stride;
+};
+
 template <typename S, typename T, int M, int GI>
-dr_status fold_fwd2_launch_mc(dr_plan *P, const void *u, void *out, const void *gm, int mode, double sigma,
-                              cudaStream_t st) {
+dr_status fold_static_launch(dr_plan *P, const void *u, cudaStream_t st, StaticOut &rs) {
     constexpr int MC = fold_static_mc(GI), THREADS = fold_static_threads(GI), RPT = fold_static_rpt_gi(GI),
                   MINB = fold_static_min_blocks(GI);
     constexpr bool BF16_STRIP = sizeof(S) == 2;
@@ -779,47 +786,61 @@ dr_status fold_fwd2_launch_mc(dr_plan *P, const void *u, void *out, const void *
     }
     const int bv = P->d_fold2_blocks[gi][P->fold2_bv] ? P->fold2_bv : 0;
     dim3 grid(P->fold2_nblocks[gi][bv] * P->fold2_nchunk[gi], P->nz * ngroups, nsplit);
-    kern<<<grid, THREADS, smem, st>>>((const S *)u, (S *)out, (const S *)gm, P->d_fold_fwd, P->d_fold_start,
+    kern<<<grid, THREADS, smem, st>>>((const S *)u, (S *)nullptr, (const S *)nullptr, P->d_fold_fwd, P->d_fold_start,
                                            P->d_fold_member, (const T *)P->d_PhiP, P->d_fold2_blocks[gi][bv],
                                            P->nx, P->ny, P->ns, P->K, P->m, P->MP, P->fold2_P[gi][bv], R,
                                            P->fold2_nchunk[gi],
-                                           mode, (T)sigma, async, ngroups, ru, P->fold_U, ms_ru, nsplit,
+                                           0, (T)0, async, ngroups, ru, P->fold_U, ms_ru, nsplit,
                                            split_stride);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "fold_fwd_kernel (static) launch");
-    fold_dist_kernel<S, T, M><<<red_grid((size_t)P->nz * P->fold_U * P->ns), kRedThreads, 0, st>>>(
-        ru, (S *)out, (const S *)gm, P->d_fold_start, P->d_fold_member, (const T *)P->d_PhiP, P->nz, P->K, P->ns,
-        P->fold_U, ms_ru, P->m, P->MP, mode, (T)sigma, nsplit, split_stride);
-    e = cudaGetLastError();
-    return e == cudaSuccess ? DR_OK : cuda_fail(e, "fold_dist_kernel launch");
+    rs = StaticOut{ru, ms_ru, nsplit, split_stride};
+    return DR_OK;
 }
 
 template <typename S, typename T, int M>
-dr_status fold_fwd2_launch_t(dr_plan *P, const void *u, void *out, const void *gm, int mode, double sigma,
-                             cudaStream_t st) {
+dr_status fold_static_dispatch(dr_plan *P, const void *u, cudaStream_t st, StaticOut &rs) {
     if (!P->fold2_ok) return fail(DR_EINVAL, "two-kernel folded forward unavailable for this plan");
     if constexpr (M >= 4) {
         switch (P->fold2_gi) {
-            case 0: return fold_fwd2_launch_mc<S, T, M, 0>(P, u, out, gm, mode, sigma, st);
-            case 2: return fold_fwd2_launch_mc<S, T, M, 2>(P, u, out, gm, mode, sigma, st);
-            case 4: return fold_fwd2_launch_mc<S, T, M, 4>(P, u, out, gm, mode, sigma, st);
-            case 6: return fold_fwd2_launch_mc<S, T, M, 6>(P, u, out, gm, mode, sigma, st);
+            case 0: return fold_static_launch<S, T, M, 0>(P, u, st, rs);
+            case 2: return fold_static_launch<S, T, M, 2>(P, u, st, rs);
+            case 4: return fold_static_launch<S, T, M, 4>(P, u, st, rs);
+            case 6: return fold_static_launch<S, T, M, 6>(P, u, st, rs);
             case 1:
-                if constexpr (M >= 8) return fold_fwd2_launch_mc<S, T, M, 1>(P, u, out, gm, mode, sigma, st);
+                if constexpr (M >= 8) return fold_static_launch<S, T, M, 1>(P, u, st, rs);
                 break;
             case 3:
-                if constexpr (M >= 8) return fold_fwd2_launch_mc<S, T, M, 3>(P, u, out, gm, mode, sigma, st);
+                if constexpr (M >= 8) return fold_static_launch<S, T, M, 3>(P, u, st, rs);
                 break;
             case 5:
-                if constexpr (M >= 8) return fold_fwd2_launch_mc<S, T, M, 5>(P, u, out, gm, mode, sigma, st);
+                if constexpr (M >= 8) return fold_static_launch<S, T, M, 5>(P, u, st, rs);
                 break;
             case 7:
-                if constexpr (M >= 8) return fold_fwd2_launch_mc<S, T, M, 7>(P, u, out, gm, mode, sigma, st);
+                if constexpr (M >= 8) return fold_static_launch<S, T, M, 7>(P, u, st, rs);
                 break;
         }
     }
     return fail(DR_EINVAL, "two-kernel folded forward: unsupported coefficient group");
 }
+
+template <typename S, typename T, int M>
+dr_status fold_fwd2_launch_t(dr_plan *P, const void *u, void *out, const void *gm, int mode, double sigma,
+                             cudaStream_t st) {
+    StaticOut rs{};
+    {
+        dr_status s = fold_static_dispatch<S, T, M>(P, u, st, rs);
+        if (s != DR_OK) return s;
+    }
+    fold_dist_kernel<S, T, M><<<red_grid((size_t)P->nz * P->fold_U * P->ns), kRedThreads, 0, st>>>(
+        (const T *)rs.ru, (S *)out, (const S *)gm, P->d_fold_start, P->d_fold_member, (const T *)P->d_PhiP, P->nz,
+        P->K, P->ns, P->fold_U, rs.ms_ru, P->m, P->MP, mode, (T)sigma, rs.nsplit, rs.split_stride);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? DR_OK : cuda_fail(e, "fold_dist_kernel launch");
+}
+
+template <typename S, typename T, int M>
+dr_status fold_backproject(dr_plan *P, void *u, double alpha, double beta, bool u_calc, cudaStream_t st);
 
 template <typename S, typename T, int M>
 dr_status fold_adj_launch_t(dr_plan *P, const void *g, void *u, double alpha, double beta, bool u_calc,
@@ -831,7 +852,14 @@ dr_status fold_adj_launch_t(dr_plan *P, const void *g, void *u, double alpha, do
         P->K, P->MP);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "fold_data_kernel launch");
-    // step 2: back-project the folded sinograms
+    return fold_backproject<S, T, M>(P, u, alpha, beta, u_calc, st);
+}
+
+// Back-project the folded sinograms in the plan's scratch (step 2 of the
+// folded adjoint): u = alpha R*(folded) + beta u.
+template <typename S, typename T, int M>
+dr_status fold_backproject(dr_plan *P, void *u, double alpha, double beta, bool u_calc, cudaStream_t st) {
+    constexpr int MS = fold_ms(M);
     const int Wb = fold_adj_wb(M);
     CUtensorMap tm{};
     const uint64_t dims[3] = {(uint64_t)MS, (uint64_t)P->ns, (uint64_t)P->nz * P->fold_U};
@@ -855,8 +883,93 @@ dr_status fold_adj_launch_t(dr_plan *P, const void *g, void *u, double alpha, do
     dim3 grid(ntx * nty, P->nz);
     kern<<<grid, kAdjThreads, smem, st>>>(tm, P->d_fold_adj, u_calc ? nullptr : (S *)u, u_calc ? (T *)u : nullptr,
                                           P->nx, P->ny, P->fold_U, P->m, Wb, (T)alpha, (T)beta, P->d_status, pp);
-    e = cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? DR_OK : cuda_fail(e, "fold_adj_kernel launch");
+}
+
+// ===========================================================================
+// Normal operator R*R of the folded pair, as the CG steps use it.  Per
+// distinct angle a, forward then adjoint give
+//   (R*R u)_i = sum_a R_a* [ sum_j G_a[i][j] (R_a u_j) ],
+//   G_a = sum_{k in a} phi(t_k) phi(t_k)^T,
+// because the bin reversal of an odd half-turn is undone by its adjoint.  So
+// the static transforms are mixed by G_a per (slice, angle, bin) and
+// back-projected, without the K projections in between.
+// ===========================================================================
+template <typename T, int M>
+__global__ void __launch_bounds__(kRedThreads)
+    fold_gram_kernel(const T *ru, T *gt, const T *__restrict__ gram, int nz, int U, int ns, int ms_ru, int m,
+                     int nsplit, size_t split_stride) {
+    // ru and gt may be the same buffer (one chunk): each thread reads its row
+    // whole before writing it, so they are not declared __restrict__
+    constexpr int MS = fold_ms(M);
+    constexpr bool V4 = sizeof(T) == 4;
+    const size_t n = (size_t)nz * U * ns;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int a = (int)((i / ns) % U);
+        const T *r = ru + i * ms_ru;
+        T rv[M];
+#pragma unroll
+        for (int j = 0; j < M; ++j) {
+            T rj = T(0);
+            if (j < m) {
+                rj = r[j];
+                for (int c = 1; c < nsplit; ++c) rj += r[c * split_stride + j];
+            }
+            rv[j] = rj;
+        }
+        const T *G = gram + (size_t)a * M * M;
+        T ov[MS];
+#pragma unroll
+        for (int q = 0; q < MS; ++q) ov[q] = T(0);
+#pragma unroll
+        for (int q = 0; q < M; ++q) {
+            T acc = T(0);
+            if constexpr (V4 && M % 4 == 0) {
+#pragma unroll
+                for (int c = 0; c < M / 4; ++c) {
+                    const float4 gq = __ldg(reinterpret_cast<const float4 *>(G + q * M) + c);
+                    acc = fma(gq.x, rv[4 * c], acc);
+                    acc = fma(gq.y, rv[4 * c + 1], acc);
+                    acc = fma(gq.z, rv[4 * c + 2], acc);
+                    acc = fma(gq.w, rv[4 * c + 3], acc);
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < M; ++j) acc = fma(__ldg(G + q * M + j), rv[j], acc);
+            }
+            ov[q] = acc;
+        }
+        T *dst = gt + i * MS;
+        if constexpr (V4 && MS % 4 == 0) {
+#pragma unroll
+            for (int q = 0; q < MS / 4; ++q)
+                reinterpret_cast<float4 *>(dst)[q] = make_float4(ov[4 * q], ov[4 * q + 1], ov[4 * q + 2], ov[4 * q + 3]);
+        } else {
+#pragma unroll
+            for (int q = 0; q < MS; ++q) dst[q] = ov[q];
+        }
+    }
+}
+
+template <typename S, typename T, int M>
+dr_status fold_normal_launch_t(dr_plan *P, const void *x, void *y, cudaStream_t st) {
+    if (!P->d_fold_gram) return fail(DR_EINVAL, "folded normal operator unavailable for this plan");
+    StaticOut rs{};
+    {
+        dr_status s = fold_static_dispatch<S, T, M>(P, x, st, rs);
+        if (s != DR_OK) return s;
+    }
+    {
+        dr_status s = ensure_fold_scratch(P);
+        if (s != DR_OK) return s;
+    }
+    fold_gram_kernel<T, M><<<red_grid((size_t)P->nz * P->fold_U * P->ns), kRedThreads, 0, st>>>(
+        (const T *)rs.ru, (T *)P->d_gt, (const T *)P->d_fold_gram, P->nz, P->fold_U, P->ns, rs.ms_ru, P->m, rs.nsplit,
+        rs.split_stride);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "fold_gram_kernel launch");
+    return fold_backproject<S, T, M>(P, y, 1.0, 0.0, true, st);
 }
 
 template <typename S, typename T>
@@ -867,6 +980,8 @@ struct FoldOps {
                           cudaStream_t st);
     static dr_status adj(dr_plan *P, const void *g, void *u, double alpha, double beta, bool u_calc,
                          cudaStream_t st);
+    // y = R*R x on compute-typed buffers (static transforms, Gram mix, back-projection)
+    static dr_status normal(dr_plan *P, const void *x, void *y, cudaStream_t st);
 };
 
 #define DR_FOLD_DISPATCH(FN, S, T, ...)                   \
@@ -898,6 +1013,11 @@ template <typename S, typename T>
 dr_status FoldOps<S, T>::adj(dr_plan *P, const void *g, void *u, double alpha, double beta, bool u_calc,
                              cudaStream_t st) {
     DR_FOLD_DISPATCH(fold_adj_launch_t, S, T, P, g, u, alpha, beta, u_calc, st)
+}
+
+template <typename S, typename T>
+dr_status FoldOps<S, T>::normal(dr_plan *P, const void *x, void *y, cudaStream_t st) {
+    DR_FOLD_DISPATCH(fold_normal_launch_t, S, T, P, x, y, st)
 }
 
 extern template struct FoldOps<float, float>;

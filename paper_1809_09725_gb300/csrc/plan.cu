@@ -437,8 +437,27 @@ static dr_status build_tables(dr_plan *P) {
         if (!fb.empty())
             DR_CUDA_TRY(cudaMemcpy(P->d_fold_blocks, fb.data(), sizeof(int) * fb.size(), cudaMemcpyHostToDevice));
         P->gt_bytes = sizeof(float) * (size_t)P->nz * U * P->ns * MS;
-        // two-kernel folded forward: work lists and strip budgets of the six
-        // coefficient-group / CTA-size configurations
+        // per distinct angle the Gram matrix of its projections' basis rows:
+        // the folded normal operator R*R of the CG steps mixes by it
+        {
+            std::vector<float> gram((size_t)U * M * M, 0.0f);
+            std::vector<double> acc((size_t)m * m);
+            for (int a = 0; a < U; ++a) {
+                std::fill(acc.begin(), acc.end(), 0.0);
+                for (int i = start[a]; i < start[a + 1]; ++i) {
+                    const double *ph = &P->Phi[(size_t)(member[i] >> 1) * m];
+                    for (int q = 0; q < m; ++q)
+                        for (int j = 0; j < m; ++j) acc[(size_t)q * m + j] += ph[q] * ph[j];
+                }
+                for (int q = 0; q < m; ++q)
+                    for (int j = 0; j < m; ++j) gram[((size_t)a * M + q) * M + j] = (float)acc[(size_t)q * m + j];
+            }
+            DR_CUDA_TRY(cudaMalloc(&P->d_fold_gram, sizeof(float) * gram.size()));
+            DR_CUDA_TRY(cudaMemcpy(P->d_fold_gram, gram.data(), sizeof(float) * gram.size(), cudaMemcpyHostToDevice));
+            bytes += sizeof(float) * gram.size();
+        }
+        // two-kernel folded forward: work lists and strip budgets of the
+        // coefficient-group / CTA-shape configurations
         for (int gi = 0; gi < kFold2Configs; ++gi) {
             const int MC = fold_static_mc(gi);
             const int rays2 = fold_static_rays(gi);
@@ -585,7 +604,7 @@ dr_status dr_plan_destroy(dr_plan *P) {
                     P->d_dPhiF,      P->d_G,         P->d_Lt,         P->d_partials,    P->d_counters,
                     P->d_scal,       P->d_status,    P->d_fold_fwd,   P->d_fold_adj,    P->d_fold_start,
                     P->d_fold_member, P->d_fold_blocks, P->d_gt, P->d_fbp_taps, P->d_fbp_phi, P->d_fbp_q,
-                    P->d_fbp_u, P->d_ru_split};
+                    P->d_fbp_u, P->d_ru_split, P->d_fold_gram};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (auto &row : P->d_fold2_blocks)

@@ -111,6 +111,18 @@ dr_status launch_adj_calc(dr_plan *P, const void *g, void *u, double alpha, doub
     return launch_adj_variant(P, adj_choice(P), true, g, u, alpha, beta, true, st);
 }
 
+// y = R*R x: with the two-kernel folded forward and the folded adjoint, the
+// static transforms are mixed per distinct angle and back-projected directly;
+// otherwise forward into gscratch, then adjoint.
+dr_status launch_normal_calc(dr_plan *P, const void *x, void *y, void *gscratch, cudaStream_t st) {
+    if (P->prec != DR_F64 && P->fold_U > 0 && P->fold2_ok && P->d_fold_gram && fwd_choice(P) == 2 &&
+        adj_choice(P) == 1)
+        return FoldOps<float, float>::normal(P, x, y, st);
+    dr_status s = launch_fwd_calc(P, x, gscratch, nullptr, 0, 0.0, st);
+    if (s != DR_OK) return s;
+    return launch_adj_calc(P, gscratch, y, 1.0, 0.0, st);
+}
+
 // Autotuner: time the direct and folded variants of both projectors on the
 // plan's own geometry (compute-typed scratch buffers supplied by the
 // caller, contents overwritten) and keep the faster of each.  Explicit
@@ -185,8 +197,10 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
     DR_CUDA_TRY(cudaMemsetAsync(g_scratch, 0, ng_elems(P) * cs, st));
     double ms[5] = {1e30, 1e30, 1e30, 1e30, 1e30};
     double ms_st1 = 1e30, ms_st2 = 1e30;  // bf16-strip kernels of BF16 plans: fold, fold in two kernels
-    auto time_fwd = [&](int v, double &best, bool calc = true) -> dr_status {
-        for (int rep = 0; rep < 3; ++rep) {
+    // launches per trial: one warm-up, then the timed ones (reps - 1; the
+    // screening trials and the direct variant, timed only for comparison, take one)
+    auto time_fwd = [&](int v, double &best, bool calc = true, int reps = 3) -> dr_status {
+        for (int rep = 0; rep < reps; ++rep) {
             DR_CUDA_TRY(cudaEventRecord(e0, st));
             dr_status s = launch_fwd_variant(P, v, calc, u_scratch, g_scratch, nullptr, 0, 0.0, st);
             if (s != DR_OK) return s;
@@ -242,7 +256,7 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
         return DR_OK;
     };
     {
-        dr_status s = time_fwd(0, ms[0]);
+        dr_status s = time_fwd(0, ms[0], true, 2);
         if (s != DR_OK) return s;
     }
     if (P->fold_fwd_ok) {
@@ -260,7 +274,9 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
                 as ? P->fold_R / 2 : P->fold_R,
                 [&](int lines, double &t) {
                     P->fold_lines = lines;
-                    return time_fwd(1, t);
+                    // with the two-kernel form available, the fused kernel is timed
+                    // for comparison only (one timed launch per trial)
+                    return time_fwd(1, t, true, P->fold2_ok ? 2 : 3);
                 },
                 best_lines, ms[1], better);
             if (s != DR_OK) return s;
@@ -297,11 +313,11 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
         // height, staging mode, line chunks.  Group, CTA size, strip height and
         // staging change only which CTA computes a ray sum and when its lines
         // are copied: results do not depend on them.
-        auto run2 = [&](bool calc) {
-            return [&, calc](int lines, double &t) {
+        auto run2 = [&](bool calc, int reps = 3) {
+            return [&, calc, reps](int lines, double &t) {
                 if (calc) P->fold2_lines = lines;
                 else P->fold2_lines_st = lines;
-                return time_fwd(2, t, calc);
+                return time_fwd(2, t, calc, reps);
             };
         };
         bool better = false;
@@ -331,7 +347,7 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
                 for (int c : {4, std::min(12, P->fold2_R[gi])}) {
                     if (c > P->fold2_R[gi] || (c == best.lines && best.t < 1e30)) continue;
                     double t = 1e30;
-                    dr_status s = run2(true)(c, t);
+                    dr_status s = run2(true, 2)(c, t);
                     if (s != DR_OK) return s;
                     if (t < best.t) best = Cand{t, gi, as, c};
                 }
@@ -417,6 +433,28 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
                 }
             }
         }
+        // confirm the strip height against its neighbours with more timed
+        // launches (neighbouring heights often differ by less than the noise
+        // of the short trials above)
+        {
+            const int all[] = {1, 2, 3, 4, 6, 8, 12, 16};
+            int bi = 0;
+            while (bi < 7 && all[bi] != bl) ++bi;
+            double best_t = 1e30;
+            int best_c = bl;
+            for (int i : {bi - 1, bi, bi + 1}) {
+                if (i < 0 || i > 7 || all[i] > P->fold2_R[bgi]) continue;
+                double t = 1e30;
+                dr_status s = run2(true, 6)(all[i], t);
+                if (s != DR_OK) return s;
+                if (t < best_t) {
+                    best_t = t;
+                    best_c = all[i];
+                }
+            }
+            bl = best_c;
+            ms[4] = best_t;  // the chosen configuration's confirmed time
+        }
         P->fold2_lines = bl;
         P->fold2_lines_st = bl;
         P->fold2_async_st = P->fold2_async;
@@ -437,7 +475,7 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
     if (P->prec == DR_BF16_F32ACC) {
         // storage-typed calls of BF16 plans run the bf16-strip kernels: their own choice
         double ms_st0 = 1e30;
-        dr_status s0 = time_fwd(0, ms_st0, false);
+        dr_status s0 = time_fwd(0, ms_st0, false, 2);
         if (s0 != DR_OK) return s0;
         int best = 0;
         double bt = ms_st0;
@@ -445,8 +483,8 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
         if (ms_st2 < bt) { best = 2; bt = ms_st2; }
         P->sel_fwd_st = best;
     }
-    auto time_adj = [&](int v, double &best) -> dr_status {
-        for (int rep = 0; rep < 3; ++rep) {
+    auto time_adj = [&](int v, double &best, int reps = 3) -> dr_status {
+        for (int rep = 0; rep < reps; ++rep) {
             DR_CUDA_TRY(cudaEventRecord(e0, st));
             dr_status s = launch_adj_variant(P, v, true, g_scratch, u_scratch, 1.0, 0.0, true, st);
             if (s != DR_OK) return s;
@@ -459,7 +497,7 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
         return DR_OK;
     };
     {
-        dr_status s = time_adj(0, ms[2]);
+        dr_status s = time_adj(0, ms[2], 2);
         if (s != DR_OK) return s;
     }
     if (P->fold_U > 0) {

@@ -367,8 +367,7 @@ static dr_status admm_iteration(dr_plan *P, void *u, const void *g, const dr_sol
     // r += rho (D^T w - D^T D u); p = r; rr = <r,r>
     TRY(launch_rhs(P, u, w.w, w.r, w.p, rho, prm.lambda2, st));
     for (int c = 0; c < prm.n_cg; ++c) {
-        TRY(launch_fwd_calc(P, w.p, w.gd, nullptr, 0, 0.0, st));
-        TRY(launch_adj_calc(P, w.gd, w.q, 1.0, 0.0, st));
+        TRY(launch_normal_calc(P, w.p, w.q, w.gd, st));  // q = R*R p
         TRY(launch_lap(P, w.p, w.q, rho, 1.0, prm.lambda2, 1, st));
         TRY(vec(P, 0, u, w.r, w.p, w.q, nu, st));
         if (c + 1 < prm.n_cg) TRY(vec(P, 1, w.p, w.r, nullptr, nullptr, nu, st));
@@ -403,8 +402,7 @@ static dr_status power_norm(dr_plan *P, double lambda2, int iters, double *L, cu
     TRY(dot(P, x, x, nu, kSlotPow, nullptr, 0, 0, 1, st));
     TRY(vec(P, 3, x, x, nullptr, nullptr, nu, st));
     for (int it = 0; it < iters; ++it) {
-        TRY(launch_fwd_calc(P, x, w.gd, nullptr, 0, 0.0, st));
-        TRY(launch_adj_calc(P, w.gd, y, 1.0, 0.0, st));
+        TRY(launch_normal_calc(P, x, y, w.gd, st));  // y = R*R x
         TRY(launch_lap(P, x, y, 1.0, 1.0, lambda2, 0, st));
         TRY(dot(P, y, y, nu, kSlotPow, nullptr, 0, 0, 1, st));
         TRY(vec(P, 3, x, y, nullptr, nullptr, nu, st));

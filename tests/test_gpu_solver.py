@@ -79,13 +79,16 @@ F32_SOLVE_TOL_U = 3e-4
 F32_SOLVE_TOL_OBJ = 2e-3
 
 
-@pytest.mark.parametrize("variant", [dr.DIRECT, dr.FOLD])
-def test_admm_f32_matches_oracle(disks, disks_oracle_admm, variant):
+@pytest.mark.parametrize("fwd,adj", [(dr.DIRECT, dr.DIRECT), (dr.FOLD, dr.FOLD), (dr.FOLD2, dr.FOLD)])
+def test_admm_f32_matches_oracle(disks, disks_oracle_admm, fwd, adj):
+    """(FOLD2, FOLD) runs the CG products through the folded normal operator:
+    static transforms mixed per distinct angle by the Gram matrix of its
+    projections' basis rows, then back-projected."""
     w, theta, t, g, P = disks
     uo, oo, po = disks_oracle_admm["f32"]
     g32 = g.astype(np.float32).astype(np.float64)
     plan = dr.Plan(w.N, w.N, w.nz, w.ns, theta, t, w.basis, w.m, w.nt, dr.F32)
-    plan.set_variant(variant, variant)
+    plan.set_variant(fwd, adj)
     ud = torch.zeros(plan.u_shape(), dtype=torch.float32, device="cuda")
     prm = dr.solve_params(dr.ADMM_CG, iters=w.iters, n_cg=w.n_cg, lambda1=w.lambda1, lambda2=w.lambda2, rho=w.rho)
     res = dr.admm_solve(plan, dev_tensor(g32, dr.F32), ud, prm)
@@ -177,3 +180,25 @@ def test_solver_rejects_bad_parameters(disks):
     for bad in (dict(iters=-1), dict(n_cg=0), dict(lambda1=-1.0), dict(cp_theta=2.0, algo=dr.CHAMBOLLE_POCK)):
         with pytest.raises(dr.DynreconError):
             dr.admm_solve(plan, dev_tensor(g, dr.F32), ud, dr.solve_params(**bad))
+
+
+def test_folded_normal_operator_matches_forward_then_adjoint():
+    """One power-iteration estimate of ||[R; D]|| through the folded normal
+    operator equals the one through forward + adjoint to FP32 rounding, with
+    and without line chunks (Chambolle-Pock reports the norm it used)."""
+    args = (40, 36, 3, 44, *synth.scan(200, 5.0), dr.LEGENDRE, 6, 4)
+    nx, ny, nz, ns, theta, t, basis, m, nt = args
+    rng = synth.rng_for(61)
+    g = rng.standard_normal((nz, len(theta), ns)).astype(np.float32)
+    norms = {}
+    for key, fwd, nsplit in (("plain", dr.FOLD, 1), ("normal", dr.FOLD2, 1), ("normal_split", dr.FOLD2, 3)):
+        plan = dr.Plan(nx, ny, nz, ns, theta, t, basis, m, nt, dr.F32)
+        plan.set_variant(fwd, dr.FOLD)
+        if fwd == dr.FOLD2:
+            plan.set_fold_march(nsplit, 1)
+        u = torch.zeros(plan.u_shape(), dtype=torch.float32, device="cuda")
+        res = dr.admm_solve(plan, torch.from_numpy(g).cuda(), u,
+                            dr.solve_params(dr.CHAMBOLLE_POCK, iters=1, lambda1=0.01, lambda2=1.0, power_iters=30))
+        norms[key] = res["op_norm"]
+    assert abs(norms["normal"] - norms["plain"]) <= 1e-5 * norms["plain"]
+    assert abs(norms["normal_split"] - norms["plain"]) <= 1e-5 * norms["plain"]
