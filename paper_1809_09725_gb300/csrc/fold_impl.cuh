@@ -909,14 +909,38 @@ __global__ void __launch_bounds__(kRedThreads)
         const int a = (int)((i / ns) % U);
         const T *r = ru + i * ms_ru;
         T rv[M];
+        if constexpr (V4 && M % 4 == 0) {
+            // rows are multiples of 4 floats from 16-byte aligned bases
 #pragma unroll
-        for (int j = 0; j < M; ++j) {
-            T rj = T(0);
-            if (j < m) {
-                rj = r[j];
-                for (int c = 1; c < nsplit; ++c) rj += r[c * split_stride + j];
+            for (int q = 0; q < M / 4; ++q) {
+                if (4 * q < m) {
+                    float4 v = *reinterpret_cast<const float4 *>(r + 4 * q);
+                    for (int c = 1; c < nsplit; ++c) {
+                        const float4 w = *reinterpret_cast<const float4 *>(r + c * split_stride + 4 * q);
+                        v.x += w.x;
+                        v.y += w.y;
+                        v.z += w.z;
+                        v.w += w.w;
+                    }
+                    // slots at or beyond m: zero (the G rows and columns there are zero)
+                    rv[4 * q] = v.x;
+                    rv[4 * q + 1] = 4 * q + 1 < m ? v.y : T(0);
+                    rv[4 * q + 2] = 4 * q + 2 < m ? v.z : T(0);
+                    rv[4 * q + 3] = 4 * q + 3 < m ? v.w : T(0);
+                } else {
+                    rv[4 * q] = rv[4 * q + 1] = rv[4 * q + 2] = rv[4 * q + 3] = T(0);
+                }
             }
-            rv[j] = rj;
+        } else {
+#pragma unroll
+            for (int j = 0; j < M; ++j) {
+                T rj = T(0);
+                if (j < m) {
+                    rj = r[j];
+                    for (int c = 1; c < nsplit; ++c) rj += r[c * split_stride + j];
+                }
+                rv[j] = rj;
+            }
         }
         const T *G = gram + (size_t)a * M * M;
         T ov[MS];
