@@ -44,6 +44,16 @@ def smem_peak_tbs():
     return SMS * 128 * SM_MAX_GHZ * 1e9 / 1e12
 
 
+def hbm_peak_gbs():
+    """Measured copy bandwidth of this GPU model (generated file), else
+    the fallback figure of an earlier GB300 measurement."""
+    try:
+        with open(PEAKS_PATH) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json copy bandwidth)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback (6.8 TB/s, earlier GB300 copy measurement)"
+
+
 def fp32_peak_tflops(sm_mhz=None):
     ghz = (sm_mhz / 1000.0) if sm_mhz else SM_MAX_GHZ
     return SMS * FP32_LANES * 2 * ghz * 1e9 / 1e12
@@ -374,8 +384,10 @@ def run_ours(a):
 
     # FBP initial guess (Sec. 5), one window per half-turn: filter + one back-projection
     fbp = None
+    tv_kernels = None
     if not a.no_extras:
         fbp = run_fbp(plan, g, w, dev, stream)
+        tv_kernels = run_tv_kernels(plan, w, dev, stream)
 
     # end to end through the public call with host buffers (one full job per call)
     e2e = None
@@ -467,6 +479,7 @@ def run_ours(a):
             "accuracy_vs_fp64_oracle": accuracy,
             "batched_jobs": batched,
             "fbp_init": fbp,
+            "tv_kernels": tv_kernels,
             "bf16_operators": bf16_ops,
             "slab_streaming": slabs,
         }
@@ -536,6 +549,50 @@ def run_serving(a, device, prec):
                       "half-turns, m in {4,8,16}, 30 ADMM-CG iterations" % len(jobs),
             "max_queue_s": max(r["queue_s"] for r in res),
             "errors": [{"job": i, "rc": r["rc"], "error": r["error"]} for i, r in enumerate(res) if r["rc"] != 0]}
+
+
+def run_tv_kernels(plan, w, dev, stream, reps=10):
+    """The HBM-bound TV stencils through the C ABI on the workload's volume:
+    tv4d_prox (shrink + dual update: reads u and mu, writes mu and w),
+    tv4d_grad_adj (D^T p: reads p, writes u) and tv4d_grad (D u: reads u,
+    writes p), each timed alone with CUDA events; achieved = algorithmic
+    bytes / time against the measured HBM copy bandwidth."""
+    import torch
+
+    from paper_1809_09725_gb300 import dynrecon as dr
+
+    V = w.voxels()
+    ub = w.m * V * 4  # u, float
+    fb = 4 * w.nt * V * 4  # one dual field, float
+    u = torch.randn(plan.u_shape(), dtype=torch.float32, device=dev)
+    mu = torch.randn(plan.field_shape(), dtype=torch.float32, device=dev) * 1e-3
+    wf = torch.empty_like(mu)
+    ua = torch.empty_like(u)
+    peak, src = hbm_peak_gbs()
+    calls = {
+        "prox": (lambda: dr.tv4d_prox(plan, u, mu, wf, w.rho, w.lambda1, w.lambda2), ub + 3 * fb),
+        "grad_adj": (lambda: dr.tv4d_grad_adj(plan, wf, ua, w.lambda2), fb + ub),
+        "grad": (lambda: dr.tv4d_grad(plan, u, wf, w.lambda2), ub + fb),
+        "normal": (lambda: dr.tv4d_normal(plan, u, ua, w.lambda2, 1.0), 3 * ub),
+    }
+    out = {"hbm_peak_gbs": peak, "peak_source": src,
+           "note": "one call each through the C ABI, inputs %.0f MB > L2; algorithmic bytes: prox u + 3 fields, "
+                   "grad_adj and grad one field + u, normal (out += D^T D x, as in a CG step) 3 x u; u alone "
+                   "(%.0f MB) fits in L2" % ((ub + fb) / 1e6, ub / 1e6)}
+    for name, (fn, nbytes) in calls.items():
+        for _ in range(3):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        gbs = nbytes / (ms * 1e-3) / 1e9
+        out[name] = {"ms": ms, "bytes": nbytes, "achieved_gbs": gbs, "frac": gbs / peak}
+    return out
 
 
 def run_fbp(plan, g, w, dev, stream):

@@ -22,8 +22,8 @@
  * Layouts (row-major, last index fastest; all arrays dense):
  *   u    [nz][ny][nx][m]      coefficient volumes
  *   g    [nz][K][ns]          projection data
- *   p,mu,w [nz][ny][nx][nt][4] 4-vector fields on frames
- *        (components d/dx, d/dy, d/dz, lambda2 d/dt)
+ *   p,mu,w [nz][nt][ny][nx][4] 4-vector fields on frames, frame-major
+ *        within each slice (components d/dx, d/dy, d/dz, lambda2 d/dt)
  * Element type is set by the plan's precision:
  *   DR_F32          u, g, fields: float
  *   DR_BF16_F32ACC  u, g: bfloat16 (raw 16-bit); fields: float; all
@@ -306,7 +306,7 @@ dr_status dr_fbp_init(dr_plan *plan, const void *g, void *u, int n_windows);
 /*
  * 4D gradient of the synthesised frames, D = nabla_{lambda2} o PhiF
  * (Eq. TV1; frames f(t_l) = sum_j phi_j(t_l) u_j):  p = D u.
- * u: device [nz][ny][nx][m]; p: device [nz][ny][nx][nt][4] (overwritten).
+ * u: device [nz][ny][nx][m]; p: device [nz][nt][ny][nx][4] (overwritten).
  */
 dr_status tv4d_grad(dr_plan *plan, const void *u, void *p, double lambda2);
 
@@ -317,11 +317,24 @@ dr_status tv4d_grad(dr_plan *plan, const void *u, void *p, double lambda2);
 dr_status tv4d_grad_adj(dr_plan *plan, const void *p, void *u, double lambda2, double beta);
 
 /*
+ * The regulariser's normal operator, the D^T D term of the ADMM u-step
+ * operator R*R + rho D^T D (D of Eq. TV1, D^T its adjoint, Sec. 3):
+ *     out = beta * out + D^T D x
+ * applied without forming D x: with G = PhiF^T PhiF and Lt = PhiF^T L_t PhiF
+ * (m x m, built in double at plan time), D^T D = G (x) L_s + lambda2^2 Lt,
+ * L_s / L_t the Neumann Laplacians in space and over the frames.
+ * x, out: device [nz][ny][nx][m] in the plan's COMPUTE type (float for
+ * DR_F32 and DR_BF16_F32ACC plans, double for DR_F64), distinct buffers.
+ * DR_EINVAL for NULL pointers, x == out, or non-finite lambda2/beta.
+ */
+dr_status tv4d_normal(dr_plan *plan, const void *x, void *out, double lambda2, double beta);
+
+/*
  * ADMM proximal and dual step on psi = D u (the shrink is the Moreau dual of
  * the projection that Sec. 3 uses as prox of sigma F_2^*):
  *     v = D u + mu/rho;  psi = v * max(0, 1 - (lambda1/rho)/|v|)  per (voxel, frame);
  *     mu <- mu + rho (D u - psi);  w <- psi - mu/rho.
- * u: device [nz][ny][nx][m]; mu (in/out), w (out): device [nz][ny][nx][nt][4].
+ * u: device [nz][ny][nx][m]; mu (in/out), w (out): device [nz][nt][ny][nx][4].
  * primal_res: HOST double, nullable; when given the call synchronises and
  * stores ||D u - psi||_2 (accumulated in double).  rho > 0, lambda1 >= 0.
  */

@@ -125,7 +125,7 @@ struct Workspace {
     void *ut = nullptr, *uold = nullptr;            // CP
     void *gd = nullptr;                             // data-sized scratch (S)
     void *h1 = nullptr;                             // CP dual, data sized (S)
-    void *mu = nullptr, *w = nullptr;               // [V][nt][4] field type
+    void *mu = nullptr, *w = nullptr;               // [nz][nt][ny][nx][4] field type
     void *u_dev = nullptr, *g_dev = nullptr;        // staging copies of host buffers
     double *obj = nullptr;                          // [iters][3] fid, tv, primal^2
     int obj_cap = 0;

@@ -81,6 +81,15 @@ dr_status tv4d_grad_adj(dr_plan *P, const void *p, void *u, double lambda2, doub
     return launch_grad_adj(P, p, u, false, lambda2, 1.0, beta, P->stream);
 }
 
+dr_status tv4d_normal(dr_plan *P, const void *x, void *out, double lambda2, double beta) {
+    clear_error();
+    if (!P || !x || !out) return fail(DR_EINVAL, "tv4d_normal: NULL argument");
+    if (x == out) return fail(DR_EINVAL, "tv4d_normal: x and out must be distinct buffers");
+    if (!(lambda2 >= 0.0) || !std::isfinite(lambda2) || !std::isfinite(beta))
+        return fail(DR_EINVAL, "tv4d_normal: bad lambda2/beta");
+    return launch_lap(P, x, out, 1.0, beta, lambda2, 0, P->stream);
+}
+
 dr_status tv4d_prox(dr_plan *P, const void *u, void *mu, void *w, double rho, double lambda1, double lambda2,
                     double *primal_res) {
     clear_error();

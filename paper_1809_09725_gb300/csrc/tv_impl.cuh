@@ -70,6 +70,16 @@ __device__ __forceinline__ void vox_xyz(size_t v, const Geo &g, int &x, int &y, 
     z = (int)(r / g.ny);
 }
 
+// 4-vector fields on frames (D u, the duals) are stored frame-major within
+// each slice, [nz][nt][ny][nx][4]: the threads of a warp (consecutive voxels)
+// read or write one frame as one contiguous run of 16-byte vectors, and a
+// z-slab of slices is still one contiguous block.  field_base is the offset
+// of voxel v's frame 0; frame l adds l * frame_stride.
+__device__ __forceinline__ size_t field_base(size_t v, int z, const Geo &g) {
+    return (v + (size_t)z * (g.nt - 1) * g.nx * g.ny) * 4;
+}
+__device__ __forceinline__ size_t frame_stride(const Geo &g) { return (size_t)g.nx * g.ny * 4; }
+
 // Shared-memory copies of PhiF / dPhiF ([nt][M]) and G / Lt ([M][M]).
 template <typename T, int M>
 __device__ __forceinline__ void load_tables(T *sm, const T *PhiF, const T *dPhiF, const T *G, const T *Lt, int nt,
@@ -157,6 +167,7 @@ __global__ void __launch_bounds__(kRedThreads)
         vox_xyz(v, g, x, y, z);
         T uc[M], ex[M], ey[M], ez[M];
         coeff_diffs<T, S, M>(u, v, x, y, z, g, uc, ex, ey, ez);
+        const size_t fb = field_base(v, z, g), fs = frame_stride(g);
         for (int l = 0; l < g.nt; ++l) {
             T gx, gy, gz, gt;
             grad_frame<T, M>(sm, l, ex, ey, ez, gx, gy, gz);
@@ -166,7 +177,7 @@ __global__ void __launch_bounds__(kRedThreads)
             o.y = gy;
             o.z = gz;
             o.w = gt;
-            st4<T>(p + (v * g.nt + l) * 4, o);
+            st4<T>(p + fb + l * fs, o);
         }
     }
 }
@@ -178,8 +189,9 @@ __device__ __forceinline__ void gradT_voxel(const T *__restrict__ p, size_t v, i
     const T *dph = sm + g.nt * M;
 #pragma unroll
     for (int j = 0; j < M; ++j) outj[j] = T(0);
-    const size_t sx = (size_t)g.nt * 4, sy = (size_t)g.nx * g.nt * 4, sz = (size_t)g.nx * g.ny * g.nt * 4;
-    const T *pv = p + v * g.nt * 4;
+    const size_t fs = frame_stride(g);
+    const size_t sx = 4, sy = (size_t)g.nx * 4, sz = (size_t)g.nt * fs;
+    const T *pv = p + field_base(v, z, g);
     const bool hx = x + 1 < g.nx, lx = x > 0, hy = y + 1 < g.ny, ly = y > 0;
     const bool hz = z + 1 < g.nz || g.zhi, lz = z > 0 || g.zlo;
     // frames in groups of FG: all their loads are issued before the sums
@@ -192,10 +204,10 @@ __device__ __forceinline__ void gradT_voxel(const T *__restrict__ p, size_t v, i
         for (int f = 0; f < FG; ++f) {
             const int l = l0 + f;
             if (l < g.nt) {
-                q[f] = ld4<T>(pv + l * 4);
-                nbx[f] = lx ? (pv - sx)[l * 4 + 0] : T(0);
-                nby[f] = ly ? (pv - sy)[l * 4 + 1] : T(0);
-                nbz[f] = lz ? (pv - sz)[l * 4 + 2] : T(0);
+                q[f] = ld4<T>(pv + l * fs);
+                nbx[f] = lx ? (pv - sx)[l * fs + 0] : T(0);
+                nby[f] = ly ? (pv - sy)[l * fs + 1] : T(0);
+                nbz[f] = lz ? (pv - sz)[l * fs + 2] : T(0);
             }
         }
 #pragma unroll
@@ -289,11 +301,12 @@ __global__ void __launch_bounds__(kRedThreads, prox_min_blocks(M, sizeof(T)))
         // frames in groups of FG: the group's dual loads are issued first (more
         // bytes in flight per thread); the frames are then processed in order
         constexpr int FG = 2;
+        const size_t fb = field_base(v, z, g), fs = frame_stride(g);
         for (int l0 = 0; l0 < g.nt; l0 += FG) {
             typename V4<T>::type mg[FG];
 #pragma unroll
             for (int h = 0; h < FG; ++h)
-                if (l0 + h < g.nt) mg[h] = ld4<T>(mu + (v * g.nt + l0 + h) * 4);
+                if (l0 + h < g.nt) mg[h] = ld4<T>(mu + fb + (l0 + h) * fs);
 #pragma unroll
             for (int h = 0; h < FG; ++h) {
                 const int l = l0 + h;
@@ -301,7 +314,7 @@ __global__ void __launch_bounds__(kRedThreads, prox_min_blocks(M, sizeof(T)))
                 T d[4];
                 grad_frame<T, M>(sm, l, ex, ey, ez, d[0], d[1], d[2]);
                 d[3] = dt_frame<T, M>(dph + l * M, lambda2, uc);
-                const size_t o = (v * g.nt + l) * 4;
+                const size_t o = fb + l * fs;
                 const T mv[4] = {mg[h].x, mg[h].y, mg[h].z, mg[h].w};
                 T vv[4];
                 T n2 = T(0), dn2 = T(0);
@@ -462,11 +475,12 @@ __global__ void __launch_bounds__(kRedThreads)
         vox_xyz(v, g, x, y, z);
         T uc[M], ex[M], ey[M], ez[M];
         coeff_diffs<T, T, M>(ut, v, x, y, z, g, uc, ex, ey, ez);
+        const size_t fb = field_base(v, z, g), fs = frame_stride(g);
         for (int l = 0; l < g.nt; ++l) {
             T d[4];
             grad_frame<T, M>(sm, l, ex, ey, ez, d[0], d[1], d[2]);
             d[3] = dt_frame<T, M>(dph + l * M, lambda2, uc);
-            const size_t o = (v * g.nt + l) * 4;
+            const size_t o = fb + l * fs;
             typename V4<T>::type h = ld4<T>(h2 + o);
             h.x += sigma * d[0];
             h.y += sigma * d[1];

@@ -32,8 +32,8 @@ _STATUS = {DR_EINVAL: "EINVAL", DR_ENOMEM: "ENOMEM", DR_ECUDA: "ECUDA", DR_ETIME
 EXPORTS = ("dr_plan_create", "dr_plan_destroy", "dr_plan_set_stream", "dr_plan_device_bytes",
            "dr_plan_workspace_bytes", "dr_plan_sync", "dr_plan_set_variant", "dr_plan_autotune",
            "dr_plan_set_fold_strip", "dr_plan_set_fold_groups", "dr_plan_set_fold_march", "dr_plan_set_fold_adj_stage", "dr_plan_set_fold_blocks", "dr_plan_info",
-           "dyn_radon_fwd", "dyn_radon_adj", "dyn_radon_adj_noalloc", "dr_fbp_init", "tv4d_grad", "tv4d_grad_adj", "tv4d_prox",
-           "dr_solve_params_default", "admm_solve", "admm_solve_batch", "cp_solve_slabs",
+           "dyn_radon_fwd", "dyn_radon_adj", "dyn_radon_adj_noalloc", "dr_fbp_init", "tv4d_grad", "tv4d_grad_adj", "tv4d_normal",
+           "tv4d_prox", "dr_solve_params_default", "admm_solve", "admm_solve_batch", "cp_solve_slabs",
            "cp_solve_slabs_device_bytes", "dr_job_device_bytes", "dr_job_slab_device_bytes", "dr_server_create",
            "dr_server_submit", "dr_server_cancel", "dr_server_wait", "dr_server_stats", "dr_server_destroy",
            "dr_last_error", "dr_version")
@@ -124,6 +124,7 @@ def load(path: str = LIB_PATH):
         "dr_fbp_init": (i, [vp, vp, vp, i]),
         "tv4d_grad": (i, [vp, vp, vp, d]),
         "tv4d_grad_adj": (i, [vp, vp, vp, d, d]),
+        "tv4d_normal": (i, [vp, vp, vp, d, d]),
         "tv4d_prox": (i, [vp, vp, vp, vp, d, d, d, pd]),
         "dr_solve_params_default": (None, [ctypes.POINTER(SolveParams)]),
         "admm_solve": (i, [vp, vp, vp, ctypes.POINTER(SolveParams)]),
@@ -231,7 +232,9 @@ class Plan:
         return (self.nz, self.K, self.ns)
 
     def field_shape(self):
-        return (self.nz, self.ny, self.nx, self.nt, 4)
+        """4-vector fields on frames (D u, the ADMM duals): frame-major within
+        each slice, [nz][nt][ny][nx][4]."""
+        return (self.nz, self.nt, self.ny, self.nx, 4)
 
     @property
     def storage_dtype(self) -> str:
@@ -351,6 +354,15 @@ def tv4d_grad_adj(plan: Plan, p, u, lambda2: float, beta: float = 0.0):
                                 _ptr(u, plan.storage_dtype, plan.u_shape(), "u"), float(lambda2),
                                 float(beta)))
     return u
+
+
+def tv4d_normal(plan: Plan, x, out, lambda2: float, beta: float = 0.0):
+    """out = beta out + D^T D x on compute-typed coefficient arrays (the
+    plan's field dtype: float for F32/BF16 plans, double for F64)."""
+    plan.use_current_stream()
+    _check(load().tv4d_normal(plan.handle, _ptr(x, plan.field_dtype, plan.u_shape(), "x"),
+                              _ptr(out, plan.field_dtype, plan.u_shape(), "out"), float(lambda2), float(beta)))
+    return out
 
 
 def tv4d_prox(plan: Plan, u, mu, w, rho: float, lambda1: float, lambda2: float,

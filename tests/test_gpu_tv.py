@@ -33,6 +33,16 @@ CASES = {
 }
 
 
+def _to_field(a):
+    """Oracle layout [nz][ny][nx][nt][4] -> the library's [nz][nt][ny][nx][4]."""
+    return np.ascontiguousarray(np.asarray(a).transpose(0, 3, 1, 2, 4))
+
+
+def _from_field(a):
+    """The library's [nz][nt][ny][nx][4] -> oracle layout [nz][ny][nx][nt][4]."""
+    return np.asarray(a).transpose(0, 2, 3, 1, 4)
+
+
 def _setup(case, seed=0):
     nx, ny, nz, basis, m, nt = CASES[case]
     K = 8
@@ -59,9 +69,9 @@ def test_grad_and_adjoint(case, prec, tol):
     pg = torch.zeros(plan.field_shape(), dtype=fdt, device="cuda")
     dr.tv4d_grad(plan, dev_tensor(u, prec), pg, lam2)
     ua = torch.zeros(plan.u_shape(), dtype=getattr(torch, plan.storage_dtype), device="cuda")
-    dr.tv4d_grad_adj(plan, dev_tensor(p, prec), ua, lam2)
+    dr.tv4d_grad_adj(plan, dev_tensor(_to_field(p), prec), ua, lam2)
     plan.sync()
-    assert rel(host_values(pg), P.D(u, lam2)) <= tol
+    assert rel(_from_field(host_values(pg)), P.D(u, lam2)) <= tol
     assert rel(host_values(ua), P.DT(p, lam2)) <= tol
 
 
@@ -70,9 +80,52 @@ def test_grad_adj_beta(case):
     args, P, u, p, _ = _setup(case, seed=1)
     plan = dr.Plan(*args, prec=dr.F64)
     ut = dev_tensor(u, dr.F64)
-    dr.tv4d_grad_adj(plan, dev_tensor(p, dr.F64), ut, 0.6, beta=2.5)
+    dr.tv4d_grad_adj(plan, dev_tensor(_to_field(p), dr.F64), ut, 0.6, beta=2.5)
     plan.sync()
     assert rel(host_values(ut), 2.5 * u + P.DT(p, 0.6)) <= 1e-12
+
+
+# Tall volumes: enough (x, y) tiles x slices that the z-marching D^T D kernel
+# walks runs of several slices (carrying rows between steps), with a ragged
+# last run, tiles cut by nx and ny, and m below the template size.
+TALL = {"tall_m8": (40, 20, 400, dr.FOURIER, 8, 3), "tall_m5": (33, 9, 700, dr.LEGENDRE, 5, 4),
+        "tall_m16": (70, 17, 150, dr.FOURIER, 16, 2)}
+
+
+@pytest.mark.parametrize("case", sorted(CASES) + sorted(TALL))
+@pytest.mark.parametrize("prec,tol", [(dr.F64, 1e-12), (dr.F32, 1e-5)])
+def test_normal_matches_oracle(case, prec, tol):
+    """out = beta out + D^T D x against the oracle's D^T (D x)."""
+    if case in TALL:
+        nx, ny, nz, basis, m, nt = TALL[case]
+        theta, t = synth.scan(8, 2.0)
+        args = (nx, ny, nz, 9, theta, t, basis, m, nt)
+        P = oracle.Problem(*args)
+        rng = synth.rng_for(900 + sum(map(ord, case)))
+        x = rng.standard_normal((nz, ny, nx, m))
+    else:
+        args, P, x, _, _ = _setup(case, seed=3)
+    o0 = synth.rng_for(17).standard_normal(x.shape)
+    lam2, beta = 1.9, -0.75
+    if prec == dr.F32:
+        x = x.astype(np.float32).astype(np.float64)
+        o0 = o0.astype(np.float32).astype(np.float64)
+    plan = dr.Plan(*args, prec=prec)
+    cdt = np.float64 if prec == dr.F64 else np.float32
+    xd = torch.from_numpy(x.astype(cdt)).cuda()
+    od = torch.from_numpy(o0.astype(cdt)).cuda()
+    dr.tv4d_normal(plan, xd, od, lam2, beta)
+    plan.sync()
+    ref = beta * o0 + P.DT(P.D(x, lam2), lam2)
+    assert rel(host_values(od), ref) <= tol
+
+
+def test_normal_rejects_aliasing():
+    args, _, x, _, _ = _setup("m1")
+    plan = dr.Plan(*args, prec=dr.F32)
+    xd = torch.from_numpy(x.astype(np.float32)).cuda()
+    with pytest.raises(dr.DynreconError):
+        dr.tv4d_normal(plan, xd, xd, 1.0)
 
 
 @pytest.mark.parametrize("case", sorted(CASES))
@@ -84,13 +137,13 @@ def test_prox_matches_oracle(case, prec, tol):
         u = u.astype(np.float32).astype(np.float64)
         mu0 = mu0.astype(np.float32).astype(np.float64)
     plan = dr.Plan(*args, prec=prec)
-    mu = dev_tensor(mu0, prec if prec != dr.BF16 else dr.F32)
+    mu = dev_tensor(_to_field(mu0), prec if prec != dr.BF16 else dr.F32)
     w = torch.zeros_like(mu)
     res = dr.tv4d_prox(plan, dev_tensor(u, prec), mu, w, rho, lam1, lam2, want_residual=True)
     mu_o, w_o = mu0.copy(), np.zeros_like(mu0)
     tv_o, pr_o = oracle.tv4d_prox(u, mu_o, w_o, P.PhiF, rho, lam1, lam2)
-    assert rel(host_values(mu), mu_o) <= tol
-    assert rel(host_values(w), w_o) <= tol
+    assert rel(_from_field(host_values(mu)), mu_o) <= tol
+    assert rel(_from_field(host_values(w)), w_o) <= tol
     assert abs(res - np.sqrt(pr_o)) <= 10 * tol * np.sqrt(pr_o)
 
 
@@ -99,20 +152,20 @@ def test_prox_bf16_coefficients():
     ub = to_bf16_f64(u)
     mu0 = mu0.astype(np.float32).astype(np.float64)
     plan = dr.Plan(*args, prec=dr.BF16)
-    mu = dev_tensor(mu0, dr.F32)
+    mu = dev_tensor(_to_field(mu0), dr.F32)
     w = torch.zeros_like(mu)
     dr.tv4d_prox(plan, dev_tensor(ub, dr.BF16), mu, w, 0.7, 0.4, 1.3)
     plan.sync()
     mu_o, w_o = mu0.copy(), np.zeros_like(mu0)
     oracle.tv4d_prox(ub, mu_o, w_o, P.PhiF, 0.7, 0.4, 1.3)
-    assert rel(host_values(mu), mu_o) <= 1e-5
-    assert rel(host_values(w), w_o) <= 1e-5
+    assert rel(_from_field(host_values(mu)), mu_o) <= 1e-5
+    assert rel(_from_field(host_values(w)), w_o) <= 1e-5
 
 
 def test_prox_rejects_bad_parameters():
     args, _, u, _, mu0 = _setup("m1")
     plan = dr.Plan(*args, prec=dr.F32)
-    mu = dev_tensor(mu0, dr.F32)
+    mu = dev_tensor(_to_field(mu0), dr.F32)
     w = torch.zeros_like(mu)
     with pytest.raises(dr.DynreconError):
         dr.tv4d_prox(plan, dev_tensor(u, dr.F32), mu, w, 0.0, 0.4, 1.3)
