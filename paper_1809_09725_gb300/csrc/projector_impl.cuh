@@ -40,7 +40,7 @@ namespace dr {
 __host__ __device__ inline size_t fwd_align16(size_t b) { return (b + 15) & ~(size_t)15; }
 
 template <typename S, typename T, int M>
-__global__ void __launch_bounds__(kFwdThreads)
+__global__ void __launch_bounds__(kFwdThreads, (sizeof(T) == 4 && M <= 8) ? 3 : 1)
     fwd_kernel(const S *__restrict__ u, S *__restrict__ out, const S *__restrict__ gm,
                const FwdProj *__restrict__ proj, const T *__restrict__ phip, const int *__restrict__ blocks,
                int nx, int ny, int ns, int K, int m, int MP, int P, int R, int mode, T sigma) {
@@ -124,28 +124,54 @@ __global__ void __launch_bounds__(kFwdThreads)
     for (int r0 = 0; r0 < H; r0 += R) {
         const int nl = min(R, H - r0);
         // ---- synthesis of the P object states on lines [r0, r0+nl) ----
+        // A thread synthesises two pixels (qq and qq + kFwdThreads) per pass,
+        // so every phi row read from shared memory (as 16-byte vectors when
+        // they are float rows) serves both; each f is the same FMA chain
+        // over j as for one pixel.
         const int npx = nl * W;
-        for (int qq = tid; qq < npx; qq += kFwdThreads) {
-            int rl, a;
-            size_t pix;
+        auto pixel_of = [&](int qq, int &rl, int &a) -> size_t {
             if (branch == 0) {
                 rl = qq / W;
                 a = qq - rl * W;
-                pix = zoff + (size_t)(r0 + rl) * nx + a;
-            } else {
-                a = qq / nl;
-                rl = qq - a * nl;
-                pix = zoff + (size_t)a * nx + (r0 + rl);
+                return zoff + (size_t)(r0 + rl) * nx + a;
             }
-            T uj[M];
-            load_coeffs<T, S, M>(u + pix * m, m, uj);
-            T *dst = frames + (size_t)rl * wpad + kFwdGuard + a;
+            a = qq / nl;
+            rl = qq - a * nl;
+            return zoff + (size_t)a * nx + (r0 + rl);
+        };
+        for (int qq = tid; qq < npx; qq += 2 * kFwdThreads) {
+            const bool two = qq + kFwdThreads < npx;
+            int rlA, aA, rlB = 0, aB = 0;
+            const size_t pixA = pixel_of(qq, rlA, aA);
+            const size_t pixB = two ? pixel_of(qq + kFwdThreads, rlB, aB) : pixA;
+            T uA[M], uB[M];
+            load_coeffs<T, S, M>(u + pixA * m, m, uA);
+            load_coeffs<T, S, M>(u + pixB * m, m, uB);
+            T *dstA = frames + (size_t)rlA * wpad + kFwdGuard + aA;
+            T *dstB = frames + (size_t)rlB * wpad + kFwdGuard + aB;
             for (int p = 0; p < P; ++p) {
-                const T *ph = phi_s + p * M;
-                T f = T(0);
+                T ph[M];
+                if constexpr (sizeof(T) == 4 && (M % 4) == 0) {
 #pragma unroll
-                for (int j = 0; j < M; ++j) f = fma(ph[j], uj[j], f);
-                dst[(size_t)p * R * wpad] = f;
+                    for (int c = 0; c < M / 4; ++c) {
+                        const float4 v4 = reinterpret_cast<const float4 *>(phi_s + p * M)[c];
+                        ph[4 * c] = v4.x;
+                        ph[4 * c + 1] = v4.y;
+                        ph[4 * c + 2] = v4.z;
+                        ph[4 * c + 3] = v4.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < M; ++j) ph[j] = phi_s[p * M + j];
+                }
+                T fA = T(0), fB = T(0);
+#pragma unroll
+                for (int j = 0; j < M; ++j) {
+                    fA = fma(ph[j], uA[j], fA);
+                    fB = fma(ph[j], uB[j], fB);
+                }
+                dstA[(size_t)p * R * wpad] = fA;
+                if (two) dstB[(size_t)p * R * wpad] = fB;
             }
         }
         __syncthreads();
