@@ -547,17 +547,29 @@ __global__ void __launch_bounds__(kRedThreads)
 struct alignas(16) FoldPrm {
     float c, s, c8, qb;   // cos, sin, 8 cos, window-relative origin position - 1/2
     float e0, inv_c2;     // 1/c - 1/(2c^2), 1/c^2
-    int idx_base, pad_;   // integer origin position minus the float magic
+    int idx_base;         // integer origin position minus the float magic
+    float c16;            // 16 cos
 };
 
+// Tile of TX x kAdjTY voxels per CTA of 128 threads, VPT voxels per thread.
+// PAIRED (VPT even): a thread holds voxel pairs (x, y), (x, y+1) in VPT/2
+// columns x0 + tx + 16 v (threads 16 x 8, rows y0 + 2 ty + {0, 1}).  The two
+// voxels of a pair project sin(theta) apart, so their taps lie in three
+// consecutive bins: one read of three bins serves both (3 instead of 4 bin
+// reads per voxel and angle).  Otherwise threads 8 x 16, columns x0 + tx + 8 v.
 template <int M>
 struct FoldAdjShape {
     static constexpr int VPT = (M <= 8) ? 4 : ((M <= 16) ? 2 : 1);
     static constexpr int TX = 8 * VPT;
+    static constexpr bool PAIRED = (VPT % 2) == 0;
 };
 
+// Seven 128-thread CTAs per SM (<= 72 registers): with the default seven
+// angles per pipeline stage, shared memory admits seven too (M <= 16).
+__host__ __device__ constexpr int fold_adj_min_blocks(int M) { return M <= 16 ? 7 : 6; }
+
 template <typename S, typename T, int M>
-__global__ void __launch_bounds__(kAdjThreads)
+__global__ void __launch_bounds__(kAdjThreads, fold_adj_min_blocks(M))
     fold_adj_kernel(const __grid_constant__ CUtensorMap tm_gt, const AdjProj *__restrict__ uproj,
                     S *__restrict__ u_s, T *__restrict__ u_c, int nx, int ny, int U, int m, int Wb, T alpha, T beta,
                     int *status, int PP) {
@@ -585,8 +597,9 @@ __global__ void __launch_bounds__(kAdjThreads)
     const int x0 = (blockIdx.x % ntx) * TX, y0 = (blockIdx.x / ntx) * TY;
     const int z = blockIdx.y;
     const int xo = x0 + TX / 2, yo = y0 + TY / 2;
-    const int tx = tid & 7, ty = tid >> 3;
-    const int dx0 = x0 + tx - xo, dy = y0 + ty - yo;
+    constexpr bool PAIRED = FoldAdjShape<M>::PAIRED;
+    const int tx = PAIRED ? (tid & 15) : (tid & 7), ty = PAIRED ? (tid >> 4) : (tid >> 3);
+    const int dx0 = x0 + tx - xo, dy = (PAIRED ? y0 + 2 * ty : y0 + ty) - yo;
     const int nkb = (U + PP - 1) / PP;
 
     auto issue = [&](int st, int kb) {
@@ -609,7 +622,7 @@ __global__ void __launch_bounds__(kAdjThreads)
             pr.inv_c2 = (float)(pj.inv_c * pj.inv_c);
             pr.e0 = (float)(pj.inv_c - 0.5 * pj.inv_c * pj.inv_c);
             pr.idx_base = (int)ri - kMagI;
-            pr.pad_ = 0;
+            pr.c16 = (float)(16.0 * pj.c);
             prm_s(st)[lane] = pr;
             row = z * U + aa;
         }
@@ -645,11 +658,57 @@ __global__ void __launch_bounds__(kAdjThreads)
                 const FoldPrm a = prm[p];
                 const T *w = win_s(st, p);
                 float q = fmaf(dyf, a.s, fmaf(dxf, a.c, a.qb));
+                // Pairs need the two rows' taps within three bins: |qB - qA| < 1.
+                // With |sin| <= 1 - 1e-5 and |q| < 64 (rounding of qA + sin below
+                // 4e-6) the rounded bin indices differ by at most one; angles
+                // closer to |sin| = 1 (a warp-uniform test) use the per-voxel path.
+                if (PAIRED && fabsf(a.s) <= 0.99999f) {
+#pragma unroll
+                    for (int v = 0; v < VPT / 2; ++v) {
+                        // rows y (A) and y + 1 (B) of column v
+                        const float qA = q, qB = q + a.s;
+                        const float tA = qA + kMag, tB = qB + kMag;
+                        const float dA = qA - (tA - kMag), dB = qB - (tB - kMag);
+                        const int iA = __float_as_int(tA) + a.idx_base, iB = __float_as_int(tB) + a.idx_base;
+                        const float w0A = fmaxf(0.0f, fmaf(-dA, a.inv_c2, a.e0));
+                        const float w1A = fmaxf(0.0f, fmaf(dA, a.inv_c2, a.e0));
+                        const float w0B = fmaxf(0.0f, fmaf(-dB, a.inv_c2, a.e0));
+                        const float w1B = fmaxf(0.0f, fmaf(dB, a.inv_c2, a.e0));
+                        {
+                            // taps iA, iA+1 and iB, iB+1 within bins b, b+1, b+2: each
+                            // voxel's weights on the three bins (one of them an exact 0)
+                            const int b = min(iA, iB);
+                            const bool lA = iA == b, lB = iB == b;
+                            const float oA0 = lA ? w0A : 0.0f, oA1 = lA ? w1A : w0A, oA2 = lA ? 0.0f : w1A;
+                            const float oB0 = lB ? w0B : 0.0f, oB1 = lB ? w1B : w0B, oB2 = lB ? 0.0f : w1B;
+                            const T *r0 = w + b * MS;
+                            constexpr int CH = (M % 4) == 0 ? 4 : M;  // coefficients per chunk
+#pragma unroll
+                            for (int c0 = 0; c0 < M; c0 += CH) {
+                                T b0[CH], b1[CH], b2[CH];
+                                load_vec<T, CH>(r0 + c0, b0);
+                                load_vec<T, CH>(r0 + MS + c0, b1);
+                                load_vec<T, CH>(r0 + 2 * MS + c0, b2);
+#pragma unroll
+                                for (int j = 0; j < CH; ++j) {
+                                    T &ra = acc[2 * v][c0 + j];
+                                    ra = fmaf(oA2, b2[j], fmaf(oA1, b1[j], fmaf(oA0, b0[j], ra)));
+                                    T &rb = acc[2 * v + 1][c0 + j];
+                                    rb = fmaf(oB2, b2[j], fmaf(oB1, b1[j], fmaf(oB0, b0[j], rb)));
+                                }
+                            }
+                        }
+                        q += a.c16;
+                    }
+                    continue;
+                }
+                // one voxel at a time: voxel v at q (+ sin for the second row of a pair)
 #pragma unroll
                 for (int v = 0; v < VPT; ++v) {
-                    const float t = q + kMag;
+                    const float qv = (PAIRED && (v & 1)) ? q + a.s : q;
+                    const float t = qv + kMag;
                     const float fl = t - kMag;
-                    const float d = q - fl;
+                    const float d = qv - fl;
                     const int idx = __float_as_int(t) + a.idx_base;
                     const float w0 = fmaxf(0.0f, fmaf(-d, a.inv_c2, a.e0));
                     const float w1 = fmaxf(0.0f, fmaf(d, a.inv_c2, a.e0));
@@ -658,7 +717,8 @@ __global__ void __launch_bounds__(kAdjThreads)
                     load_vec<T, M>(w + (idx + 1) * MS, t1);
 #pragma unroll
                     for (int j = 0; j < M; ++j) acc[v][j] = fmaf(w1, t1[j], fmaf(w0, t0[j], acc[v][j]));
-                    q += a.c8;
+                    if (!PAIRED) q += a.c8;
+                    else if (v & 1) q += a.c16;
                 }
             }
         }
@@ -673,7 +733,8 @@ __global__ void __launch_bounds__(kAdjThreads)
 
 #pragma unroll
     for (int v = 0; v < VPT; ++v) {
-        const int x = x0 + tx + 8 * v, y = y0 + ty;
+        const int x = PAIRED ? x0 + tx + 16 * (v >> 1) : x0 + tx + 8 * v;
+        const int y = PAIRED ? y0 + 2 * ty + (v & 1) : y0 + ty;
         if (x >= nx || y >= ny) continue;
         const size_t base = (((size_t)z * ny + y) * nx + x) * m;
 #pragma unroll
