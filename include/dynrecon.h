@@ -182,8 +182,11 @@ dr_status dr_plan_set_fold_groups(dr_plan *plan, int group, int threads, int ray
  * only by the rounding of those additions.  nsplit > 1 costs nsplit * nz * U
  * * ns * ceil(m / 4) * 4 floats of device memory, allocated on the next
  * forward (call that outside graph capture); slab-streamed solves use one
- * chunk.  async (0/1): double-buffered strips, the next copied with cp.async
- * while the current is marched (same arithmetic, results identical).
+ * chunk.  async 0: synchronous strip staging; 1: double-buffered strips, the
+ * next copied with cp.async while the current is marched; 2: three buffers,
+ * two strips ahead, one CTA barrier per strip (strips limited to twice the
+ * strip budget; where one line does not fit three times, two buffers).  Same
+ * arithmetic in every mode: results identical.
  * DR_EINVAL if the variant is unavailable or an argument is out of range.
  */
 dr_status dr_plan_set_fold_march(dr_plan *plan, int nsplit, int async);

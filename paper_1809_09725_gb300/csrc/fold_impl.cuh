@@ -211,7 +211,8 @@ __global__ void __launch_bounds__(THREADS, THREADS == kFoldThreads ? fold_fwd_mi
         scale_s[p] = (T)f.scale;
         bfx_s[p] = f.B_fx;
     }
-    for (int i = tid; i < (async_stage ? 2 : 1) * R * wpad * MS; i += THREADS) strip[i] = ST(0.0f);
+    // strip buffers: 1 (synchronous staging), 2 (async_stage 1) or 3 (async_stage 2)
+    for (int i = tid; i < (async_stage + 1) * R * wpad * MS; i += THREADS) strip[i] = ST(0.0f);
 
     const int rays_per_cta = THREADS * RPT;
     const int b_base = chunk * rays_per_cta;
@@ -276,15 +277,32 @@ __global__ void __launch_bounds__(THREADS, THREADS == kFoldThreads ? fold_fwd_mi
         }
     };
     const size_t buf_elems = (size_t)R * wpad * MS;  // buffer b starts at strip + b * buf_elems
-    if (async_stage && L0 < L1) {
+    if (async_stage == 1 && L0 < L1) {
         stage(strip, L0, min(R, L1 - L0));
+        cp_async_commit();
+    }
+    if (async_stage == 2) {
+        // three buffers: strips s+1 and s+2 are copied while strip s is marched,
+        // and one barrier per strip suffices (the buffer refilled after the
+        // barrier of strip s held strip s-1, which every thread has finished);
+        // one commit group per strip, empty ones included, so that waiting for
+        // all but the newest group always means strip s has landed
+        if (L0 < L1) stage(strip, L0, min(R, L1 - L0));
+        cp_async_commit();
+        if (L0 + R < L1) stage(strip + buf_elems, L0 + R, min(R, L1 - L0 - R));
         cp_async_commit();
     }
     int s_idx = 0;
     for (int r0 = L0; r0 < L1; r0 += R, ++s_idx) {
         const int nl = min(R, L1 - r0);
         ST *cur;
-        if (async_stage) {
+        if (async_stage == 2) {
+            cp_async_wait<1>();
+            __syncthreads();
+            if (r0 + 2 * R < L1) stage(strip + ((s_idx + 2) % 3) * buf_elems, r0 + 2 * R, min(R, L1 - r0 - 2 * R));
+            cp_async_commit();
+            cur = strip + (s_idx % 3) * buf_elems;
+        } else if (async_stage) {
             // prefetch the next strip into the other buffer, then wait for this one
             if (r0 + R < L1) {
                 stage(strip + ((s_idx + 1) & 1) * buf_elems, r0 + R, min(R, L1 - r0 - R));
@@ -330,8 +348,9 @@ __global__ void __launch_bounds__(THREADS, THREADS == kFoldThreads ? fold_fwd_mi
                 row += (size_t)wpad * MS;
             }
         }
-        __syncthreads();
+        if (async_stage != 2) __syncthreads();
     }
+    if (async_stage == 2) cp_async_wait<0>();  // no copy outlives the CTA
 
     if constexpr (STATIC) {
         // ---- epilogue: the scaled static transforms of this coefficient group ----
@@ -776,7 +795,7 @@ dr_status fold_fwd_launch_t(dr_plan *P, const void *u, void *out, const void *gm
     const bool bf16_strip = sizeof(S) == 2;
     const int async_stage = async_ok && (bf16_strip ? P->fold_async_st : P->fold_async);
     const int R = std::max(1, bf16_strip ? P->fold_lines_st : P->fold_lines);
-    const size_t smem = 768 + sizeof(ST) * (size_t)(async_stage ? 2 : 1) * R * wpad * MS;
+    const size_t smem = 768 + sizeof(ST) * (size_t)(async_stage + 1) * R * wpad * MS;
     auto kern = fold_fwd_kernel<S, T, M, false>;
     {
         dr_status s = allow_dynamic_smem((const void *)kern, smem);
@@ -813,14 +832,23 @@ dr_status fold_static_launch(dr_plan *P, const void *u, cudaStream_t st, StaticO
     const int ngroups = (P->m + MC - 1) / MC;
     const int wpad = std::max(P->nx, P->ny) + 2 * kFwdGuard;
     const bool bf16_kernel = sizeof(S) == 2;
-    const int R = std::max(1, std::min(bf16_kernel ? P->fold2_lines_st : P->fold2_lines, P->fold2_R[gi]));
+    const int R0 = std::max(1, std::min(bf16_kernel ? P->fold2_lines_st : P->fold2_lines, P->fold2_R[gi]));
     if ((size_t)P->nz * ngroups > 65535) return fail(DR_EINVAL, "two-kernel folded forward: too many slice groups");
-    // async: two strip buffers, the next strip copied with cp.async while the
+    // async 1: two strip buffers, the next strip copied with cp.async while the
     // current one is marched (groups of whole 16-byte vectors; other pixels
-    // are staged through registers)
+    // are staged through registers); async 2: three buffers, two strips ahead
     (void)VW;
-    const int async = bf16_kernel ? P->fold2_async_st : P->fold2_async;
-    const size_t smem = 768 + sizeof(ST) * (size_t)(async ? 2 : 1) * R * wpad * MS;
+    int async = bf16_kernel ? P->fold2_async_st : P->fold2_async;
+    int R = R0;
+    if (async == 2) {
+        // three buffers within twice the strip budget (below the 227 KB a CTA
+        // may hold); where even one line does not fit, two buffers (same march)
+        const long long line = (long long)sizeof(ST) * wpad * MS;
+        const int r3 = (int)((2LL * kFoldStripBudget) / (3 * line));
+        if (r3 >= 1) R = std::min(R, r3);
+        else async = 1;
+    }
+    const size_t smem = 768 + sizeof(ST) * (size_t)(async + 1) * R * wpad * MS;
     auto kern = fold_fwd_kernel<S, T, MC, true, THREADS, RPT, MINB>;
     {
         dr_status s = allow_dynamic_smem((const void *)kern, smem);

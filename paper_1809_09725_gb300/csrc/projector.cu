@@ -325,9 +325,9 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
         P->fold2_split = 1;
         P->fold2_async = 0;
         P->fold2_bv = 0;
-        // screen the group / CTA configurations, each with and without
-        // double-buffered cp.async strips (which doubles the strip memory and can
-        // halve the CTAs an SM holds) at two strip heights; refine the two best
+        // screen the group / CTA configurations, each with synchronous,
+        // double- and triple-buffered cp.async strips (more strip memory, so
+        // possibly fewer CTAs per SM) at two strip heights; refine the two best
         auto gi_ok = [&](int gi) {
             const int MC = fold_static_mc(gi);
             return P->fold2_R[gi] >= 1 && !(MC == 8 && P->m <= 4) &&
@@ -341,7 +341,7 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
         for (int gi = 0; gi < kFold2Configs; ++gi) {
             if (!gi_ok(gi)) continue;
             P->fold2_gi = gi;
-            for (int as = 0; as < 2; ++as) {
+            for (int as = 0; as < 3; ++as) {
                 P->fold2_async = as;
                 Cand best{1e30, gi, as, 1};
                 for (int c : {4, std::min(12, P->fold2_R[gi])}) {
@@ -461,7 +461,7 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
         if (P->prec == DR_BF16_F32ACC) {
             double best_t = 1e30;
             int bls = bl, bas = 0;
-            for (int as = 0; as < 2; ++as) {
+            for (int as = 0; as < 3; ++as) {
                 P->fold2_async_st = as;
                 dr_status s = search_lines(P->fold2_R[bgi], run2(false), bls, best_t, better);
                 if (s != DR_OK) return s;
@@ -653,8 +653,8 @@ dr_status dr_plan_set_fold_march(dr_plan *P, int nsplit, int async) {
     clear_error();
     if (!P) return fail(DR_EINVAL, "dr_plan_set_fold_march: NULL plan");
     if (!(P->fold_U > 0 && P->fold2_ok)) return fail(DR_EINVAL, "dr_plan_set_fold_march: variant unavailable");
-    if (nsplit < 1 || nsplit > 8 || async < 0 || async > 1)
-        return fail(DR_EINVAL, "dr_plan_set_fold_march: nsplit must be 1..8 and async 0 or 1");
+    if (nsplit < 1 || nsplit > 8 || async < 0 || async > 2)
+        return fail(DR_EINVAL, "dr_plan_set_fold_march: nsplit must be 1..8 and async 0, 1 or 2");
     P->fold2_split = nsplit;
     P->fold2_async = P->fold2_async_st = async;
     return DR_OK;

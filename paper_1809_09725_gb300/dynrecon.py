@@ -276,7 +276,7 @@ class Plan:
 
     def set_fold_march(self, nsplit: int = 1, async_stage: int = 0):
         """Two-kernel folded forward: line chunks of each ray's march, and
-        double-buffered cp.async strips."""
+        strip staging (0 synchronous, 1 double-, 2 triple-buffered cp.async)."""
         _check(load().dr_plan_set_fold_march(self._h, int(nsplit), int(async_stage)))
 
     def set_fold_adj_stage(self, angles: int):

@@ -465,22 +465,30 @@ def test_fold2_line_split_inside_solvers():
 @pytest.mark.parametrize("prec", [dr.F32, dr.BF16])
 @pytest.mark.parametrize("case", ["m16", "ragged", "narrow_det"])
 def test_fold2_async_strips_bitwise(case, prec):
-    """Double-buffered cp.async strips stage the same lines for the same
-    march (whole 16-byte groups by cp.async, the rest through registers):
-    projections identical bit for bit, with and without line chunks."""
+    """Double- and triple-buffered cp.async strips stage the same lines for
+    the same march (whole 16-byte groups by cp.async, the rest through
+    registers): projections identical bit for bit, with and without line
+    chunks, at several strip heights (strips of one line to more lines than
+    the image has)."""
     args, u, _, _ = _setup(case, seed=41)
     plan = _plan(args, prec)
     plan.set_variant(dr.FOLD2, dr.FOLD)
     ud = dev_tensor(u, prec)
-    outs = []
-    for nsplit, async_stage in ((1, 0), (1, 1), (3, 0), (3, 1)):
-        plan.set_fold_march(nsplit, async_stage)
-        g = torch.zeros(plan.g_shape(), dtype=getattr(torch, plan.storage_dtype), device="cuda")
-        dr.dyn_radon_fwd(plan, ud, g)
-        plan.sync()
-        outs.append(host_values(g))
-    np.testing.assert_array_equal(outs[1], outs[0])
-    np.testing.assert_array_equal(outs[3], outs[2])
+    for lines in (1, 3, 16):
+        for nsplit in (1, 3):
+            outs = []
+            for async_stage in (0, 1, 2):
+                try:
+                    plan.set_fold_groups(4, lines, 256, 0)
+                except dr.DynreconError:
+                    pytest.skip("strip of %d lines exceeds the budget" % lines)
+                plan.set_fold_march(nsplit, async_stage)
+                g = torch.zeros(plan.g_shape(), dtype=getattr(torch, plan.storage_dtype), device="cuda")
+                dr.dyn_radon_fwd(plan, ud, g)
+                plan.sync()
+                outs.append(host_values(g))
+            np.testing.assert_array_equal(outs[1], outs[0])
+            np.testing.assert_array_equal(outs[2], outs[0])
 
 
 @pytest.mark.parametrize("case", ["narrow_det", "m16", "ragged"])
