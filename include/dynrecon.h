@@ -357,7 +357,28 @@ typedef struct {
     double *primal_res_out; /* HOST [iters], nullable: ADMM ||D u - psi|| after each iteration */
     double *op_norm_out;    /* HOST, nullable: Chambolle-Pock operator norm estimate used */
     double op_norm;         /* Chambolle-Pock: > 0 uses this ||[R; D]|| instead of the power iteration */
+    void *state;            /* DEVICE, nullable: the solver's state besides u, in the plan's compute
+                             * type (dr_plan_state_bytes), written at the end of the call, so that a
+                             * later call can continue the iteration (checkpoint / resume) */
+    int resume;             /* != 0: start from `state` instead of zero duals (needs state) */
 } dr_solve_params;
+
+/*
+ * Bytes of the solver state admm_solve keeps besides u (dr_solve_params.state),
+ * in the plan's compute type (float for DR_F32 / DR_BF16_F32ACC, double for
+ * DR_F64), laid out as
+ *   DR_ADMM_CG:         mu, w                 (two [nz][nt][ny][nx][4] fields)
+ *   DR_CHAMBOLLE_POCK:  h2, h1, u~            ([nz][nt][ny][nx][4], [nz][K][ns],
+ *                                              [nz][ny][nx][m])
+ * A call with state != NULL writes its final state there; a call with
+ * resume != 0 starts from it, so iters = a + b in one call and a then b with
+ * the state carried over give the same iterates (Chambolle-Pock: pass the
+ * same op_norm to both calls, e.g. the first call's op_norm_out).  u itself
+ * is handed over in storage precision (bf16 for DR_BF16_F32ACC plans).  The
+ * state is the caller's device memory; cp_solve_slabs takes none (DR_EINVAL).
+ * Returns 0 for a NULL plan or an unknown algo.
+ */
+size_t dr_plan_state_bytes(const dr_plan *plan, dr_algo algo);
 
 /* Fill params with defaults: ADMM-CG, 20 iterations, 4 CG steps, lambda1 = lambda2 = 1e-3... */
 void dr_solve_params_default(dr_solve_params *params);
@@ -367,8 +388,9 @@ void dr_solve_params_default(dr_solve_params *params);
  *   DR_ADMM_CG: split psi = D u; per iteration n_cg CG steps on
  *       (R*R + rho D^T D) u = R* g + rho D^T (psi - mu/rho)   (warm start,
  *       explicit residual, early stop when <r,r> = 0 or <p,Ap> <= 0), then
- *       the tv4d_prox step.  mu = psi = 0 at the start.
- *   DR_CHAMBOLLE_POCK: Sec. 3, Fig. 2 with h1 = h2 = 0 at the start and
+ *       the tv4d_prox step.  mu = psi = 0 at the start (or the state of an
+ *       earlier call: dr_solve_params.state / resume).
+ *   DR_CHAMBOLLE_POCK: Sec. 3, Fig. 2 with h1 = h2 = 0 (or a resumed state) at the start and
  *       tau = sigma = 0.99 / L, L = ||[R; D]|| from power_iters power
  *       iterations started from a SplitMix64 vector (seed 1809).
  * g: [nz][K][ns]; u: [nz][ny][nx][m], initial guess in, result out.  Either

@@ -562,6 +562,7 @@ dr_status cp_solve_slabs(dr_plan *P, const void *g, void *u, const dr_solve_para
                     "cp_solve_slabs: slab streaming runs Chambolle-Pock (ADMM-CG needs whole-volume inner products "
                     "inside every CG step)");
     if (slab_nz < 1) return fail(DR_EINVAL, "cp_solve_slabs: slab_nz must be >= 1");
+    if (prm->state || prm->resume) return fail(DR_EINVAL, "cp_solve_slabs: takes no solver state buffer");
     if (prm->iters < 0) return fail(DR_EINVAL, "cp_solve_slabs: iters must be >= 0");
     if (!(prm->lambda1 >= 0.0) || !(prm->lambda2 >= 0.0) || !std::isfinite(prm->lambda1) ||
         !std::isfinite(prm->lambda2) || !std::isfinite(prm->op_norm))

@@ -482,12 +482,24 @@ static dr_status solve_begin(dr_plan *P, const void *g_in, void *u_io, const dr_
     DR_CUDA_TRY(cudaMemsetAsync(w.obj, 0, sizeof(double) * 3 * (size_t)(prm.iters + 1), st));
     c.rho = prm.rho > 0.0 ? prm.rho : (prm.lambda1 > 0.0 ? 10.0 * prm.lambda1 : 1.0);
 
+    // the state besides u: zero at a fresh start, the caller's on resume
+    const unsigned char *rs = prm.resume ? (const unsigned char *)prm.state : nullptr;
     if (prm.algo == DR_ADMM_CG) {
-        DR_CUDA_TRY(cudaMemsetAsync(w.mu, 0, nf * cs, st));
-        DR_CUDA_TRY(cudaMemsetAsync(w.w, 0, nf * cs, st));
+        if (rs) {
+            DR_CUDA_TRY(cudaMemcpyAsync(w.mu, rs, nf * cs, cudaMemcpyDeviceToDevice, st));
+            DR_CUDA_TRY(cudaMemcpyAsync(w.w, rs + nf * cs, nf * cs, cudaMemcpyDeviceToDevice, st));
+        } else {
+            DR_CUDA_TRY(cudaMemsetAsync(w.mu, 0, nf * cs, st));
+            DR_CUDA_TRY(cudaMemsetAsync(w.w, 0, nf * cs, st));
+        }
     } else {
-        DR_CUDA_TRY(cudaMemsetAsync(w.h1, 0, ng * cs, st));
-        DR_CUDA_TRY(cudaMemsetAsync(w.mu, 0, nf * cs, st));
+        if (rs) {
+            DR_CUDA_TRY(cudaMemcpyAsync(w.mu, rs, nf * cs, cudaMemcpyDeviceToDevice, st));
+            DR_CUDA_TRY(cudaMemcpyAsync(w.h1, rs + nf * cs, ng * cs, cudaMemcpyDeviceToDevice, st));
+        } else {
+            DR_CUDA_TRY(cudaMemsetAsync(w.h1, 0, ng * cs, st));
+            DR_CUDA_TRY(cudaMemsetAsync(w.mu, 0, nf * cs, st));
+        }
         if (prm.op_norm > 0.0) {
             c.L = prm.op_norm;
         } else {
@@ -497,7 +509,8 @@ static dr_status solve_begin(dr_plan *P, const void *g_in, void *u_io, const dr_
         if (!(c.L > 0.0) || !std::isfinite(c.L)) return fail(DR_EINVAL, "admm_solve: operator norm is zero");
         c.sigma = c.tau = 0.99 / c.L;
         if (prm.op_norm_out) *prm.op_norm_out = c.L;
-        DR_CUDA_TRY(cudaMemcpyAsync(w.ut, c.u, nu * cs, cudaMemcpyDeviceToDevice, st));
+        DR_CUDA_TRY(cudaMemcpyAsync(w.ut, rs ? (const void *)(rs + (nf + ng) * cs) : (const void *)c.u, nu * cs,
+                                    cudaMemcpyDeviceToDevice, st));
         iter_kernel<<<1, 1, 0, st>>>(P->d_scal, 1, 0);
         TRY(launched("iter_kernel"));
     }
@@ -521,6 +534,19 @@ static dr_status solve_end(dr_plan *P, SolveCtx &c) {
         // fidelity of the final u (row iters)
         TRY(launch_fwd_calc(P, c.u, w.gd, c.g, 1, 0.0, st));
         TRY(dot(P, w.gd, w.gd, ng, kSlotFid, w.obj, 0, 0, 0, st));
+    }
+    if (prm.state) {
+        // the state besides u, for a later call to continue from
+        unsigned char *sd = (unsigned char *)prm.state;
+        const size_t nf = nf_elems(P);
+        if (prm.algo == DR_ADMM_CG) {
+            DR_CUDA_TRY(cudaMemcpyAsync(sd, w.mu, nf * cs, cudaMemcpyDeviceToDevice, st));
+            DR_CUDA_TRY(cudaMemcpyAsync(sd + nf * cs, w.w, nf * cs, cudaMemcpyDeviceToDevice, st));
+        } else {
+            DR_CUDA_TRY(cudaMemcpyAsync(sd, w.mu, nf * cs, cudaMemcpyDeviceToDevice, st));
+            DR_CUDA_TRY(cudaMemcpyAsync(sd + nf * cs, w.h1, ng * cs, cudaMemcpyDeviceToDevice, st));
+            DR_CUDA_TRY(cudaMemcpyAsync(sd + (nf + ng) * cs, w.ut, nu * cs, cudaMemcpyDeviceToDevice, st));
+        }
     }
     if (!c.u_dev || c.bf) {
         void *dst = c.u_io;
@@ -701,6 +727,8 @@ static dr_status check_params(const dr_solve_params &p) {
         return fail(DR_EINVAL, "admm_solve: lambdas must be finite and >= 0");
     if (p.algo == DR_CHAMBOLLE_POCK && !(p.cp_theta >= 0.0 && p.cp_theta <= 1.0))
         return fail(DR_EINVAL, "admm_solve: cp_theta must be in [0, 1]");
+    if (p.resume && !p.state) return fail(DR_EINVAL, "admm_solve: resume needs a state buffer");
+    if (p.state && !is_device_ptr(p.state)) return fail(DR_EINVAL, "admm_solve: state must be device memory");
     return DR_OK;
 }
 
@@ -711,6 +739,14 @@ using namespace dr;
 extern "C" {
 
 size_t dr_plan_workspace_bytes(const dr_plan *P, dr_algo algo) { return P ? ws_bytes(P, algo, 1) : 0; }
+
+size_t dr_plan_state_bytes(const dr_plan *P, dr_algo algo) {
+    if (!P) return 0;
+    const size_t cs = calc_size(P->prec);
+    if (algo == DR_ADMM_CG) return 2 * nf_elems(P) * cs;
+    if (algo == DR_CHAMBOLLE_POCK) return (nf_elems(P) + ng_elems(P) + nu_elems(P)) * cs;
+    return 0;
+}
 
 dr_status admm_solve(dr_plan *P, const void *g, void *u, const dr_solve_params *prm) {
     clear_error();

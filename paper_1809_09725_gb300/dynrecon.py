@@ -30,7 +30,7 @@ _STATUS = {DR_EINVAL: "EINVAL", DR_ENOMEM: "ENOMEM", DR_ECUDA: "ECUDA", DR_ETIME
 
 # Every symbol include/dynrecon.h declares.
 EXPORTS = ("dr_plan_create", "dr_plan_destroy", "dr_plan_set_stream", "dr_plan_device_bytes",
-           "dr_plan_workspace_bytes", "dr_plan_sync", "dr_plan_set_variant", "dr_plan_autotune",
+           "dr_plan_workspace_bytes", "dr_plan_state_bytes", "dr_plan_sync", "dr_plan_set_variant", "dr_plan_autotune",
            "dr_plan_set_fold_strip", "dr_plan_set_fold_groups", "dr_plan_set_fold_march", "dr_plan_set_fold_adj_stage", "dr_plan_set_fold_blocks", "dr_plan_info",
            "dyn_radon_fwd", "dyn_radon_adj", "dyn_radon_adj_noalloc", "dr_fbp_init", "tv4d_grad", "tv4d_grad_adj", "tv4d_normal",
            "tv4d_prox", "dr_solve_params_default", "admm_solve", "admm_solve_batch", "cp_solve_slabs",
@@ -67,7 +67,8 @@ class SolveParams(ctypes.Structure):
                 ("cp_theta", ctypes.c_double), ("power_iters", ctypes.c_int),
                 ("objective_out", ctypes.POINTER(ctypes.c_double)),
                 ("primal_res_out", ctypes.POINTER(ctypes.c_double)),
-                ("op_norm_out", ctypes.POINTER(ctypes.c_double)), ("op_norm", ctypes.c_double)]
+                ("op_norm_out", ctypes.POINTER(ctypes.c_double)), ("op_norm", ctypes.c_double),
+                ("state", ctypes.c_void_p), ("resume", ctypes.c_int)]
 
 
 class JobDesc(ctypes.Structure):
@@ -109,6 +110,7 @@ def load(path: str = LIB_PATH):
         "dr_plan_set_stream": (i, [vp, vp]),
         "dr_plan_device_bytes": (sz, [vp]),
         "dr_plan_workspace_bytes": (sz, [vp, i]),
+        "dr_plan_state_bytes": (sz, [vp, i]),
         "dr_plan_sync": (i, [vp]),
         "dr_plan_set_variant": (i, [vp, i, i]),
         "dr_plan_autotune": (i, [vp, pd]),
@@ -250,6 +252,10 @@ class Plan:
     def workspace_bytes(self, algo: int = ADMM_CG) -> int:
         return load().dr_plan_workspace_bytes(self._h, int(algo))
 
+    def state_bytes(self, algo: int = ADMM_CG) -> int:
+        """Bytes of the solver state besides u (checkpoint / resume buffer)."""
+        return load().dr_plan_state_bytes(self._h, int(algo))
+
     def sync(self):
         _check(load().dr_plan_sync(self._h))
 
@@ -380,13 +386,21 @@ def tv4d_prox(plan: Plan, u, mu, w, rho: float, lambda1: float, lambda2: float,
 
 def solve_params(algo: int = ADMM_CG, iters: int = 20, n_cg: int = 4, lambda1: float = 1e-3,
                  lambda2: float = 1.0, rho: float = 0.0, cp_theta: float = 1.0,
-                 power_iters: int = 100, op_norm: float = 0.0) -> SolveParams:
+                 power_iters: int = 100, op_norm: float = 0.0, state=None, resume: bool = False) -> SolveParams:
+    """state: a device tensor of Plan.state_bytes(algo) bytes (kept alive by
+    the caller) that receives the solver state at the end of the call;
+    resume: start from it instead of zero duals."""
     p = SolveParams()
     load().dr_solve_params_default(ctypes.byref(p))
     p.algo, p.iters, p.n_cg = int(algo), int(iters), int(n_cg)
     p.lambda1, p.lambda2, p.rho, p.cp_theta = float(lambda1), float(lambda2), float(rho), float(cp_theta)
     p.power_iters = int(power_iters)
     p.op_norm = float(op_norm)
+    if state is not None:
+        if not getattr(state, "is_cuda", False):
+            raise ValueError("state must be a device tensor")
+        p.state = ctypes.c_void_p(state.data_ptr())
+    p.resume = 1 if resume else 0
     return p
 
 

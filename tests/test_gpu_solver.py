@@ -202,3 +202,46 @@ def test_folded_normal_operator_matches_forward_then_adjoint():
         norms[key] = res["op_norm"]
     assert abs(norms["normal"] - norms["plain"]) <= 1e-5 * norms["plain"]
     assert abs(norms["normal_split"] - norms["plain"]) <= 1e-5 * norms["plain"]
+
+
+@pytest.mark.parametrize("algo", [dr.ADMM_CG, dr.CHAMBOLLE_POCK])
+@pytest.mark.parametrize("prec", [dr.F64, dr.F32])
+def test_checkpoint_resume_continues_the_iteration(disks, algo, prec):
+    """A solve of a + b iterations equals a solve of a iterations whose
+    state buffer (duals; Chambolle-Pock also h1 and the extrapolated u) is
+    handed to a second solve of b iterations with resume (same operator norm
+    for Chambolle-Pock): iterates and objective rows continue unchanged.
+    (With BF16 storage the u handed between the calls is rounded to bf16.)"""
+    w, theta, t, g, P = disks
+    a, b = 3, 4
+    plan = dr.Plan(w.N, w.N, w.nz, w.ns, theta, t, w.basis, w.m, w.nt, prec)
+    sdt = getattr(torch, plan.storage_dtype)
+    gd = dev_tensor(g, prec)
+    kw = dict(n_cg=w.n_cg, lambda1=w.lambda1, lambda2=w.lambda2, rho=w.rho)
+    u_all = torch.zeros(plan.u_shape(), dtype=sdt, device="cuda")
+    r_all = dr.admm_solve(plan, gd, u_all, dr.solve_params(algo, iters=a + b, **kw))
+    kw["op_norm"] = r_all["op_norm"] if algo == dr.CHAMBOLLE_POCK else 0.0
+    state = torch.empty(plan.state_bytes(algo), dtype=torch.uint8, device="cuda")
+    u = torch.zeros_like(u_all)
+    r1 = dr.admm_solve(plan, gd, u, dr.solve_params(algo, iters=a, state=state, **kw))
+    r2 = dr.admm_solve(plan, gd, u, dr.solve_params(algo, iters=b, state=state, resume=True, **kw))
+    plan.sync()
+    tol = 1e-12 if prec == dr.F64 else 1e-6
+    assert rel(host_values(u), host_values(u_all)) <= tol
+    assert rel(np.concatenate([r1["objective"], r2["objective"]]), r_all["objective"]) <= tol
+    # without the state the second call restarts the duals: a different iterate
+    u_re = torch.zeros_like(u_all)
+    dr.admm_solve(plan, gd, u_re, dr.solve_params(algo, iters=a, **kw))
+    dr.admm_solve(plan, gd, u_re, dr.solve_params(algo, iters=b, **kw))
+    assert rel(host_values(u_re), host_values(u_all)) > 10 * tol
+
+
+def test_resume_without_state_is_rejected(disks):
+    w, theta, t, g, P = disks
+    plan = dr.Plan(w.N, w.N, w.nz, w.ns, theta, t, w.basis, w.m, w.nt, dr.F32)
+    u = torch.zeros(plan.u_shape(), dtype=torch.float32, device="cuda")
+    with pytest.raises(dr.DynreconError):
+        dr.admm_solve(plan, dev_tensor(g, dr.F32), u, dr.solve_params(dr.ADMM_CG, iters=2, resume=True))
+    assert plan.state_bytes(dr.ADMM_CG) == 2 * 4 * w.nt * w.N * w.N * w.nz * 4
+    assert plan.state_bytes(dr.CHAMBOLLE_POCK) == 4 * (4 * w.nt * w.N * w.N * w.nz + w.K * w.ns * w.nz
+                                                       + w.m * w.N * w.N * w.nz)
