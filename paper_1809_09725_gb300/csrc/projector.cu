@@ -325,9 +325,10 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
         P->fold2_split = 1;
         P->fold2_async = 0;
         P->fold2_bv = 0;
-        // screen the group / CTA configurations, each with synchronous,
-        // double- and triple-buffered cp.async strips (more strip memory, so
-        // possibly fewer CTAs per SM) at two strip heights; refine the two best
+        // screen the group / CTA configurations, each with synchronous and
+        // double-buffered cp.async strips (twice the strip memory, so possibly
+        // fewer CTAs per SM) at two strip heights; refine the two best, then
+        // try triple buffering on the best
         auto gi_ok = [&](int gi) {
             const int MC = fold_static_mc(gi);
             return P->fold2_R[gi] >= 1 && !(MC == 8 && P->m <= 4) &&
@@ -341,7 +342,7 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
         for (int gi = 0; gi < kFold2Configs; ++gi) {
             if (!gi_ok(gi)) continue;
             P->fold2_gi = gi;
-            for (int as = 0; as < 3; ++as) {
+            for (int as = 0; as < 2; ++as) {
                 P->fold2_async = as;
                 Cand best{1e30, gi, as, 1};
                 for (int c : {4, std::min(12, P->fold2_R[gi])}) {
@@ -376,6 +377,22 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
         }
         P->fold2_gi = bgi;
         P->fold2_async = basync;
+        // triple-buffered strips on the best configuration (one barrier per
+        // strip; three buffers, so a third fewer lines within the same memory)
+        if (basync == 1) {
+            P->fold2_async = 2;
+            for (int c : {std::max(1, 2 * bl / 3), bl}) {
+                double t = 1e30;
+                dr_status s = run2(true)(c, t);
+                if (s != DR_OK) return s;
+                if (t < ms[4]) {
+                    ms[4] = t;
+                    basync = 2;
+                    bl = c;
+                }
+            }
+            P->fold2_async = basync;
+        }
         // smaller angle blocks (more CTAs, each with less work): a fuller last wave
         {
             int bbv = 0;

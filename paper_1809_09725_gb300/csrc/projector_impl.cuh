@@ -437,8 +437,20 @@ __global__ void __launch_bounds__(kAdjThreads)
             for (int p = 0; p < np; ++p) {
                 const AdjPrm<T> a = prm[p];
                 T ph[M];
+                if constexpr (sizeof(T) == 4 && (M % 4) == 0) {
+                    // phi rows are MP = M rounded up to 4 floats, 16-byte aligned
 #pragma unroll
-                for (int j = 0; j < M; ++j) ph[j] = phs[p * MP + j];
+                    for (int c = 0; c < M / 4; ++c) {
+                        const float4 v4 = reinterpret_cast<const float4 *>(phs + p * MP)[c];
+                        ph[4 * c] = v4.x;
+                        ph[4 * c + 1] = v4.y;
+                        ph[4 * c + 2] = v4.z;
+                        ph[4 * c + 3] = v4.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < M; ++j) ph[j] = phs[p * MP + j];
+                }
                 const S *w = win + (size_t)p * wbs;
                 if constexpr (sizeof(T) == 4) {
                     float q = fmaf(dyf, a.s, fmaf(dxf, a.c, a.qb));
