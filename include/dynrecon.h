@@ -244,6 +244,18 @@ dr_status dr_plan_info(const dr_plan *plan, dr_plan_info_t *info);
 dr_status dr_plan_sync(dr_plan *plan);
 
 /*
+ * Failure-path check of the library's bounded device-side waits (the paper
+ * has no counterpart).  Launches, on the plan's stream, one CTA that waits
+ * with the same bounded mbarrier wait the TMA pipelines use on a barrier
+ * nothing arrives at; after limit_s seconds (0 < limit_s <= 2) the wait
+ * gives up, records the failure in the plan's status word and the kernel
+ * returns.  Then behaves as dr_plan_sync: DR_ETIMEOUT is the expected
+ * result (the give-up path works and the context stays usable); DR_OK would
+ * mean the wait did not give up.  DR_EINVAL for a NULL plan or a bad limit.
+ */
+dr_status dr_plan_wait_selftest(dr_plan *plan, double limit_s);
+
+/*
  * Dynamic forward projection, Eq. (radapr) (Eq. Rfwd with Eq. repr):
  *     g[z][k][b] = sum_j phi_j(t_k) (R_{theta_k} u_j[z])(s_b)
  * u: device [nz][ny][nx][m], g: device [nz][K][ns] (overwritten).  u and g

@@ -10,6 +10,7 @@
 #include <mutex>
 #include <string>
 
+#include "dr_device.cuh"
 #include "dr_internal.cuh"
 
 namespace dr {
@@ -625,6 +626,34 @@ dr_status dr_plan_set_stream(dr_plan *P, void *s) {
 
 size_t dr_plan_device_bytes(const dr_plan *P) {
     return P ? P->table_bytes + P->ws.bytes + (P->d_gt ? P->gt_bytes : 0) + P->fbp_bytes + P->ru_split_bytes : 0;
+}
+
+}  // extern "C"
+
+namespace dr {
+// Failure-path check of the bounded waits: an mbarrier that nothing arrives
+// at, waited on with the same bounded wait the TMA pipelines use.  Every
+// thread gives up after limit_ns, sets the status word and returns.
+__global__ void wait_selftest_kernel(int *status, unsigned long long limit_ns) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    mbar_wait_bounded(&bar, 0u, status, limit_ns);
+}
+}  // namespace dr
+
+extern "C" {
+
+dr_status dr_plan_wait_selftest(dr_plan *P, double limit_s) {
+    clear_error();
+    if (!P) return fail(DR_EINVAL, "dr_plan_wait_selftest: NULL plan");
+    if (!(limit_s > 0.0 && limit_s <= 2.0)) return fail(DR_EINVAL, "dr_plan_wait_selftest: limit_s must be in (0, 2]");
+    dr::wait_selftest_kernel<<<1, 32, 0, P->stream>>>(P->d_status, (unsigned long long)(limit_s * 1e9));
+    DR_CUDA_TRY(cudaGetLastError());
+    return dr_plan_sync(P);
 }
 
 dr_status dr_plan_sync(dr_plan *P) {

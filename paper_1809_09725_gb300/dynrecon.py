@@ -30,7 +30,7 @@ _STATUS = {DR_EINVAL: "EINVAL", DR_ENOMEM: "ENOMEM", DR_ECUDA: "ECUDA", DR_ETIME
 
 # Every symbol include/dynrecon.h declares.
 EXPORTS = ("dr_plan_create", "dr_plan_destroy", "dr_plan_set_stream", "dr_plan_device_bytes",
-           "dr_plan_workspace_bytes", "dr_plan_state_bytes", "dr_plan_sync", "dr_plan_set_variant", "dr_plan_autotune",
+           "dr_plan_workspace_bytes", "dr_plan_state_bytes", "dr_plan_sync", "dr_plan_wait_selftest", "dr_plan_set_variant", "dr_plan_autotune",
            "dr_plan_set_fold_strip", "dr_plan_set_fold_groups", "dr_plan_set_fold_march", "dr_plan_set_fold_adj_stage", "dr_plan_set_fold_blocks", "dr_plan_info",
            "dyn_radon_fwd", "dyn_radon_adj", "dyn_radon_adj_noalloc", "dr_fbp_init", "tv4d_grad", "tv4d_grad_adj", "tv4d_normal",
            "tv4d_prox", "dr_solve_params_default", "admm_solve", "admm_solve_batch", "cp_solve_slabs",
@@ -112,6 +112,7 @@ def load(path: str = LIB_PATH):
         "dr_plan_workspace_bytes": (sz, [vp, i]),
         "dr_plan_state_bytes": (sz, [vp, i]),
         "dr_plan_sync": (i, [vp]),
+        "dr_plan_wait_selftest": (i, [vp, d]),
         "dr_plan_set_variant": (i, [vp, i, i]),
         "dr_plan_autotune": (i, [vp, pd]),
         "dr_plan_set_fold_strip": (i, [vp, i, i]),
@@ -251,6 +252,11 @@ class Plan:
 
     def workspace_bytes(self, algo: int = ADMM_CG) -> int:
         return load().dr_plan_workspace_bytes(self._h, int(algo))
+
+    def wait_selftest(self, limit_s: float = 0.05) -> int:
+        """Run the bounded-wait failure check; returns the status code
+        (DR_ETIMEOUT expected) without raising."""
+        return int(load().dr_plan_wait_selftest(self._h, float(limit_s)))
 
     def state_bytes(self, algo: int = ADMM_CG) -> int:
         """Bytes of the solver state besides u (checkpoint / resume buffer)."""

@@ -539,3 +539,20 @@ def test_fold2_angle_blocks_bitwise(case):
     for o in outs[1:]:
         np.testing.assert_array_equal(o, outs[0])
     assert rel(outs[0], P.fwd(u)) <= 1e-5
+
+
+def test_bounded_wait_gives_up_and_the_context_stays_usable():
+    """Failure detection without a fault: a kernel waits, with the bounded
+    mbarrier wait the TMA pipelines use, on a barrier nothing arrives at.
+    The wait gives up after its limit, the status word reports it
+    (DR_ETIMEOUT, cleared on read), and the same plan then computes a
+    correct forward projection."""
+    args, u, _, P = _setup("ragged", seed=77)
+    plan = _plan(args, dr.F32)
+    assert plan.wait_selftest(0.05) == dr.DR_ETIMEOUT
+    plan.sync()  # status word cleared: no error now
+    g = torch.zeros(plan.g_shape(), dtype=torch.float32, device="cuda")
+    dr.dyn_radon_fwd(plan, dev_tensor(u, dr.F32), g)
+    plan.sync()
+    assert rel(host_values(g), P.fwd(u.astype(np.float32).astype(np.float64))) <= 1e-5
+    assert plan.wait_selftest(3.0) == dr.DR_EINVAL
