@@ -189,6 +189,7 @@ struct dr_plan {
     int fold2_bv = 0;                 // angle-block variant in use
     bool fold2_ok = false;
     int fold2_gi = 0;                 // configuration in use
+    int fold2_gi_st = 0;              // configuration of storage-typed (bf16-strip) calls of BF16 plans
     int sel_fwd_st = 0;               // forward variant of storage-typed calls on BF16 plans (bf16 strips)
     int fold2_split = 1;              // line chunks of the static march (partial sums added by the distribution)
     int fold2_async = 0, fold2_async_st = 0;  // double-buffered cp.async strips (compute-typed / bf16 kernels)

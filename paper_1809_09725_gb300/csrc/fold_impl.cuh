@@ -891,7 +891,7 @@ template <typename S, typename T, int M>
 dr_status fold_static_dispatch(dr_plan *P, const void *u, cudaStream_t st, StaticOut &rs) {
     if (!P->fold2_ok) return fail(DR_EINVAL, "two-kernel folded forward unavailable for this plan");
     if constexpr (M >= 4) {
-        switch (P->fold2_gi) {
+        switch (sizeof(S) == 2 ? P->fold2_gi_st : P->fold2_gi) {
             case 0: return fold_static_launch<S, T, M, 0>(P, u, st, rs);
             case 2: return fold_static_launch<S, T, M, 2>(P, u, st, rs);
             case 4: return fold_static_launch<S, T, M, 4>(P, u, st, rs);

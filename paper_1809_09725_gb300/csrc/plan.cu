@@ -490,7 +490,7 @@ static dr_status build_tables(dr_plan *P) {
         }
         P->fold2_ok = P->m >= 4 && P->fold2_R[0] >= 1;
         // default: groups of 4 coefficients, 256 threads (the autotuner times all)
-        P->fold2_gi = 0;
+        P->fold2_gi = P->fold2_gi_st = 0;
         P->fold2_lines = P->fold2_lines_st = std::max(1, std::min(4, P->fold2_R[0]));
         // cost model until measured: fold when the unique angles carry the work
         const double direct = (double)K * (P->m + 16), fold = (double)U * (3.0 * P->m + 12) + 0.05 * K * P->m;

@@ -141,7 +141,7 @@ struct TuneKey {
 };
 struct TuneVal {
     int fwd, adj, lines, async, lines_st, async_st, f2_gi, f2_lines, f2_lines_st, fwd_st, f2_split, f2_async,
-        f2_async_st, adj_pp, f2_bv;
+        f2_async_st, adj_pp, f2_bv, f2_gi_st;
     double ms[5];
 };
 static std::mutex g_tune_mutex;
@@ -175,6 +175,7 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
             P->fold_lines_st = it->second.lines_st;
             P->fold_async_st = it->second.async_st;
             P->fold2_gi = it->second.f2_gi;
+            P->fold2_gi_st = it->second.f2_gi_st;
             P->fold2_lines = it->second.f2_lines;
             P->fold2_lines_st = it->second.f2_lines_st;
             P->sel_fwd_st = it->second.fwd_st;
@@ -475,15 +476,31 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
         P->fold2_lines = bl;
         P->fold2_lines_st = bl;
         P->fold2_async_st = P->fold2_async;
+        P->fold2_gi_st = bgi;
         if (P->prec == DR_BF16_F32ACC) {
+            // storage-typed calls march bf16 strips: the compute-typed group and
+            // its 8-coefficient partner (same CTA shape), whose 16-byte bf16
+            // pixel vectors load like the 4-coefficient float ones
             double best_t = 1e30;
-            int bls = bl, bas = 0;
-            for (int as = 0; as < 3; ++as) {
-                P->fold2_async_st = as;
-                dr_status s = search_lines(P->fold2_R[bgi], run2(false), bls, best_t, better);
-                if (s != DR_OK) return s;
-                if (better) bas = as;
+            int bls = bl, bas = 0, bgs = bgi;
+            int cand[2] = {bgi, -1};
+            if ((bgi | 1) != bgi && gi_ok(bgi | 1)) cand[1] = bgi | 1;
+            for (int gs : cand) {
+                if (gs < 0) continue;
+                P->fold2_gi_st = gs;
+                for (int as = 0; as < (gs == bgi ? 3 : 2); ++as) {
+                    P->fold2_async_st = as;
+                    int lines = bls;
+                    dr_status s = search_lines(P->fold2_R[gs], run2(false), lines, best_t, better);
+                    if (s != DR_OK) return s;
+                    if (better) {
+                        bas = as;
+                        bls = lines;
+                        bgs = gs;
+                    }
+                }
             }
+            P->fold2_gi_st = bgs;
             P->fold2_lines_st = bls;
             P->fold2_async_st = bas;
             ms_st2 = best_t;
@@ -550,7 +567,7 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
                                                  P->fold_lines_st, P->fold_async_st, P->fold2_gi, P->fold2_lines,
                                                  P->fold2_lines_st, P->sel_fwd_st, P->fold2_split,
                                                  P->fold2_async, P->fold2_async_st, P->fold_adj_pp, P->fold2_bv,
-                                                 {0, 0, 0, 0, 0}});
+                                                 P->fold2_gi_st, {0, 0, 0, 0, 0}});
     if (ins.second) {
         for (int i = 0; i < 5; ++i) ins.first->second.ms[i] = P->tune_ms[i];
     } else {  // another thread tuned the same problem first: follow its choice
@@ -561,6 +578,7 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
         P->fold_lines_st = ins.first->second.lines_st;
         P->fold_async_st = ins.first->second.async_st;
         P->fold2_gi = ins.first->second.f2_gi;
+        P->fold2_gi_st = ins.first->second.f2_gi_st;
         P->fold2_lines = ins.first->second.f2_lines;
         P->fold2_lines_st = ins.first->second.f2_lines_st;
         P->sel_fwd_st = ins.first->second.fwd_st;
@@ -660,7 +678,7 @@ dr_status dr_plan_set_fold_groups(dr_plan *P, int group, int threads, int rays_p
         return fail(DR_EINVAL, "dr_plan_set_fold_groups: no such configuration (group 4 or 8, 8 only for m > 4; "
                                "threads 256, 512 or 1024 with their rays per thread) or lines outside the strip "
                                "budget");
-    P->fold2_gi = gi;
+    P->fold2_gi = P->fold2_gi_st = gi;
     P->fold2_lines = P->fold2_lines_st = lines;
     P->fold2_bv = 0;
     return DR_OK;
