@@ -103,3 +103,20 @@ def test_slab_estimate_lets_the_largest_serving_job_fit(lib):
     sizes = [dr.job_slab_device_bytes(d, s) for s in (1, 2, 4, 8, 16)]
     assert all(a < b for a, b in zip(sizes, sizes[1:]))
     assert sizes[3] < budget  # slabs of 8 slices
+
+
+def test_host_side_argument_checks_without_a_gpu(lib):
+    """Entry points reject missing arguments on the host, before any CUDA
+    call: a NULL plan, a resume request without a state buffer; the solver
+    defaults keep checkpointing off."""
+    import ctypes
+    from paper_1809_09725_gb300 import dynrecon as dr
+    assert lib.dr_plan_state_bytes(None, dr.ADMM_CG) == 0
+    assert lib.dr_plan_wait_selftest(None, 0.1) == dr.DR_EINVAL
+    assert lib.tv4d_normal(None, None, None, 1.0, 0.0) == dr.DR_EINVAL
+    p = dr.SolveParams()
+    lib.dr_solve_params_default(ctypes.byref(p))
+    assert not p.state and p.resume == 0
+    assert (p.algo, p.iters, p.n_cg) == (dr.ADMM_CG, 20, 4)
+    assert lib.admm_solve(None, None, None, ctypes.byref(p)) == dr.DR_EINVAL
+    assert "NULL" in lib.dr_last_error().decode()
