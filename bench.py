@@ -1,9 +1,10 @@
 """Benchmark of the dynamic-tomography hot path on GB300.
 
-Workload (default): 16 slices of 256^2 voxels, 256 detector bins, K = 1800
-projections over 10 continuous half-turns, m = 8 real Fourier coefficient
-volumes, nt = 10 frames, moving-ellipsoid phantom with Poisson noise (1e4
-photons), FP32 -- reconstructed with ADMM-CG (4 CG steps per u-step).
+Workload (default, the large mixed-precision volume): 64 slices of
+1024^2 voxels, 1024 detector bins, K = 6000 projections over 20 continuous
+half-turns, m = 16 shifted-Legendre coefficient volumes, nt = 20 frames,
+sharp-edged moving ellipsoids with Poisson noise (1e4 photons), FP32,
+reconstructed with ADMM-CG (4 CG steps per u-step).
 
 One step = one ADMM-CG iteration: 5 dynamic forward projections, 5 dynamic
 back-projections (1 residual + 4 CG), the 4D TV stencils, the prox and the
@@ -62,30 +63,33 @@ def fp32_peak_tflops(sm_mhz=None):
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="ellipsoids256")
+    ap.add_argument("--workload", default="ellipsoids1024")
+    ap.add_argument("--op-reps", type=int, default=5, help="timed launches of each projector for the roofline")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-iters", type=int, default=5, help="ADMM-CG iterations of each end-to-end job")
+    ap.add_argument("--e2e-jobs", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-jobs", type=int, default=24)
+    ap.add_argument("--batch-jobs", type=int, default=16)
+    ap.add_argument("--extra-workloads", default="ellipsoids256",
+                    help="comma-separated workloads also timed (FP32 ADMM-CG) as extra keys")
     ap.add_argument("--no-slabs", action="store_true", help="skip the slab-streaming measurement")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the BF16-operator, FBP and slab-streaming measurements")
-    ap.add_argument("--fold-strip", type=int, default=0,
-                    help="with --variant: fix the folded forward's strip height (lines) instead of the default")
+                    help="skip the BF16, TV-kernel, FBP, extra-workload, batched, slab and serving measurements")
     ap.add_argument("--variant", default=None,
                     help="force projector variants 'fwd,adj' (0 direct, 1 fold, 2 fold in two kernels: forward "
                          "only); default: autotuned")
     ap.add_argument("--fold2-config", default=None,
-                    help="with --variant 2,x or --profile-small: fix the two-kernel folded forward's "
+                    help="with --variant 2,x: fix the two-kernel folded forward's "
                          "'group,threads,lines[,split[,async[,rays_per_thread]]]' instead of the default")
     ap.add_argument("--fold-adj-angles", type=int, default=0,
-                    help="with --variant x,1 or --profile-small: fix the folded adjoint's distinct angles per "
-                         "pipeline stage instead of the default")
+                    help="with --variant x,1: fix the folded adjoint's distinct angles per pipeline stage")
     ap.add_argument("--profile-small", action="store_true",
-                    help="run only one launch of each projector kernel on the workload (for ncu captures)")
+                    help="run only one launch of each projector call on the workload (for ncu captures)")
     return ap.parse_args()
 
 
@@ -233,96 +237,20 @@ def algorithmic_flops(w, variant, U):
     return 2.0 * (w.m + 2) * w.K * w.voxels()
 
 
-def run_ours(a):
+def time_projectors(plan, dev, stream, reps=5, dtype=None):
+    """Mean device time (CUDA events on the launching stream) of one forward
+    and one back-projection through the C ABI, in the variants the plan
+    selected, on random inputs of the plan's shapes."""
     import torch
 
     from paper_1809_09725_gb300 import dynrecon as dr
-    from paper_1809_09725_gb300 import synth
-
-    rank, world, tdist = dist_init(a.gpus)
-    local = int(os.environ.get("LOCAL_RANK", rank))
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    w = synth.WORKLOADS[a.workload]
-    theta, t, g_np = synth.make_data(w)
-    plan = dr.Plan(w.N, w.N, w.nz, w.ns, theta, t, w.basis, w.m, w.nt, dr.F32)
-    g = torch.from_numpy(g_np.astype(np.float32)).to(dev)
-    u = torch.zeros(plan.u_shape(), dtype=torch.float32, device=dev)
-    units_per_iter = 2 * (w.n_cg + 1) * w.K * w.voxels()  # projector applications x K V
-    if a.variant:
-        fv, av = (int(x) for x in a.variant.split(","))
-        plan.set_variant(fv, av)
-        if a.fold_strip > 0:
-            plan.set_fold_strip(a.fold_strip, False)
-        if fv == dr.FOLD2 and a.fold2_config:
-            set_fold2_config(plan, a.fold2_config)
-        if av == dr.FOLD and a.fold_adj_angles > 0:
-            plan.set_fold_adj_stage(a.fold_adj_angles)
-
-    if a.profile_small:
-        # one forward and one adjoint of each variant (direct, half-turn fold)
-        # on the benchmark workload, for profiler captures
-        uin = torch.randn(plan.u_shape(), dtype=torch.float32, device=dev)
-        gout = torch.empty_like(g)
-        for var in (dr.DIRECT, dr.FOLD):
-            plan.set_variant(var, var)
-            if var == dr.FOLD and a.fold_strip > 0:
-                plan.set_fold_strip(a.fold_strip, False)
-            if var == dr.FOLD and a.fold_adj_angles > 0:
-                plan.set_fold_adj_stage(a.fold_adj_angles)
-            dr.dyn_radon_fwd(plan, uin, gout)
-            dr.dyn_radon_adj(plan, g, u)
-        # the two-kernel folded forward (static transforms + distribution)
-        plan.set_variant(dr.FOLD2, dr.FOLD)
-        if a.fold2_config:
-            set_fold2_config(plan, a.fold2_config)
-        dr.dyn_radon_fwd(plan, uin, gout)
-        # the folded forward on BF16 storage (bf16 strip)
-        pb = dr.Plan(w.N, w.N, w.nz, w.ns, theta, t, w.basis, w.m, w.nt, dr.BF16)
-        pb.set_variant(dr.FOLD, dr.FOLD)
-        pb.set_fold_strip(6, False)
-        gb = torch.empty(pb.g_shape(), dtype=torch.bfloat16, device=dev)
-        dr.dyn_radon_fwd(pb, uin.to(torch.bfloat16), gb)
-        torch.cuda.synchronize()
-        print(json.dumps({"profile_small": True}))
-        return
-
-    prm = dr.solve_params(dr.ADMM_CG, iters=a.warmup, n_cg=w.n_cg, lambda1=w.lambda1, lambda2=w.lambda2,
-                          rho=w.rho)
-    dr.admm_solve(plan, g, u, prm, want_objective=False)  # warm-up iterations (untimed)
-    u.zero_()
-    torch.cuda.synchronize()
-    prm = dr.solve_params(dr.ADMM_CG, iters=a.steps, n_cg=w.n_cg, lambda1=w.lambda1, lambda2=w.lambda2,
-                          rho=w.rho)
-    stream = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
-        if tdist is not None:
-            tdist.barrier()
-        torch.cuda.synchronize()
-        e0.record(stream)
-        res = dr.admm_solve(plan, g, u, prm, want_objective=True)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        if tdist is not None:
-            tdist.barrier()
-    ms = e0.elapsed_time(e1)
-    ms = barrier_max(tdist, ms, dev)
-    total_units = replica_units(units_per_iter * a.steps, world)
-    value = total_units / (ms * 1e-3)
-    obj = res["objective"]
-
-    # dominant kernels: time the projector pair alone on the same stream, in
-    # the variant the solver selected (autotuned inside admm_solve)
-    info = plan.info()
-    tune = plan.autotune() if not a.variant else None
-    p_in = torch.randn(plan.u_shape(), dtype=torch.float32, device=dev)
-    gbuf = torch.empty(plan.g_shape(), dtype=torch.float32, device=dev)
-    ubuf = torch.empty(plan.u_shape(), dtype=torch.float32, device=dev)
-    for _ in range(3):
+    dt = dtype or getattr(torch, plan.storage_dtype)
+    p_in = torch.randn(plan.u_shape(), dtype=torch.float32, device=dev).to(dt)
+    gbuf = torch.empty(plan.g_shape(), dtype=dt, device=dev)
+    ubuf = torch.empty(plan.u_shape(), dtype=dt, device=dev)
+    for _ in range(2):
         dr.dyn_radon_fwd(plan, p_in, gbuf)
         dr.dyn_radon_adj(plan, gbuf, ubuf)
-    reps = 10
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     torch.cuda.synchronize()
     ev[0].record(stream)
@@ -333,157 +261,258 @@ def run_ours(a):
         dr.dyn_radon_adj(plan, gbuf, ubuf)
     ev[2].record(stream)
     torch.cuda.synchronize()
-    fwd_ms = ev[0].elapsed_time(ev[1]) / reps
-    adj_ms = ev[1].elapsed_time(ev[2]) / reps
+    out = ev[0].elapsed_time(ev[1]) / reps, ev[1].elapsed_time(ev[2]) / reps
+    del p_in, gbuf, ubuf
+    return out
+
+
+def roofline_of(w, theta, info, fwd_ms, adj_ms, tune=None):
+    """Roofline of the dominant projector call (the slower of the pair):
+    FP32 ALU flops of the half-turn fold (or of the direct form) against
+    the derived FP32 pipe peak; algorithmic HBM bytes against the measured
+    copy bandwidth; algorithmic shared-memory bytes against the derived
+    shared-memory bandwidth (side key)."""
     U = info["unique_angles"]
     if fwd_ms >= adj_ms:
         variant = info["fwd_variant"]
         kname = {1: "fold_fwd_kernel", 2: "fold_fwd_kernel(static)+fold_dist_kernel"}.get(variant, "fwd_kernel")
         launch_ms = fwd_ms
+        smem_bytes = algorithmic_smem_bytes(w, theta, variant, U)
     else:
         variant = info["adj_variant"]
         kname = "fold_adj_kernel+fold_data_kernel" if variant == 1 else "adj_kernel"
         launch_ms = adj_ms
+        smem_bytes = 2 * w.m * 4 * (U if variant == 1 else w.K) * w.voxels()
     flops = algorithmic_flops(w, variant, U)
     achieved = flops / (launch_ms * 1e-3) / 1e12
-    clocks = clk.summary()
     peak = fp32_peak_tflops()
-    traffic = load_traffic(kname)
-    if fwd_ms >= adj_ms:
-        smem_bytes = algorithmic_smem_bytes(w, theta, variant, U)
-    else:
-        smem_bytes = 2 * w.m * 4 * (U if variant == 1 else w.K) * w.voxels()
+    hbm_bytes = 4 * (w.m * w.voxels() + w.K * w.ns * w.nz)  # read u + write g (or the reverse), FP32
+    hbm_peak, hbm_src = hbm_peak_gbs()
+    hbm_gbs = hbm_bytes / (launch_ms * 1e-3) / 1e9
     smem_achieved = smem_bytes / (launch_ms * 1e-3) / 1e12
-    smem_peak = smem_peak_tbs()
+    samples = joseph_samples(theta, w.N, w.N, w.ns) * w.nz if variant in (1, 2) else None
+    traffic = load_traffic(kname, w.name)
+    return {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": traffic,
+            "algorithmic_flops_per_launch": flops,
+            "flops_formula": ("2 (2 m U V + m K ns nz), U distinct angles mod pi" if variant in (1, 2)
+                              else "2 (m + 2) K V"),
+            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (max SM clock)",
+            "joseph_samples_per_launch": samples,
+            "hbm": {"achieved_gbs": hbm_gbs, "peak_gbs": hbm_peak, "frac": hbm_gbs / hbm_peak,
+                    "algorithmic_bytes": hbm_bytes, "traffic": traffic, "peak_source": hbm_src},
+            "smem": {"achieved_tbs": smem_achieved, "peak_tbs": smem_peak_tbs(),
+                     "frac": smem_achieved / smem_peak_tbs(), "algorithmic_bytes": smem_bytes,
+                     "peak_source": "derived: 152 SMs x 128 B/clk x 2.07 GHz"},
+            "launch_ms": launch_ms, "fwd_ms": fwd_ms, "adj_ms": adj_ms,
+            "variants": {"unique_angles": U, "fwd": info["fwd_variant"], "adj": info["adj_variant"],
+                         "fold2_group_threads_lines_split_async_rpt": [
+                             info["fold2_group"], info["fold2_threads"], info["fold2_lines"],
+                             info["fold2_split"], info["fold2_async"], info["fold2_rays_per_thread"]],
+                         "fold_adj_angles_per_stage": info["fold_adj_angles"],
+                         "autotune_ms_fwd_direct_fold_adj_direct_fold_fwd_fold2": tune}}
 
-    # the projector pair on BF16 storage (FP32 accumulation) next to FP32
-    bf16_ops = None
-    if rank == 0 and not a.no_extras:
-        pb = dr.Plan(w.N, w.N, w.nz, w.ns, theta, t, w.basis, w.m, w.nt, dr.BF16)
-        pb.autotune()
-        ub = p_in.to(torch.bfloat16)
-        gb = torch.empty(pb.g_shape(), dtype=torch.bfloat16, device=dev)
-        uab = torch.empty_like(ub)
-        for _ in range(3):
-            dr.dyn_radon_fwd(pb, ub, gb)
-            dr.dyn_radon_adj(pb, gb, uab)
-        bev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+
+def launches_per_iteration(info, n_cg):
+    """Kernels one ADMM-CG iteration launches: n_cg + 1 forwards and adjoints
+    (the folded adjoint is two launches: data fold + back-projection; the
+    two-kernel folded forward too: static transforms + distribution; with
+    both folded, a CG step's R*R p is the folded normal operator: static
+    transforms, Gram mix, back-projection), n_cg + 1 D^T D (right-hand side +
+    CG steps), prox, D^T w, n_cg updates, n_cg - 1 direction updates, the
+    fidelity dot and the iteration counter."""
+    adj_launches = 2 if info["adj_variant"] == 1 else 1
+    fwd_launches = 2 if info["fwd_variant"] == 2 else 1
+    normal_launches = 3 if (info["fwd_variant"], info["adj_variant"]) == (2, 1) else fwd_launches + adj_launches
+    per_iter = (1 + fwd_launches + adj_launches) + n_cg * (1 + normal_launches) + 2 * n_cg + 3
+    return per_iter, fwd_launches
+
+
+def solve_timed(plan, g, u, w, steps, warmup, tdist, dev, local, want_obj=True):
+    """W untimed ADMM-CG iterations (autotuning on the first call), then
+    exactly `steps` iterations in one admm_solve call bracketed by a barrier
+    and a device synchronisation, timed with CUDA events on the plan's
+    stream, clocks sampled meanwhile."""
+    import torch
+
+    from paper_1809_09725_gb300 import dynrecon as dr
+    prm = dr.solve_params(dr.ADMM_CG, iters=warmup, n_cg=w.n_cg, lambda1=w.lambda1, lambda2=w.lambda2,
+                          rho=w.rho)
+    dr.admm_solve(plan, g, u, prm, want_objective=False)
+    u.zero_()
+    torch.cuda.synchronize()
+    prm = dr.solve_params(dr.ADMM_CG, iters=steps, n_cg=w.n_cg, lambda1=w.lambda1, lambda2=w.lambda2,
+                          rho=w.rho)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        if tdist is not None:
+            tdist.barrier()
         torch.cuda.synchronize()
-        bev[0].record(stream)
-        for _ in range(reps):
-            dr.dyn_radon_fwd(pb, ub, gb)
-        bev[1].record(stream)
-        for _ in range(reps):
-            dr.dyn_radon_adj(pb, gb, uab)
-        bev[2].record(stream)
-        torch.cuda.synchronize()
-        bf16_ops = {"fwd_ms": bev[0].elapsed_time(bev[1]) / reps, "adj_ms": bev[1].elapsed_time(bev[2]) / reps,
-                    "fp32_fwd_ms": fwd_ms, "fp32_adj_ms": adj_ms,
-                    "note": "dyn_radon_fwd / dyn_radon_adj on bf16 u and g (FP32 accumulation), same workload"}
-        del pb, ub, gb, uab
-
-    # FBP initial guess (Sec. 5), one window per half-turn: filter + one back-projection
-    fbp = None
-    tv_kernels = None
-    if not a.no_extras:
-        fbp = run_fbp(plan, g, w, dev, stream)
-        tv_kernels = run_tv_kernels(plan, w, dev, stream)
-
-    # end to end through the public call with host buffers (one full job per call)
-    e2e = None
-    if not a.no_e2e:
-        gh = torch.from_numpy(g_np.astype(np.float32)).pin_memory()
-        uh = torch.zeros(plan.u_shape(), dtype=torch.float32).pin_memory()
-        ghn, uhn = gh.numpy(), uh.numpy()
-        jobs = 2
-        prm_e = dr.solve_params(dr.ADMM_CG, iters=w.iters, n_cg=w.n_cg, lambda1=w.lambda1, lambda2=w.lambda2,
-                                rho=w.rho)
-        dr.admm_solve(plan, ghn, uhn, dr.solve_params(dr.ADMM_CG, iters=2, n_cg=w.n_cg, lambda1=w.lambda1,
-                                                      lambda2=w.lambda2, rho=w.rho), want_objective=False)
+        e0.record(stream)
+        res = dr.admm_solve(plan, g, u, prm, want_objective=want_obj)
+        e1.record(stream)
         torch.cuda.synchronize()
         if tdist is not None:
             tdist.barrier()
-        t0 = time.perf_counter()
-        for _ in range(jobs):
-            uhn[...] = 0.0
-            dr.admm_solve(plan, ghn, uhn, prm_e, want_objective=False)
+    ms = barrier_max(tdist, e0.elapsed_time(e1), dev)
+    return ms, res, clk.summary()
+
+
+def run_ours(a):
+    import torch
+
+    from paper_1809_09725_gb300 import dynrecon as dr
+    from paper_1809_09725_gb300 import synth
+
+    rank, world, tdist = dist_init(a.gpus)
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    w = synth.WORKLOADS[a.workload]
+    t_data = time.perf_counter()
+    theta, t, g_np = synth.make_data(w)
+    g32 = g_np.astype(np.float32)
+    del g_np
+    t_data = time.perf_counter() - t_data
+    plan = dr.Plan(w.N, w.N, w.nz, w.ns, theta, t, w.basis, w.m, w.nt, dr.F32)
+    g = torch.from_numpy(g32).to(dev)
+    u = torch.zeros(plan.u_shape(), dtype=torch.float32, device=dev)
+    units_per_iter = 2 * (w.n_cg + 1) * w.K * w.voxels()  # projector applications x K V
+    if a.variant:
+        fv, av = (int(x) for x in a.variant.split(","))
+        plan.set_variant(fv, av)
+        if fv == dr.FOLD2 and a.fold2_config:
+            set_fold2_config(plan, a.fold2_config)
+        if av == dr.FOLD and a.fold_adj_angles > 0:
+            plan.set_fold_adj_stage(a.fold_adj_angles)
+
+    if a.profile_small:
+        # one launch of the selected projector pair on the workload, for profiler captures
+        if not a.variant:
+            plan.autotune()
+        uin = torch.randn(plan.u_shape(), dtype=torch.float32, device=dev)
+        gout = torch.empty_like(g)
+        dr.dyn_radon_fwd(plan, uin, gout)
+        dr.dyn_radon_adj(plan, g, u)
         torch.cuda.synchronize()
-        el = barrier_max(tdist, time.perf_counter() - t0, dev)
-        e2e = {"value": units_per_iter * w.iters * jobs * world / el, "unit": "voxel*projection/s",
-               "h2d_bytes_per_step": int(g_np.size * 4 + uhn.nbytes), "d2h_bytes_per_step": int(uhn.nbytes),
-               "step": "one %d-iteration reconstruction job via admm_solve on pinned host buffers" % w.iters,
-               "jobs": jobs, "s_per_job": el / jobs}
+        print(json.dumps({"profile_small": True, "info": plan.info()}))
+        return
 
-    serving = None
-    if not a.no_serving:
-        serving = {name: run_serving(a, local, prec) for name, prec in (("fp32", dr.F32), ("bf16", dr.BF16))}
-        if rank == 0 and not a.no_extras:
-            serving["load_sweep_fp32"] = run_serving_sweep(a, local)
+    t_tune = time.perf_counter()
+    tune = plan.autotune() if not a.variant else None
+    t_tune = time.perf_counter() - t_tune
+    ms, res, clocks = solve_timed(plan, g, u, w, a.steps, a.warmup, tdist, dev, local)
+    value = replica_units(units_per_iter * a.steps, world) / (ms * 1e-3)
+    obj = res["objective"]
+    info = plan.info()
 
-    batched = None
-    if rank == 0 and not a.no_extras:
-        batched = run_batched(dev)
+    # the dominant kernels alone, on the same stream, in the variants the solver used
+    fwd_ms, adj_ms = time_projectors(plan, dev, stream, reps=a.op_reps)
+    roof = roofline_of(w, theta, info, fwd_ms, adj_ms, tune)
+    per_iter, fwd_launches = launches_per_iteration(info, w.n_cg)
 
-    slabs = None
-    if rank == 0 and not (a.no_slabs or a.no_extras):
-        slabs = run_slabs(w, theta, t, g_np, dev)
+    # end to end through the public call with host buffers: each step is one
+    # reconstruction job of e2e_iters iterations from pinned host memory
+    e2e = None
+    if not a.no_e2e:
+        e2e = run_e2e(plan, g32, w, a.e2e_iters, a.e2e_jobs, tdist, dev, units_per_iter, world)
 
+    extras = {}
     cpu = None
-    accuracy = None
     if rank == 0 and not a.no_cpu_baseline:
-        cpu = cpu_baseline(w, theta, t, g_np)
+        cpu, acc_ops = cpu_baseline_and_accuracy(plan, w, theta, t, g32, dev)
         cpu["one_thread"] = cpu_baseline_1thread(w)
-        accuracy = accuracy_vs_oracle(w, theta, t, g_np, dev)
+        extras["operator_accuracy_vs_fp64_oracle"] = acc_ops
+    del g, u
+    torch.cuda.empty_cache()
+
+    if rank == 0 and not a.no_extras:
+        extras["tv_kernels"] = guarded(run_tv_kernels, plan, w, dev, stream)
+        extras["fbp_init"] = guarded(run_fbp, plan, torch.from_numpy(g32).to(dev), w, dev, stream)
+        torch.cuda.empty_cache()
+    plan.close()
+    torch.cuda.empty_cache()
+    if rank == 0 and not a.no_extras:
+        extras["bf16_storage"] = guarded(run_bf16_storage, w, theta, t, g32, dev, stream, a)
+        torch.cuda.empty_cache()
+    del g32
+    if rank == 0 and not a.no_extras:
+        for name in a.extra_workloads.split(",") if a.extra_workloads else []:
+            extras[name] = guarded(run_workload_line, name, dev, stream, local, a)
+            torch.cuda.empty_cache()
+        extras["disks64_fp64_whole_solve"] = guarded(run_disks_fp64, dev)
+        extras["batched_jobs"] = guarded(run_batched, dev, a.batch_jobs)
+        if not a.no_slabs:
+            extras["slab_streaming"] = guarded(run_slabs_workload, "ellipsoids256", dev)
+    if not a.no_serving and rank == 0 and not a.no_extras:
+        extras["serving"] = {name: guarded(run_serving, a, local, prec) for name, prec in
+                             (("fp32", dr.F32), ("bf16", dr.BF16))}
+        extras["serving"]["load_sweep_fp32"] = guarded(run_serving_sweep, a, local)
 
     if rank == 0:
-        # per ADMM-CG iteration: n_cg + 1 forwards and adjoints (the folded
-        # adjoint is two launches: data fold + back-projection), n_cg + 1 D^T D
-        # (right-hand side + CG steps), prox, D^T w, n_cg updates, n_cg - 1
-        # direction updates, the fidelity dot, the iteration counter
-        # (the two-kernel folded forward is two launches too: static transforms +
-        # distribution).  With both folded, the CG steps' R*R p is the folded
-        # normal operator: static transforms, Gram mix, back-projection.
-        adj_launches = 2 if info["adj_variant"] == 1 else 1
-        fwd_launches = 2 if info["fwd_variant"] == 2 else 1
-        normal_launches = 3 if (info["fwd_variant"], info["adj_variant"]) == (2, 1) else fwd_launches + adj_launches
-        launches_per_iter = ((1 + fwd_launches + adj_launches) + w.n_cg * (1 + normal_launches) + 2 * w.n_cg + 3)
         line = {
             "metric": "voxel*projection updates/s (dynamic projector + back-projector applications "
                       "inside ADMM-CG iterations)",
             "value": value, "unit": "voxel*projection/s", "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded moving ellipsoids, Poisson 1e4)",
-            "config": bench_config(world),
+            "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded %s, exact line integrals + Poisson noise at 1e4 photons)" % (
+                "sharp-edged moving ellipsoids" if w.name == "ellipsoids1024" else "moving ellipsoids"),
+            "config": bench_config(w, world),
             "admm_iters_per_s": a.steps * world / (ms * 1e-3),
             "objective_first_last": [float(obj[0]), float(obj[-1])],
             "clocks": clocks,
             "e2e": e2e,
-            "gpu_launches": launches_per_iter * a.steps + fwd_launches + 1,  # + the final fidelity (forward + dot)
-            "roofline": {"bound": "smem", "kernel": kname, "achieved": smem_achieved, "peak": smem_peak,
-                         "unit": "TB/s", "frac": smem_achieved / smem_peak, "traffic": traffic,
-                         "algorithmic_smem_bytes_per_launch": smem_bytes,
-                         "peak_source": "derived: 152 SMs x 128 B/clk shared-memory bandwidth x 2.07 GHz max SM clock",
-                         "alu": {"achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                                 "algorithmic_flops_per_launch": flops,
-                                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"},
-                         "launch_ms": launch_ms, "fwd_ms": fwd_ms, "adj_ms": adj_ms,
-                         "variants": {"unique_angles": U, "fwd": info["fwd_variant"], "adj": info["adj_variant"],
-                                      "fold_lines": info["fold_lines"], "fold_async": info["fold_async"],
-                                      "fold_adj_angles_per_stage": info["fold_adj_angles"],
-                                      "fold2_group_threads_lines_split_async_rpt": [
-                                          info["fold2_group"], info["fold2_threads"], info["fold2_lines"],
-                                          info["fold2_split"], info["fold2_async"], info["fold2_rays_per_thread"]],
-                                      "autotune_ms_fwd_direct_fold_adj_direct_fold_fwd_fold2": tune}},
+            "gpu_launches": per_iter * a.steps + fwd_launches + 1,  # + the final fidelity (forward + dot)
+            "roofline": roof,
             "cpu_baseline": cpu,
-            "serving": serving,
-            "accuracy_vs_fp64_oracle": accuracy,
-            "batched_jobs": batched,
-            "fbp_init": fbp,
-            "tv_kernels": tv_kernels,
-            "bf16_operators": bf16_ops,
-            "slab_streaming": slabs,
+            "setup_s": {"data": t_data, "autotune": t_tune},
         }
+        line.update(extras)
         print(json.dumps(line))
+
+
+def guarded(fn, *args, **kw):
+    """Run one optional measurement; its failure is reported in its key
+    instead of ending the benchmark."""
+    try:
+        return fn(*args, **kw)
+    except Exception as exc:  # noqa: BLE001 -- reported in the JSON line
+        import traceback
+        return {"error": repr(exc)[:300], "where": traceback.format_exc().splitlines()[-3:]}
+
+
+def run_e2e(plan, g32, w, iters, jobs, tdist, dev, units_per_iter, world):
+    """The same metric through admm_solve on pinned host buffers: every job
+    copies its data and initial guess in and its result out inside the
+    timed region (host wall clock, device synchronised on both sides)."""
+    import torch
+
+    from paper_1809_09725_gb300 import dynrecon as dr
+    gh = torch.from_numpy(g32).pin_memory()
+    uh = torch.zeros(plan.u_shape(), dtype=torch.float32).pin_memory()
+    ghn, uhn = gh.numpy(), uh.numpy()
+    prm = lambda n: dr.solve_params(dr.ADMM_CG, iters=n, n_cg=w.n_cg, lambda1=w.lambda1, lambda2=w.lambda2,
+                                    rho=w.rho)
+    dr.admm_solve(plan, ghn, uhn, prm(1), want_objective=False)  # staging buffers allocated once
+    torch.cuda.synchronize()
+    if tdist is not None:
+        tdist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(jobs):
+        uhn[...] = 0.0
+        dr.admm_solve(plan, ghn, uhn, prm(iters), want_objective=False)
+    torch.cuda.synchronize()
+    el = barrier_max(tdist, time.perf_counter() - t0, dev)
+    out = {"value": units_per_iter * iters * jobs * world / el, "unit": "voxel*projection/s",
+           "h2d_bytes_per_step": int(g32.nbytes + uhn.nbytes), "d2h_bytes_per_step": int(uhn.nbytes),
+           "step": "one %d-iteration reconstruction job via admm_solve on pinned host buffers "
+                   "(data and initial guess in, result out)" % iters,
+           "jobs": jobs, "s_per_job": el / jobs}
+    del gh, uh
+    return out
 
 
 def serving_jobs(n, seed=180905):
@@ -551,7 +580,7 @@ def run_serving(a, device, prec):
             "errors": [{"job": i, "rc": r["rc"], "error": r["error"]} for i, r in enumerate(res) if r["rc"] != 0]}
 
 
-def run_tv_kernels(plan, w, dev, stream, reps=10):
+def run_tv_kernels(plan, w, dev, stream, reps=5):
     """The HBM-bound TV stencils through the C ABI on the workload's volume:
     tv4d_prox (shrink + dual update: reads u and mu, writes mu and w),
     tv4d_grad_adj (D^T p: reads p, writes u) and tv4d_grad (D u: reads u,
@@ -575,10 +604,10 @@ def run_tv_kernels(plan, w, dev, stream, reps=10):
         "grad": (lambda: dr.tv4d_grad(plan, u, wf, w.lambda2), ub + fb),
         "normal": (lambda: dr.tv4d_normal(plan, u, ua, w.lambda2, 1.0), 3 * ub),
     }
-    out = {"hbm_peak_gbs": peak, "peak_source": src,
+    out = {"hbm_peak_gbs": peak, "peak_source": src, "workload": w.name,
            "note": "one call each through the C ABI, inputs %.0f MB > L2; algorithmic bytes: prox u + 3 fields, "
-                   "grad_adj and grad one field + u, normal (out += D^T D x, as in a CG step) 3 x u; u alone "
-                   "(%.0f MB) fits in L2" % ((ub + fb) / 1e6, ub / 1e6)}
+                   "grad_adj and grad one field + u, normal (out += D^T D x, as in a CG step) 3 x u (u: %.0f MB)"
+                   % ((ub + fb) / 1e6, ub / 1e6)}
     for name, (fn, nbytes) in calls.items():
         for _ in range(3):
             fn()
@@ -667,87 +696,6 @@ def run_slabs(w, theta, t, g_np, dev, slab=4, iters=10):
             "copy_gbs": (h2d + d2h) * iters / t_sl / 1e9, "setup_s_per_call": setup_s,
             "note": "Chambolle-Pock, same operator norm; streamed = volume in pinned host memory, per-iteration "
                     "time from the difference of a %d- and a %d-iteration call" % (iters, 3 * iters)}
-
-
-def load_traffic(kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary
-    (profiles/traffic.txt), or None if that kernel was not captured."""
-    path = os.path.join(ROOT, "profiles", "traffic.txt")
-    try:
-        for line in open(path):
-            parts = line.split()
-            if len(parts) == 2 and not line.startswith("#") and parts[0] == kernel:
-                return int(parts[1])
-    except OSError:
-        pass
-    return None
-
-
-def cpu_baseline(w, theta, t, g_np, sample_slices=None):
-    """The FP64 oracle as it stands, on the host cores: one forward and one
-    back-projection of the same workload (bounded sample)."""
-    import oracle
-    nz = w.nz if sample_slices is None else sample_slices
-    P = oracle.Problem(w.N, w.N, nz, w.ns, theta, t, w.basis, w.m, w.nt)
-    rng = np.random.default_rng(1)
-    u = rng.standard_normal((nz, w.N, w.N, w.m))
-    t0 = time.perf_counter()
-    P.fwd(u)
-    P.adj(g_np[:nz])
-    el = time.perf_counter() - t0
-    units = 2 * w.K * w.N * w.N * nz
-    return {"value": units / el, "unit": "voxel*projection/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": "one forward + one back-projection, FP64 oracle, %d slices of the workload (%.1f s)"
-                      % (nz, el)}
-
-
-def cpu_baseline_1thread(w):
-    """The oracle on one host thread (OMP_NUM_THREADS=1, a separate process):
-    one forward and one back-projection of one slice of the workload."""
-    code = (
-        "import sys, time, numpy as np; sys.path.insert(0, %r); import oracle\n"
-        "from paper_1809_09725_gb300 import synth\n"
-        "w = synth.WORKLOADS[%r]; theta, t = synth.scan(w.K, w.n_halfturns, w.mod_pi)\n"
-        "P = oracle.Problem(w.N, w.N, 1, w.ns, theta, t, w.basis, w.m, w.nt)\n"
-        "rng = np.random.default_rng(1); u = rng.standard_normal((1, w.N, w.N, w.m))\n"
-        "g = rng.standard_normal((1, w.K, w.ns))\n"
-        "t0 = time.perf_counter(); P.fwd(u); P.adj(g); print(time.perf_counter() - t0)\n"
-    ) % (os.path.dirname(os.path.abspath(__file__)), w.name)
-    env = dict(os.environ, OMP_NUM_THREADS="1")
-    try:
-        out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
-        el = float(out.stdout.strip().splitlines()[-1])
-    except Exception as exc:  # noqa: BLE001 -- reported in the JSON line
-        return {"error": repr(exc)[:200]}
-    units = 2 * w.K * w.N * w.N
-    return {"value": units / el, "unit": "voxel*projection/s", "cores": 1, "kind": "oracle",
-            "sample": "one forward + one back-projection, FP64 oracle, 1 slice, one thread (%.1f s)" % el}
-
-
-def accuracy_vs_oracle(w, theta, t, g_np, dev, iters=3):
-    """Relative L2 error of the GPU solve against the FP64 oracle running the
-    same ADMM-CG iterations on a 1-slice cut of the workload."""
-    import torch
-
-    import oracle
-    from paper_1809_09725_gb300 import dynrecon as dr
-
-    g1 = g_np[:1]
-    P = oracle.Problem(w.N, w.N, 1, w.ns, theta, t, w.basis, w.m, w.nt)
-    t0 = time.perf_counter()
-    uo, oo, _ = P.admm_cg(g1, np.zeros((1, w.N, w.N, w.m)), iters, w.n_cg, w.lambda1, w.lambda2, w.rho)
-    t_or = time.perf_counter() - t0
-    out = {"cut": "slice 0 of the workload, %d ADMM-CG iterations from zero" % iters, "oracle_s": t_or}
-    for name, prec in (("fp32", dr.F32), ("bf16", dr.BF16)):
-        plan = dr.Plan(w.N, w.N, 1, w.ns, theta, t, w.basis, w.m, w.nt, prec)
-        dt = getattr(torch, plan.storage_dtype)
-        u = torch.zeros(plan.u_shape(), dtype=dt, device=dev)
-        prm = dr.solve_params(dr.ADMM_CG, iters=iters, n_cg=w.n_cg, lambda1=w.lambda1, lambda2=w.lambda2, rho=w.rho)
-        res = dr.admm_solve(plan, torch.from_numpy(g1).to(dt).to(dev), u, prm)
-        uu = u.to(torch.float64).cpu().numpy()
-        out[name] = {"rel_l2_u": float(np.linalg.norm(uu - uo) / np.linalg.norm(uo)),
-                     "rel_objective": float(abs(res["objective"][-1] - oo[-1]) / abs(oo[-1]))}
-    return out
 
 
 def run_serving_sweep(a, device, utilisations=(0.5, 0.8, 0.95)):
@@ -847,43 +795,248 @@ def run_batched(dev, n_jobs=16, iters=10, seed=180903):
                     "autotuning timed separately; jobs whose angles do not repeat mod pi use the direct pair"}
 
 
-def bench_config(world: int) -> dict:
+def load_traffic(kernel, workload):
+    """DRAM bytes per launch of `kernel` on `workload` from the committed ncu
+    summary (profiles/traffic.txt: kernel, workload, bytes), or None if that
+    kernel was not captured since it last changed."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    try:
+        for line in open(path):
+            parts = line.split()
+            if len(parts) == 3 and not line.startswith("#") and parts[0] == kernel and parts[1] == workload:
+                return int(parts[2])
+    except OSError:
+        pass
+    return None
+
+
+def cpu_baseline_and_accuracy(plan, w, theta, t, g32, dev):
+    """The FP64 oracle as it stands, on the host cores: one forward and one
+    back-projection of one slice of the workload with all K projections
+    (bounded sample).  The same inputs go through the GPU plan (slice 0 of
+    an otherwise zero volume / data set) and the outputs are compared."""
+    import torch
+
+    import oracle
+    from paper_1809_09725_gb300 import dynrecon as dr
+    P = oracle.Problem(w.N, w.N, 1, w.ns, theta, t, w.basis, w.m, w.nt)
+    rng = np.random.default_rng(1)
+    u0 = rng.standard_normal((1, w.N, w.N, w.m)).astype(np.float32).astype(np.float64)
+    g0 = g32[:1].astype(np.float64)
+    t0 = time.perf_counter()
+    ref_g = P.fwd(u0)
+    ref_u = P.adj(g0)
+    el = time.perf_counter() - t0
+    units = 2 * w.K * w.N * w.N
+    cpu = {"value": units / el, "unit": "voxel*projection/s", "cores": os.cpu_count(), "kind": "oracle",
+           "sample": "one forward + one back-projection of 1 of the %d slices with all %d projections, FP64 "
+                     "oracle (%.1f s)" % (w.nz, w.K, el)}
+    uin = torch.zeros(plan.u_shape(), dtype=torch.float32, device=dev)
+    uin[0] = torch.from_numpy(u0[0].astype(np.float32)).to(dev)
+    gout = torch.empty(plan.g_shape(), dtype=torch.float32, device=dev)
+    dr.dyn_radon_fwd(plan, uin, gout)
+    gin = torch.zeros(plan.g_shape(), dtype=torch.float32, device=dev)
+    gin[0] = torch.from_numpy(g32[0]).to(dev)
+    dr.dyn_radon_adj(plan, gin, uin)
+    torch.cuda.synchronize()
+    got_g = gout[0].double().cpu().numpy()
+    got_u = uin[0].double().cpu().numpy()
+
+    def errs(a, b):
+        return {"rel_l2": float(np.linalg.norm(a - b) / np.linalg.norm(b)),
+                "max_abs_over_max_ref": float(np.max(np.abs(a - b)) / np.max(np.abs(b)))}
+
+    acc = {"forward": errs(got_g, ref_g[0]), "adjoint": errs(got_u, ref_u[0]),
+           "sample": "slice 0: random N(0,1) coefficients (forward), the workload's data (adjoint); the plan's "
+                     "autotuned variants", "info": plan.info()}
+    del uin, gout, gin
+    return cpu, acc
+
+
+def cpu_baseline_1thread(w, kproj=100):
+    """The oracle on one host thread (OMP_NUM_THREADS=1, a separate process):
+    one forward and one back-projection of one slice with the first `kproj`
+    projections of the workload."""
+    code = (
+        "import sys, time, numpy as np; sys.path.insert(0, %r); import oracle\n"
+        "from paper_1809_09725_gb300 import synth\n"
+        "w = synth.WORKLOADS[%r]; theta, t = w.geometry(); kp = %d\n"
+        "P = oracle.Problem(w.N, w.N, 1, w.ns, theta[:kp], t[:kp], w.basis, w.m, w.nt)\n"
+        "rng = np.random.default_rng(1); u = rng.standard_normal((1, w.N, w.N, w.m))\n"
+        "g = rng.standard_normal((1, kp, w.ns))\n"
+        "t0 = time.perf_counter(); P.fwd(u); P.adj(g); print(time.perf_counter() - t0)\n"
+    ) % (os.path.dirname(os.path.abspath(__file__)), w.name, kproj)
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+        el = float(out.stdout.strip().splitlines()[-1])
+    except Exception as exc:  # noqa: BLE001 -- reported in the JSON line
+        return {"error": repr(exc)[:200]}
+    units = 2 * kproj * w.N * w.N
+    return {"value": units / el, "unit": "voxel*projection/s", "cores": 1, "kind": "oracle",
+            "sample": "one forward + one back-projection, FP64 oracle, 1 slice, first %d projections, one "
+                      "thread (%.1f s)" % (kproj, el)}
+
+
+def run_bf16_storage(w, theta, t, g32, dev, stream, a):
+    """The same workload on a BF16-storage plan (FP32 accumulation): the
+    projector pair on bf16 data, and ADMM-CG iterations on bf16 data and
+    coefficients."""
+    import torch
+
+    from paper_1809_09725_gb300 import dynrecon as dr
+    pb = dr.Plan(w.N, w.N, w.nz, w.ns, theta, t, w.basis, w.m, w.nt, dr.BF16)
+    t0 = time.perf_counter()
+    pb.autotune()
+    t_tune = time.perf_counter() - t0
+    fwd_ms, adj_ms = time_projectors(pb, dev, stream, reps=a.op_reps)
+    gb = torch.from_numpy(g32).to(dev).to(torch.bfloat16)
+    ub = torch.zeros(pb.u_shape(), dtype=torch.bfloat16, device=dev)
+    iters = 3
+    prm = dr.solve_params(dr.ADMM_CG, iters=1, n_cg=w.n_cg, lambda1=w.lambda1, lambda2=w.lambda2, rho=w.rho)
+    dr.admm_solve(pb, gb, ub, prm, want_objective=False)
+    ub.zero_()
+    prm = dr.solve_params(dr.ADMM_CG, iters=iters, n_cg=w.n_cg, lambda1=w.lambda1, lambda2=w.lambda2, rho=w.rho)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    dr.admm_solve(pb, gb, ub, prm, want_objective=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / iters
+    out = {"fwd_ms": fwd_ms, "adj_ms": adj_ms, "admm_ms_per_iter": ms, "autotune_s": t_tune,
+           "voxel_projection_per_s": 2 * (w.n_cg + 1) * w.K * w.voxels() / (ms * 1e-3),
+           "info": pb.info(),
+           "note": "dyn_radon_fwd / dyn_radon_adj on bf16 u and g (FP32 accumulation); admm_solve on bf16 g and u"}
+    del gb, ub
+    pb.close()
+    return out
+
+
+def run_workload_line(name, dev, stream, local, a, steps=20, warmup=3):
+    """Another workload's headline numbers (FP32, autotuned, ADMM-CG)."""
+    import torch
+
+    from paper_1809_09725_gb300 import dynrecon as dr
+    from paper_1809_09725_gb300 import synth
+    w = synth.WORKLOADS[name]
+    theta, t, g_np = synth.make_data(w)
+    plan = dr.Plan(w.N, w.N, w.nz, w.ns, theta, t, w.basis, w.m, w.nt, dr.F32)
+    g = torch.from_numpy(g_np.astype(np.float32)).to(dev)
+    u = torch.zeros(plan.u_shape(), dtype=torch.float32, device=dev)
+    tune = plan.autotune()
+    ms, res, clocks = solve_timed(plan, g, u, w, steps, warmup, None, dev, local, want_obj=False)
+    fwd_ms, adj_ms = time_projectors(plan, dev, stream, reps=10)
+    roof = roofline_of(w, theta, plan.info(), fwd_ms, adj_ms, tune)
+    units = 2 * (w.n_cg + 1) * w.K * w.voxels() * steps
+    out = {"workload": bench_config(w, 1)["workload"], "value": units / (ms * 1e-3), "unit": "voxel*projection/s",
+           "steps": steps, "ms_per_step": ms / steps, "clocks": clocks,
+           "roofline_alu_frac": roof["frac"], "roofline": roof}
+    del g, u
+    plan.close()
+    return out
+
+
+def run_disks_fp64(dev):
+    """The plain method in FP64 on the single-slice disks problem, timed
+    whole (20 ADMM-CG iterations x 4 CG steps): the GPU FP64 plan against the
+    FP64 oracle on the host cores, with the relative difference of u."""
+    import torch
+
+    import oracle
+    from paper_1809_09725_gb300 import dynrecon as dr
+    from paper_1809_09725_gb300 import synth
+    w = synth.WORKLOADS["disks64"]
+    theta, t, g_np = synth.make_data(w)
+    plan = dr.Plan(w.N, w.N, w.nz, w.ns, theta, t, w.basis, w.m, w.nt, dr.F64)
+    g = torch.from_numpy(g_np).to(dev)
+    u = torch.zeros(plan.u_shape(), dtype=torch.float64, device=dev)
+    prm = lambda: dr.solve_params(dr.ADMM_CG, iters=w.iters, n_cg=w.n_cg, lambda1=w.lambda1, lambda2=w.lambda2,
+                                  rho=w.rho)
+    dr.admm_solve(plan, g, u, prm(), want_objective=False)
+    u.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    dr.admm_solve(plan, g, u, prm(), want_objective=False)
+    torch.cuda.synchronize()
+    t_gpu = time.perf_counter() - t0
+    P = oracle.Problem(w.N, w.N, w.nz, w.ns, theta, t, w.basis, w.m, w.nt)
+    t0 = time.perf_counter()
+    uo, _, _ = P.admm_cg(g_np, np.zeros(plan.u_shape()), w.iters, w.n_cg, w.lambda1, w.lambda2, w.rho)
+    t_or = time.perf_counter() - t0
+    uu = u.cpu().numpy()
+    units = 2 * (w.n_cg + 1) * w.K * w.voxels() * w.iters
+    plan.close()
+    return {"workload": "disks64: 64^2, 1 slice, 64 bins, K=256 over 4 half-turns (mod pi), m=4 Fourier, "
+                        "20 ADMM x 4 CG, FP64",
+            "gpu_s": t_gpu, "oracle_s": t_or, "oracle_cores": os.cpu_count(),
+            "gpu_voxel_projection_per_s": units / t_gpu, "oracle_voxel_projection_per_s": units / t_or,
+            "rel_l2_u_gpu_vs_oracle": float(np.linalg.norm(uu - uo) / np.linalg.norm(uo))}
+
+
+def run_slabs_workload(name, dev):
+    from paper_1809_09725_gb300 import synth
+    w = synth.WORKLOADS[name]
+    theta, t, g_np = synth.make_data(w)
+    out = run_slabs(w, theta, t, g_np, dev)
+    out["workload"] = name
+    return out
+
+
+def bench_config(w, world: int) -> dict:
     """The workload both arms are quoted on."""
-    return {"workload": "ellipsoids256: nz=16 x 256^2 voxels, 256 bins, K=1800 over 10 half-turns, "
-                        "m=8 Fourier, nt=10, ADMM-CG n_cg=4, FP32",
+    basis = {0: "Fourier", 1: "Legendre"}[w.basis]
+    ws = {"ellipsoids1024": "per-iteration working set ~65 GB > 129 MB L2",
+          "ellipsoids256": "per-iteration working set 0.54 GB > 129 MB L2 (duals stream through every iteration)"}
+    return {"workload": "%s: nz=%d x %d^2 voxels, %d bins, K=%d over %g half-turns, m=%d %s, nt=%d, "
+                        "ADMM-CG n_cg=%d, FP32" % (w.name, w.nz, w.N, w.ns, w.K, w.n_halfturns, w.m, basis, w.nt,
+                                                   w.n_cg),
             "parallelism": "replicas" if world > 1 else "single GPU",
-            "l2": "per-iteration working set 0.54 GB > 129 MB L2 (duals stream through every iteration)"}
+            "l2": ws.get(w.name, "inputs larger than L2")}
+
+
+def reference_sample(w, steps, warmup):
+    """Projections per reference step: one slice with the first kp
+    projections, so that warm-up + timed steps stay within a few minutes."""
+    n = steps + warmup
+    kp = 600 if n <= 40 else (300 if n <= 100 else 150)
+    return min(kp, w.K)
 
 
 def run_reference(a):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    import oracle
     from paper_1809_09725_gb300 import synth
     w = synth.WORKLOADS[a.workload]
-    theta, t, g_np = synth.make_data(w)
-    # slices per step: 4 (about half a second on 16 host cores), fewer for
-    # long runs, so that the whole reference run stays within minutes
-    nz = 4 if a.steps <= 100 else (2 if a.steps <= 200 else 1)
+    theta, t = w.geometry()
+    kp = reference_sample(w, a.steps, a.warmup)
+    P = oracle.Problem(w.N, w.N, 1, w.ns, theta[:kp], t[:kp], w.basis, w.m, w.nt)
+    rng = np.random.default_rng(1)
+    u = rng.standard_normal((1, w.N, w.N, w.m))
+    g = rng.standard_normal((1, kp, w.ns))
     for _ in range(a.warmup):
-        cpu_baseline(w, theta, t, g_np, sample_slices=1)
+        P.fwd(u)
+        P.adj(g)
     t0 = time.perf_counter()
-    vals = []
     for _ in range(a.steps):
-        vals.append(cpu_baseline(w, theta, t, g_np, sample_slices=nz))
+        P.fwd(u)
+        P.adj(g)
     el = time.perf_counter() - t0
-    units = 2 * w.K * w.N * w.N * nz * a.steps
+    units = 2 * kp * w.N * w.N * a.steps
     value = units / el
+    sample = ("per step: one forward + one back-projection of 1 of the %d slices with the first %d of the %d "
+              "projections, FP64 oracle on the host cores (no GPU used)" % (w.nz, kp, w.K))
     line = {"impl": "reference", "metric": "voxel*projection updates/s (dynamic projector + back-projector "
                                            "applications inside ADMM-CG iterations)",
             "value": value, "unit": "voxel*projection/s", "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": el * 1e3 / a.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded moving ellipsoids, Poisson 1e4)",
-            "config": bench_config(1),
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded random coefficients and data of the "
+                                                         "workload's shape)",
+            "config": bench_config(w, 1),
             "cpu_baseline": {"value": value, "unit": "voxel*projection/s", "cores": os.cpu_count(),
-                             "kind": "oracle", "sample": "per step: one forward + one back-projection on %d of "
-                                                         "the %d slices of the workload, FP64 oracle on the host "
-                                                         "cores (no GPU used)" % (nz, w.nz)},
+                             "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "voxel*projection/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
