@@ -88,6 +88,8 @@ def parse():
                          "'group,threads,lines[,split[,async[,rays_per_thread]]]' instead of the default")
     ap.add_argument("--fold-adj-angles", type=int, default=0,
                     help="with --variant x,1: fix the folded adjoint's distinct angles per pipeline stage")
+    ap.add_argument("--slices", type=int, default=0,
+                    help="with --profile-small: the workload's geometry on this many slices (a small case for ncu)")
     ap.add_argument("--profile-small", action="store_true",
                     help="run only one launch of each projector call on the workload (for ncu captures)")
     return ap.parse_args()
@@ -371,6 +373,9 @@ def run_ours(a):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     w = synth.WORKLOADS[a.workload]
+    if a.profile_small and a.slices > 0:
+        import dataclasses
+        w = dataclasses.replace(w, nz=a.slices)
     t_data = time.perf_counter()
     theta, t, g_np = synth.make_data(w)
     g32 = g_np.astype(np.float32)

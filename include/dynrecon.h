@@ -286,11 +286,17 @@ dr_status dyn_radon_adj(dr_plan *plan, const void *g, void *u, double beta);
  * nz * U * ns * MS * 4 <= 8388608 bytes (U = distinct angles mod pi; MS =
  * 4 for m <= 4, 12 for m <= 12, 20 for m <= 16, 28 for m <= 24, 36 for
  * m <= 32): larger problems get DR_EINVAL with the size in dr_last_error();
- * call it per slab of slices instead.  Calls no cudaMalloc/cudaFree.  The first call
- * on a device looks up the array's device address (cudaGetSymbolAddress);
- * make that first call before any stream capture.  All calls share the
- * array: calls whose work overlaps on the GPU (other streams or threads)
- * race; calls in order on one stream are safe.  Asynchronous.
+ * call it per slab of slices instead.  Calls no cudaMalloc/cudaFree.
+ * Set-up done by first calls: the first call on a device (and CUDA context)
+ * looks up the array's device address (cudaGetSymbolAddress) and caches it
+ * with the context's id; with lazy module loading (CUDA_MODULE_LOADING=LAZY,
+ * the default) the array is reserved on that device by this first call, not
+ * when the library loads; and the first call for each precision (F32, BF16)
+ * and template size of m loads that kernel instantiation and raises its
+ * dynamic shared-memory limit.  Make one call for every (precision, m) a
+ * caller will use before any stream capture.  All calls share the array:
+ * calls whose work overlaps on the GPU (other streams or threads) race;
+ * calls in order on one stream are safe.  Asynchronous.
  */
 dr_status dyn_radon_adj_noalloc(dr_plan *plan, const void *g, void *u, double beta);
 

@@ -20,6 +20,8 @@
 #include <cmath>
 #include <mutex>
 
+#include <cudaTypedefs.h>
+
 #include "fold_impl.cuh"
 
 namespace dr {
@@ -30,23 +32,55 @@ constexpr size_t kNoAllocFloats = kNoAllocBytes / sizeof(float);
 
 static __device__ __align__(256) float g_noalloc_fold_scratch[kNoAllocFloats];
 
-// Device address of the array, looked up once per device (with that device
-// current) and cached; host code must not use the symbol itself as a
-// device pointer.
+// Device address of the array.  Host code must not use the symbol itself as
+// a device pointer: the address is looked up with cudaGetSymbolAddress, with
+// the device current, once per device and CUDA context, and cached together
+// with the context's process-unique id (cuCtxGetId), so that a context torn
+// down and re-created (cudaDeviceReset) gets a fresh lookup instead of a
+// stale pointer.  If those driver calls cannot be resolved, every call looks
+// the address up.
 constexpr int kMaxDevices = 64;
+struct NoAllocEntry {
+    unsigned long long ctx_id;
+    float *ptr;
+};
 static std::mutex g_noalloc_mutex;
-static float *g_noalloc_ptr[kMaxDevices];
+static NoAllocEntry g_noalloc_ptr[kMaxDevices];
+static std::once_flag g_noalloc_ctx_once;
+static PFN_cuCtxGetCurrent_v4000 g_ctx_current = nullptr;
+static PFN_cuCtxGetId_v12000 g_ctx_id = nullptr;
+
+static bool current_context_id(unsigned long long *id) {
+    std::call_once(g_noalloc_ctx_once, [] {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_ctx_current = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(fn);
+        fn = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_ctx_id = reinterpret_cast<PFN_cuCtxGetId_v12000>(fn);
+    });
+    CUcontext ctx = nullptr;
+    if (!g_ctx_current || !g_ctx_id || g_ctx_current(&ctx) != CUDA_SUCCESS || !ctx) return false;
+    return g_ctx_id(ctx, id) == CUDA_SUCCESS;
+}
 
 static dr_status noalloc_scratch(int device, float **out) {
     if (device < 0 || device >= kMaxDevices) return fail(DR_EINVAL, "dyn_radon_adj_noalloc: device index out of range");
+    unsigned long long id = 0;
+    const bool have_id = current_context_id(&id);
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_ptr[device]) {
+    NoAllocEntry &e = g_noalloc_ptr[device];
+    if (!have_id || !e.ptr || e.ctx_id != id) {
         void *p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_fold_scratch);
-        if (e != cudaSuccess) return cuda_fail(e, "dyn_radon_adj_noalloc: cudaGetSymbolAddress");
-        g_noalloc_ptr[device] = static_cast<float *>(p);
+        const cudaError_t ce = cudaGetSymbolAddress(&p, g_noalloc_fold_scratch);
+        if (ce != cudaSuccess) return cuda_fail(ce, "dyn_radon_adj_noalloc: cudaGetSymbolAddress");
+        e.ptr = static_cast<float *>(p);
+        e.ctx_id = have_id ? id : 0;
     }
-    *out = g_noalloc_ptr[device];
+    *out = e.ptr;
     return DR_OK;
 }
 

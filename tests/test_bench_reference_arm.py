@@ -21,6 +21,6 @@ def test_reference_arm_prints_one_json_line():
                 "config", "cpu_baseline", "e2e"):
         assert key in d, key
     assert d["value"] > 0 and d["steps"] == 1 and d["higher_is_better"] is True
-    assert d["config"]["workload"].startswith("ellipsoids256")
+    assert d["config"]["workload"].startswith("ellipsoids1024")
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0

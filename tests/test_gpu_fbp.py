@@ -16,7 +16,7 @@ import oracle
 from paper_1809_09725_gb300 import dynrecon as dr
 from paper_1809_09725_gb300 import synth
 
-from _common import dev_tensor, host_values, rel, to_bf16_f64
+from _common import assert_close, dev_tensor, host_values, rel, to_bf16_f64
 
 pytestmark = pytest.mark.gpu
 
@@ -60,7 +60,7 @@ def test_fbp_init_matches_oracle(case, prec, tol):
     if prec == dr.F32:
         g = g.astype(np.float32).astype(np.float64)
     u = _run(args, g, prec, nw)
-    assert rel(u, P.fbp_init(g, nw)) <= tol
+    assert_close(u, P.fbp_init(g, nw), tol)
 
 
 @pytest.mark.parametrize("case", ["disks64_halfturns", "ragged", "heaviside"])
@@ -69,7 +69,7 @@ def test_fbp_init_both_variants(case):
     g = g.astype(np.float32).astype(np.float64)
     ref = P.fbp_init(g, nw)
     for v in (dr.DIRECT, dr.FOLD):
-        assert rel(_run(args, g, dr.F32, nw, variant=v), ref) <= 1e-5
+        assert_close(_run(args, g, dr.F32, nw, variant=v), ref, 1e-5)
 
 
 @pytest.mark.parametrize("case", ["disks64_static", "ragged"])
@@ -80,8 +80,8 @@ def test_fbp_init_bf16(case):
     gb = to_bf16_f64(g)
     u = _run(args, gb, dr.BF16, nw)
     ref = P.fbp_init(gb, nw)
-    assert rel(u, to_bf16_f64(ref)) <= 1e-3
-    assert rel(u, ref) <= 2.0 ** -8
+    assert_close(u, to_bf16_f64(ref), 1e-3)
+    assert_close(u, ref, 2.0 ** -8)
 
 
 def test_fbp_init_reconstructs_disks():
@@ -115,7 +115,7 @@ def test_fbp_init_ellipsoids256_cut():
     plan = dr.Plan(w.N, w.N, 2, w.ns, theta, t, w.basis, w.m, w.nt, dr.F32)
     u = torch.zeros(plan.u_shape(), dtype=torch.float32, device="cuda")
     dr.fbp_init(plan, dev_tensor(g, dr.F32), u, 10)
-    assert rel(host_values(u), ref) <= 1e-5
+    assert_close(host_values(u), ref, 1e-5)
 
 
 def test_fbp_init_then_solve_lowers_objective():
@@ -157,4 +157,4 @@ def test_fbp_init_dependent_basis_takes_minimum_norm_fit():
     g = rng.standard_normal((1, 12, 16))
     P = oracle.Problem(16, 16, 1, 16, theta, t, oracle.LEGENDRE, 4, 2)
     u = _run((16, 16, 1, 16, theta, t, dr.LEGENDRE, 4, 2), g, dr.F64, 3)
-    assert rel(u, P.fbp_init(g, 3)) <= 1e-9
+    assert_close(u, P.fbp_init(g, 3), 1e-9)

@@ -12,7 +12,7 @@ import oracle
 from paper_1809_09725_gb300 import dynrecon as dr
 from paper_1809_09725_gb300 import synth
 
-from _common import dev_tensor, host_values, rel, to_bf16_f64
+from _common import assert_close, dev_tensor, host_values, rel, to_bf16_f64
 
 pytestmark = pytest.mark.gpu
 
@@ -71,8 +71,8 @@ def test_grad_and_adjoint(case, prec, tol):
     ua = torch.zeros(plan.u_shape(), dtype=getattr(torch, plan.storage_dtype), device="cuda")
     dr.tv4d_grad_adj(plan, dev_tensor(_to_field(p), prec), ua, lam2)
     plan.sync()
-    assert rel(_from_field(host_values(pg)), P.D(u, lam2)) <= tol
-    assert rel(host_values(ua), P.DT(p, lam2)) <= tol
+    assert_close(_from_field(host_values(pg)), P.D(u, lam2), tol)
+    assert_close(host_values(ua), P.DT(p, lam2), tol)
 
 
 @pytest.mark.parametrize("case", ["ragged", "m8"])
@@ -82,7 +82,7 @@ def test_grad_adj_beta(case):
     ut = dev_tensor(u, dr.F64)
     dr.tv4d_grad_adj(plan, dev_tensor(_to_field(p), dr.F64), ut, 0.6, beta=2.5)
     plan.sync()
-    assert rel(host_values(ut), 2.5 * u + P.DT(p, 0.6)) <= 1e-12
+    assert_close(host_values(ut), 2.5 * u + P.DT(p, 0.6), 1e-12)
 
 
 # Tall volumes: enough (x, y) tiles x slices that the z-marching D^T D kernel
@@ -117,7 +117,7 @@ def test_normal_matches_oracle(case, prec, tol):
     dr.tv4d_normal(plan, xd, od, lam2, beta)
     plan.sync()
     ref = beta * o0 + P.DT(P.D(x, lam2), lam2)
-    assert rel(host_values(od), ref) <= tol
+    assert_close(host_values(od), ref, tol)
 
 
 def test_normal_rejects_aliasing():
@@ -142,8 +142,8 @@ def test_prox_matches_oracle(case, prec, tol):
     res = dr.tv4d_prox(plan, dev_tensor(u, prec), mu, w, rho, lam1, lam2, want_residual=True)
     mu_o, w_o = mu0.copy(), np.zeros_like(mu0)
     tv_o, pr_o = oracle.tv4d_prox(u, mu_o, w_o, P.PhiF, rho, lam1, lam2)
-    assert rel(_from_field(host_values(mu)), mu_o) <= tol
-    assert rel(_from_field(host_values(w)), w_o) <= tol
+    assert_close(_from_field(host_values(mu)), mu_o, tol)
+    assert_close(_from_field(host_values(w)), w_o, tol)
     assert abs(res - np.sqrt(pr_o)) <= 10 * tol * np.sqrt(pr_o)
 
 
@@ -158,8 +158,8 @@ def test_prox_bf16_coefficients():
     plan.sync()
     mu_o, w_o = mu0.copy(), np.zeros_like(mu0)
     oracle.tv4d_prox(ub, mu_o, w_o, P.PhiF, 0.7, 0.4, 1.3)
-    assert rel(_from_field(host_values(mu)), mu_o) <= 1e-5
-    assert rel(_from_field(host_values(w)), w_o) <= 1e-5
+    assert_close(_from_field(host_values(mu)), mu_o, 1e-5)
+    assert_close(_from_field(host_values(w)), w_o, 1e-5)
 
 
 def test_prox_rejects_bad_parameters():
