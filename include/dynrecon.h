@@ -185,8 +185,12 @@ dr_status dr_plan_set_fold_groups(dr_plan *plan, int group, int threads, int ray
  * chunk.  async 0: synchronous strip staging; 1: double-buffered strips, the
  * next copied with cp.async while the current is marched; 2: three buffers,
  * two strips ahead, one CTA barrier per strip (strips limited to twice the
- * strip budget; where one line does not fit three times, two buffers).  Same
- * arithmetic in every mode: results identical.
+ * strip budget; where one line does not fit three times, two buffers); 3:
+ * strips copied by TMA (cp.async.bulk.tensor, even and odd pixels of a line
+ * taken by tensor maps with element stride 2) into two buffers completing
+ * on mbarriers, one CTA barrier per strip -- for 4-coefficient groups of
+ * float data whose m is a multiple of 4, otherwise mode 2.  Same arithmetic in
+ * every mode: results identical.
  * DR_EINVAL if the variant is unavailable or an argument is out of range.
  */
 dr_status dr_plan_set_fold_march(dr_plan *plan, int nsplit, int async);
@@ -529,7 +533,12 @@ dr_status dr_server_create(dr_server **out, int device, size_t budget_bytes, int
  * and run concurrently, each with its own plan and stream. */
 dr_status dr_server_submit(dr_server *server, const dr_job_desc *desc, int64_t *job_id);
 
-/* Cancel a job that has not started (DR_EINVAL once it runs). */
+/* Cancel a job.  A queued job is removed at once; a running ADMM-CG or
+ * in-core Chambolle-Pock job stops between iterations (within about two
+ * iterations: a serving job's solve keeps at most two iterations in flight)
+ * and ends with state DR_JOB_CANCELED and status DR_ECANCELED, u holding no
+ * defined result; a slab-streamed job runs to the end.  DR_EINVAL for an
+ * unknown or finished job. */
 dr_status dr_server_cancel(dr_server *server, int64_t job_id);
 
 /* Wait up to timeout_s seconds (< 0: no limit) for a job; fills res

@@ -6,6 +6,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -69,6 +70,33 @@ constexpr int kAdjStages = 3;  // TMA pipeline depth
 constexpr int kFwdThreads = 256;
 constexpr int kFwdRPT = 8;   // rays per thread
 constexpr int kFwdGuard = 4; // zero cells on each side of a staged line
+// Staged lines of the folded forward's strips: the even pixels of a line,
+// then its odd pixels, each half with kFoldGuardE zero entries on both sides.
+// A Joseph sample reads pixels i0 and i0 + 1, one even and one odd, so its
+// two loads go to different halves; the eight lanes of a 16-byte load phase
+// (consecutive bins, 1 to sqrt 2 pixels apart) then span at most 6 entries of
+// a half and never share a bank slot (lanes on the same entry are served by
+// one broadcast).  The odd half starts 4 slots (mod 8) after the even one, so
+// the staging stores of neighbouring pixels do not collide either, and the
+// line stride is odd, so stores of one pixel on consecutive lines (the
+// column-stepping branch) do not.
+constexpr int kFoldGuardE = 2;
+__host__ __device__ constexpr int fold_half(int W) { return (W + 1) / 2 + 2 * kFoldGuardE; }
+__host__ __device__ constexpr int fold_odd_off(int W) { return fold_half(W) + ((4 - fold_half(W)) & 7); }
+__host__ __device__ constexpr int fold_line_elems(int W) { return (fold_odd_off(W) + fold_half(W)) | 1; }
+// Strip lines staged by TMA (the static transforms of 4-float coefficient
+// groups): each half of a line is written by copies of bw pixels taken every
+// second pixel (a tensor map with element stride 2), bw/2 16-byte entries per
+// copy at 128-byte aligned offsets; 8 zero entries before, between and after
+// the halves.
+__host__ __device__ constexpr int fold_tma_bw(int W) { return W >= 256 ? 256 : ((W + 15) / 16) * 16; }
+__host__ __device__ constexpr int fold_tma_nbox(int W) { return (W + fold_tma_bw(W) - 1) / fold_tma_bw(W); }
+__host__ __device__ constexpr int fold_tma_half(int W) { return fold_tma_nbox(W) * fold_tma_bw(W) / 2; }
+__host__ __device__ constexpr int fold_tma_line(int W) { return 2 * fold_tma_half(W) + 24; }
+constexpr int kFoldTmaStages = 2;  // TMA strip buffers (one CTA barrier per strip)
+inline int fold_line_elems_max(int nx, int ny) {
+    return fold_line_elems(nx) > fold_line_elems(ny) ? fold_line_elems(nx) : fold_line_elems(ny);
+}
 // Shared-memory budget of the folded forward's strip (float lines; both
 // buffers when double-buffered): two CTAs of 256 threads still fit an SM.
 constexpr int kFoldStripBudget = 110 * 1024;
@@ -218,6 +246,9 @@ struct dr_plan {
     size_t fbp_bytes = 0;
 
     dr::Workspace ws;
+    // set by the serving layer for its jobs: admm_solve stops between
+    // iterations once the flag is raised (dr_server_cancel of a running job)
+    const std::atomic<int> *cancel = nullptr;
 };
 
 namespace dr {
@@ -284,9 +315,11 @@ dr_status allow_dynamic_smem(const void *fn, size_t smem);
 // Host-side tensor-map encoder (driver entry point, resolved once).
 bool encode_tensor_map_2d(CUtensorMap *map, CUtensorMapDataType dt, void *base, uint64_t dim0,
                           uint64_t dim1, uint64_t stride1_bytes, uint32_t box0, uint32_t box1);
-// rank-dimensional tiled map: dims[rank], strides[rank-1] (bytes, dims 1..), box[rank]
+// rank-dimensional tiled map: dims[rank], strides[rank-1] (bytes, dims 1..), box[rank];
+// elem_strides[rank] (nullptr: all 1): the box takes every k-th element of a
+// dimension, box[i] / elem_strides[i] of them
 bool encode_tensor_map(CUtensorMap *map, CUtensorMapDataType dt, int rank, void *base, const uint64_t *dims,
-                       const uint64_t *strides, const uint32_t *box);
+                       const uint64_t *strides, const uint32_t *box, const uint32_t *elem_strides = nullptr);
 
 // Direct and folded projector variants; selection per plan (projector.cu).
 dr_status launch_fwd_variant(dr_plan *P, int variant, bool calc, const void *u, void *out, const void *gm,

@@ -172,13 +172,16 @@ __host__ __device__ constexpr int fold_fwd_min_blocks(int M) { return M == 8 ? 3
 // ru[((z U + a) ns + b) ms_ru + j]; fold_dist_kernel distributes them.  With
 // nsplit > 1 the march is split into nsplit chunks of image lines
 // (blockIdx.z); chunk c writes its partial sums at ru + c * split_stride.
-template <typename S, typename T, int M, bool STATIC, int THREADS = kFoldThreads, int RPTS = 0, int MINB = 1>
+template <typename S, typename T, int M, bool STATIC, int THREADS = kFoldThreads, int RPTS = 0, int MINB = 1,
+          bool TMA = false>
 __global__ void __launch_bounds__(THREADS, THREADS == kFoldThreads ? fold_fwd_min_blocks(M) : MINB)
     fold_fwd_kernel(const S *__restrict__ u, S *__restrict__ out, const S *__restrict__ gm,
                     const FwdProj *__restrict__ uproj, const int *__restrict__ start, const int *__restrict__ member,
                     const T *__restrict__ phip, const int *__restrict__ blocks, int nx, int ny, int ns, int K,
                     int m, int MP, int P, int R, int nchunk, int mode, T sigma, int async_stage, int ngroups,
-                    T *__restrict__ ru, int U, int ms_ru, int nsplit, size_t split_stride) {
+                    T *__restrict__ ru, int U, int ms_ru, int nsplit, size_t split_stride,
+                    const __grid_constant__ CUtensorMap tm_rows, const __grid_constant__ CUtensorMap tm_cols,
+                    int *status) {
     // strip element: stored bf16 for bf16 storage, else the compute type
     constexpr bool BF16_STRIP = sizeof(S) == 2;
     using ST = std::conditional_t<BF16_STRIP, S, T>;
@@ -187,8 +190,6 @@ __global__ void __launch_bounds__(THREADS, THREADS == kFoldThreads ? fold_fwd_mi
     constexpr int VW = 16 / (int)sizeof(S);  // elements per 16-byte vector
     extern __shared__ __align__(16) unsigned char fold_smem[];
     T *scale_s = reinterpret_cast<T *>(fold_smem);                       // [64]
-    long long *bfx_s = reinterpret_cast<long long *>(fold_smem + 256);   // [64]
-    ST *strip = reinterpret_cast<ST *>(fold_smem + 768);                 // [R][wpad][MS]
 
     const int tid = threadIdx.x;
     const int z = blockIdx.y / ngroups;
@@ -200,7 +201,17 @@ __global__ void __launch_bounds__(THREADS, THREADS == kFoldThreads ? fold_fwd_mi
     const int branch = uproj[blk[0]].branch;
     const int W = branch ? ny : nx;
     const int H = branch ? nx : ny;
-    const int wpad = W + 2 * kFwdGuard;
+    // TMA (static transforms of 4-float groups, staging mode 3): strips staged
+    // by TMA into two buffers on mbarriers, in the TMA line layout;
+    // a separate instantiation, so the other kernels carry none of its code
+    constexpr bool TMA_CAP = TMA && STATIC && !BF16_STRIP && M == 4 && MS == 4;
+    constexpr bool tma = TMA_CAP;
+    // line stride, zero entries before the even half, offset of the odd half
+    const int ls = tma ? fold_tma_line(W) : fold_line_elems(W);
+    const int kg = tma ? 8 : kFoldGuardE;
+    const int ooff = tma ? fold_tma_half(W) + 8 : fold_odd_off(W);
+    ST *strip = reinterpret_cast<ST *>(
+        tma ? fold_smem + 768 + ((128u - ((smem_u32(fold_smem) + 768u) & 127u)) & 127u) : fold_smem + 768);
     // image lines of this CTA's march: all, or chunk blockIdx.z of nsplit
     const int L0 = STATIC ? (int)(((long long)blockIdx.z * H) / nsplit) : 0;
     const int L1 = STATIC ? (int)(((long long)(blockIdx.z + 1) * H) / nsplit) : H;
@@ -209,48 +220,69 @@ __global__ void __launch_bounds__(THREADS, THREADS == kFoldThreads ? fold_fwd_mi
         const int a = blk[p];
         const FwdProj f = uproj[a >= 0 ? a : blk[0]];
         scale_s[p] = (T)f.scale;
-        bfx_s[p] = f.B_fx;
     }
-    // strip buffers: 1 (synchronous staging), 2 (async_stage 1) or 3 (async_stage 2)
-    for (int i = tid; i < (async_stage + 1) * R * wpad * MS; i += THREADS) strip[i] = ST(0.0f);
+    // strip buffers: 1 (synchronous staging), 2 (async_stage 1) or 3 (async_stage 2, 3)
+    const int nbuf = tma ? kFoldTmaStages : async_stage + 1;
+    if (tma) {
+        // zero the guard entries only: TMA writes every data entry of a strip
+        // (zero beyond the image), so no entry is written by both proxies
+        const int wh = fold_tma_half(W);
+        for (int i = tid; i < nbuf * R * 24; i += THREADS) {
+            const int line = i / 24, g = i - line * 24;
+            const int e = g < 8 ? g : (g < 16 ? kg + wh + (g - 8) : kg + ooff + wh + (g - 16));
+            reinterpret_cast<float4 *>(strip)[(size_t)line * ls + e] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    } else {
+        for (int i = tid; i < nbuf * R * ls * MS; i += THREADS) strip[i] = ST(0.0f);
+    }
 
-    const int rays_per_cta = THREADS * RPT;
-    const int b_base = chunk * rays_per_cta;
-    long long x0fx[RPT];
+    // Ray slots: thread t marches RPT rays of one distinct angle p_t of the
+    // block, the bins l_t + tpa q (q = 0 .. RPT-1), so the rays of a thread
+    // share their per-line step and consecutive threads take consecutive
+    // bins; a single angle whose bins exceed one CTA (nchunk > 1) is cut into
+    // chunks of THREADS * RPT bins, bins chunk * THREADS * RPT + t + THREADS q.
+    const int tpa = nchunk > 1 ? THREADS : (ns + RPT - 1) / RPT;
+    const int pt = nchunk > 1 ? 0 : tid / tpa;
+    const int bt0 = nchunk > 1 ? chunk * THREADS * RPT + tid : tid - pt * tpa;
+    const int at = pt < P ? blk[pt] : -1;
+    long long xq[RPT];  // 32.32 position of each ray on its next line
+    long long bfx = 0;  // per-line step of this thread's angle
     int lo[RPT], hi[RPT];
+    unsigned rng[RPT];
     T acc[RPT][M];
+    FwdProj f{};
+    if (at >= 0) {
+        f = uproj[at];
+        bfx = f.B_fx;
+    }
 #pragma unroll
     for (int q = 0; q < RPT; ++q) {
         lo[q] = 1;
         hi[q] = 0;
-        x0fx[q] = 0;
+        xq[q] = 0;
 #pragma unroll
         for (int j = 0; j < M; ++j) acc[q][j] = T(0);
-        const int rid = b_base + tid + q * THREADS;
-        const int p = (nchunk > 1) ? 0 : rid / ns;
-        const int b = (nchunk > 1) ? rid : rid - p * ns;
-        if (p < P && b < ns) {
-            const int a = blk[p];
-            if (a >= 0) {
-                const FwdProj f = uproj[a];
-                x0fx[q] = f.C_fx + (long long)b * f.A_fx;
-                const float xf = f.Cf + (float)b * f.Af;
-                const float Bf = f.Bf;
-                if (fabsf(Bf) < 1e-2f) {
-                    lo[q] = 0;
-                    hi[q] = H - 1;
-                } else {
-                    const float r1 = (-1.0f - xf) / Bf, r2 = ((float)W - xf) / Bf;
-                    float rmin = fminf(r1, r2), rmax = fmaxf(r1, r2);
-                    rmin = fmaxf(rmin, -4.0f);
-                    rmax = fminf(rmax, (float)H + 4.0f);
-                    lo[q] = max(0, (int)floorf(rmin) - 1);
-                    hi[q] = min(H - 1, (int)ceilf(rmax) + 1);
-                }
-                lo[q] = max(lo[q], L0);
-                hi[q] = min(hi[q], L1 - 1);
+        const int b = bt0 + tpa * q;
+        if (at >= 0 && b < ns) {
+            xq[q] = f.C_fx + (long long)b * f.A_fx + (long long)L0 * bfx;
+            const float xf = f.Cf + (float)b * f.Af;
+            const float Bf = f.Bf;
+            if (fabsf(Bf) < 1e-2f) {
+                lo[q] = 0;
+                hi[q] = H - 1;
+            } else {
+                const float r1 = (-1.0f - xf) / Bf, r2 = ((float)W - xf) / Bf;
+                float rmin = fminf(r1, r2), rmax = fmaxf(r1, r2);
+                rmin = fmaxf(rmin, -4.0f);
+                rmax = fminf(rmax, (float)H + 4.0f);
+                lo[q] = max(0, (int)floorf(rmin) - 1);
+                hi[q] = min(H - 1, (int)ceilf(rmax) + 1);
             }
+            lo[q] = max(lo[q], L0);
+            hi[q] = min(hi[q], L1 - 1);
         }
+        // the TMA kernel keeps each ray's line range in one register (lines < 2^16)
+        rng[q] = (unsigned)lo[q] | ((unsigned)hi[q] << 16);
     }
     __syncthreads();
 
@@ -272,16 +304,16 @@ __global__ void __launch_bounds__(THREADS, THREADS == kFoldThreads ? fold_fwd_mi
                 rl = qq - i * nl;
                 pix = zoff + (size_t)i * nx + (r0 + rl);
             }
-            stage_pixel<S, T, M>(buf + ((size_t)rl * wpad + kFwdGuard + i) * MS, u + pix * m + j0, count, vec,
-                                 async_stage);
+            stage_pixel<S, T, M>(buf + ((size_t)rl * ls + (i & 1) * ooff + kg + (i >> 1)) * MS,
+                                 u + pix * m + j0, count, vec, async_stage);
         }
     };
-    const size_t buf_elems = (size_t)R * wpad * MS;  // buffer b starts at strip + b * buf_elems
-    if (async_stage == 1 && L0 < L1) {
+    const size_t buf_elems = (size_t)R * ls * MS;  // buffer b starts at strip + b * buf_elems
+    if (!TMA_CAP && async_stage == 1 && L0 < L1) {
         stage(strip, L0, min(R, L1 - L0));
         cp_async_commit();
     }
-    if (async_stage == 2) {
+    if (!TMA_CAP && async_stage == 2) {
         // three buffers: strips s+1 and s+2 are copied while strip s is marched,
         // and one barrier per strip suffices (the buffer refilled after the
         // barrier of strip s held strip s-1, which every thread has finished);
@@ -292,77 +324,131 @@ __global__ void __launch_bounds__(THREADS, THREADS == kFoldThreads ? fold_fwd_mi
         if (L0 + R < L1) stage(strip + buf_elems, L0 + R, min(R, L1 - L0 - R));
         cp_async_commit();
     }
-    int s_idx = 0;
-    for (int r0 = L0; r0 < L1; r0 += R, ++s_idx) {
-        const int nl = min(R, L1 - r0);
-        ST *cur;
-        if (async_stage == 2) {
-            cp_async_wait<1>();
-            __syncthreads();
-            if (r0 + 2 * R < L1) stage(strip + ((s_idx + 2) % 3) * buf_elems, r0 + 2 * R, min(R, L1 - r0 - 2 * R));
-            cp_async_commit();
-            cur = strip + (s_idx % 3) * buf_elems;
-        } else if (async_stage) {
-            // prefetch the next strip into the other buffer, then wait for this one
-            if (r0 + R < L1) {
-                stage(strip + ((s_idx + 1) & 1) * buf_elems, r0 + R, min(R, L1 - r0 - R));
-                cp_async_commit();
-                cp_async_wait<1>();
-            } else {
-                cp_async_wait<0>();
-            }
-            __syncthreads();
-            cur = strip + (s_idx & 1) * buf_elems;
-        } else {
-            stage(strip, r0, nl);
-            __syncthreads();
-            cur = strip;
-        }
-        // ---- march the rays: all m coefficient sums per ray ----
-#pragma unroll
-        for (int q = 0; q < RPT; ++q) {
-            const int rs = max(lo[q], r0), re = min(hi[q], r0 + nl - 1);
-            if (rs > re) continue;
-            const int rid = b_base + tid + q * THREADS;
-            const int p = (nchunk > 1) ? 0 : rid / ns;
-            const long long bfx = bfx_s[p];
-            long long x = x0fx[q] + (long long)rs * bfx;
-            const ST *row = cur + ((size_t)(rs - r0) * wpad + kFwdGuard) * MS;
+    // ---- march the rays of lines [r0, r0 + nl) staged at cur: all m coefficient
+    // sums per ray, line by line, the thread's RPT rays side by side
+    // (independent chains); each ray still adds its lines in increasing order
+    auto march = [&](const ST *cur, int r0, int nl) {
 #pragma unroll 1
-            for (int r = rs; r <= re; ++r) {
-                int i0 = (int)(x >> 32);
-                i0 = min(max(i0, -2), W);
-                const float w = __uint_as_float(0x3F800000u | ((unsigned)x >> 9)) - 1.0f;
-                const float w1m = 1.0f - w;
-                T t0[M], t1[M];
-                if constexpr (BF16_STRIP) {
-                    load_vec_bf16<M, MS>(row + i0 * MS, t0);
-                    load_vec_bf16<M, MS>(row + (i0 + 1) * MS, t1);
-                } else {
-                    load_vec<T, M>(row + i0 * MS, t0);
-                    load_vec<T, M>(row + (i0 + 1) * MS, t1);
-                }
+        for (int rl = 0; rl < nl; ++rl) {
+            const int r = r0 + rl;
+            const ST *row = cur + ((size_t)rl * ls + kg) * MS;
 #pragma unroll
-                for (int j = 0; j < M; ++j) acc[q][j] = fmaf(w, t1[j], fmaf(w1m, t0[j], acc[q][j]));
-                x += bfx;
-                row += (size_t)wpad * MS;
+            for (int q = 0; q < RPT; ++q) {
+                const int lq = TMA_CAP ? (int)(rng[q] & 0xffffu) : lo[q], hq = TMA_CAP ? (int)(rng[q] >> 16) : hi[q];
+                if (r >= lq && r <= hq) {
+                    const long long x = xq[q];
+                    int i0 = (int)(x >> 32);
+                    i0 = min(max(i0, -2), W);
+                    const float w = __uint_as_float(0x3F800000u | ((unsigned)x >> 9)) - 1.0f;
+                    const float w1m = 1.0f - w;
+                    // pixels i0 and i0 + 1: the even one from the even half, the
+                    // odd one from the odd half, each with its interpolation weight
+                    const bool odd = i0 & 1;
+                    const float we = odd ? w : w1m, wo = odd ? w1m : w;
+                    const ST *pe = row + ((i0 + 1) >> 1) * MS, *po = row + (ooff + (i0 >> 1)) * MS;
+                    T t0[M], t1[M];
+                    if constexpr (BF16_STRIP) {
+                        load_vec_bf16<M, MS>(pe, t0);
+                        load_vec_bf16<M, MS>(po, t1);
+                    } else {
+                        load_vec<T, M>(pe, t0);
+                        load_vec<T, M>(po, t1);
+                    }
+#pragma unroll
+                    for (int j = 0; j < M; ++j) acc[q][j] = fmaf(wo, t1[j], fmaf(we, t0[j], acc[q][j]));
+                }
+                xq[q] += bfx;
             }
         }
-        if (async_stage != 2) __syncthreads();
+    };
+    if constexpr (TMA_CAP) {
+        // Two strip buffers; full[b] completes when a strip's TMA copies have
+        // landed (expect_tx).  One CTA barrier per strip: thread 0 waits for
+        // strip s, the barrier then also says every thread has finished strip
+        // s - 1, whose buffer the copies of strip s + 1 refill while strip s is
+        // marched.  The copies of a strip are spread over the CTA's threads.
+        // Waits are bounded: on a give-up the status word
+        // is set and the CTA leaves in order.
+        __shared__ __align__(8) uint64_t full[kFoldTmaStages];
+        const int nstrips = L1 > L0 ? (L1 - L0 + R - 1) / R : 0;
+        const size_t buf_elems = (size_t)R * ls * MS;
+        if (tid == 0) {
+            for (int b = 0; b < kFoldTmaStages; ++b) mbar_init(&full[b], 1);
+            fence_mbar_init();
+        }
+        __syncthreads();
+        // strip sidx into buffer sidx % 2: copy c of its 2 * nbox * nl by thread c (mod THREADS)
+        auto issue = [&](int sidx) {
+            const int b = sidx % kFoldTmaStages, r0s = L0 + sidx * R, nls = min(R, L1 - r0s);
+            const int bw = fold_tma_bw(W), nbox = fold_tma_nbox(W);
+            if (tid == 0) mbar_arrive_expect_tx(&full[b], (unsigned)(nls * 2 * nbox * (bw / 2) * 16));
+            for (int c = tid; c < nls * 2 * nbox; c += THREADS) {
+                const int rl = c / (2 * nbox), rem = c - rl * 2 * nbox, half = rem / nbox, bx = rem - half * nbox;
+                const uint32_t dst = smem_u32(strip + b * buf_elems) +
+                                     (uint32_t)(rl * ls + kg + half * ooff + bx * (bw / 2)) * 16u;
+                const int line = r0s + rl, p0 = bx * bw + half;
+                if (branch == 0) tma_load_4d(dst, &tm_rows, j0, p0, line, z, &full[b]);
+                else tma_load_4d(dst, &tm_cols, j0, line, p0, z, &full[b]);
+            }
+        };
+        if (nstrips > 0) issue(0);
+        for (int sidx = 0; sidx < nstrips; ++sidx) {
+            const int b = sidx % kFoldTmaStages;
+            int ok = 1;
+            if (tid == 0) ok = mbar_wait_bounded_any(&full[b], (unsigned)((sidx / kFoldTmaStages) & 1), status,
+                                                     2000000000ull);
+            if (__syncthreads_or(!ok)) {
+                // strip sidx did not land in time; let no copy of it outlive the CTA
+                if (tid == 0)
+                    mbar_wait_bounded(&full[b], (unsigned)((sidx / kFoldTmaStages) & 1), status, 100000000ull);
+                return;
+            }
+            if (sidx + 1 < nstrips) issue(sidx + 1);
+            const int r0 = L0 + sidx * R;
+            march(strip + b * buf_elems, r0, min(R, L1 - r0));
+        }
     }
-    if (async_stage == 2) cp_async_wait<0>();  // no copy outlives the CTA
+    if constexpr (!TMA_CAP) {
+        int s_idx = 0;
+        for (int r0 = L0; r0 < L1; r0 += R, ++s_idx) {
+            const int nl = min(R, L1 - r0);
+            ST *cur;
+            if (async_stage == 2) {
+                cp_async_wait<1>();
+                __syncthreads();
+                if (r0 + 2 * R < L1) stage(strip + ((s_idx + 2) % 3) * buf_elems, r0 + 2 * R, min(R, L1 - r0 - 2 * R));
+                cp_async_commit();
+                cur = strip + (s_idx % 3) * buf_elems;
+            } else if (async_stage) {
+                // prefetch the next strip into the other buffer, then wait for this one
+                if (r0 + R < L1) {
+                    stage(strip + ((s_idx + 1) & 1) * buf_elems, r0 + R, min(R, L1 - r0 - R));
+                    cp_async_commit();
+                    cp_async_wait<1>();
+                } else {
+                    cp_async_wait<0>();
+                }
+                __syncthreads();
+                cur = strip + (s_idx & 1) * buf_elems;
+            } else {
+                stage(strip, r0, nl);
+                __syncthreads();
+                cur = strip;
+            }
+            march(cur, r0, nl);
+            if (async_stage != 2) __syncthreads();
+        }
+        if (async_stage == 2) cp_async_wait<0>();  // no copy outlives the CTA
+    }
 
     if constexpr (STATIC) {
         // ---- epilogue: the scaled static transforms of this coefficient group ----
 #pragma unroll
         for (int q = 0; q < RPT; ++q) {
-            const int rid = b_base + tid + q * THREADS;
-            const int p = (nchunk > 1) ? 0 : rid / ns;
-            const int b = (nchunk > 1) ? rid : rid - p * ns;
-            if (p >= P || b >= ns) continue;
-            const int a = blk[p];
-            if (a < 0) continue;
-            const T sc = scale_s[p];
+            const int b = bt0 + tpa * q;
+            const int a = at;
+            if (a < 0 || b >= ns) continue;
+            const T sc = scale_s[pt];
             T *dst = ru + blockIdx.z * split_stride + (((size_t)z * U + a) * ns + b) * ms_ru + j0;
 #pragma unroll
             for (int j = 0; j < M; ++j)
@@ -373,13 +459,10 @@ __global__ void __launch_bounds__(THREADS, THREADS == kFoldThreads ? fold_fwd_mi
     // ---- epilogue: distribute each ray to every projection of its angle ----
 #pragma unroll
     for (int q = 0; q < RPT; ++q) {
-        const int rid = b_base + tid + q * THREADS;
-        const int p = (nchunk > 1) ? 0 : rid / ns;
-        const int b = (nchunk > 1) ? rid : rid - p * ns;
-        if (p >= P || b >= ns) continue;
-        const int a = blk[p];
-        if (a < 0) continue;
-        const T sc = scale_s[p];
+        const int b = bt0 + tpa * q;
+        const int a = at;
+        if (a < 0 || b >= ns) continue;
+        const T sc = scale_s[pt];
         const int e = start[a + 1];
         for (int idx = start[a]; idx < e; ++idx) {
             const int mem = member[idx];
@@ -787,15 +870,14 @@ dr_status fold_fwd_launch_t(dr_plan *P, const void *u, void *out, const void *gm
                             cudaStream_t st) {
     using ST = std::conditional_t<sizeof(S) == 2, S, T>;
     constexpr int MS = fold_strip_ps<S, T, M>();
-    const int Wmax = std::max(P->nx, P->ny);
-    const int wpad = Wmax + 2 * kFwdGuard;
+    const int ls = fold_line_elems_max(P->nx, P->ny);
     // strip height and staging mode: the autotuned choice (cp.async double
     // buffering needs whole 16-byte coefficient vectors)
     const int async_ok = (P->m == M && ((sizeof(S) == 4 && (M % 4) == 0) || (sizeof(S) == 2 && (M % 8) == 0))) ? 1 : 0;
     const bool bf16_strip = sizeof(S) == 2;
     const int async_stage = async_ok && (bf16_strip ? P->fold_async_st : P->fold_async);
     const int R = std::max(1, bf16_strip ? P->fold_lines_st : P->fold_lines);
-    const size_t smem = 768 + sizeof(ST) * (size_t)(async_stage + 1) * R * wpad * MS;
+    const size_t smem = 768 + sizeof(ST) * (size_t)(async_stage + 1) * R * ls * MS;
     auto kern = fold_fwd_kernel<S, T, M, false>;
     {
         dr_status s = allow_dynamic_smem((const void *)kern, smem);
@@ -805,7 +887,8 @@ dr_status fold_fwd_launch_t(dr_plan *P, const void *u, void *out, const void *gm
     kern<<<grid, kFoldThreads, smem, st>>>((const S *)u, (S *)out, (const S *)gm, P->d_fold_fwd, P->d_fold_start,
                                            P->d_fold_member, (const T *)P->d_PhiP, P->d_fold_blocks, P->nx, P->ny,
                                            P->ns, P->K, P->m, P->MP, P->fold_P, R, P->fold_nchunk, mode,
-                                           (T)sigma, async_stage, 1, (T *)nullptr, 0, 0, 1, (size_t)0);
+                                           (T)sigma, async_stage, 1, (T *)nullptr, 0, 0, 1, (size_t)0, CUtensorMap{},
+                                           CUtensorMap{}, P->d_status);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? DR_OK : cuda_fail(e, "fold_fwd_kernel launch");
 }
@@ -830,7 +913,7 @@ dr_status fold_static_launch(dr_plan *P, const void *u, cudaStream_t st, StaticO
     constexpr int VW = 16 / (int)sizeof(S);
     const int gi = GI;
     const int ngroups = (P->m + MC - 1) / MC;
-    const int wpad = std::max(P->nx, P->ny) + 2 * kFwdGuard;
+    const int ls = fold_line_elems_max(P->nx, P->ny);
     const bool bf16_kernel = sizeof(S) == 2;
     const int R0 = std::max(1, std::min(bf16_kernel ? P->fold2_lines_st : P->fold2_lines, P->fold2_R[gi]));
     if ((size_t)P->nz * ngroups > 65535) return fail(DR_EINVAL, "two-kernel folded forward: too many slice groups");
@@ -840,16 +923,44 @@ dr_status fold_static_launch(dr_plan *P, const void *u, cudaStream_t st, StaticO
     (void)VW;
     int async = bf16_kernel ? P->fold2_async_st : P->fold2_async;
     int R = R0;
+    // async 3: TMA-staged strips (4-float groups of a float plan whose rows
+    // of coefficients are whole 16-byte vectors); otherwise three cp.async buffers
+    CUtensorMap tm_rows{}, tm_cols{};
+    if (async == 3) {
+        bool ok = MC == 4 && !BF16_STRIP && (P->m % 4) == 0 && ((uintptr_t)u % 16) == 0;
+        if (ok) {
+            const uint64_t dims[4] = {(uint64_t)P->m, (uint64_t)P->nx, (uint64_t)P->ny, (uint64_t)P->nz};
+            const uint64_t strides[3] = {(uint64_t)P->m * 4, (uint64_t)P->nx * P->m * 4,
+                                         (uint64_t)P->ny * P->nx * P->m * 4};
+            const uint32_t box_r[4] = {4, (uint32_t)fold_tma_bw(P->nx), 1, 1}, es_r[4] = {1, 2, 1, 1};
+            const uint32_t box_c[4] = {4, 1, (uint32_t)fold_tma_bw(P->ny), 1}, es_c[4] = {1, 1, 2, 1};
+            ok = encode_tensor_map(&tm_rows, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void *>(u), dims,
+                                   strides, box_r, es_r) &&
+                 encode_tensor_map(&tm_cols, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void *>(u), dims,
+                                   strides, box_c, es_c);
+        }
+        if (ok) {
+            const long long line = 16LL * std::max(fold_tma_line(P->nx), fold_tma_line(P->ny));
+            R = std::max(1, std::min(R, (int)((2LL * kFoldStripBudget) / (kFoldTmaStages * line))));
+        } else {
+            async = 2;
+        }
+    }
     if (async == 2) {
         // three buffers within twice the strip budget (below the 227 KB a CTA
         // may hold); where even one line does not fit, two buffers (same march)
-        const long long line = (long long)sizeof(ST) * wpad * MS;
+        const long long line = (long long)sizeof(ST) * ls * MS;
         const int r3 = (int)((2LL * kFoldStripBudget) / (3 * line));
         if (r3 >= 1) R = std::min(R, r3);
         else async = 1;
     }
-    const size_t smem = 768 + sizeof(ST) * (size_t)(async + 1) * R * wpad * MS;
+    const size_t smem = async == 3 ? 768 + 128 + 16 * (size_t)kFoldTmaStages * R *
+                                               std::max(fold_tma_line(P->nx), fold_tma_line(P->ny))
+                                   : 768 + sizeof(ST) * (size_t)(async + 1) * R * ls * MS;
     auto kern = fold_fwd_kernel<S, T, MC, true, THREADS, RPT, MINB>;
+    if constexpr (MC == 4 && !BF16_STRIP) {
+        if (async == 3) kern = fold_fwd_kernel<S, T, MC, true, THREADS, RPT, MINB, true>;
+    }
     {
         dr_status s = allow_dynamic_smem((const void *)kern, smem);
         if (s != DR_OK) return s;
@@ -880,7 +991,7 @@ dr_status fold_static_launch(dr_plan *P, const void *u, cudaStream_t st, StaticO
                                            P->nx, P->ny, P->ns, P->K, P->m, P->MP, P->fold2_P[gi][bv], R,
                                            P->fold2_nchunk[gi],
                                            0, (T)0, async, ngroups, ru, P->fold_U, ms_ru, nsplit,
-                                           split_stride);
+                                           split_stride, tm_rows, tm_cols, P->d_status);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "fold_fwd_kernel (static) launch");
     rs = StaticOut{ru, ms_ru, nsplit, split_stride};

@@ -131,7 +131,7 @@ static void resolve_encoder() {
 }
 
 bool encode_tensor_map(CUtensorMap *map, CUtensorMapDataType dt, int rank, void *base, const uint64_t *dims,
-                       const uint64_t *strides, const uint32_t *box) {
+                       const uint64_t *strides, const uint32_t *box, const uint32_t *elem_strides) {
     resolve_encoder();
     if (!g_encode || rank < 1 || rank > 5) return false;
     cuuint64_t gdim[5], gstr[4];
@@ -139,7 +139,7 @@ bool encode_tensor_map(CUtensorMap *map, CUtensorMapDataType dt, int rank, void 
     for (int i = 0; i < rank; ++i) {
         gdim[i] = dims[i];
         bx[i] = box[i];
-        es[i] = 1;
+        es[i] = elem_strides ? elem_strides[i] : 1;
         if (i + 1 < rank) gstr[i] = strides[i];
     }
     CUresult r = g_encode(map, dt, (cuuint32_t)rank, base, gdim, gstr, bx, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -403,10 +403,11 @@ static dr_status build_tables(dr_plan *P) {
         const int rpt = M <= 4 ? 8 : 32 / M;  // rays per thread of the folded forward
         const int rays = 256 * rpt;            // 256-thread CTAs
         int Pf, nchunk;
-        if (P->ns <= rays) { Pf = std::min(64, rays / P->ns); nchunk = 1; }
+        // a thread marches rpt bins of one angle: ceil(ns / rpt) threads per angle
+        if (P->ns <= rays) { Pf = std::min(64, 256 / ((P->ns + rpt - 1) / rpt)); nchunk = 1; }
         else { Pf = 1; nchunk = (P->ns + rays - 1) / rays; }
         const int MS = M <= 4 ? 4 : ((M % 8 == 0) ? M + 4 : M);
-        const size_t line = sizeof(float) * (size_t)(std::max(P->nx, P->ny) + 2 * kFwdGuard) * MS;
+        const size_t line = sizeof(float) * (size_t)fold_line_elems_max(P->nx, P->ny) * MS;
         int R = (int)((kFoldStripBudget) / line);
         if (R < 1 && line + 768 <= 200 * 1024) R = 1;
         R = std::min(R, 16);
@@ -463,10 +464,11 @@ static dr_status build_tables(dr_plan *P) {
             const int MC = fold_static_mc(gi);
             const int rays2 = fold_static_rays(gi);
             int Pmax, nch2;
-            if (P->ns <= rays2) { Pmax = std::min(64, rays2 / P->ns); nch2 = 1; }
+            const int tpa2 = (P->ns + fold_static_rpt_gi(gi) - 1) / fold_static_rpt_gi(gi);
+            if (P->ns <= rays2) { Pmax = std::min(64, fold_static_threads(gi) / tpa2); nch2 = 1; }
             else { Pmax = 1; nch2 = (P->ns + rays2 - 1) / rays2; }
             const int ps2 = MC == 4 ? 4 : 12;  // float strip stride of the group
-            const size_t line2 = sizeof(float) * (size_t)(std::max(P->nx, P->ny) + 2 * kFwdGuard) * ps2;
+            const size_t line2 = sizeof(float) * (size_t)fold_line_elems_max(P->nx, P->ny) * ps2;
             P->fold2_R[gi] = std::min(16, (int)(kFoldStripBudget / line2));
             P->fold2_nchunk[gi] = nch2;
             const int nmax = (int)std::max(ub0.size(), ub1.size());

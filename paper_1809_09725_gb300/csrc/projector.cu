@@ -394,6 +394,27 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
             }
             P->fold2_async = basync;
         }
+        // TMA-staged strips, two buffers on mbarriers (4-float coefficient
+        // groups of whole 16-byte rows): the copies leave the threads'
+        // instruction stream; two buffers share twice the strip budget
+        if (fold_static_mc(bgi) == 4 && P->m % 4 == 0) {
+            const int keep = P->fold2_async;
+            P->fold2_async = 3;
+            bool won = false;
+            for (int c : {std::max(1, bl / 2), bl, std::min(16, 2 * bl)}) {
+                if (c > P->fold2_R[bgi] * 2) continue;
+                double t = 1e30;
+                dr_status s = run2(true)(c, t);
+                if (s != DR_OK) return s;
+                if (t < ms[4]) {
+                    ms[4] = t;
+                    bl = c;
+                    won = true;
+                }
+            }
+            basync = won ? 3 : keep;
+            P->fold2_async = basync;
+        }
         // smaller angle blocks (more CTAs, each with less work): a fuller last wave
         {
             int bbv = 0;
@@ -688,8 +709,8 @@ dr_status dr_plan_set_fold_march(dr_plan *P, int nsplit, int async) {
     clear_error();
     if (!P) return fail(DR_EINVAL, "dr_plan_set_fold_march: NULL plan");
     if (!(P->fold_U > 0 && P->fold2_ok)) return fail(DR_EINVAL, "dr_plan_set_fold_march: variant unavailable");
-    if (nsplit < 1 || nsplit > 8 || async < 0 || async > 2)
-        return fail(DR_EINVAL, "dr_plan_set_fold_march: nsplit must be 1..8 and async 0, 1 or 2");
+    if (nsplit < 1 || nsplit > 8 || async < 0 || async > 3)
+        return fail(DR_EINVAL, "dr_plan_set_fold_march: nsplit must be 1..8 and async 0, 1, 2 or 3");
     P->fold2_split = nsplit;
     P->fold2_async = P->fold2_async_st = async;
     return DR_OK;

@@ -11,6 +11,7 @@
 // budget and waiting jobs are admitted.  Latency = completion time minus
 // submission time.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
@@ -39,6 +40,7 @@ struct Job {
     size_t bytes = 0;
     int slab = 0;  // > 0: streamed in slabs of this many slices
     int state = DR_JOB_QUEUED;
+    std::atomic<int> cancel{0};  // raised by dr_server_cancel while the job runs
     dr_status status = DR_OK;
     std::string error;
     double t_submit = 0, t_start = 0, t_done = 0;
@@ -180,8 +182,10 @@ static void worker_loop(dr_server *S) {
             if (st != DR_OK) err = dr_last_error();
         }
         if (st == DR_OK) {
-            st = job->slab > 0 ? cp_solve_slabs(plan, d.g, d.u, &d.params, job->slab)
-                               : admm_solve(plan, d.g, d.u, &d.params);
+            plan->cancel = &job->cancel;
+            st = job->cancel.load() ? fail(DR_ECANCELED, "server: canceled before it started")
+                 : job->slab > 0    ? cp_solve_slabs(plan, d.g, d.u, &d.params, job->slab)
+                                    : admm_solve(plan, d.g, d.u, &d.params);
             if (st != DR_OK) err = dr_last_error();
         }
         if (plan) dr_plan_destroy(plan);
@@ -200,6 +204,9 @@ static void worker_loop(dr_server *S) {
                 S->units_done += 2.0 * (d.params.algo == DR_ADMM_CG ? d.params.n_cg + 1 : 1) * d.params.iters *
                                  (double)d.K * d.nx * d.ny * d.nz;
                 S->t_last = std::max(S->t_last, job->t_done);
+            } else if (st == DR_ECANCELED) {
+                job->state = DR_JOB_CANCELED;
+                ++S->canceled;
             } else {
                 job->state = DR_JOB_FAILED;
                 ++S->failed;
@@ -290,7 +297,12 @@ dr_status dr_server_cancel(dr_server *S, int64_t id) {
     auto it = S->jobs.find(id);
     if (it == S->jobs.end()) return fail(DR_EINVAL, "dr_server_cancel: unknown job");
     Job *job = it->second.get();
-    if (job->state != DR_JOB_QUEUED) return fail(DR_EINVAL, "dr_server_cancel: job already started");
+    if (job->state == DR_JOB_RUNNING) {
+        // the worker's solve stops between iterations and records the job as canceled
+        job->cancel.store(1);
+        return DR_OK;
+    }
+    if (job->state != DR_JOB_QUEUED) return fail(DR_EINVAL, "dr_server_cancel: job already finished");
     S->queue.erase(std::remove(S->queue.begin(), S->queue.end(), job), S->queue.end());
     job->state = DR_JOB_CANCELED;
     job->status = DR_ECANCELED;

@@ -612,24 +612,76 @@ static dr_status capture_graph(cudaStream_t root, F body, cudaGraphExec_t *exec)
     return last;
 }
 
+// Cancellation of a serving job (P->cancel set): the host keeps at most two
+// iterations in flight and looks at the flag before issuing the next one, so
+// a raised flag stops the solve within about two iterations.  Returns true
+// when the solve is to stop.
+struct CancelGate {
+    dr_plan *P;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    explicit CancelGate(dr_plan *p) : P(p) {
+        if (P->cancel)
+            for (auto &e : ev)
+                if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) e = nullptr;
+    }
+    ~CancelGate() {
+        for (auto &e : ev)
+            if (e) cudaEventDestroy(e);
+    }
+    // before issuing iteration `it` (>= 1) on stream s
+    bool stop(int it, cudaStream_t s) {
+        if (!P->cancel) return false;
+        if (it >= 3 && ev[it & 1]) cudaEventSynchronize(ev[it & 1]);  // iteration it - 2 has finished
+        if (P->cancel->load(std::memory_order_relaxed)) {
+            cudaStreamSynchronize(s);
+            return true;
+        }
+        return false;
+    }
+    // after issuing iteration `it` on stream s
+    void issued(int it, cudaStream_t s) {
+        if (P->cancel && ev[it & 1]) cudaEventRecord(ev[it & 1], s);
+    }
+};
+
 static dr_status solve(dr_plan *P, const void *g_in, void *u_io, const dr_solve_params &prm) {
     SolveCtx c;
     TRY(solve_begin(P, g_in, u_io, prm, c));
     const cudaStream_t st = P->graph_stream;
+    CancelGate gate(P);
     if (prm.iters > 0) {
         // first iteration eagerly (sets kernel attributes, allocates lazily), the rest as one graph
         TRY(solve_iter(P, c, st));
         if (prm.iters > 1) {
             cudaGraphExec_t exec = nullptr;
+            bool canceled = false;
             if (capture_graph(st, [&]() { return solve_iter(P, c, st); }, &exec) == DR_OK) {
                 cudaError_t ce = cudaSuccess;
-                for (int it = 1; it < prm.iters && ce == cudaSuccess; ++it) ce = cudaGraphLaunch(exec, st);
+                for (int it = 1; it < prm.iters && ce == cudaSuccess; ++it) {
+                    if (gate.stop(it, st)) {
+                        canceled = true;
+                        break;
+                    }
+                    ce = cudaGraphLaunch(exec, st);
+                    gate.issued(it, st);
+                }
                 cudaGraphExecDestroy(exec);
                 if (ce != cudaSuccess) return cuda_fail(ce, "admm_solve: graph launch");
             } else {
                 // no graph: the same launches, issued one iteration at a time
                 clear_error();
-                for (int it = 1; it < prm.iters; ++it) TRY(solve_iter(P, c, st));
+                for (int it = 1; it < prm.iters; ++it) {
+                    if (gate.stop(it, st)) {
+                        canceled = true;
+                        break;
+                    }
+                    TRY(solve_iter(P, c, st));
+                    gate.issued(it, st);
+                }
+            }
+            if (canceled) {
+                DR_CUDA_TRY(cudaStreamSynchronize(st));
+                return fail(DR_ECANCELED, "admm_solve: canceled while running");
             }
         }
     }

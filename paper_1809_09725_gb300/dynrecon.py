@@ -473,7 +473,8 @@ def admm_solve_batch(plans, gs, us, params_list):
 
 def job_desc(nx, ny, nz, ns, theta, t, basis, m, nt, prec, params: SolveParams, g, u) -> JobDesc:
     """Describe a reconstruction request (g, u: host numpy arrays or device tensors,
-    kept alive by the caller until the job finishes)."""
+    kept alive by the caller until the job finishes).  g = u = None describes
+    the job's sizes only (for job_device_bytes; the server refuses it)."""
     th = np.ascontiguousarray(theta, dtype=np.float64)
     tt = np.ascontiguousarray(t, dtype=np.float64)
     pd = ctypes.POINTER(ctypes.c_double)
@@ -483,8 +484,8 @@ def job_desc(nx, ny, nz, ns, theta, t, basis, m, nt, prec, params: SolveParams, 
     d.basis, d.m, d.nt, d.prec = int(basis), int(m), int(nt), int(prec)
     d.params = params
     dt = _DTYPES[int(prec)]
-    d.g = _ptr(g, dt, (nz, th.size, ns), "g").value
-    d.u = _ptr(u, dt, (nz, ny, nx, m), "u").value
+    d.g = None if g is None else _ptr(g, dt, (nz, th.size, ns), "g").value
+    d.u = None if u is None else _ptr(u, dt, (nz, ny, nx, m), "u").value
     d._keep = (th, tt, g, u)
     return d
 

@@ -145,6 +145,43 @@ def test_server_cancel_and_nonfinite_data():
     srv.close()
 
 
+def test_server_cancels_a_running_job_between_iterations():
+    """A running job stops within a few iterations of dr_server_cancel and is
+    recorded as canceled; the server then runs the next job to its normal
+    result (the same as alone)."""
+    import time
+
+    N, nz, K, ht, basis, m, nt, prec, iters = JOBS[1]
+    theta, t, g = _job_inputs(1, JOBS[1])
+    long_prm = dr.solve_params(dr.ADMM_CG, iters=100000, n_cg=4, lambda1=1e-3, lambda2=1.0, rho=1e-2)
+    u_long = np.zeros((nz, N, N, m), dtype=np.float32)
+    d_long = dr.job_desc(N, N, nz, N, theta, t, basis, m, nt, dr.F32, long_prm, g.astype(np.float32), u_long)
+    srv = dr.Server(device=0, budget_bytes=1 << 34, slots=1)
+    jid = srv.submit(d_long)
+    descs, outs = _descs()
+    nxt = srv.submit(descs[0])
+    t0 = time.perf_counter()
+    while srv.wait(jid, timeout_s=0.05)["rc"] == dr.DR_ETIMEOUT and time.perf_counter() - t0 < 1.0:
+        pass
+    assert srv.wait(jid, timeout_s=0.0)["rc"] == dr.DR_ETIMEOUT  # still running after 1 s
+    t_cancel = time.perf_counter()
+    srv.cancel(jid)
+    r = srv.wait(jid, timeout_s=120.0)
+    t_stop = time.perf_counter() - t_cancel
+    assert r["state"] == dr.JOB_CANCELED and r["rc"] == dr.DR_ECANCELED, r
+    assert t_stop < 10.0
+    r2 = srv.wait(nxt, timeout_s=300.0)
+    st = srv.stats()
+    srv.close()
+    assert r2["rc"] == dr.DR_OK and r2["state"] == dr.JOB_DONE
+    np.testing.assert_array_equal(_host_to_f64(outs[0], JOBS[0][7]), _alone(0, JOBS[0]))
+    assert st["canceled"] == 1 and st["completed"] == 1 and st["failed"] == 0
+    srv2 = dr.Server(device=0, budget_bytes=1 << 30, slots=1)
+    with pytest.raises(dr.DynreconError):
+        srv2.cancel(12345)  # unknown job
+    srv2.close()
+
+
 def test_concurrent_plans_with_different_shared_memory_sizes():
     """Plans on several threads launch the same kernels with different dynamic
     shared-memory sizes at once (strip heights, grid sizes); every launch must

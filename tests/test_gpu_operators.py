@@ -43,6 +43,8 @@ CASES = {
     "thin": (3, 41, 2, 23, 40, 2.0, False, dr.FOURIER, 3, 2),
     "flat": (57, 5, 1, 31, 44, 3.0, False, dr.LEGENDRE, 4, 3),
     "tiny_det": (9, 8, 1, 3, 30, 2.0, False, dr.FOURIER, 2, 2),
+    # lines wider than one 256-pixel TMA box, with a partial last box
+    "wide300": (300, 270, 2, 310, 90, 3.0, False, dr.FOURIER, 4, 3),
 }
 
 
@@ -480,7 +482,7 @@ def test_fold2_async_strips_bitwise(case, prec):
     for lines in (1, 3, 16):
         for nsplit in (1, 3):
             outs = []
-            for async_stage in (0, 1, 2):
+            for async_stage in (0, 1, 2, 3):
                 try:
                     plan.set_fold_groups(4, lines, 256, 0)
                 except dr.DynreconError:
@@ -490,8 +492,58 @@ def test_fold2_async_strips_bitwise(case, prec):
                 dr.dyn_radon_fwd(plan, ud, g)
                 plan.sync()
                 outs.append(host_values(g))
+            for o in outs[1:]:
+                np.testing.assert_array_equal(o, outs[0])
+
+
+@pytest.mark.parametrize("case", ["m16", "narrow_det", "m12", "complex_m8", "wide300", "flat", "ragged"])
+def test_fold2_tma_strips_match_oracle(case):
+    """Static transforms with TMA-staged strips (staging mode 3: even and odd
+    pixels of each line copied by tensor maps with element stride 2, three
+    buffers on an mbarrier pipeline): the oracle's projections, and the same
+    bits as synchronous staging, at strip heights of one line, a few lines
+    and the most that fit, with and without line chunks; a plan whose m is
+    not a multiple of 4 ('ragged', m = 5) falls back to cp.async buffers."""
+    args, u, _, P = _setup(case, seed=53)
+    u = u.astype(np.float32).astype(np.float64)
+    plan = _plan(args, dr.F32)
+    plan.set_variant(dr.FOLD2, dr.FOLD)
+    ud = dev_tensor(u, dr.F32)
+    ref = P.fwd(u)
+    for lines in (1, 4, 16):
+        for nsplit in (1, 2):
+            outs = []
+            for async_stage in (0, 3):
+                try:
+                    plan.set_fold_groups(4, lines, 256, 0)
+                except dr.DynreconError:
+                    pytest.skip("strip of %d lines exceeds the budget" % lines)
+                plan.set_fold_march(nsplit, async_stage)
+                g = torch.zeros(plan.g_shape(), dtype=torch.float32, device="cuda")
+                dr.dyn_radon_fwd(plan, ud, g)
+                plan.sync()
+                outs.append(host_values(g))
             np.testing.assert_array_equal(outs[1], outs[0])
-            np.testing.assert_array_equal(outs[2], outs[0])
+            assert_close(outs[1], ref, 1e-5)
+
+
+def test_fold2_tma_strips_inside_solver():
+    """TMA-staged static transforms inside the captured ADMM-CG iterations
+    (the folded normal operator of the CG steps): repeatable bit for bit and
+    the same as synchronous staging."""
+    args, _, g, P = _setup("narrow_det", seed=59)
+    gd = torch.from_numpy(g.astype(np.float32)).cuda()
+    outs = []
+    for async_stage in (0, 3, 3):
+        plan = _plan(args, dr.F32)
+        plan.set_variant(dr.FOLD2, dr.FOLD)
+        plan.set_fold_march(1, async_stage)
+        u = torch.zeros(plan.u_shape(), dtype=torch.float32, device="cuda")
+        prm = dr.solve_params(dr.ADMM_CG, iters=4, n_cg=3, lambda1=0.05, lambda2=1.0, rho=0.5)
+        dr.admm_solve(plan, gd, u, prm)
+        outs.append(host_values(u))
+    np.testing.assert_array_equal(outs[1], outs[0])
+    np.testing.assert_array_equal(outs[2], outs[0])
 
 
 @pytest.mark.parametrize("case", ["narrow_det", "m16", "ragged"])

@@ -72,10 +72,14 @@ def test_admm_f64_matches_oracle_every_iteration(disks, disks_oracle_admm):
 # FP32 solves: the data residual g - R u carries an absolute rounding error of
 # about eps32 * |g|, and the CG right-hand side R*(g - R u) is ~1e-4 of R* g
 # on this near-interpolating problem (16384 unknowns, 16384 data, lambda1 =
-# 1e-3), so the FP32 iterates differ from FP64 ones by ~1e4 eps32 ~ 1e-4
-# (measured 1.2e-4 for u, 9.6e-4 for the objective).  The FP64 plan, which
-# runs the same algorithm, matches to 1e-9 (test above).
-F32_SOLVE_TOL_U = 3e-4
+# 1e-3), so the FP32 iterates differ from FP64 ones by ~1e4 eps32 ~ 1e-4.
+# Which rounding errors get amplified depends on the order of the float sums
+# (projector variant, interpolation order, normal operator): after 20
+# iterations u is measured between 5e-5 and 3.4e-4 from the FP64 iterates
+# over the three variant pairs and two summation orders of the Joseph taps,
+# the objective within 9.6e-4.  The FP64 plan, which runs the same algorithm,
+# matches to 1e-9 (test above).
+F32_SOLVE_TOL_U = 6e-4
 F32_SOLVE_TOL_OBJ = 2e-3
 
 
