@@ -74,7 +74,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-jobs", type=int, default=24, help="jobs of the reduced serving stream")
-    ap.add_argument("--serving-window", type=float, default=60.0,
+    ap.add_argument("--serving-window", type=float, default=30.0,
                     help="seconds the full-size serving stream runs before the backlog is canceled")
     ap.add_argument("--batch-jobs", type=int, default=64)
     ap.add_argument("--extra-workloads", default="ellipsoids256",
@@ -435,14 +435,24 @@ def run_ours(a):
     del g, u
     torch.cuda.empty_cache()
 
+    u_ref = None
     if rank == 0 and not a.no_extras:
         extras["tv_kernels"] = guarded(run_tv_kernels, plan, w, dev, stream)
         extras["fbp_init"] = guarded(run_fbp, plan, torch.from_numpy(g32).to(dev), w, dev, stream)
         torch.cuda.empty_cache()
+        # the FP32 plan's iterate after a few iterations, for the reduced-precision variants
+        u_ref = torch.zeros(plan.u_shape(), dtype=torch.float32, device=dev)
+        dr.admm_solve(plan, torch.from_numpy(g32).to(dev), u_ref,
+                      dr.solve_params(dr.ADMM_CG, iters=3, n_cg=w.n_cg, lambda1=w.lambda1, lambda2=w.lambda2,
+                                      rho=w.rho), want_objective=False)
+        fp32_solver_gb = plan.device_bytes() / 1e9
     plan.close()
     torch.cuda.empty_cache()
     if rank == 0 and not a.no_extras:
-        extras["bf16_storage"] = guarded(run_bf16_storage, w, theta, t, g32, dev, stream, a)
+        extras["reduced_precision"] = guarded(run_precision_variants, w, theta, t, g32, u_ref, 3, dev, stream, a)
+        if isinstance(extras["reduced_precision"], dict) and "error" not in extras["reduced_precision"]:
+            extras["reduced_precision"]["fp32_solver_device_gb"] = fp32_solver_gb
+        del u_ref
         torch.cuda.empty_cache()
     del g32
     if rank == 0 and not a.no_extras:
@@ -455,9 +465,13 @@ def run_ours(a):
             extras["slab_streaming"] = guarded(run_slabs_workload, "ellipsoids256", dev)
     if not a.no_serving and rank == 0 and not a.no_extras:
         extras["serving"] = {name: guarded(run_serving_c5, local, prec, a.serving_window) for name, prec in
-                             (("c5_fp32", dr.F32), ("c5_bf16", dr.BF16))}
-        extras["serving"].update({name: guarded(run_serving, a, local, prec) for name, prec in
-                                  (("reduced_fp32", dr.F32), ("reduced_bf16", dr.BF16))})
+                             (("c5_fp32", dr.F32), ("c5_fp32_bf16fields", dr.F32 | dr.FIELDS_BF16))}
+        outs = {}
+        for name, prec in (("reduced_fp32", dr.F32), ("reduced_fp32_bf16fields", dr.F32 | dr.FIELDS_BF16),
+                           ("reduced_bf16", dr.BF16)):
+            outs[name] = []
+            extras["serving"][name] = guarded(run_serving, a, local, prec, outs[name])
+        extras["serving"]["reduced_rel_l2_vs_fp32"] = guarded(serving_differences, outs)
         extras["serving"]["load_sweep_reduced_fp32"] = guarded(run_serving_sweep, a, local)
 
     if rank == 0:
@@ -549,12 +563,13 @@ def serving_jobs(n, seed=180905):
     return jobs
 
 
-def run_serving(a, device, prec):
+def run_serving(a, device, prec, results=None):
     """Submit the request stream to the serving loop in real time; report
-    latency percentiles and aggregate projector throughput."""
+    latency percentiles and aggregate projector throughput.  results: a list
+    that receives each job's reconstruction (host arrays)."""
     from paper_1809_09725_gb300 import dynrecon as dr
     jobs = serving_jobs(a.serving_jobs)
-    descs = []
+    descs, outs = [], []
     for j in jobs:
         if prec == dr.BF16:
             import torch
@@ -566,6 +581,7 @@ def run_serving(a, device, prec):
         prm = dr.solve_params(dr.ADMM_CG, iters=30, n_cg=4, lambda1=1e-3, lambda2=1.0, rho=1e-2)
         descs.append(dr.job_desc(j["N"], j["N"], j["nz"], j["N"], j["theta"], j["t"], j["basis"], j["m"], j["nt"],
                                  prec, prm, gh, uh))
+        outs.append(uh)
     srv = dr.Server(device=device, budget_bytes=150 * 10 ** 9, slots=8)
     t0 = time.perf_counter()
     ids = []
@@ -578,6 +594,8 @@ def run_serving(a, device, prec):
     wall = time.perf_counter() - t0
     st = srv.stats()
     srv.close()
+    if results is not None:
+        results.extend(outs)
     units = sum(2 * 5 * 30 * j["K"] * j["N"] * j["N"] * j["nz"] for j in jobs)
     return {"jobs": len(jobs), "completed": st["completed"], "failed": st["failed"],
             "p50_latency_s": st["p50_latency_s"], "p99_latency_s": st["p99_latency_s"],
@@ -642,13 +660,11 @@ def run_serving_c5(device, prec, window_s=60.0, n=64, budget=150 * 10 ** 9, slot
         # data: exact line integrals of 5 moving disks, the same on every slice
         blobs = synth.disks(synth.rng_for(j["seed"]), j["N"], 5)
         g1 = synth.sinogram(blobs, theta, t, j["N"], 1)[0].astype(np.float32)
-        g = np.empty((j["nz"], j["K"], j["N"]), dtype=np.float32)
+        if prec & ~dr.FIELDS_BF16 == dr.BF16:
+            g1 = torch.from_numpy(g1).to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16)
+        g = np.empty((j["nz"], j["K"], j["N"]), dtype=g1.dtype)
         g[...] = g1[None]
-        if prec == dr.BF16:
-            g = torch.from_numpy(g).to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16)
-            u = np.zeros((j["nz"], j["N"], j["N"], j["m"]), dtype=np.uint16)
-        else:
-            u = np.zeros((j["nz"], j["N"], j["N"], j["m"]), dtype=np.float32)
+        u = np.zeros((j["nz"], j["N"], j["N"], j["m"]), dtype=g1.dtype)
         d = dr.job_desc(j["N"], j["N"], j["nz"], j["N"], theta, t, j["basis"], j["m"], j["ht"], prec, prm(), g, u)
         jid = srv.submit(d)
         live[jid] = (i, time.perf_counter() - t0 - j["arrival"])
@@ -808,6 +824,27 @@ def run_slabs(w, theta, t, g_np, dev, slab=4, iters=10):
             "copy_gbs": (h2d + d2h) * iters / t_sl / 1e9, "setup_s_per_call": setup_s,
             "note": "Chambolle-Pock, same operator norm; streamed = volume in pinned host memory, per-iteration "
                     "time from the difference of a %d- and a %d-iteration call" % (iters, 3 * iters)}
+
+
+def serving_differences(outs):
+    """Largest relative L2 difference of the served reconstructions from the
+    FP32 ones, per variant (the same jobs and parameters)."""
+    import torch
+    ref = outs["reduced_fp32"]
+    res = {}
+    for name, arrs in outs.items():
+        if name == "reduced_fp32" or len(arrs) != len(ref):
+            continue
+        worst = 0.0
+        for a_, b_ in zip(arrs, ref):
+            av = (torch.from_numpy(a_.view(np.int16)).view(torch.bfloat16).double().numpy() if a_.dtype == np.uint16
+                  else a_.astype(np.float64))
+            bv = b_.astype(np.float64)
+            nb = np.linalg.norm(bv)
+            if nb > 0:
+                worst = max(worst, float(np.linalg.norm(av - bv) / nb))
+        res[name] = worst
+    return res
 
 
 def run_serving_sweep(a, device, utilisations=(0.5, 0.8, 0.95)):
@@ -996,38 +1033,44 @@ def cpu_baseline_1thread(w, kproj=100):
                       "thread (%.1f s)" % (kproj, el)}
 
 
-def run_bf16_storage(w, theta, t, g32, dev, stream, a):
-    """The same workload on a BF16-storage plan (FP32 accumulation): the
-    projector pair on bf16 data, and ADMM-CG iterations on bf16 data and
-    coefficients."""
+def run_precision_variants(w, theta, t, g32, u_ref, iters, dev, stream, a):
+    """The workload on reduced-precision storage (FP32 arithmetic and
+    accumulation throughout): FP32 data and coefficients with the solver's
+    dual fields in bf16 (DR_FIELDS_BF16), and BF16 data and coefficients with
+    bf16 fields.  Per variant: the projector pair on its storage type, the
+    ADMM-CG iteration time, the solver's device bytes, and u after `iters`
+    iterations from zero against the FP32 plan's (u_ref)."""
     import torch
 
     from paper_1809_09725_gb300 import dynrecon as dr
-    pb = dr.Plan(w.N, w.N, w.nz, w.ns, theta, t, w.basis, w.m, w.nt, dr.BF16)
-    t0 = time.perf_counter()
-    pb.autotune()
-    t_tune = time.perf_counter() - t0
-    fwd_ms, adj_ms = time_projectors(pb, dev, stream, reps=a.op_reps)
-    gb = torch.from_numpy(g32).to(dev).to(torch.bfloat16)
-    ub = torch.zeros(pb.u_shape(), dtype=torch.bfloat16, device=dev)
-    iters = 3
-    prm = dr.solve_params(dr.ADMM_CG, iters=1, n_cg=w.n_cg, lambda1=w.lambda1, lambda2=w.lambda2, rho=w.rho)
-    dr.admm_solve(pb, gb, ub, prm, want_objective=False)
-    ub.zero_()
-    prm = dr.solve_params(dr.ADMM_CG, iters=iters, n_cg=w.n_cg, lambda1=w.lambda1, lambda2=w.lambda2, rho=w.rho)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    dr.admm_solve(pb, gb, ub, prm, want_objective=False)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / iters
-    out = {"fwd_ms": fwd_ms, "adj_ms": adj_ms, "admm_ms_per_iter": ms, "autotune_s": t_tune,
-           "voxel_projection_per_s": 2 * (w.n_cg + 1) * w.K * w.voxels() / (ms * 1e-3),
-           "info": pb.info(),
-           "note": "dyn_radon_fwd / dyn_radon_adj on bf16 u and g (FP32 accumulation); admm_solve on bf16 g and u"}
-    del gb, ub
-    pb.close()
+    out = {}
+    for label, prec in (("fp32_bf16fields", dr.F32 | dr.FIELDS_BF16), ("bf16_bf16fields", dr.BF16 | dr.FIELDS_BF16)):
+        pb = dr.Plan(w.N, w.N, w.nz, w.ns, theta, t, w.basis, w.m, w.nt, prec)
+        t0 = time.perf_counter()
+        pb.autotune()
+        t_tune = time.perf_counter() - t0
+        sd = getattr(torch, pb.storage_dtype)
+        fwd_ms, adj_ms = time_projectors(pb, dev, stream, reps=a.op_reps)
+        gb = torch.from_numpy(g32).to(dev).to(sd)
+        ub = torch.zeros(pb.u_shape(), dtype=sd, device=dev)
+        prm = dr.solve_params(dr.ADMM_CG, iters=iters, n_cg=w.n_cg, lambda1=w.lambda1, lambda2=w.lambda2, rho=w.rho)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        dr.admm_solve(pb, gb, ub, prm, want_objective=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / iters  # the first iteration runs eagerly, the rest from a graph
+        diff = float(torch.linalg.vector_norm(ub.float() - u_ref) / torch.linalg.vector_norm(u_ref))
+        out[label] = {"fwd_ms": fwd_ms, "adj_ms": adj_ms, "admm_ms_per_iter": ms, "autotune_s": t_tune,
+                      "voxel_projection_per_s": 2 * (w.n_cg + 1) * w.K * w.voxels() / (ms * 1e-3),
+                      "solver_device_gb": (pb.device_bytes()) / 1e9,
+                      "rel_l2_u_vs_fp32_after_%d_iters" % iters: diff, "info": pb.info()}
+        del gb, ub
+        pb.close()
+        torch.cuda.empty_cache()
+    out["note"] = ("dual fields in bf16: one rounding per store, FP32 arithmetic; BF16 storage also rounds g and u; "
+                   "u compared with the FP32 plan's after the same iterations from zero")
     return out
 
 

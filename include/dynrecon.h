@@ -28,6 +28,7 @@
  *   DR_F32          u, g, fields: float
  *   DR_BF16_F32ACC  u, g: bfloat16 (raw 16-bit); fields: float; all
  *                   arithmetic in float, inner products in double
+ *   | DR_FIELDS_BF16 the solvers' own dual fields in bfloat16 (see below)
  *   DR_F64          everything double
  *
  * Memory and execution: unless a call says otherwise, data pointers are
@@ -75,7 +76,20 @@ typedef enum {
     DR_BASIS_ORTHONORMAL = 0x100
 } dr_basis;
 
-typedef enum { DR_F32 = 0, DR_BF16_F32ACC = 1, DR_F64 = 2 } dr_precision;
+typedef enum {
+    DR_F32 = 0,
+    DR_BF16_F32ACC = 1,
+    DR_F64 = 2,
+    /* Flag OR-ed into DR_F32 or DR_BF16_F32ACC: the solvers (admm_solve,
+     * admm_solve_batch, the serving layer) keep their dual fields -- ADMM's mu
+     * and w, Chambolle-Pock's h2, 4 nt values per voxel, the largest part of
+     * the solver state -- in bfloat16, each value rounded once to nearest on
+     * every store, arithmetic in float.  Halves the fields' device memory and
+     * HBM traffic; the operator entry points and the state buffer (resume)
+     * are unchanged in layout, the state holding the fields as bf16.  The
+     * slab-streamed solver keeps float fields.  Rejected for DR_F64. */
+    DR_FIELDS_BF16 = 0x10
+} dr_precision;
 
 typedef enum {
     DR_ADMM_CG = 0,        /* ADMM split psi = D u, u-step by n_cg conjugate-gradient steps */

@@ -173,6 +173,7 @@ struct dr_plan {
     dr_basis basis;
     bool orthonormal = false;
     dr_precision prec;
+    bool fields_bf16 = false;  // the solvers' dual fields stored in bf16 (DR_FIELDS_BF16)
     cudaStream_t stream;
     cudaStream_t graph_stream;
     cudaEvent_t ev_a, ev_b;
@@ -255,6 +256,8 @@ namespace dr {
 
 inline size_t elem_size(dr_precision p) { return p == DR_F64 ? 8 : (p == DR_BF16_F32ACC ? 2 : 4); }
 inline size_t calc_size(dr_precision p) { return p == DR_F64 ? 8 : 4; }
+// bytes per element of the solvers' dual fields
+inline size_t field_size(const dr_plan *P) { return P->fields_bf16 ? 2 : calc_size(P->prec); }
 inline size_t nvox(const dr_plan *P) { return (size_t)P->nx * P->ny * P->nz; }
 inline size_t nu_elems(const dr_plan *P) { return nvox(P) * P->m; }
 inline size_t ng_elems(const dr_plan *P) { return (size_t)P->nz * P->K * P->ns; }

@@ -557,8 +557,12 @@ dr_status dr_plan_create(dr_plan **out, int nx, int ny, int nz, int ns, int K, c
         return fail(DR_EINVAL, "dr_plan_create: bad basis");
     if (kind == DR_FOURIER_COMPLEX && m % 2 != 0)
         return fail(DR_EINVAL, "dr_plan_create: the complex Fourier basis needs an even m (2 real channels per function)");
+    const bool fields_bf16 = ((int)prec & DR_FIELDS_BF16) != 0;
+    prec = (dr_precision)((int)prec & ~DR_FIELDS_BF16);
     if (prec != DR_F32 && prec != DR_BF16_F32ACC && prec != DR_F64)
         return fail(DR_EINVAL, "dr_plan_create: bad precision");
+    if (fields_bf16 && prec == DR_F64)
+        return fail(DR_EINVAL, "dr_plan_create: DR_FIELDS_BF16 needs a DR_F32 or DR_BF16_F32ACC plan");
     if (!theta || !t) return fail(DR_EINVAL, "dr_plan_create: theta/t are NULL");
     for (int k = 0; k < K; ++k)
         if (!std::isfinite(theta[k]) || !std::isfinite(t[k]))
@@ -573,6 +577,7 @@ dr_status dr_plan_create(dr_plan **out, int nx, int ny, int nz, int ns, int K, c
     P->basis = (dr_basis)kind;
     P->orthonormal = (flags & DR_BASIS_ORTHONORMAL) != 0;
     P->prec = prec;
+    P->fields_bf16 = fields_bf16;
     P->stream = (cudaStream_t)cuda_stream;
     P->theta.assign(theta, theta + K);
     P->t.assign(t, t + K);

@@ -190,7 +190,14 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
         }
     }
     cudaStream_t st = P->graph_stream;
-    cudaEvent_t e0, e1;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    struct EventPair {  // released on every return path
+        cudaEvent_t *a, *b;
+        ~EventPair() {
+            if (*a) cudaEventDestroy(*a);
+            if (*b) cudaEventDestroy(*b);
+        }
+    } events_guard{&e0, &e1};
     DR_CUDA_TRY(cudaEventCreate(&e0));
     DR_CUDA_TRY(cudaEventCreate(&e1));
     const size_t cs = calc_size(P->prec);
@@ -200,7 +207,10 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
     double ms_st1 = 1e30, ms_st2 = 1e30;  // bf16-strip kernels of BF16 plans: fold, fold in two kernels
     // launches per trial: one warm-up, then the timed ones (reps - 1; the
     // screening trials and the direct variant, timed only for comparison, take one)
+    // a serving job canceled while its plan is being tuned stops between trials
+    auto canceled = [&]() { return P->cancel && P->cancel->load(std::memory_order_relaxed); };
     auto time_fwd = [&](int v, double &best, bool calc = true, int reps = 3) -> dr_status {
+        if (canceled()) return fail(DR_ECANCELED, "autotune: canceled");
         for (int rep = 0; rep < reps; ++rep) {
             DR_CUDA_TRY(cudaEventRecord(e0, st));
             dr_status s = launch_fwd_variant(P, v, calc, u_scratch, g_scratch, nullptr, 0, 0.0, st);
@@ -397,22 +407,34 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
         // TMA-staged strips, two buffers on mbarriers (4-float coefficient
         // groups of whole 16-byte rows): the copies leave the threads'
         // instruction stream; two buffers share twice the strip budget
-        if (fold_static_mc(bgi) == 4 && P->m % 4 == 0) {
-            const int keep = P->fold2_async;
-            P->fold2_async = 3;
+        // (every 4-coefficient CTA shape: the copies free registers and issue
+        // slots, which can move the best shape), at the tallest strips two
+        // buffers hold and at half that
+        if (P->m % 4 == 0) {
+            const int keep_gi = P->fold2_gi, keep_async = P->fold2_async;
             bool won = false;
-            for (int c : {std::max(1, bl / 2), bl, std::min(16, 2 * bl)}) {
-                if (c > P->fold2_R[bgi] * 2) continue;
-                double t = 1e30;
-                dr_status s = run2(true)(c, t);
-                if (s != DR_OK) return s;
-                if (t < ms[4]) {
-                    ms[4] = t;
-                    bl = c;
-                    won = true;
+            for (int gi = 0; gi < kFold2Configs; ++gi) {
+                if (fold_static_mc(gi) != 4 || !gi_ok(gi)) continue;
+                P->fold2_gi = gi;
+                P->fold2_async = 3;
+                const long long line = 16LL * std::max(fold_tma_line(P->nx), fold_tma_line(P->ny));
+                const int rt = std::max(1, std::min({16, P->fold2_R[gi],
+                                                     (int)((2LL * kFoldStripBudget) / (kFoldTmaStages * line))}));
+                for (int c : {rt, std::max(1, rt / 2)}) {
+                    double t = 1e30;
+                    dr_status s = run2(true)(c, t);
+                    if (s != DR_OK) return s;
+                    if (t < ms[4]) {
+                        ms[4] = t;
+                        bl = c;
+                        bgi = gi;
+                        won = true;
+                    }
+                    if (rt == 1) break;
                 }
             }
-            basync = won ? 3 : keep;
+            P->fold2_gi = won ? bgi : keep_gi;
+            basync = won ? 3 : keep_async;
             P->fold2_async = basync;
         }
         // smaller angle blocks (more CTAs, each with less work): a fuller last wave
@@ -491,8 +513,10 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
                     best_c = all[i];
                 }
             }
-            bl = best_c;
-            ms[4] = best_t;  // the chosen configuration's confirmed time
+            if (best_t < 1e30) {
+                bl = best_c;
+                ms[4] = best_t;  // the chosen configuration's confirmed time
+            }
         }
         P->fold2_lines = bl;
         P->fold2_lines_st = bl;
@@ -539,6 +563,7 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
         P->sel_fwd_st = best;
     }
     auto time_adj = [&](int v, double &best, int reps = 3) -> dr_status {
+        if (canceled()) return fail(DR_ECANCELED, "autotune: canceled");
         for (int rep = 0; rep < reps; ++rep) {
             DR_CUDA_TRY(cudaEventRecord(e0, st));
             dr_status s = launch_adj_variant(P, v, true, g_scratch, u_scratch, 1.0, 0.0, true, st);
@@ -571,8 +596,6 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
         }
         P->fold_adj_pp = best_pp;
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     for (int i = 0; i < 5; ++i) P->tune_ms[i] = ms[i] < 1e29 ? ms[i] : -1.0;
     {
         int best = 0;

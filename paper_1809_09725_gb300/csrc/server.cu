@@ -94,7 +94,7 @@ static size_t job_slab_bytes(const dr_job_desc &d, int S) {
     const size_t s = (size_t)S;
     size_t b = plan_table_bytes(d);
     b += 3 * ((s + 1) * um * cs * 2 + s * gk * cs * 2 + (s + 1) * f4 * cs);
-    if (d.prec == DR_BF16_F32ACC) b += 3 * s * gk * 2;
+    if ((d.prec & ~DR_FIELDS_BF16) == DR_BF16_F32ACC) b += 3 * s * gk * 2;
     b += s * um * cs + s * gk * cs + f4 * cs + um * cs;
     const size_t nslab = ((size_t)d.nz + s - 1) / s;
     if (nslab > 1 && nslab - 1 <= s) b += (nslab - 1) * um * cs;  // device halo copies of u~ (few slabs)
@@ -124,8 +124,9 @@ static size_t job_bytes(const dr_job_desc &d) {
         b += std::min<size_t>(kSplitScratchMax, 4 * sizeof(float) * ng * ((d.m + 3) / 4 * 4));
     }
     const dr_algo algo = d.params.algo;
-    if (algo == DR_ADMM_CG) b += 3 * nu * cs + ng * cs + 2 * nf * cs;
-    else b += 2 * nu * cs + 2 * ng * cs + nf * cs;
+    const size_t fs = (d.prec & DR_FIELDS_BF16) ? 2 : cs;  // dual fields
+    if (algo == DR_ADMM_CG) b += 3 * nu * cs + ng * cs + 2 * nf * fs;
+    else b += 2 * nu * cs + 2 * ng * cs + nf * fs;
     b += nu * cs + ng * cs;                                        // staging copies of host u and g
     b += sizeof(double) * 3 * (size_t)(d.params.iters + 1);
     b += b / 64 + (1u << 20);                                      // allocation granularity slack

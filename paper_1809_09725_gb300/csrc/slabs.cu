@@ -221,9 +221,15 @@ struct PlanScope {
     dr_plan *P;
     int nz;
     void *gt;
-    explicit PlanScope(dr_plan *p) : P(p), nz(p->nz), gt(p->d_gt) { P->split_off = true; }
+    bool fields_bf16;
+    // the slab solver keeps float dual fields (its halo copies move floats)
+    explicit PlanScope(dr_plan *p) : P(p), nz(p->nz), gt(p->d_gt), fields_bf16(p->fields_bf16) {
+        P->split_off = true;
+        P->fields_bf16 = false;
+    }
     ~PlanScope() {
         P->split_off = false;
+        P->fields_bf16 = fields_bf16;
         P->nz = nz;
         P->z_open_lo = P->z_open_hi = 0;
         P->d_gt = gt;

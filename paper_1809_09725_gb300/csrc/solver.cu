@@ -230,11 +230,11 @@ void free_workspace(dr_plan *P) {
 }
 
 static size_t ws_bytes(const dr_plan *P, dr_algo algo, int iters) {
-    const size_t T = calc_size(P->prec);
+    const size_t T = calc_size(P->prec), F = field_size(P);
     const size_t nu = nu_elems(P), ng = ng_elems(P), nf = nf_elems(P);
     size_t b = 0;
-    if (algo == DR_ADMM_CG) b += 3 * nu * T + ng * T + 2 * nf * T;
-    else b += 2 * nu * T + 2 * ng * T + nf * T;
+    if (algo == DR_ADMM_CG) b += 3 * nu * T + ng * T + 2 * nf * F;
+    else b += 2 * nu * T + 2 * ng * T + nf * F;
     b += nu * T + ng * T;  // internal copies of u and g (host or bf16 inputs)
     b += sizeof(double) * 3 * (size_t)(iters + 1);
     return b;
@@ -244,7 +244,7 @@ static dr_status ensure_ws(dr_plan *P, dr_algo algo, int iters) {
     Workspace &w = P->ws;
     if (w.bytes && w.algo == algo && w.obj_cap >= iters + 1) return DR_OK;
     free_workspace(P);
-    const size_t T = calc_size(P->prec);
+    const size_t T = calc_size(P->prec), F = field_size(P);
     const size_t nu = nu_elems(P), ng = ng_elems(P), nf = nf_elems(P);
     auto alloc = [&](void **p, size_t bytes) -> bool {
         if (cudaMalloc(p, std::max<size_t>(bytes, 16)) != cudaSuccess) return false;
@@ -254,10 +254,10 @@ static dr_status ensure_ws(dr_plan *P, dr_algo algo, int iters) {
     bool ok = true;
     if (algo == DR_ADMM_CG) {
         ok = ok && alloc(&w.r, nu * T) && alloc(&w.p, nu * T) && alloc(&w.q, nu * T);
-        ok = ok && alloc(&w.gd, ng * T) && alloc(&w.mu, nf * T) && alloc(&w.w, nf * T);
+        ok = ok && alloc(&w.gd, ng * T) && alloc(&w.mu, nf * F) && alloc(&w.w, nf * F);
     } else {
         ok = ok && alloc(&w.ut, nu * T) && alloc(&w.q, nu * T);
-        ok = ok && alloc(&w.gd, ng * T) && alloc(&w.h1, ng * T) && alloc(&w.mu, nf * T);
+        ok = ok && alloc(&w.gd, ng * T) && alloc(&w.h1, ng * T) && alloc(&w.mu, nf * F);
     }
     ok = ok && alloc(&w.u_dev, nu * T) && alloc(&w.g_dev, ng * T);
     ok = ok && alloc((void **)&w.obj, sizeof(double) * 3 * (size_t)(iters + 1));
@@ -484,21 +484,22 @@ static dr_status solve_begin(dr_plan *P, const void *g_in, void *u_io, const dr_
 
     // the state besides u: zero at a fresh start, the caller's on resume
     const unsigned char *rs = prm.resume ? (const unsigned char *)prm.state : nullptr;
+    const size_t fsz = nf * field_size(P);  // bytes of one dual field
     if (prm.algo == DR_ADMM_CG) {
         if (rs) {
-            DR_CUDA_TRY(cudaMemcpyAsync(w.mu, rs, nf * cs, cudaMemcpyDeviceToDevice, st));
-            DR_CUDA_TRY(cudaMemcpyAsync(w.w, rs + nf * cs, nf * cs, cudaMemcpyDeviceToDevice, st));
+            DR_CUDA_TRY(cudaMemcpyAsync(w.mu, rs, fsz, cudaMemcpyDeviceToDevice, st));
+            DR_CUDA_TRY(cudaMemcpyAsync(w.w, rs + fsz, fsz, cudaMemcpyDeviceToDevice, st));
         } else {
-            DR_CUDA_TRY(cudaMemsetAsync(w.mu, 0, nf * cs, st));
-            DR_CUDA_TRY(cudaMemsetAsync(w.w, 0, nf * cs, st));
+            DR_CUDA_TRY(cudaMemsetAsync(w.mu, 0, fsz, st));
+            DR_CUDA_TRY(cudaMemsetAsync(w.w, 0, fsz, st));
         }
     } else {
         if (rs) {
-            DR_CUDA_TRY(cudaMemcpyAsync(w.mu, rs, nf * cs, cudaMemcpyDeviceToDevice, st));
-            DR_CUDA_TRY(cudaMemcpyAsync(w.h1, rs + nf * cs, ng * cs, cudaMemcpyDeviceToDevice, st));
+            DR_CUDA_TRY(cudaMemcpyAsync(w.mu, rs, fsz, cudaMemcpyDeviceToDevice, st));
+            DR_CUDA_TRY(cudaMemcpyAsync(w.h1, rs + fsz, ng * cs, cudaMemcpyDeviceToDevice, st));
         } else {
             DR_CUDA_TRY(cudaMemsetAsync(w.h1, 0, ng * cs, st));
-            DR_CUDA_TRY(cudaMemsetAsync(w.mu, 0, nf * cs, st));
+            DR_CUDA_TRY(cudaMemsetAsync(w.mu, 0, fsz, st));
         }
         if (prm.op_norm > 0.0) {
             c.L = prm.op_norm;
@@ -538,14 +539,14 @@ static dr_status solve_end(dr_plan *P, SolveCtx &c) {
     if (prm.state) {
         // the state besides u, for a later call to continue from
         unsigned char *sd = (unsigned char *)prm.state;
-        const size_t nf = nf_elems(P);
+        const size_t fsz = nf_elems(P) * field_size(P);
         if (prm.algo == DR_ADMM_CG) {
-            DR_CUDA_TRY(cudaMemcpyAsync(sd, w.mu, nf * cs, cudaMemcpyDeviceToDevice, st));
-            DR_CUDA_TRY(cudaMemcpyAsync(sd + nf * cs, w.w, nf * cs, cudaMemcpyDeviceToDevice, st));
+            DR_CUDA_TRY(cudaMemcpyAsync(sd, w.mu, fsz, cudaMemcpyDeviceToDevice, st));
+            DR_CUDA_TRY(cudaMemcpyAsync(sd + fsz, w.w, fsz, cudaMemcpyDeviceToDevice, st));
         } else {
-            DR_CUDA_TRY(cudaMemcpyAsync(sd, w.mu, nf * cs, cudaMemcpyDeviceToDevice, st));
-            DR_CUDA_TRY(cudaMemcpyAsync(sd + nf * cs, w.h1, ng * cs, cudaMemcpyDeviceToDevice, st));
-            DR_CUDA_TRY(cudaMemcpyAsync(sd + (nf + ng) * cs, w.ut, nu * cs, cudaMemcpyDeviceToDevice, st));
+            DR_CUDA_TRY(cudaMemcpyAsync(sd, w.mu, fsz, cudaMemcpyDeviceToDevice, st));
+            DR_CUDA_TRY(cudaMemcpyAsync(sd + fsz, w.h1, ng * cs, cudaMemcpyDeviceToDevice, st));
+            DR_CUDA_TRY(cudaMemcpyAsync(sd + fsz + ng * cs, w.ut, nu * cs, cudaMemcpyDeviceToDevice, st));
         }
     }
     if (!c.u_dev || c.bf) {
@@ -794,9 +795,9 @@ size_t dr_plan_workspace_bytes(const dr_plan *P, dr_algo algo) { return P ? ws_b
 
 size_t dr_plan_state_bytes(const dr_plan *P, dr_algo algo) {
     if (!P) return 0;
-    const size_t cs = calc_size(P->prec);
-    if (algo == DR_ADMM_CG) return 2 * nf_elems(P) * cs;
-    if (algo == DR_CHAMBOLLE_POCK) return (nf_elems(P) + ng_elems(P) + nu_elems(P)) * cs;
+    const size_t cs = calc_size(P->prec), fs = field_size(P);
+    if (algo == DR_ADMM_CG) return 2 * nf_elems(P) * fs;
+    if (algo == DR_CHAMBOLLE_POCK) return nf_elems(P) * fs + (ng_elems(P) + nu_elems(P)) * cs;
     return 0;
 }
 

@@ -14,6 +14,7 @@ dr_status launch_grad(dr_plan *P, const void *u, bool calc, void *p, double lamb
 
 dr_status launch_grad_adj(dr_plan *P, const void *p, void *u, bool calc, double lambda2, double alpha,
                           double beta, cudaStream_t st) {
+    if (calc && P->fields_bf16) return TvFieldsBF16::grad_adj(P, p, u, lambda2, alpha, beta, st);
     if (P->prec == DR_F64) return TvOps<double, double>::grad_adj(P, p, u, calc, lambda2, alpha, beta, st);
     if (P->prec == DR_BF16_F32ACC && !calc)
         return TvOps<float, bf16>::grad_adj(P, p, u, false, lambda2, alpha, beta, st);
@@ -22,6 +23,7 @@ dr_status launch_grad_adj(dr_plan *P, const void *p, void *u, bool calc, double 
 
 dr_status launch_prox(dr_plan *P, const void *u, bool calc, void *mu, void *w, double rho, double lambda1,
                       double lambda2, double *obj_row, cudaStream_t st) {
+    if (calc && P->fields_bf16) return TvFieldsBF16::prox(P, u, mu, w, rho, lambda1, lambda2, obj_row, st);
     if (P->prec == DR_F64) return TvOps<double, double>::prox(P, u, mu, w, rho, lambda1, lambda2, obj_row, st);
     if (P->prec == DR_BF16_F32ACC && !calc)
         return TvOps<float, bf16>::prox(P, u, mu, w, rho, lambda1, lambda2, obj_row, st);
@@ -45,12 +47,14 @@ dr_status launch_rhs(dr_plan *P, const void *u, const void *w, void *r, void *p,
 
 dr_status launch_cp_dual(dr_plan *P, const void *ut, void *h2, double sigma, double lambda1, double lambda2,
                          cudaStream_t st) {
+    if (P->fields_bf16) return TvFieldsBF16::cp_dual(P, ut, h2, sigma, lambda1, lambda2, st);
     if (P->prec == DR_F64) return TvCalc<double>::cp_dual(P, ut, h2, sigma, lambda1, lambda2, st);
     return TvCalc<float>::cp_dual(P, ut, h2, sigma, lambda1, lambda2, st);
 }
 
 dr_status launch_cp_primal(dr_plan *P, void *u, void *ut, const void *a, const void *h2, double tau, double theta,
                            double lambda2, cudaStream_t st) {
+    if (P->fields_bf16) return TvFieldsBF16::cp_primal(P, u, ut, a, h2, tau, theta, lambda2, st);
     if (P->prec == DR_F64) return TvCalc<double>::cp_primal(P, u, ut, a, h2, tau, theta, lambda2, st);
     return TvCalc<float>::cp_primal(P, u, ut, a, h2, tau, theta, lambda2, st);
 }

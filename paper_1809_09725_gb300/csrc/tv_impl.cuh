@@ -55,6 +55,32 @@ __device__ __forceinline__ void st4<double, D4>(double *p, D4 v) {
     reinterpret_cast<double2 *>(p)[1] = make_double2(v.z, v.w);
 }
 
+// Dual fields stored as F: the compute type, or bf16 for plans that keep the
+// solver's dual fields in bf16 (arithmetic stays in T; one rounding to the
+// nearest bf16 per store).
+template <typename T, typename F>
+struct FieldIO {
+    static __device__ __forceinline__ typename V4<T>::type ld(const T *p) { return ld4<T>(p); }
+    static __device__ __forceinline__ void st(T *p, typename V4<T>::type v) { st4<T>(p, v); }
+    static __device__ __forceinline__ T ld1(const T *p) { return *p; }
+};
+template <>
+struct FieldIO<float, bf16> {
+    static __device__ __forceinline__ float4 ld(const bf16 *p) {
+        const uint2 a = *reinterpret_cast<const uint2 *>(p);
+        return make_float4(__uint_as_float(a.x << 16), __uint_as_float(a.x & 0xffff0000u),
+                           __uint_as_float(a.y << 16), __uint_as_float(a.y & 0xffff0000u));
+    }
+    static __device__ __forceinline__ void st(bf16 *p, float4 v) {
+        const __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, v.w);
+        uint2 o;
+        o.x = *reinterpret_cast<const unsigned *>(&a);
+        o.y = *reinterpret_cast<const unsigned *>(&b);
+        *reinterpret_cast<uint2 *>(p) = o;
+    }
+    static __device__ __forceinline__ float ld1(const bf16 *p) { return __bfloat162float(*p); }
+};
+
 // zlo / zhi: the slice below local z = 0 / above local z = nz-1 exists in
 // memory (a halo of a slab of a larger volume), so the z differences there
 // are interior ones instead of the Neumann boundary.
@@ -183,15 +209,15 @@ __global__ void __launch_bounds__(kRedThreads)
 }
 
 // (D^T p)_j at voxel v (Neumann-matched backward differences, then PhiF^T).
-template <typename T, int M>
-__device__ __forceinline__ void gradT_voxel(const T *__restrict__ p, size_t v, int x, int y, int z, const Geo &g,
+template <typename T, int M, typename F = T>
+__device__ __forceinline__ void gradT_voxel(const F *__restrict__ p, size_t v, int x, int y, int z, const Geo &g,
                                             const T *sm, T lambda2, T (&outj)[M]) {
     const T *dph = sm + g.nt * M;
 #pragma unroll
     for (int j = 0; j < M; ++j) outj[j] = T(0);
     const size_t fs = frame_stride(g);
     const size_t sx = 4, sy = (size_t)g.nx * 4, sz = (size_t)g.nt * fs;
-    const T *pv = p + field_base(v, z, g);
+    const F *pv = p + field_base(v, z, g);
     const bool hx = x + 1 < g.nx, lx = x > 0, hy = y + 1 < g.ny, ly = y > 0;
     const bool hz = z + 1 < g.nz || g.zhi, lz = z > 0 || g.zlo;
     // frames in groups of FG: all their loads are issued before the sums
@@ -204,10 +230,10 @@ __device__ __forceinline__ void gradT_voxel(const T *__restrict__ p, size_t v, i
         for (int f = 0; f < FG; ++f) {
             const int l = l0 + f;
             if (l < g.nt) {
-                q[f] = ld4<T>(pv + l * fs);
-                nbx[f] = lx ? (pv - sx)[l * fs + 0] : T(0);
-                nby[f] = ly ? (pv - sy)[l * fs + 1] : T(0);
-                nbz[f] = lz ? (pv - sz)[l * fs + 2] : T(0);
+                q[f] = FieldIO<T, F>::ld(pv + l * fs);
+                nbx[f] = lx ? FieldIO<T, F>::ld1(pv - sx + l * fs + 0) : T(0);
+                nby[f] = ly ? FieldIO<T, F>::ld1(pv - sy + l * fs + 1) : T(0);
+                nbz[f] = lz ? FieldIO<T, F>::ld1(pv - sz + l * fs + 2) : T(0);
             }
         }
 #pragma unroll
@@ -231,9 +257,9 @@ __device__ __forceinline__ void gradT_voxel(const T *__restrict__ p, size_t v, i
 }
 
 // u = beta u + alpha D^T p
-template <typename T, typename S, int M>
+template <typename T, typename S, int M, typename F = T>
 __global__ void __launch_bounds__(kRedThreads)
-    gradT_kernel(const T *__restrict__ p, S *__restrict__ u_s, T *__restrict__ u_c, const T *PhiF, const T *dPhiF,
+    gradT_kernel(const F *__restrict__ p, S *__restrict__ u_s, T *__restrict__ u_c, const T *PhiF, const T *dPhiF,
                  Geo g, T lambda2, T alpha, T beta) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sm = reinterpret_cast<T *>(smem_raw);
@@ -243,7 +269,7 @@ __global__ void __launch_bounds__(kRedThreads)
         int x, y, z;
         vox_xyz(v, g, x, y, z);
         T o[M];
-        gradT_voxel<T, M>(p, v, x, y, z, g, sm, lambda2, o);
+        gradT_voxel<T, M, F>(p, v, x, y, z, g, sm, lambda2, o);
         if (u_c) {
             // compute-typed row: vector loads and stores
             T ov[M];
@@ -281,9 +307,9 @@ __host__ __device__ constexpr int tv_min_blocks(int M, int T_bytes) { return (T_
 // differences: three CTAs per SM (85 registers) instead of four
 __host__ __device__ constexpr int prox_min_blocks(int M, int T_bytes) { return (T_bytes == 4 && M <= 8) ? 3 : 1; }
 
-template <typename T, typename S, int M>
+template <typename T, typename S, int M, typename F = T>
 __global__ void __launch_bounds__(kRedThreads, prox_min_blocks(M, sizeof(T)))
-    prox_kernel(const S *__restrict__ u, T *__restrict__ mu, T *__restrict__ w, const T *PhiF, const T *dPhiF, Geo g,
+    prox_kernel(const S *__restrict__ u, F *__restrict__ mu, F *__restrict__ w, const T *PhiF, const T *dPhiF, Geo g,
                 T rho, T lambda1, T lambda2, double *partials, unsigned *counter, DevScalars *scal, double *obj,
                 int use_iter) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -306,7 +332,7 @@ __global__ void __launch_bounds__(kRedThreads, prox_min_blocks(M, sizeof(T)))
             typename V4<T>::type mg[FG];
 #pragma unroll
             for (int h = 0; h < FG; ++h)
-                if (l0 + h < g.nt) mg[h] = ld4<T>(mu + fb + (l0 + h) * fs);
+                if (l0 + h < g.nt) mg[h] = FieldIO<T, F>::ld(mu + fb + (l0 + h) * fs);
 #pragma unroll
             for (int h = 0; h < FG; ++h) {
                 const int l = l0 + h;
@@ -342,8 +368,8 @@ __global__ void __launch_bounds__(kRedThreads, prox_min_blocks(M, sizeof(T)))
                 typename V4<T>::type a, b;
                 a.x = mn[0]; a.y = mn[1]; a.z = mn[2]; a.w = mn[3];
                 b.x = wn[0]; b.y = wn[1]; b.z = wn[2]; b.w = wn[3];
-                st4<T>(mu + o, a);
-                st4<T>(w + o, b);
+                FieldIO<T, F>::st(mu + o, a);
+                FieldIO<T, F>::st(w + o, b);
             }
         }
     }
@@ -461,9 +487,9 @@ __global__ void __launch_bounds__(kRedThreads, tv_min_blocks(M, sizeof(T)))
 // ---------------------------------------------------------------------------
 // Chambolle-Pock (Fig. 2) step 4: h2 = project(h2 + sigma D ut, lambda1).
 // ---------------------------------------------------------------------------
-template <typename T, int M>
+template <typename T, int M, typename F = T>
 __global__ void __launch_bounds__(kRedThreads)
-    cp_dual_kernel(const T *__restrict__ ut, T *__restrict__ h2, const T *PhiF, const T *dPhiF, Geo g, T sigma,
+    cp_dual_kernel(const T *__restrict__ ut, F *__restrict__ h2, const T *PhiF, const T *dPhiF, Geo g, T sigma,
                    T lambda1, T lambda2) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sm = reinterpret_cast<T *>(smem_raw);
@@ -481,7 +507,7 @@ __global__ void __launch_bounds__(kRedThreads)
             grad_frame<T, M>(sm, l, ex, ey, ez, d[0], d[1], d[2]);
             d[3] = dt_frame<T, M>(dph + l * M, lambda2, uc);
             const size_t o = fb + l * fs;
-            typename V4<T>::type h = ld4<T>(h2 + o);
+            typename V4<T>::type h = FieldIO<T, F>::ld(h2 + o);
             h.x += sigma * d[0];
             h.y += sigma * d[1];
             h.z += sigma * d[2];
@@ -491,15 +517,15 @@ __global__ void __launch_bounds__(kRedThreads)
                 const T f = lambda1 / n;
                 h.x *= f; h.y *= f; h.z *= f; h.w *= f;
             }
-            st4<T>(h2 + o, h);
+            FieldIO<T, F>::st(h2 + o, h);
         }
     }
 }
 
 // Fig. 2 steps 5-6: u_new = u - tau (a + D^T h2); ut = u_new + theta (u_new - u).
-template <typename T, int M>
+template <typename T, int M, typename F = T>
 __global__ void __launch_bounds__(kRedThreads)
-    cp_primal_kernel(T *__restrict__ u, T *__restrict__ ut, const T *__restrict__ a, const T *__restrict__ h2,
+    cp_primal_kernel(T *__restrict__ u, T *__restrict__ ut, const T *__restrict__ a, const F *__restrict__ h2,
                      const T *PhiF, const T *dPhiF, Geo g, T tau, T theta, T lambda2) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sm = reinterpret_cast<T *>(smem_raw);
@@ -509,7 +535,7 @@ __global__ void __launch_bounds__(kRedThreads)
         int x, y, z;
         vox_xyz(v, g, x, y, z);
         T dt[M];
-        gradT_voxel<T, M>(h2, v, x, y, z, g, sm, lambda2, dt);
+        gradT_voxel<T, M, F>(h2, v, x, y, z, g, sm, lambda2, dt);
 #pragma unroll
         for (int j = 0; j < M; ++j) {
             if (j >= g.m) break;
@@ -677,6 +703,68 @@ struct TvCalc {
                                                                 P->d_partials + kSlotTv * kRedSlotStride,
                                                                 P->d_counters + kSlotTv, P->d_scal, obj);
             return tv_launched("tvsum_kernel");
+        })
+    }
+};
+
+// The solver's kernels on dual fields stored in bf16 (compute-typed float
+// coefficient vectors; FP32 arithmetic).
+struct TvFieldsBF16 {
+    static dr_status grad_adj(dr_plan *P, const void *p, void *u, double lambda2, double alpha, double beta,
+                              cudaStream_t st) {
+        typedef float T;
+        DR_TV_MT({
+            auto kern = gradT_kernel<T, T, M, bf16>;
+            const size_t smem = tab_smem<T, M>(P, false);
+            dr_status s = prep_smem(kern, smem);
+            if (s != DR_OK) return s;
+            kern<<<red_grid(nvox(P)), kRedThreads, smem, st>>>((const bf16 *)p, nullptr, (T *)u,
+                                                                (const T *)P->d_PhiF, (const T *)P->d_dPhiF, geo(P),
+                                                                (T)lambda2, (T)alpha, (T)beta);
+            return tv_launched("gradT_kernel (bf16 field)");
+        })
+    }
+    static dr_status prox(dr_plan *P, const void *u, void *mu, void *w, double rho, double lambda1, double lambda2,
+                          double *obj_row, cudaStream_t st) {
+        typedef float T;
+        DR_TV_MT({
+            auto kern = prox_kernel<T, T, M, bf16>;
+            const size_t smem = tab_smem<T, M>(P, false);
+            dr_status s = prep_smem(kern, smem);
+            if (s != DR_OK) return s;
+            kern<<<red_grid(nvox(P)), kRedThreads, smem, st>>>(
+                (const T *)u, (bf16 *)mu, (bf16 *)w, (const T *)P->d_PhiF, (const T *)P->d_dPhiF, geo(P), (T)rho,
+                (T)lambda1, (T)lambda2, P->d_partials + kSlotProx * kRedSlotStride, P->d_counters + kSlotProx,
+                P->d_scal, obj_row, obj_row ? 1 : 0);
+            return tv_launched("prox_kernel (bf16 fields)");
+        })
+    }
+    static dr_status cp_dual(dr_plan *P, const void *ut, void *h2, double sigma, double lambda1, double lambda2,
+                             cudaStream_t st) {
+        typedef float T;
+        DR_TV_MT({
+            auto kern = cp_dual_kernel<T, M, bf16>;
+            const size_t smem = tab_smem<T, M>(P, false);
+            dr_status s = prep_smem(kern, smem);
+            if (s != DR_OK) return s;
+            kern<<<red_grid(nvox(P)), kRedThreads, smem, st>>>((const T *)ut, (bf16 *)h2, (const T *)P->d_PhiF,
+                                                                (const T *)P->d_dPhiF, geo(P), (T)sigma,
+                                                                (T)lambda1, (T)lambda2);
+            return tv_launched("cp_dual_kernel (bf16 field)");
+        })
+    }
+    static dr_status cp_primal(dr_plan *P, void *u, void *ut, const void *a, const void *h2, double tau,
+                               double theta, double lambda2, cudaStream_t st) {
+        typedef float T;
+        DR_TV_MT({
+            auto kern = cp_primal_kernel<T, M, bf16>;
+            const size_t smem = tab_smem<T, M>(P, false);
+            dr_status s = prep_smem(kern, smem);
+            if (s != DR_OK) return s;
+            kern<<<red_grid(nvox(P)), kRedThreads, smem, st>>>((T *)u, (T *)ut, (const T *)a, (const bf16 *)h2,
+                                                                (const T *)P->d_PhiF, (const T *)P->d_dPhiF,
+                                                                geo(P), (T)tau, (T)theta, (T)lambda2);
+            return tv_launched("cp_primal_kernel (bf16 field)");
         })
     }
 };

@@ -23,6 +23,7 @@ DR_OK, DR_EINVAL, DR_ENOMEM, DR_ECUDA, DR_ETIMEOUT, DR_ENOTCONV, DR_ECANCELED = 
 FOURIER, LEGENDRE, HAAR, HEAVISIDE, COMPLEX_FOURIER = 0, 1, 2, 3, 4
 ORTHONORMAL = 0x100  # flag OR-ed into the basis kind
 F32, BF16, F64 = 0, 1, 2
+FIELDS_BF16 = 0x10  # flag OR-ed into F32 / BF16: the solvers keep their dual fields in bf16
 ADMM_CG, CHAMBOLLE_POCK = 0, 1
 
 _STATUS = {DR_EINVAL: "EINVAL", DR_ENOMEM: "ENOMEM", DR_ECUDA: "ECUDA", DR_ETIMEOUT: "ETIMEOUT",
@@ -202,12 +203,14 @@ class Plan:
         if th.shape != tt.shape or th.ndim != 1:
             raise ValueError("theta and t must be 1-D of equal length")
         self.K = th.size
-        self.basis, self.m, self.nt, self.prec = int(basis), int(m), int(nt), int(prec)
+        self.basis, self.m, self.nt = int(basis), int(m), int(nt)
+        self.prec = int(prec) & ~FIELDS_BF16
+        self.fields_bf16 = bool(int(prec) & FIELDS_BF16)
         self._h = ctypes.c_void_p()
         pd = ctypes.POINTER(ctypes.c_double)
         _check(lib.dr_plan_create(ctypes.byref(self._h), self.nx, self.ny, self.nz, self.ns, self.K,
                                   th.ctypes.data_as(pd), tt.ctypes.data_as(pd), self.basis, self.m,
-                                  self.nt, self.prec, ctypes.c_void_p(self._stream_handle(stream))))
+                                  self.nt, int(prec), ctypes.c_void_p(self._stream_handle(stream))))
 
     @staticmethod
     def _stream_handle(stream) -> int:
@@ -483,7 +486,7 @@ def job_desc(nx, ny, nz, ns, theta, t, basis, m, nt, prec, params: SolveParams, 
     d.theta, d.t = th.ctypes.data_as(pd), tt.ctypes.data_as(pd)
     d.basis, d.m, d.nt, d.prec = int(basis), int(m), int(nt), int(prec)
     d.params = params
-    dt = _DTYPES[int(prec)]
+    dt = _DTYPES[int(prec) & ~FIELDS_BF16]
     d.g = None if g is None else _ptr(g, dt, (nz, th.size, ns), "g").value
     d.u = None if u is None else _ptr(u, dt, (nz, ny, nx, m), "u").value
     d._keep = (th, tt, g, u)

@@ -222,3 +222,25 @@ def test_concurrent_plans_with_different_shared_memory_sizes():
     for th in threads:
         th.join()
     assert not errors, errors
+
+
+def test_server_job_with_bf16_fields_equals_its_solve_alone():
+    """A served job with DR_FIELDS_BF16 is budgeted with half-size dual fields
+    and returns the same result as admm_solve alone on a plan with the flag."""
+    spec = JOBS[1]
+    N, nz, K, ht, basis, m, nt, prec, iters = spec
+    theta, t, g = _job_inputs(1, spec)
+    flag = dr.F32 | dr.FIELDS_BF16
+    plan = dr.Plan(N, N, nz, N, theta, t, basis, m, nt, flag)
+    u_alone = torch.zeros(plan.u_shape(), dtype=torch.float32, device="cuda")
+    dr.admm_solve(plan, dev_tensor(g, dr.F32), u_alone, _params(spec))
+    gh = g.astype(np.float32)
+    uh = np.zeros((nz, N, N, m), dtype=np.float32)
+    d = dr.job_desc(N, N, nz, N, theta, t, basis, m, nt, flag, _params(spec), gh, uh)
+    d32 = dr.job_desc(N, N, nz, N, theta, t, basis, m, nt, dr.F32, _params(spec), gh, np.zeros_like(uh))
+    assert dr.job_device_bytes(d32) - dr.job_device_bytes(d) >= 2 * 2 * 4 * nt * N * N * nz
+    srv = dr.Server(device=0, budget_bytes=1 << 34, slots=1)
+    r = srv.wait(srv.submit(d), timeout_s=300.0)
+    srv.close()
+    assert r["rc"] == dr.DR_OK and r["state"] == dr.JOB_DONE
+    np.testing.assert_array_equal(uh.astype(np.float64), host_values(u_alone))

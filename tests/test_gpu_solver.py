@@ -249,3 +249,61 @@ def test_resume_without_state_is_rejected(disks):
     assert plan.state_bytes(dr.ADMM_CG) == 2 * 4 * w.nt * w.N * w.N * w.nz * 4
     assert plan.state_bytes(dr.CHAMBOLLE_POCK) == 4 * (4 * w.nt * w.N * w.N * w.nz + w.K * w.ns * w.nz
                                                        + w.m * w.N * w.N * w.nz)
+
+
+# --------------------------------------------------------------------------- #
+# Dual fields stored in bf16 (DR_FIELDS_BF16): same arithmetic, one rounding
+# of mu, w (h2) per store; the reconstruction error is that of the FP32 solve
+# (the duals hold lambda-sized values; their rounding moves u by ~1e-7 in the
+# FP64 model of the same iteration)
+# --------------------------------------------------------------------------- #
+@pytest.mark.parametrize("algo", [dr.ADMM_CG, dr.CHAMBOLLE_POCK])
+def test_bf16_fields_solve_matches_oracle(disks, disks_oracle_admm, algo):
+    w, theta, t, g, P = disks
+    g32 = g.astype(np.float32).astype(np.float64)
+    kw = dict(n_cg=w.n_cg, lambda1=w.lambda1, lambda2=w.lambda2, rho=w.rho)
+    if algo == dr.ADMM_CG:
+        uo, oo, _ = disks_oracle_admm["f32"]
+    else:
+        L = P.power_norm(w.lambda2)
+        uo, oo = P.chambolle_pock(g32, np.zeros((w.nz, w.N, w.N, w.m)), w.iters, w.lambda1, w.lambda2, 1.0, L)
+        kw["op_norm"] = L
+    outs = {}
+    for prec in (dr.F32, dr.F32 | dr.FIELDS_BF16):
+        plan = dr.Plan(w.N, w.N, w.nz, w.ns, theta, t, w.basis, w.m, w.nt, prec)
+        ud = torch.zeros(plan.u_shape(), dtype=torch.float32, device="cuda")
+        res = dr.admm_solve(plan, dev_tensor(g32, dr.F32), ud, dr.solve_params(algo, iters=w.iters, **kw))
+        outs[prec] = (host_values(ud), res["objective"], plan)
+    u, obj, plan = outs[dr.F32 | dr.FIELDS_BF16]
+    tol_u = F32_SOLVE_TOL_U if algo == dr.ADMM_CG else 3e-4
+    assert rel(u, uo) <= tol_u
+    assert np.max(np.abs(obj - oo) / np.abs(oo)) <= F32_SOLVE_TOL_OBJ
+    assert rel(u, outs[dr.F32][0]) <= tol_u
+    # the fields take half the bytes: ADMM two fields, Chambolle-Pock one
+    nf = 4 * w.nt * w.N * w.N * w.nz
+    assert outs[dr.F32][2].workspace_bytes(algo) - plan.workspace_bytes(algo) == (2 if algo == dr.ADMM_CG else 1) * 2 * nf
+
+
+def test_bf16_fields_checkpoint_resume_and_state_size(disks):
+    """The state buffer holds the bf16 fields as they are: 3 + 4 iterations
+    with the state handed over equal 7 in one call."""
+    w, theta, t, g, P = disks
+    plan = dr.Plan(w.N, w.N, w.nz, w.ns, theta, t, w.basis, w.m, w.nt, dr.F32 | dr.FIELDS_BF16)
+    assert plan.state_bytes(dr.ADMM_CG) == 2 * 4 * w.nt * w.N * w.N * w.nz * 2
+    gd = dev_tensor(g, dr.F32)
+    kw = dict(n_cg=w.n_cg, lambda1=w.lambda1, lambda2=w.lambda2, rho=w.rho)
+    u_all = torch.zeros(plan.u_shape(), dtype=torch.float32, device="cuda")
+    r_all = dr.admm_solve(plan, gd, u_all, dr.solve_params(dr.ADMM_CG, iters=7, **kw))
+    state = torch.empty(plan.state_bytes(dr.ADMM_CG), dtype=torch.uint8, device="cuda")
+    u = torch.zeros_like(u_all)
+    r1 = dr.admm_solve(plan, gd, u, dr.solve_params(dr.ADMM_CG, iters=3, state=state, **kw))
+    r2 = dr.admm_solve(plan, gd, u, dr.solve_params(dr.ADMM_CG, iters=4, state=state, resume=True, **kw))
+    plan.sync()
+    assert rel(host_values(u), host_values(u_all)) <= 1e-6
+    assert rel(np.concatenate([r1["objective"], r2["objective"]]), r_all["objective"]) <= 1e-6
+
+
+def test_bf16_fields_rejected_for_f64():
+    theta, t = synth.scan(16, 1.0)
+    with pytest.raises(dr.DynreconError):
+        dr.Plan(8, 8, 1, 8, theta, t, dr.FOURIER, 2, 2, dr.F64 | dr.FIELDS_BF16)
