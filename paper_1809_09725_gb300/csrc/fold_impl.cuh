@@ -185,7 +185,14 @@ __global__ void __launch_bounds__(THREADS, THREADS == kFoldThreads ? fold_fwd_mi
     // strip element: stored bf16 for bf16 storage, else the compute type
     constexpr bool BF16_STRIP = sizeof(S) == 2;
     using ST = std::conditional_t<BF16_STRIP, S, T>;
-    constexpr int MS = STATIC ? fold_static_ps(M, BF16_STRIP) : fold_strip_ps<S, T, M>();
+    // TMA (static transforms of float coefficient groups of 4 or 8, staging
+    // mode 3): strips staged by TMA into two buffers on mbarriers, in the TMA
+    // line layout, each 4-coefficient plane of a group a line layout of its
+    // own (16-byte entries: the even/odd halves stay conflict free); a
+    // separate instantiation, so the other kernels carry none of its code
+    constexpr bool TMA_CAP = TMA && STATIC && !BF16_STRIP && (M == 4 || M == 8);
+    constexpr int NP = TMA_CAP ? M / 4 : 1;  // 16-byte planes per pixel (TMA strips)
+    constexpr int MS = TMA_CAP ? 4 : (STATIC ? fold_static_ps(M, BF16_STRIP) : fold_strip_ps<S, T, M>());
     constexpr int RPT = STATIC ? RPTS : fold_rpt(M);
     constexpr int VW = 16 / (int)sizeof(S);  // elements per 16-byte vector
     extern __shared__ __align__(16) unsigned char fold_smem[];
@@ -201,13 +208,10 @@ __global__ void __launch_bounds__(THREADS, THREADS == kFoldThreads ? fold_fwd_mi
     const int branch = uproj[blk[0]].branch;
     const int W = branch ? ny : nx;
     const int H = branch ? nx : ny;
-    // TMA (static transforms of 4-float groups, staging mode 3): strips staged
-    // by TMA into two buffers on mbarriers, in the TMA line layout;
-    // a separate instantiation, so the other kernels carry none of its code
-    constexpr bool TMA_CAP = TMA && STATIC && !BF16_STRIP && M == 4 && MS == 4;
     constexpr bool tma = TMA_CAP;
     // line stride, zero entries before the even half, offset of the odd half
-    const int ls = tma ? fold_tma_line(W) : fold_line_elems(W);
+    // (TMA strips: a line is NP planes of fold_tma_line(W) entries each)
+    const int ls = tma ? NP * fold_tma_line(W) : fold_line_elems(W);
     const int kg = tma ? 8 : kFoldGuardE;
     const int ooff = tma ? fold_tma_half(W) + 8 : fold_odd_off(W);
     ST *strip = reinterpret_cast<ST *>(
@@ -226,11 +230,11 @@ __global__ void __launch_bounds__(THREADS, THREADS == kFoldThreads ? fold_fwd_mi
     if (tma) {
         // zero the guard entries only: TMA writes every data entry of a strip
         // (zero beyond the image), so no entry is written by both proxies
-        const int wh = fold_tma_half(W);
-        for (int i = tid; i < nbuf * R * 24; i += THREADS) {
-            const int line = i / 24, g = i - line * 24;
+        const int wh = fold_tma_half(W), lp = fold_tma_line(W);  // plane line: 24 guard entries
+        for (int i = tid; i < nbuf * R * NP * 24; i += THREADS) {
+            const int pl = i / 24, g = i - pl * 24;  // pl: (buffer, line, plane)
             const int e = g < 8 ? g : (g < 16 ? kg + wh + (g - 8) : kg + ooff + wh + (g - 16));
-            reinterpret_cast<float4 *>(strip)[(size_t)line * ls + e] = make_float4(0.f, 0.f, 0.f, 0.f);
+            reinterpret_cast<float4 *>(strip)[(size_t)pl * lp + e] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
     } else {
         for (int i = tid; i < nbuf * R * ls * MS; i += THREADS) strip[i] = ST(0.0f);
@@ -327,6 +331,7 @@ __global__ void __launch_bounds__(THREADS, THREADS == kFoldThreads ? fold_fwd_mi
     // ---- march the rays of lines [r0, r0 + nl) staged at cur: all m coefficient
     // sums per ray, line by line, the thread's RPT rays side by side
     // (independent chains); each ray still adds its lines in increasing order
+    const int pstride = tma ? fold_tma_line(W) : 0;  // entries between the planes of a TMA line
     auto march = [&](const ST *cur, int r0, int nl) {
 #pragma unroll 1
         for (int rl = 0; rl < nl; ++rl) {
@@ -350,6 +355,15 @@ __global__ void __launch_bounds__(THREADS, THREADS == kFoldThreads ? fold_fwd_mi
                     if constexpr (BF16_STRIP) {
                         load_vec_bf16<M, MS>(pe, t0);
                         load_vec_bf16<M, MS>(po, t1);
+                    } else if constexpr (NP > 1) {
+                        // 4 coefficients per plane; plane p of the line pstride entries on
+#pragma unroll
+                        for (int pl = 0; pl < NP; ++pl) {
+                            const float4 a = *reinterpret_cast<const float4 *>(pe + (size_t)pl * pstride * MS);
+                            const float4 c = *reinterpret_cast<const float4 *>(po + (size_t)pl * pstride * MS);
+                            t0[4 * pl] = a.x; t0[4 * pl + 1] = a.y; t0[4 * pl + 2] = a.z; t0[4 * pl + 3] = a.w;
+                            t1[4 * pl] = c.x; t1[4 * pl + 1] = c.y; t1[4 * pl + 2] = c.z; t1[4 * pl + 3] = c.w;
+                        }
                     } else {
                         load_vec<T, M>(pe, t0);
                         load_vec<T, M>(po, t1);
@@ -380,15 +394,17 @@ __global__ void __launch_bounds__(THREADS, THREADS == kFoldThreads ? fold_fwd_mi
         // strip sidx into buffer sidx % 2: copy c of its 2 * nbox * nl by thread c (mod THREADS)
         auto issue = [&](int sidx) {
             const int b = sidx % kFoldTmaStages, r0s = L0 + sidx * R, nls = min(R, L1 - r0s);
-            const int bw = fold_tma_bw(W), nbox = fold_tma_nbox(W);
-            if (tid == 0) mbar_arrive_expect_tx(&full[b], (unsigned)(nls * 2 * nbox * (bw / 2) * 16));
-            for (int c = tid; c < nls * 2 * nbox; c += THREADS) {
-                const int rl = c / (2 * nbox), rem = c - rl * 2 * nbox, half = rem / nbox, bx = rem - half * nbox;
+            const int bw = fold_tma_bw(W), nbox = fold_tma_nbox(W), per_line = NP * 2 * nbox;
+            if (tid == 0) mbar_arrive_expect_tx(&full[b], (unsigned)(nls * per_line * (bw / 2) * 16));
+            for (int c = tid; c < nls * per_line; c += THREADS) {
+                // copy c: line rl, plane pl (coefficients j0 + 4 pl ..), half, box bx
+                const int rl = c / per_line, rem = c - rl * per_line, pl = rem / (2 * nbox),
+                          rem2 = rem - pl * 2 * nbox, half = rem2 / nbox, bx = rem2 - half * nbox;
                 const uint32_t dst = smem_u32(strip + b * buf_elems) +
-                                     (uint32_t)(rl * ls + kg + half * ooff + bx * (bw / 2)) * 16u;
+                                     (uint32_t)(rl * ls + pl * pstride + kg + half * ooff + bx * (bw / 2)) * 16u;
                 const int line = r0s + rl, p0 = bx * bw + half;
-                if (branch == 0) tma_load_4d(dst, &tm_rows, j0, p0, line, z, &full[b]);
-                else tma_load_4d(dst, &tm_cols, j0, line, p0, z, &full[b]);
+                if (branch == 0) tma_load_4d(dst, &tm_rows, j0 + 4 * pl, p0, line, z, &full[b]);
+                else tma_load_4d(dst, &tm_cols, j0 + 4 * pl, line, p0, z, &full[b]);
             }
         };
         if (nstrips > 0) issue(0);
@@ -926,8 +942,9 @@ dr_status fold_static_launch(dr_plan *P, const void *u, cudaStream_t st, StaticO
     // async 3: TMA-staged strips (4-float groups of a float plan whose rows
     // of coefficients are whole 16-byte vectors); otherwise three cp.async buffers
     CUtensorMap tm_rows{}, tm_cols{};
+    constexpr int NPT = MC / 4;  // 16-byte planes per pixel of a TMA strip
     if (async == 3) {
-        bool ok = MC == 4 && !BF16_STRIP && (P->m % 4) == 0 && ((uintptr_t)u % 16) == 0;
+        bool ok = !BF16_STRIP && (P->m % 4) == 0 && ((uintptr_t)u % 16) == 0;
         if (ok) {
             const uint64_t dims[4] = {(uint64_t)P->m, (uint64_t)P->nx, (uint64_t)P->ny, (uint64_t)P->nz};
             const uint64_t strides[3] = {(uint64_t)P->m * 4, (uint64_t)P->nx * P->m * 4,
@@ -940,7 +957,7 @@ dr_status fold_static_launch(dr_plan *P, const void *u, cudaStream_t st, StaticO
                                    strides, box_c, es_c);
         }
         if (ok) {
-            const long long line = 16LL * std::max(fold_tma_line(P->nx), fold_tma_line(P->ny));
+            const long long line = 16LL * NPT * std::max(fold_tma_line(P->nx), fold_tma_line(P->ny));
             R = std::max(1, std::min(R, (int)((2LL * kFoldStripBudget) / (kFoldTmaStages * line))));
         } else {
             async = 2;
@@ -954,11 +971,11 @@ dr_status fold_static_launch(dr_plan *P, const void *u, cudaStream_t st, StaticO
         if (r3 >= 1) R = std::min(R, r3);
         else async = 1;
     }
-    const size_t smem = async == 3 ? 768 + 128 + 16 * (size_t)kFoldTmaStages * R *
+    const size_t smem = async == 3 ? 768 + 128 + 16 * (size_t)kFoldTmaStages * R * NPT *
                                                std::max(fold_tma_line(P->nx), fold_tma_line(P->ny))
                                    : 768 + sizeof(ST) * (size_t)(async + 1) * R * ls * MS;
     auto kern = fold_fwd_kernel<S, T, MC, true, THREADS, RPT, MINB>;
-    if constexpr (MC == 4 && !BF16_STRIP) {
+    if constexpr (!BF16_STRIP) {
         if (async == 3) kern = fold_fwd_kernel<S, T, MC, true, THREADS, RPT, MINB, true>;
     }
     {
@@ -1039,33 +1056,38 @@ dr_status fold_fwd2_launch_t(dr_plan *P, const void *u, void *out, const void *g
     return e == cudaSuccess ? DR_OK : cuda_fail(e, "fold_dist_kernel launch");
 }
 
+// gt: where the folded data live (nz U ns MS floats); nullptr: the plan's
+// scratch buffer.
 template <typename S, typename T, int M>
-dr_status fold_backproject(dr_plan *P, void *u, double alpha, double beta, bool u_calc, cudaStream_t st);
+dr_status fold_backproject(dr_plan *P, void *u, double alpha, double beta, bool u_calc, cudaStream_t st,
+                           void *gt = nullptr);
 
 template <typename S, typename T, int M>
 dr_status fold_adj_launch_t(dr_plan *P, const void *g, void *u, double alpha, double beta, bool u_calc,
-                            cudaStream_t st) {
+                            cudaStream_t st, void *gt = nullptr) {
     constexpr int MS = fold_ms(M);
-    // step 1: fold the data into the plan's scratch buffer
+    if (!gt) gt = P->d_gt;
+    // step 1: fold the data into the scratch buffer
     fold_data_kernel<S, T, M><<<red_grid((size_t)P->nz * P->fold_U * P->ns), kRedThreads, 0, st>>>(
-        (const S *)g, (T *)P->d_gt, P->d_fold_start, P->d_fold_member, (const T *)P->d_PhiP, P->nz, P->fold_U, P->ns,
+        (const S *)g, (T *)gt, P->d_fold_start, P->d_fold_member, (const T *)P->d_PhiP, P->nz, P->fold_U, P->ns,
         P->K, P->MP);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "fold_data_kernel launch");
-    return fold_backproject<S, T, M>(P, u, alpha, beta, u_calc, st);
+    return fold_backproject<S, T, M>(P, u, alpha, beta, u_calc, st, gt);
 }
 
-// Back-project the folded sinograms in the plan's scratch (step 2 of the
-// folded adjoint): u = alpha R*(folded) + beta u.
+// Back-project the folded sinograms (step 2 of the folded adjoint):
+// u = alpha R*(folded) + beta u.
 template <typename S, typename T, int M>
-dr_status fold_backproject(dr_plan *P, void *u, double alpha, double beta, bool u_calc, cudaStream_t st) {
+dr_status fold_backproject(dr_plan *P, void *u, double alpha, double beta, bool u_calc, cudaStream_t st, void *gt) {
     constexpr int MS = fold_ms(M);
+    if (!gt) gt = P->d_gt;
     const int Wb = fold_adj_wb(M);
     CUtensorMap tm{};
     const uint64_t dims[3] = {(uint64_t)MS, (uint64_t)P->ns, (uint64_t)P->nz * P->fold_U};
     const uint64_t strides[2] = {(uint64_t)MS * sizeof(T), (uint64_t)P->ns * MS * sizeof(T)};
     const uint32_t box[3] = {(uint32_t)MS, (uint32_t)Wb, 1};
-    if (!encode_tensor_map(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, P->d_gt, dims, strides, box))
+    if (!encode_tensor_map(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, gt, dims, strides, box))
         return fail(DR_ECUDA, "fold adj: tensor map encode failed");
     // angles per pipeline stage: fewer shrink the windows' shared memory so that
     // more CTAs fit on an SM (the angles are summed in the same order)

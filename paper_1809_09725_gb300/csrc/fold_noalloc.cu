@@ -84,38 +84,11 @@ static dr_status noalloc_scratch(int device, float **out) {
     return DR_OK;
 }
 
+// The plan's folded adjoint (data fold, then back-projection) with the folded
+// data in the fixed array instead of the plan's scratch buffer.
 template <typename S, int M>
 static dr_status noalloc_adj_t(dr_plan *P, const void *g, void *u, double beta, float *scratch, cudaStream_t st) {
-    typedef float T;
-    constexpr int MS = fold_ms(M);
-    fold_data_kernel<S, T, M><<<red_grid((size_t)P->nz * P->fold_U * P->ns), kRedThreads, 0, st>>>(
-        (const S *)g, scratch, P->d_fold_start, P->d_fold_member, (const T *)P->d_PhiP, P->nz, P->fold_U, P->ns, P->K,
-        P->MP);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "dyn_radon_adj_noalloc: fold_data_kernel launch");
-    const int Wb = fold_adj_wb(M);
-    CUtensorMap tm{};
-    const uint64_t dims[3] = {(uint64_t)MS, (uint64_t)P->ns, (uint64_t)P->nz * P->fold_U};
-    const uint64_t strides[2] = {(uint64_t)MS * sizeof(T), (uint64_t)P->ns * MS * sizeof(T)};
-    const uint32_t box[3] = {(uint32_t)MS, (uint32_t)Wb, 1};
-    if (!encode_tensor_map(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, scratch, dims, strides, box))
-        return fail(DR_ECUDA, "dyn_radon_adj_noalloc: tensor map encode failed");
-    const int pp = std::max(1, std::min(32, P->fold_adj_pp));
-    const size_t row_bytes = ((size_t)Wb * MS * sizeof(T) + 127) & ~(size_t)127;
-    const size_t stage = pp * row_bytes + 128 * ((pp * sizeof(FoldPrm) + 127) / 128);
-    const size_t smem = stage * kFoldAdjStages + 128;
-    auto kern = fold_adj_kernel<S, T, M>;
-    {
-        dr_status s = allow_dynamic_smem((const void *)kern, smem);
-        if (s != DR_OK) return s;
-    }
-    constexpr int TX = FoldAdjShape<M>::TX;
-    const int ntx = (P->nx + TX - 1) / TX, nty = (P->ny + kAdjTY - 1) / kAdjTY;
-    dim3 grid(ntx * nty, P->nz);
-    kern<<<grid, kAdjThreads, smem, st>>>(tm, P->d_fold_adj, (S *)u, nullptr, P->nx, P->ny, P->fold_U, P->m, Wb,
-                                          1.0f, (float)beta, P->d_status, pp);
-    e = cudaGetLastError();
-    return e == cudaSuccess ? DR_OK : cuda_fail(e, "dyn_radon_adj_noalloc: fold_adj_kernel launch");
+    return fold_adj_launch_t<S, float, M>(P, g, u, 1.0, beta, false, st, scratch);
 }
 
 template <typename S>

@@ -404,20 +404,21 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
             }
             P->fold2_async = basync;
         }
-        // TMA-staged strips, two buffers on mbarriers (4-float coefficient
+        // TMA-staged strips, two buffers on mbarriers (float coefficient
         // groups of whole 16-byte rows): the copies leave the threads'
         // instruction stream; two buffers share twice the strip budget
-        // (every 4-coefficient CTA shape: the copies free registers and issue
-        // slots, which can move the best shape), at the tallest strips two
-        // buffers hold and at half that
+        // (every CTA shape: the copies free registers and issue slots, which
+        // can move the best shape), at the tallest strips two buffers hold
+        // and at half that
         if (P->m % 4 == 0) {
             const int keep_gi = P->fold2_gi, keep_async = P->fold2_async;
             bool won = false;
             for (int gi = 0; gi < kFold2Configs; ++gi) {
-                if (fold_static_mc(gi) != 4 || !gi_ok(gi)) continue;
+                if (!gi_ok(gi)) continue;
                 P->fold2_gi = gi;
                 P->fold2_async = 3;
-                const long long line = 16LL * std::max(fold_tma_line(P->nx), fold_tma_line(P->ny));
+                const long long line = 16LL * (fold_static_mc(gi) / 4) *
+                                       std::max(fold_tma_line(P->nx), fold_tma_line(P->ny));
                 const int rt = std::max(1, std::min({16, P->fold2_R[gi],
                                                      (int)((2LL * kFoldStripBudget) / (kFoldTmaStages * line))}));
                 for (int c : {rt, std::max(1, rt / 2)}) {
