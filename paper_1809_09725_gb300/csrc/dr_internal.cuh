@@ -212,6 +212,7 @@ struct dr_plan {
     // angle blocks: variant v spreads each stepping axis's angles evenly over v more
     // blocks than the fewest that fit a CTA (smaller blocks, more CTAs: fuller last wave)
     int fold2_nchunk[dr::kFold2Configs] = {}, fold2_R[dr::kFold2Configs] = {};
+    int fold2_Rt[dr::kFold2Configs] = {};  // strip lines of TMA staging (two buffers in twice the budget; 0: none)
     int fold2_P[dr::kFold2Configs][dr::kFold2BlockVariants] = {};
     int fold2_nblocks[dr::kFold2Configs][dr::kFold2BlockVariants] = {};
     int *d_fold2_blocks[dr::kFold2Configs][dr::kFold2BlockVariants] = {};

@@ -931,7 +931,10 @@ dr_status fold_static_launch(dr_plan *P, const void *u, cudaStream_t st, StaticO
     const int ngroups = (P->m + MC - 1) / MC;
     const int ls = fold_line_elems_max(P->nx, P->ny);
     const bool bf16_kernel = sizeof(S) == 2;
-    const int R0 = std::max(1, std::min(bf16_kernel ? P->fold2_lines_st : P->fold2_lines, P->fold2_R[gi]));
+    const int async_req = bf16_kernel ? P->fold2_async_st : P->fold2_async;
+    const int R0 = std::max(1, std::min(bf16_kernel ? P->fold2_lines_st : P->fold2_lines,
+                                        async_req == 3 && !bf16_kernel && P->fold2_Rt[gi] > 0 ? P->fold2_Rt[gi]
+                                                                                              : P->fold2_R[gi]));
     if ((size_t)P->nz * ngroups > 65535) return fail(DR_EINVAL, "two-kernel folded forward: too many slice groups");
     // async 1: two strip buffers, the next strip copied with cp.async while the
     // current one is marched (groups of whole 16-byte vectors; other pixels

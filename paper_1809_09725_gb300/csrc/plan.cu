@@ -470,6 +470,11 @@ static dr_status build_tables(dr_plan *P) {
             const int ps2 = MC == 4 ? 4 : 12;  // float strip stride of the group
             const size_t line2 = sizeof(float) * (size_t)fold_line_elems_max(P->nx, P->ny) * ps2;
             P->fold2_R[gi] = std::min(16, (int)(kFoldStripBudget / line2));
+            // TMA strips (float data, m a multiple of 4): MC / 4 planes of 16-byte entries per pixel
+            const size_t line_t = 16 * (size_t)(MC / 4) * std::max(fold_tma_line(P->nx), fold_tma_line(P->ny));
+            P->fold2_Rt[gi] = (P->prec != DR_F64 && P->m % 4 == 0)
+                                  ? std::min(16, (int)((2 * (size_t)kFoldStripBudget) / (kFoldTmaStages * line_t)))
+                                  : 0;
             P->fold2_nchunk[gi] = nch2;
             const int nmax = (int)std::max(ub0.size(), ub1.size());
             for (int v = 0; v < kFold2BlockVariants; ++v) {

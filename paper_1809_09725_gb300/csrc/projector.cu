@@ -417,10 +417,7 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
                 if (!gi_ok(gi)) continue;
                 P->fold2_gi = gi;
                 P->fold2_async = 3;
-                const long long line = 16LL * (fold_static_mc(gi) / 4) *
-                                       std::max(fold_tma_line(P->nx), fold_tma_line(P->ny));
-                const int rt = std::max(1, std::min({16, P->fold2_R[gi],
-                                                     (int)((2LL * kFoldStripBudget) / (kFoldTmaStages * line))}));
+                const int rt = std::max(1, P->fold2_Rt[gi]);
                 for (int c : {rt, std::max(1, rt / 2)}) {
                     double t = 1e30;
                     dr_status s = run2(true)(c, t);
@@ -505,7 +502,8 @@ dr_status autotune(dr_plan *P, void *u_scratch, void *g_scratch) {
             double best_t = 1e30;
             int best_c = bl;
             for (int i : {bi - 1, bi, bi + 1}) {
-                if (i < 0 || i > 7 || all[i] > P->fold2_R[bgi]) continue;
+                const int cap = P->fold2_async == 3 ? P->fold2_Rt[bgi] : P->fold2_R[bgi];
+                if (i < 0 || i > 7 || all[i] > cap) continue;
                 double t = 1e30;
                 dr_status s = run2(true, 6)(all[i], t);
                 if (s != DR_OK) return s;
@@ -718,7 +716,7 @@ dr_status dr_plan_set_fold_groups(dr_plan *P, int group, int threads, int rays_p
             (rays_per_thread == 0 ? (gi < 0 || fold_static_rpt_gi(c) > fold_static_rpt_gi(gi))
                                   : fold_static_rpt_gi(c) == rays_per_thread))
             gi = c;
-    if (gi < 0 || (group == 8 && P->m <= 4) || lines < 1 || lines > P->fold2_R[gi] ||
+    if (gi < 0 || (group == 8 && P->m <= 4) || lines < 1 || lines > std::max(P->fold2_R[gi], P->fold2_Rt[gi]) ||
         (size_t)P->nz * ((P->m + group - 1) / group) > 65535)
         return fail(DR_EINVAL, "dr_plan_set_fold_groups: no such configuration (group 4 or 8, 8 only for m > 4; "
                                "threads 256, 512 or 1024 with their rays per thread) or lines outside the strip "
