@@ -255,6 +255,8 @@ static dr_status build_tables(dr_plan *P) {
             G[(size_t)i * MT + j] = g;
             Lt[(size_t)i * MT + j] = lt;
         }
+    P->h_G = G;
+    P->h_Lt = Lt;
     dr_status st;
     if (dbl) {
         if ((st = upload<double>(&P->d_PhiP, phip, bytes)) != DR_OK) return st;

@@ -16,6 +16,9 @@
 // all nt frames), neighbours come through L1/L2.
 #include <algorithm>
 #include <cmath>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #pragma once
 #include "dr_device.cuh"
@@ -83,17 +86,39 @@ struct FieldIO<float, bf16> {
 
 // zlo / zhi: the slice below local z = 0 / above local z = nz-1 exists in
 // memory (a halo of a slab of a larger volume), so the z differences there
-// are interior ones instead of the Neumann boundary.
+// are interior ones instead of the Neumann boundary.  band: rows of y per
+// band of the traversal order (band_voxel).
 struct Geo {
     int nx, ny, nz, m, nt;
     int zlo, zhi;
+    int band;
 };
 
-__device__ __forceinline__ void vox_xyz(size_t v, const Geo &g, int &x, int &y, int &z) {
-    x = (int)(v % g.nx);
-    const size_t r = v / g.nx;
-    y = (int)(r % g.ny);
-    z = (int)(r / g.ny);
+// Traversal order of the stencil kernels.  The volume is cut into bands of
+// g.band rows of y; a band is walked slice by slice (its rows at one z, then
+// the same rows at z+1), and the bands follow one another.  Step w of the walk
+// is voxel v = (z ny + y) nx + x.  Consecutive steps are consecutive x (a
+// warp's loads stay coalesced), and the z neighbours of a voxel are visited
+// g.band rows before and after it, so they are still in L2 when a stencil
+// reads them; walking the whole slice before the next one (g.band = ny) puts a
+// full slice between them, more than L2 holds on large volumes.
+__device__ __forceinline__ size_t band_voxel(size_t w, const Geo &g, int &x, int &y, int &z) {
+    x = (int)(w % g.nx);
+    const size_t r = w / g.nx;  // row of the walk
+    const size_t full = (size_t)(g.ny / g.band) * g.band;  // rows of y in full bands
+    const size_t rf = full * g.nz;                          // walk rows inside full bands
+    if (r < rf) {
+        const size_t per = (size_t)g.band * g.nz;
+        const size_t b = r / per, q = r % per;
+        z = (int)(q / g.band);
+        y = (int)(b * g.band + q % g.band);
+    } else {
+        const int h = g.ny - (int)full;  // rows of the last, partial band
+        const size_t q = r - rf;
+        z = (int)(q / h);
+        y = (int)(full + q % h);
+    }
+    return ((size_t)z * g.ny + y) * g.nx + x;
 }
 
 // 4-vector fields on frames (D u, the duals) are stored frame-major within
@@ -188,9 +213,9 @@ __global__ void __launch_bounds__(kRedThreads)
     load_tables<T, M>(sm, PhiF, dPhiF, nullptr, nullptr, g.nt, false);
     const T *dph = sm + g.nt * M;
     const size_t nv = (size_t)g.nx * g.ny * g.nz;
-    for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < nv; v += (size_t)gridDim.x * blockDim.x) {
+    for (size_t it = blockIdx.x * (size_t)blockDim.x + threadIdx.x; it < nv; it += (size_t)gridDim.x * blockDim.x) {
         int x, y, z;
-        vox_xyz(v, g, x, y, z);
+        const size_t v = band_voxel(it, g, x, y, z);
         T uc[M], ex[M], ey[M], ez[M];
         coeff_diffs<T, S, M>(u, v, x, y, z, g, uc, ex, ey, ez);
         const size_t fb = field_base(v, z, g), fs = frame_stride(g);
@@ -257,17 +282,23 @@ __device__ __forceinline__ void gradT_voxel(const F *__restrict__ p, size_t v, i
 }
 
 // u = beta u + alpha D^T p
+// Resident CTAs per SM asked of the FP32 instantiations: four at m <= 8
+// (64 registers), three at m = 16 (85), two at m = 32.
+__host__ __device__ constexpr int gradT_min_blocks(int M, int T_bytes) {
+    return T_bytes == 4 ? (M <= 8 ? 4 : (M == 16 ? 3 : 2)) : 1;
+}
+
 template <typename T, typename S, int M, typename F = T>
-__global__ void __launch_bounds__(kRedThreads)
+__global__ void __launch_bounds__(kRedThreads, gradT_min_blocks(M, sizeof(T)))
     gradT_kernel(const F *__restrict__ p, S *__restrict__ u_s, T *__restrict__ u_c, const T *PhiF, const T *dPhiF,
                  Geo g, T lambda2, T alpha, T beta) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sm = reinterpret_cast<T *>(smem_raw);
     load_tables<T, M>(sm, PhiF, dPhiF, nullptr, nullptr, g.nt, false);
     const size_t nv = (size_t)g.nx * g.ny * g.nz;
-    for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < nv; v += (size_t)gridDim.x * blockDim.x) {
+    for (size_t it = blockIdx.x * (size_t)blockDim.x + threadIdx.x; it < nv; it += (size_t)gridDim.x * blockDim.x) {
         int x, y, z;
-        vox_xyz(v, g, x, y, z);
+        const size_t v = band_voxel(it, g, x, y, z);
         T o[M];
         gradT_voxel<T, M, F>(p, v, x, y, z, g, sm, lambda2, o);
         if (u_c) {
@@ -304,8 +335,12 @@ __global__ void __launch_bounds__(kRedThreads)
 __host__ __device__ constexpr int tv_min_blocks(int M, int T_bytes) { return (T_bytes == 4 && M <= 8) ? 4 : 1; }
 
 // prox keeps a group of frames' duals in registers besides the coefficient
-// differences: three CTAs per SM (85 registers) instead of four
-__host__ __device__ constexpr int prox_min_blocks(int M, int T_bytes) { return (T_bytes == 4 && M <= 8) ? 3 : 1; }
+// differences: three CTAs per SM (85 registers) at m <= 8, two (128) at
+// m = 16, where the group is four frames (64 bytes of loads in flight per
+// thread)
+__host__ __device__ constexpr int prox_min_blocks(int M, int T_bytes) {
+    return T_bytes == 4 ? (M <= 8 ? 3 : (M == 16 ? 2 : 1)) : 1;
+}
 
 template <typename T, typename S, int M, typename F = T>
 __global__ void __launch_bounds__(kRedThreads, prox_min_blocks(M, sizeof(T)))
@@ -319,14 +354,14 @@ __global__ void __launch_bounds__(kRedThreads, prox_min_blocks(M, sizeof(T)))
     const T kappa = lambda1 / rho, irho = T(1) / rho;
     PartialSum<T> acc_tv, acc_pr;
     const size_t nv = (size_t)g.nx * g.ny * g.nz;
-    for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < nv; v += (size_t)gridDim.x * blockDim.x) {
+    for (size_t it = blockIdx.x * (size_t)blockDim.x + threadIdx.x; it < nv; it += (size_t)gridDim.x * blockDim.x) {
         int x, y, z;
-        vox_xyz(v, g, x, y, z);
+        const size_t v = band_voxel(it, g, x, y, z);
         T uc[M], ex[M], ey[M], ez[M];
         coeff_diffs<T, S, M>(u, v, x, y, z, g, uc, ex, ey, ez);
         // frames in groups of FG: the group's dual loads are issued first (more
         // bytes in flight per thread); the frames are then processed in order
-        constexpr int FG = 2;
+        constexpr int FG = (M == 16 && sizeof(T) == 4) ? 4 : 2;
         const size_t fb = field_base(v, z, g), fs = frame_stride(g);
         for (int l0 = 0; l0 < g.nt; l0 += FG) {
             typename V4<T>::type mg[FG];
@@ -393,35 +428,95 @@ __global__ void __launch_bounds__(kRedThreads, prox_min_blocks(M, sizeof(T)))
 // <r,r> = 0).  mode 2 (ADMM right-hand side): also copy out into pdir and
 // reduce <out, out> into scal->rr, marking the CG active.
 // ---------------------------------------------------------------------------
+// D^T D's two m x m tables as kernel parameters (FP32, m <= 16): they sit in
+// the constant bank, and each multiply-add of the unrolled sums takes its
+// table entry from there directly, with no shared-memory load per term.
+// Other instantiations read shared-memory copies.
 template <typename T, int M>
-__global__ void __launch_bounds__(kRedThreads, tv_min_blocks(M, sizeof(T)))
+struct LapTab {
+    static constexpr bool kParam = sizeof(T) == 4 && M <= 16;
+    T G[kParam ? M * M : 1];
+    T L[kParam ? M * M : 1];  // lambda2^2 Lt
+};
+
+// Resident CTAs per SM asked of the FP32 instantiations: four at m <= 8, two
+// (128 registers) at m = 16.
+__host__ __device__ constexpr int lap_min_blocks(int M, int T_bytes) {
+    return T_bytes == 4 ? (M <= 8 ? 4 : (M == 16 ? 2 : 1)) : 1;
+}
+
+template <typename T, int M>
+__global__ void __launch_bounds__(kRedThreads, lap_min_blocks(M, sizeof(T)))
     lap_kernel(const T *__restrict__ xv, T *__restrict__ out, T *__restrict__ pdir, const T *PhiF,
-               const T *dPhiF, const T *G, const T *Lt, Geo g, T alpha, T beta, T lam2sq, double *partials,
-               unsigned *counter, DevScalars *scal, int mode) {
+               const T *dPhiF, const T *G, const T *Lt, const __grid_constant__ LapTab<T, M> tab, Geo g, T alpha,
+               T beta, T lam2sq, double *partials, unsigned *counter, DevScalars *scal, int mode) {
+    constexpr bool CT = LapTab<T, M>::kParam;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sm = reinterpret_cast<T *>(smem_raw);
-    load_tables<T, M>(sm, PhiF, dPhiF, G, Lt, g.nt, true);
     const T *Gs = sm + 2 * g.nt * M;
-    const T *Ls = Gs + M * M;
+    T *Ls = sm + 2 * g.nt * M + M * M;
+    if constexpr (!CT) {
+        load_tables<T, M>(sm, PhiF, dPhiF, G, Lt, g.nt, true);
+        // this block's copy of Lt scaled by lambda2^2 once
+        for (int i = threadIdx.x; i < M * M; i += blockDim.x) Ls[i] = lam2sq * Ls[i];
+        __syncthreads();
+    }
     PartialSum<T> acc;
     const size_t nv = (size_t)g.nx * g.ny * g.nz;
     const size_t sy = g.nx, sz = (size_t)g.nx * g.ny;
-    for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < nv; v += (size_t)gridDim.x * blockDim.x) {
-        int x, y, z;
-        vox_xyz(v, g, x, y, z);
+    // The warps step through the walk together (a lane past the end takes
+    // part in the shuffles only): the x neighbours of a voxel are the voxels
+    // of the lanes beside it whenever they exist (consecutive steps of the
+    // walk are consecutive x of one row), so only the warp's edge lanes read
+    // them from memory.
+    const int lane = threadIdx.x & 31;
+    for (size_t w0 = blockIdx.x * (size_t)blockDim.x + (threadIdx.x & ~31u); w0 < nv;
+         w0 += (size_t)gridDim.x * blockDim.x) {
+        const size_t it = w0 + lane;
+        const bool live = it < nv;
+        int x = 0, y = 0, z = 0;
+        const size_t v = live ? band_voxel(it, g, x, y, z) : 0;
         T xc[M], ls[M], nb[M];
-        load_coeffs<T, T, M>(xv + v * g.m, g.m, xc);
+        if (live) {
+            load_coeffs<T, T, M>(xv + v * g.m, g.m, xc);
+        } else {
+#pragma unroll
+            for (int j = 0; j < M; ++j) xc[j] = T(0);
+        }
 #pragma unroll
         for (int j = 0; j < M; ++j) ls[j] = T(0);
-        const bool has[6] = {x > 0, x + 1 < g.nx, y > 0, y + 1 < g.ny, z > 0 || g.zlo != 0, z + 1 < g.nz || g.zhi != 0};
-        const long long off[6] = {-1, 1, -(long long)sy, (long long)sy, -(long long)sz, (long long)sz};
-#pragma unroll
-        for (int e = 0; e < 6; ++e) {
-            if (!has[e]) continue;
-            load_coeffs<T, T, M>(xv + (size_t)((long long)v + off[e]) * g.m, g.m, nb);
+        // the six neighbours in the order -x, +x, -y, +y, -z, +z (Neumann: a
+        // missing neighbour adds nothing)
+        const T *pc = xv + v * g.m;
+        auto acc_nb = [&](bool has) {
+            if (!has) return;
 #pragma unroll
             for (int j = 0; j < M; ++j) ls[j] += xc[j] - nb[j];
+        };
+        auto add_nb = [&](bool has, long long off) {
+            if (!has) return;
+            load_coeffs<T, T, M>(pc + off, g.m, nb);
+            acc_nb(true);
+        };
+        if constexpr (M >= 16) {
+#pragma unroll
+            for (int j = 0; j < M; ++j) nb[j] = __shfl_up_sync(0xffffffffu, xc[j], 1);
+            if (lane == 0 && live && x > 0) load_coeffs<T, T, M>(pc - g.m, g.m, nb);
+            acc_nb(live && x > 0);
+#pragma unroll
+            for (int j = 0; j < M; ++j) nb[j] = __shfl_down_sync(0xffffffffu, xc[j], 1);
+            if (lane == 31 && live && x + 1 < g.nx) load_coeffs<T, T, M>(pc + g.m, g.m, nb);
+            acc_nb(live && x + 1 < g.nx);
+        } else {
+            add_nb(live && x > 0, -(long long)g.m);
+            add_nb(live && x + 1 < g.nx, g.m);
         }
+        const long long oy = (long long)sy * g.m, oz = (long long)sz * g.m;
+        add_nb(live && y > 0, -oy);
+        add_nb(live && y + 1 < g.ny, oy);
+        add_nb(live && (z > 0 || g.zlo != 0), -oz);
+        add_nb(live && (z + 1 < g.nz || g.zhi != 0), oz);
+        if (!live) continue;
         T dotv = T(0);  // this voxel's m products in the compute type (sums in a PartialSum)
         if constexpr (M <= 16) {
             // the row in registers: vector loads and stores of out (and pdir)
@@ -429,8 +524,13 @@ __global__ void __launch_bounds__(kRedThreads, tv_min_blocks(M, sizeof(T)))
 #pragma unroll
             for (int i = 0; i < M; ++i) {
                 T s = T(0);
+                if constexpr (CT) {
 #pragma unroll
-                for (int j = 0; j < M; ++j) s = fma(Gs[i * M + j], ls[j], fma(lam2sq * Ls[i * M + j], xc[j], s));
+                    for (int j = 0; j < M; ++j) s = fma(tab.G[i * M + j], ls[j], fma(tab.L[i * M + j], xc[j], s));
+                } else {
+#pragma unroll
+                    for (int j = 0; j < M; ++j) s = fma(Gs[i * M + j], ls[j], fma(Ls[i * M + j], xc[j], s));
+                }
                 rv[i] = alpha * s;
             }
             if (beta != T(0)) {
@@ -449,7 +549,7 @@ __global__ void __launch_bounds__(kRedThreads, tv_min_blocks(M, sizeof(T)))
                 if (i >= g.m) break;
                 T s = T(0);
 #pragma unroll
-                for (int j = 0; j < M; ++j) s = fma(Gs[i * M + j], ls[j], fma(lam2sq * Ls[i * M + j], xc[j], s));
+                for (int j = 0; j < M; ++j) s = fma(Gs[i * M + j], ls[j], fma(Ls[i * M + j], xc[j], s));
                 const size_t idx = v * g.m + i;
                 T r = alpha * s;
                 if (beta != T(0)) r += beta * out[idx];
@@ -496,9 +596,9 @@ __global__ void __launch_bounds__(kRedThreads)
     load_tables<T, M>(sm, PhiF, dPhiF, nullptr, nullptr, g.nt, false);
     const T *dph = sm + g.nt * M;
     const size_t nv = (size_t)g.nx * g.ny * g.nz;
-    for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < nv; v += (size_t)gridDim.x * blockDim.x) {
+    for (size_t it = blockIdx.x * (size_t)blockDim.x + threadIdx.x; it < nv; it += (size_t)gridDim.x * blockDim.x) {
         int x, y, z;
-        vox_xyz(v, g, x, y, z);
+        const size_t v = band_voxel(it, g, x, y, z);
         T uc[M], ex[M], ey[M], ez[M];
         coeff_diffs<T, T, M>(ut, v, x, y, z, g, uc, ex, ey, ez);
         const size_t fb = field_base(v, z, g), fs = frame_stride(g);
@@ -531,9 +631,9 @@ __global__ void __launch_bounds__(kRedThreads)
     T *sm = reinterpret_cast<T *>(smem_raw);
     load_tables<T, M>(sm, PhiF, dPhiF, nullptr, nullptr, g.nt, false);
     const size_t nv = (size_t)g.nx * g.ny * g.nz;
-    for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < nv; v += (size_t)gridDim.x * blockDim.x) {
+    for (size_t it = blockIdx.x * (size_t)blockDim.x + threadIdx.x; it < nv; it += (size_t)gridDim.x * blockDim.x) {
         int x, y, z;
-        vox_xyz(v, g, x, y, z);
+        const size_t v = band_voxel(it, g, x, y, z);
         T dt[M];
         gradT_voxel<T, M, F>(h2, v, x, y, z, g, sm, lambda2, dt);
 #pragma unroll
@@ -559,9 +659,9 @@ __global__ void __launch_bounds__(kRedThreads)
     const T *dph = sm + g.nt * M;
     PartialSum<T> acc;
     const size_t nv = (size_t)g.nx * g.ny * g.nz;
-    for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < nv; v += (size_t)gridDim.x * blockDim.x) {
+    for (size_t it = blockIdx.x * (size_t)blockDim.x + threadIdx.x; it < nv; it += (size_t)gridDim.x * blockDim.x) {
         int x, y, z;
-        vox_xyz(v, g, x, y, z);
+        const size_t v = band_voxel(it, g, x, y, z);
         T uc[M], ex[M], ey[M], ez[M];
         coeff_diffs<T, T, M>(u, v, x, y, z, g, uc, ex, ey, ez);
         for (int l = 0; l < g.nt; ++l) {
@@ -578,7 +678,16 @@ __global__ void __launch_bounds__(kRedThreads)
 // ===========================================================================
 // Launchers (instantiated per precision in tv_ops_*.cu and tv_calc_*.cu)
 // ===========================================================================
-inline Geo geo(const dr_plan *P) { return Geo{P->nx, P->ny, P->nz, P->m, P->nt, P->z_open_lo, P->z_open_hi}; }
+// Rows per band of the traversal: one band at one slice holds about
+// kBandBytes of u and the dual fields, so the z neighbours (a band apart in
+// the walk) stay in L2.  Volumes whose whole slice fits walk slice by slice.
+constexpr size_t kBandBytes = 8u << 20;
+inline Geo geo(const dr_plan *P) {
+    const size_t bpv = (size_t)(4 * P->nt + P->m) * (P->prec == DR_F64 ? 8 : 4);
+    const size_t row = std::max<size_t>(1, bpv * (size_t)P->nx);
+    const int band = (int)std::max<size_t>(1, std::min<size_t>((size_t)P->ny, kBandBytes / row));
+    return Geo{P->nx, P->ny, P->nz, P->m, P->nt, P->z_open_lo, P->z_open_hi, band};
+}
 
 template <typename T, int M>
 inline size_t tab_smem(const dr_plan *P, bool gl) {
@@ -588,6 +697,37 @@ inline size_t tab_smem(const dr_plan *P, bool gl) {
 template <typename K>
 inline dr_status prep_smem(K kern, size_t smem) {
     return allow_dynamic_smem((const void *)kern, smem);
+}
+
+// Blocks of a grid-stride TV launch: as many as the device holds at once, so
+// that every block is resident from the start and the walk advances as one
+// front (a larger grid leaves the later blocks a second sweep over the
+// volume, whose neighbours have long left L2); at most red_grid(n).
+// Resident blocks per SM are cached per kernel, dynamic shared memory and
+// device.
+inline int tv_grid(const void *kern, size_t smem, size_t n) {
+    static std::mutex mu;
+    static std::map<std::tuple<const void *, size_t, int>, int> cache;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return red_grid(n);
+    int per_dev = 0;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cache.find(std::make_tuple(kern, smem, dev));
+        if (it != cache.end()) per_dev = it->second;
+    }
+    if (per_dev == 0) {
+        int occ = 0, sms = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kRedThreads, smem) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || occ < 1 || sms < 1) {
+            cudaGetLastError();
+            return red_grid(n);
+        }
+        per_dev = occ * sms;
+        std::lock_guard<std::mutex> lk(mu);
+        cache[std::make_tuple(kern, smem, dev)] = per_dev;
+    }
+    return std::max(1, std::min(red_grid(n), per_dev));
 }
 
 inline dr_status tv_launched(const char *what) {
@@ -614,8 +754,9 @@ struct TvOps {
             const size_t smem = tab_smem<T, M>(P, false);
             dr_status s = prep_smem(kern, smem);
             if (s != DR_OK) return s;
-            kern<<<red_grid(nvox(P)), kRedThreads, smem, st>>>((const S *)u, (T *)p, (const T *)P->d_PhiF,
-                                                                (const T *)P->d_dPhiF, geo(P), (T)lambda2);
+            const int grid = tv_grid((const void *)kern, smem, nvox(P));
+            kern<<<grid, kRedThreads, smem, st>>>((const S *)u, (T *)p, (const T *)P->d_PhiF,
+                                                   (const T *)P->d_dPhiF, geo(P), (T)lambda2);
             return tv_launched("grad_kernel");
         })
     }
@@ -626,7 +767,8 @@ struct TvOps {
             const size_t smem = tab_smem<T, M>(P, false);
             dr_status s = prep_smem(kern, smem);
             if (s != DR_OK) return s;
-            kern<<<red_grid(nvox(P)), kRedThreads, smem, st>>>(
+            const int grid = tv_grid((const void *)kern, smem, nvox(P));
+            kern<<<grid, kRedThreads, smem, st>>>(
                 (const T *)p, calc ? nullptr : (S *)u, calc ? (T *)u : nullptr, (const T *)P->d_PhiF,
                 (const T *)P->d_dPhiF, geo(P), (T)lambda2, (T)alpha, (T)beta);
             return tv_launched("gradT_kernel");
@@ -639,7 +781,8 @@ struct TvOps {
             const size_t smem = tab_smem<T, M>(P, false);
             dr_status s = prep_smem(kern, smem);
             if (s != DR_OK) return s;
-            kern<<<red_grid(nvox(P)), kRedThreads, smem, st>>>(
+            const int grid = tv_grid((const void *)kern, smem, nvox(P));
+            kern<<<grid, kRedThreads, smem, st>>>(
                 (const S *)u, (T *)mu, (T *)w, (const T *)P->d_PhiF, (const T *)P->d_dPhiF, geo(P), (T)rho,
                 (T)lambda1, (T)lambda2, P->d_partials + kSlotProx * kRedSlotStride, P->d_counters + kSlotProx,
                 P->d_scal, obj_row, obj_row ? 1 : 0);
@@ -655,13 +798,22 @@ struct TvCalc {
                          double lambda2, int mode, cudaStream_t st) {
         DR_TV_MT({
             auto kern = lap_kernel<T, M>;
-            const size_t smem = tab_smem<T, M>(P, true);
+            LapTab<T, M> tab{};
+            if constexpr (LapTab<T, M>::kParam) {
+                const double l2 = lambda2 * lambda2;
+                for (int k = 0; k < M * M; ++k) {
+                    tab.G[k] = (T)P->h_G[k];
+                    tab.L[k] = (T)(l2 * P->h_Lt[k]);
+                }
+            }
+            const size_t smem = LapTab<T, M>::kParam ? 0 : tab_smem<T, M>(P, true);
             dr_status s = prep_smem(kern, smem);
             if (s != DR_OK) return s;
             const int slot = mode == 2 ? kSlotRhs : kSlotLap;
-            kern<<<red_grid(nvox(P)), kRedThreads, smem, st>>>(
+            const int grid = tv_grid((const void *)kern, smem, nvox(P));
+            kern<<<grid, kRedThreads, smem, st>>>(
                 (const T *)x, (T *)out, (T *)pdir, (const T *)P->d_PhiF, (const T *)P->d_dPhiF, (const T *)P->d_G,
-                (const T *)P->d_Lt, geo(P), (T)alpha, (T)beta, (T)(lambda2 * lambda2),
+                (const T *)P->d_Lt, tab, geo(P), (T)alpha, (T)beta, (T)(lambda2 * lambda2),
                 P->d_partials + slot * kRedSlotStride, P->d_counters + slot, P->d_scal, mode);
             return tv_launched("lap_kernel");
         })
@@ -673,9 +825,10 @@ struct TvCalc {
             const size_t smem = tab_smem<T, M>(P, false);
             dr_status s = prep_smem(kern, smem);
             if (s != DR_OK) return s;
-            kern<<<red_grid(nvox(P)), kRedThreads, smem, st>>>((const T *)ut, (T *)h2, (const T *)P->d_PhiF,
-                                                                (const T *)P->d_dPhiF, geo(P), (T)sigma,
-                                                                (T)lambda1, (T)lambda2);
+            const int grid = tv_grid((const void *)kern, smem, nvox(P));
+            kern<<<grid, kRedThreads, smem, st>>>((const T *)ut, (T *)h2, (const T *)P->d_PhiF,
+                                                   (const T *)P->d_dPhiF, geo(P), (T)sigma,
+                                                   (T)lambda1, (T)lambda2);
             return tv_launched("cp_dual_kernel");
         })
     }
@@ -686,9 +839,10 @@ struct TvCalc {
             const size_t smem = tab_smem<T, M>(P, false);
             dr_status s = prep_smem(kern, smem);
             if (s != DR_OK) return s;
-            kern<<<red_grid(nvox(P)), kRedThreads, smem, st>>>((T *)u, (T *)ut, (const T *)a, (const T *)h2,
-                                                                (const T *)P->d_PhiF, (const T *)P->d_dPhiF,
-                                                                geo(P), (T)tau, (T)theta, (T)lambda2);
+            const int grid = tv_grid((const void *)kern, smem, nvox(P));
+            kern<<<grid, kRedThreads, smem, st>>>((T *)u, (T *)ut, (const T *)a, (const T *)h2,
+                                                   (const T *)P->d_PhiF, (const T *)P->d_dPhiF,
+                                                   geo(P), (T)tau, (T)theta, (T)lambda2);
             return tv_launched("cp_primal_kernel");
         })
     }
@@ -698,10 +852,11 @@ struct TvCalc {
             const size_t smem = tab_smem<T, M>(P, false);
             dr_status s = prep_smem(kern, smem);
             if (s != DR_OK) return s;
-            kern<<<red_grid(nvox(P)), kRedThreads, smem, st>>>((const T *)u, (const T *)P->d_PhiF,
-                                                                (const T *)P->d_dPhiF, geo(P), (T)lambda2,
-                                                                P->d_partials + kSlotTv * kRedSlotStride,
-                                                                P->d_counters + kSlotTv, P->d_scal, obj);
+            const int grid = tv_grid((const void *)kern, smem, nvox(P));
+            kern<<<grid, kRedThreads, smem, st>>>((const T *)u, (const T *)P->d_PhiF,
+                                                   (const T *)P->d_dPhiF, geo(P), (T)lambda2,
+                                                   P->d_partials + kSlotTv * kRedSlotStride,
+                                                   P->d_counters + kSlotTv, P->d_scal, obj);
             return tv_launched("tvsum_kernel");
         })
     }
@@ -718,9 +873,10 @@ struct TvFieldsBF16 {
             const size_t smem = tab_smem<T, M>(P, false);
             dr_status s = prep_smem(kern, smem);
             if (s != DR_OK) return s;
-            kern<<<red_grid(nvox(P)), kRedThreads, smem, st>>>((const bf16 *)p, nullptr, (T *)u,
-                                                                (const T *)P->d_PhiF, (const T *)P->d_dPhiF, geo(P),
-                                                                (T)lambda2, (T)alpha, (T)beta);
+            const int grid = tv_grid((const void *)kern, smem, nvox(P));
+            kern<<<grid, kRedThreads, smem, st>>>((const bf16 *)p, nullptr, (T *)u,
+                                                   (const T *)P->d_PhiF, (const T *)P->d_dPhiF, geo(P),
+                                                   (T)lambda2, (T)alpha, (T)beta);
             return tv_launched("gradT_kernel (bf16 field)");
         })
     }
@@ -732,7 +888,8 @@ struct TvFieldsBF16 {
             const size_t smem = tab_smem<T, M>(P, false);
             dr_status s = prep_smem(kern, smem);
             if (s != DR_OK) return s;
-            kern<<<red_grid(nvox(P)), kRedThreads, smem, st>>>(
+            const int grid = tv_grid((const void *)kern, smem, nvox(P));
+            kern<<<grid, kRedThreads, smem, st>>>(
                 (const T *)u, (bf16 *)mu, (bf16 *)w, (const T *)P->d_PhiF, (const T *)P->d_dPhiF, geo(P), (T)rho,
                 (T)lambda1, (T)lambda2, P->d_partials + kSlotProx * kRedSlotStride, P->d_counters + kSlotProx,
                 P->d_scal, obj_row, obj_row ? 1 : 0);
@@ -747,9 +904,10 @@ struct TvFieldsBF16 {
             const size_t smem = tab_smem<T, M>(P, false);
             dr_status s = prep_smem(kern, smem);
             if (s != DR_OK) return s;
-            kern<<<red_grid(nvox(P)), kRedThreads, smem, st>>>((const T *)ut, (bf16 *)h2, (const T *)P->d_PhiF,
-                                                                (const T *)P->d_dPhiF, geo(P), (T)sigma,
-                                                                (T)lambda1, (T)lambda2);
+            const int grid = tv_grid((const void *)kern, smem, nvox(P));
+            kern<<<grid, kRedThreads, smem, st>>>((const T *)ut, (bf16 *)h2, (const T *)P->d_PhiF,
+                                                   (const T *)P->d_dPhiF, geo(P), (T)sigma,
+                                                   (T)lambda1, (T)lambda2);
             return tv_launched("cp_dual_kernel (bf16 field)");
         })
     }
@@ -761,9 +919,10 @@ struct TvFieldsBF16 {
             const size_t smem = tab_smem<T, M>(P, false);
             dr_status s = prep_smem(kern, smem);
             if (s != DR_OK) return s;
-            kern<<<red_grid(nvox(P)), kRedThreads, smem, st>>>((T *)u, (T *)ut, (const T *)a, (const bf16 *)h2,
-                                                                (const T *)P->d_PhiF, (const T *)P->d_dPhiF,
-                                                                geo(P), (T)tau, (T)theta, (T)lambda2);
+            const int grid = tv_grid((const void *)kern, smem, nvox(P));
+            kern<<<grid, kRedThreads, smem, st>>>((T *)u, (T *)ut, (const T *)a, (const bf16 *)h2,
+                                                   (const T *)P->d_PhiF, (const T *)P->d_dPhiF,
+                                                   geo(P), (T)tau, (T)theta, (T)lambda2);
             return tv_launched("cp_primal_kernel (bf16 field)");
         })
     }

@@ -146,6 +146,32 @@ def test_ellipsoid_workload_two_slices_fp32():
     assert np.max(np.abs(res["objective"] - oo) / np.abs(oo)) <= F32_SOLVE_TOL_OBJ
 
 
+@pytest.mark.parametrize("algo", [dr.ADMM_CG, dr.CHAMBOLLE_POCK])
+def test_banded_walk_solve_matches_oracle(algo):
+    """A volume whose rows (u plus 64 frames of duals) fill more than one
+    8 MB band per slice: every TV stencil of the solve walks it in bands
+    (60 rows in FP64, two full bands and a partial one).  Three FP64
+    iterations against the oracle from zero."""
+    nx, ny, nz, ns, K, m, nt = 64, 130, 2, 96, 16, 16, 64
+    theta, t = synth.scan(K, 2.0)
+    g = synth.rng_for(4242).standard_normal((nz, K, ns))
+    P = oracle.Problem(nx, ny, nz, ns, theta, t, dr.FOURIER, m, nt)
+    u0 = np.zeros((nz, ny, nx, m))
+    lam1, lam2, rho, n_cg = 0.05, 1.0, 0.5, 4
+    plan = dr.Plan(nx, ny, nz, ns, theta, t, dr.FOURIER, m, nt, dr.F64)
+    ud = torch.zeros(plan.u_shape(), dtype=torch.float64, device="cuda")
+    prm = dr.solve_params(algo, iters=3, n_cg=n_cg, lambda1=lam1, lambda2=lam2, rho=rho)
+    res = dr.admm_solve(plan, dev_tensor(g, dr.F64), ud, prm)
+    if algo == dr.ADMM_CG:
+        uo, oo, _ = P.admm_cg(g, u0, 3, n_cg, lam1, lam2, rho)
+    else:
+        L = P.power_norm(lam2)
+        assert abs(res["op_norm"] - L) <= 1e-10 * L
+        uo, oo = P.chambolle_pock(g, u0, 3, lam1, lam2, 1.0, L)
+    assert rel(host_values(ud), uo) <= 1e-9
+    assert np.max(np.abs(np.asarray(res["objective"]) - oo) / np.abs(oo)) <= 1e-10
+
+
 def test_bf16_storage_solve(disks):
     """BF16 data and coefficients, FP32 state: error against the oracle run on
     the bf16-rounded data (output rounding to bf16 included)."""

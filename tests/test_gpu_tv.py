@@ -30,6 +30,11 @@ CASES = {
     "haar": (20, 18, 3, dr.HAAR, 4, 8),
     "orthonormal": (18, 20, 2, dr.LEGENDRE | dr.ORTHONORMAL, 5, 6),
     "complex": (19, 17, 3, dr.COMPLEX_FOURIER, 8, 6),
+    # a row of u plus the dual fields takes so many bytes that the stencils
+    # walk the volume in bands of rows (42 rows in FP32 / 21 in FP64 here,
+    # 54 / 27 in banded_m8), the last band partial
+    "banded": (512, 100, 3, dr.LEGENDRE, 16, 20),
+    "banded_m8": (300, 60, 4, dr.FOURIER, 8, 30),
 }
 
 
@@ -85,9 +90,8 @@ def test_grad_adj_beta(case):
     assert_close(host_values(ut), 2.5 * u + P.DT(p, 0.6), 1e-12)
 
 
-# Tall volumes: enough (x, y) tiles x slices that the z-marching D^T D kernel
-# walks runs of several slices (carrying rows between steps), with a ragged
-# last run, tiles cut by nx and ny, and m below the template size.
+# Tall volumes: many slices per row of the walk, ragged nx and ny, and m
+# below the template size.
 TALL = {"tall_m8": (40, 20, 400, dr.FOURIER, 8, 3), "tall_m5": (33, 9, 700, dr.LEGENDRE, 5, 4),
         "tall_m16": (70, 17, 150, dr.FOURIER, 16, 2)}
 
