@@ -93,7 +93,8 @@ def parse():
     ap.add_argument("--slices", type=int, default=0,
                     help="with --profile-small: the workload's geometry on this many slices (a small case for ncu)")
     ap.add_argument("--profile-small", action="store_true",
-                    help="run only one launch of each projector call on the workload (for ncu captures)")
+                    help="run only one launch of each projector call and of each TV stencil on the workload "
+                         "(for ncu captures)")
     return ap.parse_args()
 
 
@@ -403,6 +404,13 @@ def run_ours(a):
         gout = torch.empty_like(g)
         dr.dyn_radon_fwd(plan, uin, gout)
         dr.dyn_radon_adj(plan, g, u)
+        # and one launch of each TV stencil (D^T D, D^T, prox, D) on the same volume
+        mu = torch.randn(plan.field_shape(), dtype=torch.float32, device=dev) * 1e-3
+        wf = torch.empty_like(mu)
+        dr.tv4d_normal(plan, uin, u, w.lambda2, 1.0)
+        dr.tv4d_grad_adj(plan, mu, u, w.lambda2)
+        dr.tv4d_prox(plan, uin, mu, wf, w.rho, w.lambda1, w.lambda2)
+        dr.tv4d_grad(plan, uin, wf, w.lambda2)
         torch.cuda.synchronize()
         print(json.dumps({"profile_small": True, "info": plan.info()}))
         return
