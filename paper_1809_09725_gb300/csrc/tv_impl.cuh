@@ -439,6 +439,26 @@ struct LapTab {
     T L[kParam ? M * M : 1];  // lambda2^2 Lt
 };
 
+// The last block's update of the solver scalars from the reduced sum of a
+// D^T D launch (see the modes above).
+__device__ __forceinline__ void lap_scalars(double sum, DevScalars *scal, int mode) {
+    if (mode == 1) {
+        const double pq = sum, rr = scal->rr;
+        scal->pq = pq;
+        if (scal->active && pq > 0.0 && rr > 0.0) {
+            scal->alpha = rr / pq;
+        } else {
+            scal->alpha = 0.0;
+            scal->active = 0;
+        }
+    } else if (mode == 2) {
+        scal->rr = sum;
+        scal->active = 1;
+    } else {
+        scal->pq = sum;
+    }
+}
+
 // Resident CTAs per SM asked of the FP32 instantiations: four at m <= 8, two
 // (128 registers) at m = 16.
 __host__ __device__ constexpr int lap_min_blocks(int M, int T_bytes) {
@@ -565,23 +585,141 @@ __global__ void __launch_bounds__(kRedThreads, lap_min_blocks(M, sizeof(T)))
         acc.add(dotv);
     }
     double vals[1] = {acc.value()}, tot[1];
-    if (block_reduce_last<1>(vals, partials, counter, tot)) {
-        if (mode == 1) {
-            const double pq = tot[0], rr = scal->rr;
-            scal->pq = pq;
-            if (scal->active && pq > 0.0 && rr > 0.0) {
-                scal->alpha = rr / pq;
-            } else {
-                scal->alpha = 0.0;
-                scal->active = 0;
+    if (block_reduce_last<1>(vals, partials, counter, tot)) lap_scalars(tot[0], scal, mode);
+}
+
+// ---------------------------------------------------------------------------
+// D^T D for FP32 coefficient rows of exactly 16 floats, as a march up z over
+// (x, y) tiles.  A CTA of 256 threads owns tiles of 32 x 8 voxels (one voxel
+// per thread) and walks each tile from z = 0 to nz - 1.  The planes z - 1, z
+// and z + 1 of the tile, with a one-voxel x / y halo (34 x 10 voxels, 64 bytes
+// each), are in shared memory in a ring of four; plane z + 2 is copied by
+// cp.async (16-byte chunks, consecutive threads on consecutive chunks of a
+// row) while plane z is computed.  In a staged plane, chunk c of tile voxel k
+// sits at position c ^ ((k >> 1) & 3) of the voxel's four, so the rows of any
+// 8 consecutive voxels (a quarter warp's 16-byte reads of one neighbour)
+// fall in 8 different bank groups: the stencil's seven row reads per voxel
+// are conflict-free shared-memory reads instead of strided global loads.
+// The arithmetic per voxel is the lap_kernel's (same neighbour order, same
+// sums, tables in the constant bank).
+// ---------------------------------------------------------------------------
+constexpr int kLapTX = 32, kLapTY = 8;
+constexpr int kLapHX = kLapTX + 2, kLapHY = kLapTY + 2;
+constexpr int kLapPlane = kLapHX * kLapHY;  // voxels of a staged plane
+constexpr int kLapRing = 4;                 // planes in the ring
+constexpr size_t kLapTileSmem = (size_t)kLapRing * kLapPlane * 64;
+
+template <int M>  // 16
+__global__ void __launch_bounds__(kRedThreads, 2)
+    lap_tile_kernel(const float *__restrict__ xv, float *__restrict__ out, float *__restrict__ pdir,
+                    const __grid_constant__ LapTab<float, 16> tab, Geo g, float alpha, float beta, double *partials,
+                    unsigned *counter, DevScalars *scal, int mode) {
+    static_assert(M == 16, "rows of four 16-byte chunks");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float4 *ring = reinterpret_cast<float4 *>(smem_raw);  // [kLapRing][kLapPlane][4]
+    const int tid = threadIdx.x, lx = tid & 31, ly = tid >> 5;
+    const int ntx = (g.nx + kLapTX - 1) / kLapTX, nty = (g.ny + kLapTY - 1) / kLapTY;
+    const int ntiles = ntx * nty;
+    PartialSum<float> acc;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int x0 = (tile % ntx) * kLapTX, y0 = (tile / ntx) * kLapTY;
+        const int x = x0 + lx, y = y0 + ly;
+        const bool live = x < g.nx && y < g.ny;
+        // copy plane zz (-1 <= zz <= nz + 1; only planes in memory) into its ring slot
+        auto stage = [&](int zz) {
+            const bool in_mem = (zz >= 0 && zz < g.nz) || (zz == -1 && g.zlo) || (zz == g.nz && g.zhi);
+            if (!in_mem) return;
+            float4 *dst = ring + (size_t)((zz + kLapRing) % kLapRing) * kLapPlane * 4;
+            for (int i = tid; i < kLapPlane * 4; i += kRedThreads) {
+                const int k = i >> 2, c = i & 3;
+                const int hy = k / kLapHX, hx = k - hy * kLapHX;
+                const int gx = x0 - 1 + hx, gy = y0 - 1 + hy;
+                if (gx < 0 || gx >= g.nx || gy < 0 || gy >= g.ny) continue;
+                const float *src = xv + (((long long)zz * g.ny + gy) * g.nx + gx) * M + 4 * c;
+                cp_async_16(dst + k * 4 + (c ^ ((k >> 1) & 3)), src);
             }
-        } else if (mode == 2) {
-            scal->rr = tot[0];
-            scal->active = 1;
-        } else {
-            scal->pq = tot[0];
+        };
+        // row of tile voxel k of ring slot sl
+        auto row = [&](int sl, int k, float (&r)[M]) {
+            const float4 *b = ring + ((size_t)sl * kLapPlane + k) * 4;
+            const int sw = (k >> 1) & 3;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const float4 a = b[c ^ sw];
+                r[4 * c] = a.x;
+                r[4 * c + 1] = a.y;
+                r[4 * c + 2] = a.z;
+                r[4 * c + 3] = a.w;
+            }
+        };
+        __syncthreads();  // the previous tile's reads of the ring are done
+        stage(-1);
+        cp_async_commit();
+        stage(0);
+        cp_async_commit();
+        stage(1);
+        cp_async_commit();
+        for (int z = 0; z < g.nz; ++z) {
+            if (z > 0) __syncthreads();  // every thread is done with step z - 1 (and slot (z + 2) % 4)
+            stage(z + 2);
+            cp_async_commit();
+            cp_async_wait<1>();  // this thread's copies of planes up to z + 1 have landed
+            __syncthreads();     // and every thread's
+            if (!live) continue;
+            const int k = (ly + 1) * kLapHX + lx + 1;
+            const int sc = z % kLapRing, sb = (z + kLapRing - 1) % kLapRing, sa = (z + 1) % kLapRing;
+            float xc[M], ls[M], nb[M];
+            row(sc, k, xc);
+#pragma unroll
+            for (int j = 0; j < M; ++j) ls[j] = 0.0f;
+            auto add_nb = [&](bool has, int sl, int kk) {
+                if (!has) return;
+                row(sl, kk, nb);
+#pragma unroll
+                for (int j = 0; j < M; ++j) ls[j] += xc[j] - nb[j];
+            };
+            // the six neighbours in the order -x, +x, -y, +y, -z, +z (as lap_kernel)
+            add_nb(x > 0, sc, k - 1);
+            add_nb(x + 1 < g.nx, sc, k + 1);
+            add_nb(y > 0, sc, k - kLapHX);
+            add_nb(y + 1 < g.ny, sc, k + kLapHX);
+            add_nb(z > 0 || g.zlo != 0, sb, k);
+            add_nb(z + 1 < g.nz || g.zhi != 0, sa, k);
+            const size_t v = ((size_t)z * g.ny + y) * g.nx + x;
+            float rv[M];
+#pragma unroll
+            for (int i = 0; i < M; ++i) {
+                float s2 = 0.0f;
+#pragma unroll
+                for (int j = 0; j < M; ++j) s2 = fmaf(tab.G[i * M + j], ls[j], fmaf(tab.L[i * M + j], xc[j], s2));
+                rv[i] = alpha * s2;
+            }
+            // out (and pdir) a 16-byte chunk at a time
+            float4 *o4 = reinterpret_cast<float4 *>(out + v * M);
+            float dotv = 0.0f;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                float4 r = make_float4(rv[4 * c], rv[4 * c + 1], rv[4 * c + 2], rv[4 * c + 3]);
+                if (beta != 0.0f) {
+                    const float4 o = o4[c];
+                    r.x += beta * o.x;
+                    r.y += beta * o.y;
+                    r.z += beta * o.z;
+                    r.w += beta * o.w;
+                }
+                o4[c] = r;
+                if (mode == 2) reinterpret_cast<float4 *>(pdir + v * M)[c] = r;
+                const float rr[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    dotv = mode == 2 ? fmaf(rr[e], rr[e], dotv) : fmaf(xc[4 * c + e], rr[e], dotv);
+            }
+            acc.add(dotv);
         }
+        cp_async_wait<0>();  // no copy of this tile is still in flight
     }
+    double vals[1] = {acc.value()}, tot[1];
+    if (block_reduce_last<1>(vals, partials, counter, tot)) lap_scalars(tot[0], scal, mode);
 }
 
 // ---------------------------------------------------------------------------
@@ -806,10 +944,28 @@ struct TvCalc {
                     tab.L[k] = (T)(l2 * P->h_Lt[k]);
                 }
             }
+            const int slot = mode == 2 ? kSlotRhs : kSlotLap;
+            if constexpr (sizeof(T) == 4 && M == 16) {
+                // rows of exactly 16 floats, 16-byte aligned, at least one full tile width:
+                // the z-marching form with the rows staged in shared memory
+                auto al16 = [](const void *q) { return ((uintptr_t)q & 15u) == 0; };
+                if (P->m == 16 && P->nx >= kLapTX && al16(x) && al16(out) && (mode != 2 || al16(pdir))) {
+                    auto tk = lap_tile_kernel<16>;
+                    dr_status s2 = prep_smem(tk, kLapTileSmem);
+                    if (s2 != DR_OK) return s2;
+                    const Geo gg = geo(P);
+                    const int ntiles = ((gg.nx + kLapTX - 1) / kLapTX) * ((gg.ny + kLapTY - 1) / kLapTY);
+                    const int grid = std::max(1, std::min(ntiles, tv_grid((const void *)tk, kLapTileSmem, nvox(P))));
+                    tk<<<grid, kRedThreads, kLapTileSmem, st>>>((const float *)x, (float *)out, (float *)pdir, tab, gg,
+                                                                (float)alpha, (float)beta,
+                                                                P->d_partials + slot * kRedSlotStride,
+                                                                P->d_counters + slot, P->d_scal, mode);
+                    return tv_launched("lap_tile_kernel");
+                }
+            }
             const size_t smem = LapTab<T, M>::kParam ? 0 : tab_smem<T, M>(P, true);
             dr_status s = prep_smem(kern, smem);
             if (s != DR_OK) return s;
-            const int slot = mode == 2 ? kSlotRhs : kSlotLap;
             const int grid = tv_grid((const void *)kern, smem, nvox(P));
             kern<<<grid, kRedThreads, smem, st>>>(
                 (const T *)x, (T *)out, (T *)pdir, (const T *)P->d_PhiF, (const T *)P->d_dPhiF, (const T *)P->d_G,
