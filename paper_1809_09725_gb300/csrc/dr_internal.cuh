@@ -194,7 +194,8 @@ struct dr_plan {
     void *d_dPhiF = nullptr;  // [nt][MT] T, row l = PhiF[l+1] - PhiF[l] (0 for the last)
     void *d_G = nullptr;      // [MT][MT] T, PhiF^T PhiF
     void *d_Lt = nullptr;     // [MT][MT] T, PhiF^T Lt PhiF (Lt = 1D Neumann Laplacian in l)
-    std::vector<double> h_G, h_Lt;  // host copies of G and Lt ([MT][MT])
+    std::vector<double> h_G, h_Lt;      // host copies of G and Lt ([MT][MT])
+    std::vector<double> h_phif, h_dphif;  // host copies of PhiF and dPhiF ([nt][MT])
     // half-turn fold (Sec. 4): projections grouped by theta mod pi
     int fold_U = 0;                   // unique angles (0: the fold is unavailable for this plan)
     int fold_maxgrp = 0;              // largest group

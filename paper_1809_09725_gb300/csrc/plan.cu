@@ -257,6 +257,8 @@ static dr_status build_tables(dr_plan *P) {
         }
     P->h_G = G;
     P->h_Lt = Lt;
+    P->h_phif = phif;
+    P->h_dphif = dphif;
     dr_status st;
     if (dbl) {
         if ((st = upload<double>(&P->d_PhiP, phip, bytes)) != DR_OK) return st;

@@ -234,9 +234,22 @@ __global__ void __launch_bounds__(kRedThreads)
 }
 
 // (D^T p)_j at voxel v (Neumann-matched backward differences, then PhiF^T).
-template <typename T, int M, typename F = T>
+// PhiF and dPhiF ([nt][M]) as a kernel parameter for FP32 D^T when nt M is at
+// most kFrameTabMax: the rows of frame l are then read through the constant
+// cache instead of shared memory (whose loads share the L1 pipe with the
+// field's).
+constexpr int kFrameTabMax = 448;
+template <typename T>
+struct FrameTab {
+    static constexpr int kMax = sizeof(T) == 4 ? kFrameTabMax : 1;
+    T ph[kMax];
+    T dph[kMax];
+};
+
+template <typename T, int M, typename F = T, bool CT = false>
 __device__ __forceinline__ void gradT_voxel(const F *__restrict__ p, size_t v, int x, int y, int z, const Geo &g,
-                                            const T *sm, T lambda2, T (&outj)[M]) {
+                                            const T *sm, T lambda2, T (&outj)[M],
+                                            const FrameTab<T> *ft = nullptr) {
     const T *dph = sm + g.nt * M;
 #pragma unroll
     for (int j = 0; j < M; ++j) outj[j] = T(0);
@@ -273,10 +286,17 @@ __device__ __forceinline__ void gradT_voxel(const F *__restrict__ p, size_t v, i
             if (hz) s -= q[f].z;
             if (lz) s += nbz[f];
             const T qt = lambda2 * q[f].w;
-            const T *ph = sm + l * M;
-            const T *dp = dph + l * M;
+            if constexpr (CT) {
+                const T *ph = ft->ph + l * M;
+                const T *dp = ft->dph + l * M;
 #pragma unroll
-            for (int j = 0; j < M; ++j) outj[j] = fma(ph[j], s, fma(dp[j], qt, outj[j]));
+                for (int j = 0; j < M; ++j) outj[j] = fma(ph[j], s, fma(dp[j], qt, outj[j]));
+            } else {
+                const T *ph = sm + l * M;
+                const T *dp = dph + l * M;
+#pragma unroll
+                for (int j = 0; j < M; ++j) outj[j] = fma(ph[j], s, fma(dp[j], qt, outj[j]));
+            }
         }
     }
 }
@@ -288,19 +308,19 @@ __host__ __device__ constexpr int gradT_min_blocks(int M, int T_bytes) {
     return T_bytes == 4 ? (M <= 8 ? 4 : (M == 16 ? 3 : 2)) : 1;
 }
 
-template <typename T, typename S, int M, typename F = T>
+template <typename T, typename S, int M, typename F = T, bool CT = false>
 __global__ void __launch_bounds__(kRedThreads, gradT_min_blocks(M, sizeof(T)))
     gradT_kernel(const F *__restrict__ p, S *__restrict__ u_s, T *__restrict__ u_c, const T *PhiF, const T *dPhiF,
-                 Geo g, T lambda2, T alpha, T beta) {
+                 Geo g, T lambda2, T alpha, T beta, const __grid_constant__ FrameTab<T> ft) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sm = reinterpret_cast<T *>(smem_raw);
-    load_tables<T, M>(sm, PhiF, dPhiF, nullptr, nullptr, g.nt, false);
+    if constexpr (!CT) load_tables<T, M>(sm, PhiF, dPhiF, nullptr, nullptr, g.nt, false);
     const size_t nv = (size_t)g.nx * g.ny * g.nz;
     for (size_t it = blockIdx.x * (size_t)blockDim.x + threadIdx.x; it < nv; it += (size_t)gridDim.x * blockDim.x) {
         int x, y, z;
         const size_t v = band_voxel(it, g, x, y, z);
         T o[M];
-        gradT_voxel<T, M, F>(p, v, x, y, z, g, sm, lambda2, o);
+        gradT_voxel<T, M, F, CT>(p, v, x, y, z, g, sm, lambda2, o, &ft);
         if (u_c) {
             // compute-typed row: vector loads and stores
             T ov[M];
@@ -883,6 +903,28 @@ inline dr_status tv_launched(const char *what) {
     }                                                      \
     return fail(DR_EINVAL, "tv: unsupported m");
 
+// u = beta u + alpha D^T p with p stored as F; FP32 plans whose frame tables
+// fit the kernel parameter take them from the constant bank.
+template <typename T, typename S, int M, typename F>
+inline dr_status launch_gradT(dr_plan *P, const F *p, S *u_s, T *u_c, double lambda2, double alpha, double beta,
+                              cudaStream_t st, const char *what) {
+    FrameTab<T> ft{};
+    const bool ct = sizeof(T) == 4 && P->nt * M <= kFrameTabMax;
+    if (ct)
+        for (int i = 0; i < P->nt * M; ++i) {
+            ft.ph[i] = (T)P->h_phif[i];
+            ft.dph[i] = (T)P->h_dphif[i];
+        }
+    auto kern = ct ? gradT_kernel<T, S, M, F, true> : gradT_kernel<T, S, M, F, false>;
+    const size_t smem = ct ? 0 : tab_smem<T, M>(P, false);
+    dr_status s = prep_smem(kern, smem);
+    if (s != DR_OK) return s;
+    const int grid = tv_grid((const void *)kern, smem, nvox(P));
+    kern<<<grid, kRedThreads, smem, st>>>(p, u_s, u_c, (const T *)P->d_PhiF, (const T *)P->d_dPhiF, geo(P), (T)lambda2,
+                                          (T)alpha, (T)beta, ft);
+    return tv_launched(what);
+}
+
 // Kernels whose coefficient input may be stored in S (bf16 for BF16 plans).
 template <typename T, typename S>
 struct TvOps {
@@ -901,15 +943,8 @@ struct TvOps {
     static dr_status grad_adj(dr_plan *P, const void *p, void *u, bool calc, double lambda2, double alpha,
                               double beta, cudaStream_t st) {
         DR_TV_MT({
-            auto kern = gradT_kernel<T, S, M>;
-            const size_t smem = tab_smem<T, M>(P, false);
-            dr_status s = prep_smem(kern, smem);
-            if (s != DR_OK) return s;
-            const int grid = tv_grid((const void *)kern, smem, nvox(P));
-            kern<<<grid, kRedThreads, smem, st>>>(
-                (const T *)p, calc ? nullptr : (S *)u, calc ? (T *)u : nullptr, (const T *)P->d_PhiF,
-                (const T *)P->d_dPhiF, geo(P), (T)lambda2, (T)alpha, (T)beta);
-            return tv_launched("gradT_kernel");
+            return launch_gradT<T, S, M, T>(P, (const T *)p, calc ? nullptr : (S *)u, calc ? (T *)u : nullptr,
+                                            lambda2, alpha, beta, st, "gradT_kernel");
         })
     }
     static dr_status prox(dr_plan *P, const void *u, void *mu, void *w, double rho, double lambda1, double lambda2,
@@ -1025,15 +1060,8 @@ struct TvFieldsBF16 {
                               cudaStream_t st) {
         typedef float T;
         DR_TV_MT({
-            auto kern = gradT_kernel<T, T, M, bf16>;
-            const size_t smem = tab_smem<T, M>(P, false);
-            dr_status s = prep_smem(kern, smem);
-            if (s != DR_OK) return s;
-            const int grid = tv_grid((const void *)kern, smem, nvox(P));
-            kern<<<grid, kRedThreads, smem, st>>>((const bf16 *)p, nullptr, (T *)u,
-                                                   (const T *)P->d_PhiF, (const T *)P->d_dPhiF, geo(P),
-                                                   (T)lambda2, (T)alpha, (T)beta);
-            return tv_launched("gradT_kernel (bf16 field)");
+            return launch_gradT<T, T, M, bf16>(P, (const bf16 *)p, nullptr, (T *)u, lambda2, alpha, beta, st,
+                                               "gradT_kernel (bf16 field)");
         })
     }
     static dr_status prox(dr_plan *P, const void *u, void *mu, void *w, double rho, double lambda1, double lambda2,

@@ -80,14 +80,36 @@ def test_grad_and_adjoint(case, prec, tol):
     assert_close(host_values(ua), P.DT(p, lam2), tol)
 
 
-@pytest.mark.parametrize("case", ["ragged", "m8"])
-def test_grad_adj_beta(case):
+@pytest.mark.parametrize("case", ["ragged", "m8", "banded", "banded_m8"])
+@pytest.mark.parametrize("prec,tol", [(dr.F64, 1e-12), (dr.F32, 1e-5)])
+def test_grad_adj_beta(case, prec, tol):
+    """u = beta u + D^T p (in FP32 with nt m <= 448 the frame tables come from
+    the constant bank; the banded cases walk in several bands)."""
     args, P, u, p, _ = _setup(case, seed=1)
-    plan = dr.Plan(*args, prec=dr.F64)
-    ut = dev_tensor(u, dr.F64)
-    dr.tv4d_grad_adj(plan, dev_tensor(_to_field(p), dr.F64), ut, 0.6, beta=2.5)
+    if prec == dr.F32:
+        u = u.astype(np.float32).astype(np.float64)
+        p = p.astype(np.float32).astype(np.float64)
+    plan = dr.Plan(*args, prec=prec)
+    ut = dev_tensor(u, prec)
+    dr.tv4d_grad_adj(plan, dev_tensor(_to_field(p), prec), ut, 0.6, beta=2.5)
     plan.sync()
-    assert_close(host_values(ut), 2.5 * u + P.DT(p, 0.6), 1e-12)
+    assert_close(host_values(ut), 2.5 * u + P.DT(p, 0.6), tol)
+
+
+@pytest.mark.parametrize("case", ["m8", "banded_m8"])
+def test_grad_adj_bf16_storage(case):
+    """D^T p into bf16 coefficients (BF16 plan: float fields, FP32 sums, one
+    rounding to bf16 per stored coefficient)."""
+    args, P, _, p, _ = _setup(case, seed=5)
+    p = p.astype(np.float32).astype(np.float64)
+    plan = dr.Plan(*args, prec=dr.BF16)
+    ua = torch.zeros(plan.u_shape(), dtype=torch.bfloat16, device="cuda")
+    dr.tv4d_grad_adj(plan, dev_tensor(_to_field(p), dr.F32), ua, 0.6)
+    plan.sync()
+    ref = P.DT(p, 0.6)
+    # bf16 keeps 8 significant bits: each stored value within 2^-8 of itself
+    got = host_values(ua)
+    assert np.all(np.abs(got - ref) <= 2.0 ** -8 * np.abs(ref) + 1e-6 * np.max(np.abs(ref)))
 
 
 # Tall volumes: many slices per row of the walk, ragged nx and ny, and m
