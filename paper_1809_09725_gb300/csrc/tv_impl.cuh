@@ -839,7 +839,7 @@ __global__ void __launch_bounds__(kRedThreads)
 // Rows per band of the traversal: one band at one slice holds about
 // kBandBytes of u and the dual fields, so the z neighbours (a band apart in
 // the walk) stay in L2.  Volumes whose whole slice fits walk slice by slice.
-constexpr size_t kBandBytes = 8u << 20;
+constexpr size_t kBandBytes = 4u << 20;
 inline Geo geo(const dr_plan *P) {
     const size_t bpv = (size_t)(4 * P->nt + P->m) * (P->prec == DR_F64 ? 8 : 4);
     const size_t row = std::max<size_t>(1, bpv * (size_t)P->nx);

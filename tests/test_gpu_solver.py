@@ -150,8 +150,8 @@ def test_ellipsoid_workload_two_slices_fp32():
 @pytest.mark.parametrize("prec", [dr.F64, dr.F32])
 def test_banded_walk_solve_matches_oracle(algo, prec):
     """A volume whose rows (u plus 64 frames of duals) fill more than one
-    8 MB band per slice: every TV stencil of the solve walks it in bands
-    (60 rows in FP64, 120 in FP32: full bands and a partial one); in FP32
+    4 MB band per slice: every TV stencil of the solve walks it in bands
+    (30 rows in FP64, 60 in FP32: full bands and a partial one); in FP32
     with m = 16 the CG's D^T D is the z-marching tiled kernel (two tiles
     across x, a partial tile row).  Three iterations against the oracle
     from zero."""

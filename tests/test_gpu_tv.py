@@ -31,8 +31,8 @@ CASES = {
     "orthonormal": (18, 20, 2, dr.LEGENDRE | dr.ORTHONORMAL, 5, 6),
     "complex": (19, 17, 3, dr.COMPLEX_FOURIER, 8, 6),
     # a row of u plus the dual fields takes so many bytes that the stencils
-    # walk the volume in bands of rows (42 rows in FP32 / 21 in FP64 here,
-    # 54 / 27 in banded_m8), the last band partial
+    # walk the volume in bands of rows (21 rows in FP32 with a partial last
+    # band / 10 in FP64 here, 27 / 13 in banded_m8, both with a partial band)
     "banded": (512, 100, 3, dr.LEGENDRE, 16, 20),
     "banded_m8": (300, 60, 4, dr.FOURIER, 8, 30),
 }
