@@ -13,7 +13,10 @@
 //              (the composition of the two stencils, exact up to rounding)
 //   ADMM shrink/dual update, CP projection and primal update (Sec. 3, Fig. 2)
 // All are HBM bound; each thread owns whole voxels (all m coefficients and
-// all nt frames), neighbours come through L1/L2.
+// all nt frames).  The volume is walked in bands of rows (band_voxel) by
+// grids of resident blocks (tv_grid), so neighbours come through L1/L2; D^T D
+// on FP32 rows of 16 floats marches tiles up z with the rows staged in shared
+// memory (lap_tile_kernel).
 #include <algorithm>
 #include <cmath>
 #include <map>
@@ -350,10 +353,6 @@ __global__ void __launch_bounds__(kRedThreads, gradT_min_blocks(M, sizeof(T)))
 // w = psi - mu/rho.  Reduces sum |Du| and ||Du - psi||^2.
 // obj: destination row (tv, primal^2); when use_iter the row is obj + 3*iter + 1.
 // ---------------------------------------------------------------------------
-// Resident CTAs per SM requested for the latency-bound per-voxel stencils
-// (more warps in flight to cover the strided dual reads).
-__host__ __device__ constexpr int tv_min_blocks(int M, int T_bytes) { return (T_bytes == 4 && M <= 8) ? 4 : 1; }
-
 // prox keeps a group of frames' duals in registers besides the coefficient
 // differences: three CTAs per SM (85 registers) at m <= 8, two (128) at
 // m = 16, where the group is four frames (64 bytes of loads in flight per
