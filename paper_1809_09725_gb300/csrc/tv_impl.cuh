@@ -15,8 +15,8 @@
 // All are HBM bound; each thread owns whole voxels (all m coefficients and
 // all nt frames).  The volume is walked in bands of rows (band_voxel) by
 // grids of resident blocks (tv_grid), so neighbours come through L1/L2; D^T D
-// on FP32 rows of 16 floats marches tiles up z with the rows staged in shared
-// memory (lap_tile_kernel).
+// on FP32 rows of 4, 8 or 16 floats marches tiles up z with the rows staged in
+// shared memory (lap_tile_kernel).
 #include <algorithm>
 #include <cmath>
 #include <map>
@@ -608,62 +608,72 @@ __global__ void __launch_bounds__(kRedThreads, lap_min_blocks(M, sizeof(T)))
 }
 
 // ---------------------------------------------------------------------------
-// D^T D for FP32 coefficient rows of exactly 16 floats, as a march up z over
-// (x, y) tiles.  A CTA of 256 threads owns tiles of 32 x 8 voxels (one voxel
-// per thread) and walks each tile from z = 0 to nz - 1.  The planes z - 1, z
-// and z + 1 of the tile, with a one-voxel x / y halo (34 x 10 voxels, 64 bytes
-// each), are in shared memory in a ring of four; plane z + 2 is copied by
-// cp.async (16-byte chunks, consecutive threads on consecutive chunks of a
-// row) while plane z is computed.  In a staged plane, chunk c of tile voxel k
-// sits at position c ^ ((k >> 1) & 3) of the voxel's four, so the rows of any
-// 8 consecutive voxels (a quarter warp's 16-byte reads of one neighbour)
-// fall in 8 different bank groups: the stencil's seven row reads per voxel
-// are conflict-free shared-memory reads instead of strided global loads.
-// The arithmetic per voxel is the lap_kernel's (same neighbour order, same
-// sums, tables in the constant bank).
+// D^T D for FP32 coefficient rows of exactly M = 4, 8 or 16 floats, as a march
+// up z over (x, y) tiles.  A CTA of 256 threads owns work items of 32 x 8
+// voxels (one voxel per thread) and a run of slices [z0, z1), and walks the
+// run up z.  The planes z - 1, z and z + 1 of the tile, with a one-voxel x / y
+// halo (34 x 10 voxels of M floats), are in shared memory in a ring of four;
+// plane z + 2 is copied by cp.async (16-byte chunks, consecutive threads on
+// consecutive chunks of a row) while plane z is computed.  In a staged plane
+// the CH = M / 4 chunks of tile voxel k sit in the order c ^ sw(k), with
+// sw(k) = (k / (8 / CH)) mod CH, so the rows of any 8 consecutive voxels (a
+// quarter warp's 16-byte reads of one neighbour) fall in 8 different bank
+// groups: the stencil's seven row reads per voxel are conflict-free
+// shared-memory reads instead of strided global loads.  Volumes with few
+// tiles are cut into several runs of slices (each run stages its own
+// boundary planes) so that the grid still fills the GPU.  The arithmetic per
+// voxel is the lap_kernel's (same neighbour order, same sums, tables in the
+// constant bank).
 // ---------------------------------------------------------------------------
 constexpr int kLapTX = 32, kLapTY = 8;
 constexpr int kLapHX = kLapTX + 2, kLapHY = kLapTY + 2;
 constexpr int kLapPlane = kLapHX * kLapHY;  // voxels of a staged plane
 constexpr int kLapRing = 4;                 // planes in the ring
-constexpr size_t kLapTileSmem = (size_t)kLapRing * kLapPlane * 64;
+constexpr size_t lap_tile_smem(int M) { return (size_t)kLapRing * kLapPlane * M * sizeof(float); }
 
-template <int M>  // 16
-__global__ void __launch_bounds__(kRedThreads, 2)
+// RUNS = false: one run of all nz slices per tile (nruns is 1).
+template <int M, bool RUNS>
+__global__ void __launch_bounds__(kRedThreads, M == 16 ? 2 : 4)
     lap_tile_kernel(const float *__restrict__ xv, float *__restrict__ out, float *__restrict__ pdir,
-                    const __grid_constant__ LapTab<float, 16> tab, Geo g, float alpha, float beta, double *partials,
-                    unsigned *counter, DevScalars *scal, int mode) {
-    static_assert(M == 16, "rows of four 16-byte chunks");
+                    const __grid_constant__ LapTab<float, M> tab, Geo g, int nruns, float alpha, float beta,
+                    double *partials, unsigned *counter, DevScalars *scal, int mode) {
+    static_assert(M == 4 || M == 8 || M == 16, "rows of whole 16-byte chunks");
+    constexpr int CH = M / 4;  // 16-byte chunks per voxel row
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float4 *ring = reinterpret_cast<float4 *>(smem_raw);  // [kLapRing][kLapPlane][4]
+    float4 *ring = reinterpret_cast<float4 *>(smem_raw);  // [kLapRing][kLapPlane][CH]
     const int tid = threadIdx.x, lx = tid & 31, ly = tid >> 5;
     const int ntx = (g.nx + kLapTX - 1) / kLapTX, nty = (g.ny + kLapTY - 1) / kLapTY;
-    const int ntiles = ntx * nty;
+    if (!RUNS) nruns = 1;
+    const int nitems = ntx * nty * nruns;
+    auto swz = [](int k) { return CH == 1 ? 0 : (k / (8 / CH)) & (CH - 1); };
     PartialSum<float> acc;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+        const int tile = RUNS ? item % (ntx * nty) : item, run = RUNS ? item / (ntx * nty) : 0;
         const int x0 = (tile % ntx) * kLapTX, y0 = (tile / ntx) * kLapTY;
+        const int z0 = RUNS ? (int)(((long long)run * g.nz) / nruns) : 0;
+        const int z1 = RUNS ? (int)(((long long)(run + 1) * g.nz) / nruns) : g.nz;
         const int x = x0 + lx, y = y0 + ly;
         const bool live = x < g.nx && y < g.ny;
-        // copy plane zz (-1 <= zz <= nz + 1; only planes in memory) into its ring slot
+        // copy plane zz (z0 - 1 <= zz <= z1 + 1; only planes in memory) into its ring slot
         auto stage = [&](int zz) {
             const bool in_mem = (zz >= 0 && zz < g.nz) || (zz == -1 && g.zlo) || (zz == g.nz && g.zhi);
-            if (!in_mem) return;
-            float4 *dst = ring + (size_t)((zz + kLapRing) % kLapRing) * kLapPlane * 4;
-            for (int i = tid; i < kLapPlane * 4; i += kRedThreads) {
-                const int k = i >> 2, c = i & 3;
+            if (!in_mem || (RUNS && zz > z1)) return;
+            float4 *dst = ring + (size_t)((zz + kLapRing) % kLapRing) * kLapPlane * CH;
+            for (int i = tid; i < kLapPlane * CH; i += kRedThreads) {
+                const int k = i / CH, c = i - k * CH;
                 const int hy = k / kLapHX, hx = k - hy * kLapHX;
                 const int gx = x0 - 1 + hx, gy = y0 - 1 + hy;
                 if (gx < 0 || gx >= g.nx || gy < 0 || gy >= g.ny) continue;
                 const float *src = xv + (((long long)zz * g.ny + gy) * g.nx + gx) * M + 4 * c;
-                cp_async_16(dst + k * 4 + (c ^ ((k >> 1) & 3)), src);
+                cp_async_16(dst + k * CH + (c ^ swz(k)), src);
             }
         };
         // row of tile voxel k of ring slot sl
         auto row = [&](int sl, int k, float (&r)[M]) {
-            const float4 *b = ring + ((size_t)sl * kLapPlane + k) * 4;
-            const int sw = (k >> 1) & 3;
+            const float4 *b = ring + ((size_t)sl * kLapPlane + k) * CH;
+            const int sw = swz(k);
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
+            for (int c = 0; c < CH; ++c) {
                 const float4 a = b[c ^ sw];
                 r[4 * c] = a.x;
                 r[4 * c + 1] = a.y;
@@ -671,22 +681,22 @@ __global__ void __launch_bounds__(kRedThreads, 2)
                 r[4 * c + 3] = a.w;
             }
         };
-        __syncthreads();  // the previous tile's reads of the ring are done
-        stage(-1);
+        __syncthreads();  // the previous item's reads of the ring are done
+        stage(z0 - 1);
         cp_async_commit();
-        stage(0);
+        stage(z0);
         cp_async_commit();
-        stage(1);
+        stage(z0 + 1);
         cp_async_commit();
-        for (int z = 0; z < g.nz; ++z) {
-            if (z > 0) __syncthreads();  // every thread is done with step z - 1 (and slot (z + 2) % 4)
+        for (int z = z0; z < z1; ++z) {
+            if (z > z0) __syncthreads();  // every thread is done with step z - 1 (and slot (z + 2) % 4)
             stage(z + 2);
             cp_async_commit();
             cp_async_wait<1>();  // this thread's copies of planes up to z + 1 have landed
             __syncthreads();     // and every thread's
             if (!live) continue;
             const int k = (ly + 1) * kLapHX + lx + 1;
-            const int sc = z % kLapRing, sb = (z + kLapRing - 1) % kLapRing, sa = (z + 1) % kLapRing;
+            const int sc = (z + kLapRing) % kLapRing, sb = (z + kLapRing - 1) % kLapRing, sa = (z + 1) % kLapRing;
             float xc[M], ls[M], nb[M];
             row(sc, k, xc);
 #pragma unroll
@@ -717,7 +727,7 @@ __global__ void __launch_bounds__(kRedThreads, 2)
             float4 *o4 = reinterpret_cast<float4 *>(out + v * M);
             float dotv = 0.0f;
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
+            for (int c = 0; c < CH; ++c) {
                 float4 r = make_float4(rv[4 * c], rv[4 * c + 1], rv[4 * c + 2], rv[4 * c + 3]);
                 if (beta != 0.0f) {
                     const float4 o = o4[c];
@@ -735,7 +745,7 @@ __global__ void __launch_bounds__(kRedThreads, 2)
             }
             acc.add(dotv);
         }
-        cp_async_wait<0>();  // no copy of this tile is still in flight
+        cp_async_wait<0>();  // no copy of this item is still in flight
     }
     double vals[1] = {acc.value()}, tot[1];
     if (block_reduce_last<1>(vals, partials, counter, tot)) lap_scalars(tot[0], scal, mode);
@@ -979,21 +989,25 @@ struct TvCalc {
                 }
             }
             const int slot = mode == 2 ? kSlotRhs : kSlotLap;
-            if constexpr (sizeof(T) == 4 && M == 16) {
-                // rows of exactly 16 floats, 16-byte aligned, at least one full tile width:
+            if constexpr (sizeof(T) == 4 && (M == 4 || M == 8 || M == 16)) {
+                // rows of exactly M floats, 16-byte aligned, at least one full tile width:
                 // the z-marching form with the rows staged in shared memory
                 auto al16 = [](const void *q) { return ((uintptr_t)q & 15u) == 0; };
-                if (P->m == 16 && P->nx >= kLapTX && al16(x) && al16(out) && (mode != 2 || al16(pdir))) {
-                    auto tk = lap_tile_kernel<16>;
-                    dr_status s2 = prep_smem(tk, kLapTileSmem);
+                if (P->m == M && P->nx >= kLapTX && al16(x) && al16(out) && (mode != 2 || al16(pdir))) {
+                    const size_t tsm = lap_tile_smem(M);
+                    dr_status s2 = prep_smem(lap_tile_kernel<M, true>, tsm);
+                    if (s2 == DR_OK) s2 = prep_smem(lap_tile_kernel<M, false>, tsm);
                     if (s2 != DR_OK) return s2;
                     const Geo gg = geo(P);
                     const int ntiles = ((gg.nx + kLapTX - 1) / kLapTX) * ((gg.ny + kLapTY - 1) / kLapTY);
-                    const int grid = std::max(1, std::min(ntiles, tv_grid((const void *)tk, kLapTileSmem, nvox(P))));
-                    tk<<<grid, kRedThreads, kLapTileSmem, st>>>((const float *)x, (float *)out, (float *)pdir, tab, gg,
-                                                                (float)alpha, (float)beta,
-                                                                P->d_partials + slot * kRedSlotStride,
-                                                                P->d_counters + slot, P->d_scal, mode);
+                    const int resident = tv_grid((const void *)lap_tile_kernel<M, false>, tsm, nvox(P));
+                    // runs of slices per tile: enough work items for two per resident CTA
+                    const int nruns = std::max(1, std::min(gg.nz, (2 * resident + ntiles - 1) / ntiles));
+                    auto tk = nruns > 1 ? lap_tile_kernel<M, true> : lap_tile_kernel<M, false>;
+                    const int grid = std::max(1, std::min(ntiles * nruns, resident));
+                    tk<<<grid, kRedThreads, tsm, st>>>((const float *)x, (float *)out, (float *)pdir, tab, gg, nruns,
+                                                       (float)alpha, (float)beta, P->d_partials + slot * kRedSlotStride,
+                                                       P->d_counters + slot, P->d_scal, mode);
                     return tv_launched("lap_tile_kernel");
                 }
             }
