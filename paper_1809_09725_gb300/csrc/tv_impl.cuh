@@ -645,7 +645,8 @@ __global__ void __launch_bounds__(kRedThreads, M == 16 ? 2 : 4)
     const int ntx = (g.nx + kLapTX - 1) / kLapTX, nty = (g.ny + kLapTY - 1) / kLapTY;
     if (!RUNS) nruns = 1;
     const int nitems = ntx * nty * nruns;
-    auto swz = [](int k) { return CH == 1 ? 0 : (k / (8 / CH)) & (CH - 1); };
+    // (indices are non-negative: unsigned arithmetic keeps the divisions shifts)
+    auto swz = [](int k) { return CH == 1 ? 0 : (int)(((unsigned)k / (8u / CH)) & (CH - 1u)); };
     PartialSum<float> acc;
     for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
         const int tile = RUNS ? item % (ntx * nty) : item, run = RUNS ? item / (ntx * nty) : 0;
@@ -660,8 +661,8 @@ __global__ void __launch_bounds__(kRedThreads, M == 16 ? 2 : 4)
             if (!in_mem || (RUNS && zz > z1)) return;
             float4 *dst = ring + (size_t)((zz + kLapRing) % kLapRing) * kLapPlane * CH;
             for (int i = tid; i < kLapPlane * CH; i += kRedThreads) {
-                const int k = i / CH, c = i - k * CH;
-                const int hy = k / kLapHX, hx = k - hy * kLapHX;
+                const int k = (int)((unsigned)i / CH), c = i - k * CH;
+                const int hy = (int)((unsigned)k / kLapHX), hx = k - hy * kLapHX;
                 const int gx = x0 - 1 + hx, gy = y0 - 1 + hy;
                 if (gx < 0 || gx >= g.nx || gy < 0 || gy >= g.ny) continue;
                 const float *src = xv + (((long long)zz * g.ny + gy) * g.nx + gx) * M + 4 * c;
